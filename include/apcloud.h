@@ -1,0 +1,206 @@
+/*
+ * apcloud.h -- C ABI of the GB300 AP-Cloud electrostatic solve.
+ *
+ * The library computes the electric potential and field of N charged
+ * particles with the Adaptive Particle-in-Cloud method (Wang, Samulyak, Jiao,
+ * Yu, arXiv 1603.04039): the Poisson equation  Lap phi = c rho  (Section 2,
+ * Eq. Poisson) is discretised by second-order generalized finite differences
+ * on the centres of an adaptive octree (Section 3), with E = grad phi.
+ *
+ * Call order for one solve (Section 3.2, "three steps", preceded by the tree
+ * construction of Section 4):
+ *     apcloud_build_octree -> apcloud_stencils -> apcloud_deposit
+ *       -> apcloud_solve -> apcloud_gather_field
+ * A call out of this order returns APCLOUD_E_STATE.  apcloud_field_host runs
+ * the whole sequence on host arrays.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named d_* are device pointers (for example the data pointer of
+ *     a CUDA tensor); pointers named h_* and the info/size out-parameters are
+ *     host pointers.  The caller owns every array it passes.
+ *   - All device work is ordered on the CUDA stream given to apcloud_create.
+ *     Only apcloud_build_octree (node counts), apcloud_deposit and
+ *     apcloud_solve (convergence checks) and the introspection getters
+ *     synchronise that stream.
+ *   - apcloud_build_octree keeps the position pointers; they must stay valid
+ *     and unchanged until the next apcloud_build_octree (apcloud_gather_field
+ *     reads them again).  No other input pointer is retained.
+ *   - No exception or abort crosses the ABI.  Negative status = error (the
+ *     outputs of that call are undefined, apcloud_last_error() explains);
+ *     positive status = warning (outputs valid).
+ *   - Node order: interior nodes (octree leaves) in Morton order of their
+ *     lowest corner, then boundary nodes ordered by (face 0..5 = -x,+x,-y,+y,
+ *     -z,+z, owner leaf).
+ */
+#ifndef APCLOUD_H
+#define APCLOUD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    APCLOUD_OK = 0,
+    APCLOUD_W_NOT_CONVERGED = 1, /* a Krylov solve reached max_iter first */
+    APCLOUD_E_INVALID = -1,      /* bad argument or parameter */
+    APCLOUD_E_DOMAIN = -2,       /* a particle lies outside the domain or is NaN */
+    APCLOUD_E_STENCIL = -3,      /* a node has no full-rank stencil within ring_max */
+    APCLOUD_E_CUDA = -4,         /* a CUDA call failed */
+    APCLOUD_E_NOMEM = -5,        /* device allocation failed */
+    APCLOUD_E_TIMEOUT = -6,      /* a bounded device wait gave up */
+    APCLOUD_E_STATE = -7         /* call out of order */
+} apcloud_status;
+
+/* Method parameters (defaults from apcloud_default_params). */
+typedef struct {
+    double lo[3], hi[3]; /* cubic domain Omega (Section 5: [-1,1]^3); hi-lo equal on all axes */
+    int max_depth;       /* deepest octree level, 0..21 (64-bit Morton key, Section 4.3) */
+    double c_refine;     /* tuning constant c of the error-balance criterion
+                            h < c N'^(-1/2) (Section 4.3, k = 2) */
+    int m_target;        /* GFD neighbours per node before distance ties, 9..32 (Section 3.1) */
+    int ring_max;        /* widest k-ring searched for a stencil, 2..5 (Section 4.3) */
+    double weight_c;     /* constant c of the normalized Gaussian weight, 4 (Section 3.1) */
+    double poisson_c;    /* c in Lap phi = c rho (Eq. Poisson), 1 in Section 5 */
+    int restart;         /* GMRES restart length, 1..64 */
+    int precision;       /* 0 = FP64 throughout (the only value accepted) */
+} apcloud_params;
+
+/* Optional device allocator; NULL selects cudaMallocAsync/cudaFreeAsync on
+ * the context stream.  alloc returns NULL on failure. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} apcloud_allocator;
+
+typedef struct {
+    int iters;        /* Krylov iterations (matrix-vector products of the Arnoldi loop) */
+    int restarts;     /* restart cycles */
+    double relres;    /* final ||b - A x|| / ||b||, recomputed after the last cycle */
+} apcloud_solve_info;
+
+typedef struct apcloud_ctx apcloud_ctx;
+
+/* Fills *p with the defaults: domain [-1,1]^3, max_depth 6, c_refine 1,
+ * m_target 20, ring_max 5, weight_c 4, poisson_c 1, restart 30, FP64. */
+void apcloud_default_params(apcloud_params *p);
+
+/* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream) on the current device.  Validates *params. */
+apcloud_status apcloud_create(const apcloud_params *params, const apcloud_allocator *alloc, void *cuda_stream,
+                              apcloud_ctx **out);
+
+/* Frees every buffer the context owns.  NULL is ignored. */
+void apcloud_destroy(apcloud_ctx *ctx);
+
+/* Message for the last non-OK status of this context (static storage of the context). */
+const char *apcloud_last_error(const apcloud_ctx *ctx);
+
+/* Section 4 (tree) and Sections 4.1-4.3 (node selection): Morton keys of the
+ * n particles, key sort, error-balance refinement, minimal 2:1 face balance,
+ * boundary nodes (one per leaf face on the domain boundary) and face
+ * adjacency.  d_x, d_y, d_z: device FP64 arrays of n positions.  Writes the
+ * interior (leaf) and boundary node counts.  Synchronises once.
+ * Errors: APCLOUD_E_DOMAIN if a position is outside [lo, hi] or NaN. */
+apcloud_status apcloud_build_octree(apcloud_ctx *ctx, const double *d_x, const double *d_y, const double *d_z,
+                                    int64_t n, int64_t *n_interior, int64_t *n_boundary);
+
+/* Node geometry after apcloud_build_octree, device outputs of n_nodes =
+ * n_interior + n_boundary entries (any may be NULL): d_xyz FP64 [n_nodes][3]
+ * centres, d_level int8 (owner's level for boundary nodes), d_kind int8
+ * (0 interior, 1 boundary). */
+apcloud_status apcloud_get_nodes(apcloud_ctx *ctx, double *d_xyz, int8_t *d_level, int8_t *d_kind);
+
+/* Leaf data after apcloud_build_octree (device, n_interior entries each, any
+ * may be NULL): Morton key of the leaf at its own level, first particle in
+ * key-sorted order and particle count N' (Section 4). */
+apcloud_status apcloud_get_leaves(apcloud_ctx *ctx, uint64_t *d_key, int32_t *d_first, int32_t *d_count);
+
+/* Section 3.1 with the neighbour search of Section 4.3: for every interior
+ * node, grow k-rings (k = 2..ring_max) over face adjacency, pick two nearest
+ * per octant then the nearest up to m_target plus every candidate tied at the
+ * cut distance (at most 32), build the weighted scaled Vandermonde V0 with
+ * the normalized Gaussian weight, factor it, and keep the pseudo-inverse
+ * operator (gradient and Hessian weights) and the Laplacian row.  Assembles
+ * the density matrix B and the Poisson matrix A (Section 3.2).
+ * Errors: APCLOUD_E_STENCIL if some node has no full-rank stencil. */
+apcloud_status apcloud_stencils(apcloud_ctx *ctx);
+
+/* Stencils after apcloud_stencils (device, any may be NULL): d_nbr int32
+ * [n_interior][32] neighbour node indices in increasing distance, -1 padded;
+ * d_m int32 stencil sizes; d_lap FP64 [n_interior][32] Laplacian weights;
+ * d_lapdiag FP64 diagonal (minus their sum); d_D FP64 [n_interior][9][32]
+ * derivative operator, rows f_x f_y f_z f_xx f_xy f_xz f_yy f_yz f_zz. */
+apcloud_status apcloud_get_stencils(apcloud_ctx *ctx, int32_t *d_nbr, int32_t *d_m, double *d_lap,
+                                    double *d_lapdiag, double *d_D);
+
+/* Step 1 of Section 3.2 (Eq. density_apcloud to Eq. density_linear_system)
+ * with the cell-indicator kernel of Section 5: rho_M of every leaf = sum of
+ * its particles' charges / h^3, then solve B rho~ = rho_M by GMRES to `rtol`.
+ * d_q: device FP64 charges in the caller's particle order, or NULL for
+ * q_uniform on every particle.  d_rho_out (optional, device, n_nodes):
+ * rho~.  info (optional, host) receives the solve statistics.
+ * Returns APCLOUD_W_NOT_CONVERGED if max_iter was reached. */
+apcloud_status apcloud_deposit(apcloud_ctx *ctx, const double *d_q, double q_uniform, double rtol, int max_iter,
+                               double *d_rho_out, apcloud_solve_info *info);
+
+/* rho_M after apcloud_deposit (device, n_nodes; boundary entries are the
+ * owner's value). */
+apcloud_status apcloud_get_rho_m(apcloud_ctx *ctx, double *d_rho_m);
+
+/* Step 2 of Section 3.2: A phi = poisson_c rho~ on interior rows and
+ * phi_b = g_b on boundary rows (Dirichlet data).  d_g: device FP64
+ * [n_boundary] or NULL for g = 0.  d_phi0: device initial guess [n_nodes] or
+ * NULL for zero.  d_phi_out (optional, device, n_nodes).  GMRES(restart) with
+ * right Jacobi preconditioning to ||b - A phi|| <= rtol ||b||.
+ * Returns APCLOUD_W_NOT_CONVERGED if max_iter was reached. */
+apcloud_status apcloud_solve(apcloud_ctx *ctx, const double *d_g, const double *d_phi0, double rtol, int max_iter,
+                             double *d_phi_out, apcloud_solve_info *info);
+
+/* Step 3 of Section 3.2: GFD gradient and Hessian of phi at every interior
+ * node, then second-order Taylor expansion about the centre of each
+ * particle's leaf: phi_p, and E_p = grad phi (Section 2).  Outputs are device
+ * FP64 arrays of n particles in the caller's order (any may be NULL). */
+apcloud_status apcloud_gather_field(apcloud_ctx *ctx, double *d_phi_p, double *d_ex, double *d_ey, double *d_ez);
+
+/* Node derivatives after apcloud_gather_field: device FP64 [n_interior][9]. */
+apcloud_status apcloud_get_derivatives(apcloud_ctx *ctx, double *d_dphi);
+
+/* y = A x (which = 1) or y = B x (which = 0) with the assembled matrices;
+ * device FP64 vectors of n_nodes entries. */
+apcloud_status apcloud_matvec(apcloud_ctx *ctx, int which, const double *d_x, double *d_y);
+
+/* Solves B x = b (which = 0) or A x = b (which = 1) for an arbitrary
+ * right-hand side with the same GMRES; d_x holds the initial guess on entry. */
+apcloud_status apcloud_solve_system(apcloud_ctx *ctx, int which, const double *d_b, double *d_x, double rtol,
+                                    int max_iter, apcloud_solve_info *info);
+
+/* The whole solve on host arrays: copies positions and charges (h_q NULL =
+ * q_uniform) to the device, runs the five steps with g = 0, and copies phi
+ * and E at the particles back.  Host arrays may be pageable or pinned; pinned
+ * memory makes the copies asynchronous. */
+apcloud_status apcloud_field_host(apcloud_ctx *ctx, const double *h_x, const double *h_y, const double *h_z,
+                                  const double *h_q, double q_uniform, int64_t n, double rtol, int max_iter,
+                                  double *h_phi, double *h_ex, double *h_ey, double *h_ez,
+                                  apcloud_solve_info *info_rho, apcloud_solve_info *info_phi);
+
+/* Per-kernel device timing with CUDA events on the context stream.
+ * apcloud_set_timing(ctx, mask) enables timing for the kernel kinds whose
+ * bit is set in mask (bit k = kind k, see apcloud_kernel_name), 0 disables.
+ * apcloud_get_timing synchronises and returns, for kind k, the summed
+ * milliseconds and launch count since the last reset (reset = 1 clears). */
+#define APCLOUD_NUM_KINDS 16
+apcloud_status apcloud_set_timing(apcloud_ctx *ctx, unsigned mask);
+apcloud_status apcloud_get_timing(apcloud_ctx *ctx, double *h_ms, int64_t *h_launches, int reset);
+const char *apcloud_kernel_name(int kind);
+
+/* Total kernel launches issued by this context since creation. */
+int64_t apcloud_launch_count(const apcloud_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* APCLOUD_H */

@@ -1,0 +1,307 @@
+"""ctypes binding of libapcloud.so: argument marshalling only.
+
+Every function here forwards to the C ABI of include/apcloud.h with the same
+name; device arrays are CUDA tensors (float64 unless stated), the stream is
+the current torch stream of the tensor's device.  All computation happens in
+the library's CUDA kernels.  A missing library raises immediately: there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libapcloud.so")
+
+NUM_KINDS = 16
+MMAX = 32
+NCOL = 9
+
+STATUS = {0: "OK", 1: "W_NOT_CONVERGED", -1: "E_INVALID", -2: "E_DOMAIN", -3: "E_STENCIL", -4: "E_CUDA",
+          -5: "E_NOMEM", -6: "E_TIMEOUT", -7: "E_STATE"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class APCloudError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__("%s (%d): %s" % (STATUS.get(status, "?"), status, message))
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("max_depth", C.c_int), ("c_refine", C.c_double),
+                ("m_target", C.c_int), ("ring_max", C.c_int), ("weight_c", C.c_double),
+                ("poisson_c", C.c_double), ("restart", C.c_int), ("precision", C.c_int)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("relres", C.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "restarts": self.restarts, "relres": self.relres}
+
+
+def load():
+    """Load libapcloud.so (built by paper_1603_04039_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libapcloud.so is not built: run `python -c \"import __graft_entry__ as g; "
+                               "g.build()\"` (or paper_1603_04039_gb300.build.build())")
+        lib = C.CDLL(LIB_PATH)
+        P, I, D, L = C.c_void_p, C.c_int, C.c_double, C.c_int64
+        sig = {
+            "apcloud_default_params": (None, [C.POINTER(Params)]),
+            "apcloud_create": (I, [C.POINTER(Params), P, P, C.POINTER(P)]),
+            "apcloud_destroy": (None, [P]),
+            "apcloud_last_error": (C.c_char_p, [P]),
+            "apcloud_build_octree": (I, [P, P, P, P, L, C.POINTER(L), C.POINTER(L)]),
+            "apcloud_get_nodes": (I, [P, P, P, P]),
+            "apcloud_get_leaves": (I, [P, P, P, P]),
+            "apcloud_stencils": (I, [P]),
+            "apcloud_get_stencils": (I, [P, P, P, P, P, P]),
+            "apcloud_deposit": (I, [P, P, D, D, I, P, C.POINTER(SolveInfo)]),
+            "apcloud_get_rho_m": (I, [P, P]),
+            "apcloud_solve": (I, [P, P, P, D, I, P, C.POINTER(SolveInfo)]),
+            "apcloud_gather_field": (I, [P, P, P, P, P]),
+            "apcloud_get_derivatives": (I, [P, P]),
+            "apcloud_matvec": (I, [P, I, P, P]),
+            "apcloud_solve_system": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo)]),
+            "apcloud_field_host": (I, [P, P, P, P, P, D, L, D, I, P, P, P, P, C.POINTER(SolveInfo),
+                                       C.POINTER(SolveInfo)]),
+            "apcloud_set_timing": (I, [P, C.c_uint]),
+            "apcloud_get_timing": (I, [P, P, P, I]),
+            "apcloud_kernel_name": (C.c_char_p, [I]),
+            "apcloud_launch_count": (L, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _f64(t, n=None):
+    if t is None:
+        return None
+    if t.dtype != torch.float64:
+        raise TypeError("expected float64, got %s" % t.dtype)
+    if n is not None and t.numel() != n:
+        raise ValueError("expected %d entries, got %d" % (n, t.numel()))
+    return t
+
+
+def kernel_names():
+    lib = load()
+    return [lib.apcloud_kernel_name(k).decode() for k in range(NUM_KINDS)]
+
+
+class APCloud:
+    """One AP-Cloud problem on one GPU (see include/apcloud.h for each call)."""
+
+    def __init__(self, lo=-1.0, hi=1.0, max_depth=6, c_refine=1.0, m_target=20, ring_max=5, weight_c=4.0,
+                 poisson_c=1.0, restart=30, device="cuda:0", stream=None):
+        lib = load()
+        self._lib = lib
+        self.device = torch.device(device)
+        p = Params()
+        lib.apcloud_default_params(C.byref(p))
+        for d in range(3):
+            p.lo[d] = float(lo)
+            p.hi[d] = float(hi)
+        p.max_depth, p.c_refine, p.m_target, p.ring_max = int(max_depth), float(c_refine), int(m_target), int(ring_max)
+        p.weight_c, p.poisson_c, p.restart = float(weight_c), float(poisson_c), int(restart)
+        self.params = p
+        with torch.cuda.device(self.device):
+            s = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.stream = s
+            ctx = C.c_void_p()
+            st = lib.apcloud_create(C.byref(p), None, C.c_void_p(s.cuda_stream), C.byref(ctx))
+        if st != 0:
+            raise APCloudError(st, "apcloud_create failed")
+        self._ctx = ctx
+        self.n_int = self.n_bnd = 0
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            with torch.cuda.device(self.device):
+                self._lib.apcloud_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st < 0:
+            raise APCloudError(st, self._lib.apcloud_last_error(self._ctx).decode())
+        return st
+
+    def _empty(self, *shape, dtype=torch.float64):
+        return torch.empty(*shape, dtype=dtype, device=self.device)
+
+    @property
+    def n_nodes(self):
+        return self.n_int + self.n_bnd
+
+    # -- entry points ---------------------------------------------------------
+    def build_octree(self, x, y, z):
+        n = x.numel()
+        for t in (x, y, z):
+            _f64(t, n)
+        self._pos = (x, y, z)   # the library keeps these pointers until the next build
+        ni, nb = C.c_int64(), C.c_int64()
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_build_octree(self._ctx, _dptr(x), _dptr(y), _dptr(z), n, C.byref(ni),
+                                                       C.byref(nb)))
+        self.n, self.n_int, self.n_bnd = n, ni.value, nb.value
+        return self.n_int, self.n_bnd
+
+    def get_nodes(self):
+        xyz = self._empty(self.n_nodes, 3)
+        lv = self._empty(self.n_nodes, dtype=torch.int8)
+        kd = self._empty(self.n_nodes, dtype=torch.int8)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_get_nodes(self._ctx, _dptr(xyz), _dptr(lv), _dptr(kd)))
+        return {"xyz": xyz, "level": lv, "kind": kd}
+
+    def get_leaves(self):
+        key = self._empty(self.n_int, dtype=torch.int64)
+        first = self._empty(self.n_int, dtype=torch.int32)
+        count = self._empty(self.n_int, dtype=torch.int32)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_get_leaves(self._ctx, _dptr(key), _dptr(first), _dptr(count)))
+        return {"key": key, "first": first, "count": count}
+
+    def stencils(self):
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_stencils(self._ctx))
+
+    def get_stencils(self):
+        n = self.n_int
+        out = {"nbr": self._empty(n, MMAX, dtype=torch.int32), "m": self._empty(n, dtype=torch.int32),
+               "lap": self._empty(n, MMAX), "lapd": self._empty(n), "D": self._empty(n, NCOL, MMAX)}
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_get_stencils(self._ctx, _dptr(out["nbr"]), _dptr(out["m"]),
+                                                       _dptr(out["lap"]), _dptr(out["lapd"]), _dptr(out["D"])))
+        return out
+
+    def deposit(self, q=None, q_uniform=None, rtol=1e-10, max_iter=100000):
+        if q is not None:
+            _f64(q, self.n)
+        if q is None and q_uniform is None:
+            q_uniform = 1.0 / max(1, self.n)
+        rho = self._empty(self.n_nodes)
+        info = SolveInfo()
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_deposit(self._ctx, _dptr(q), float(q_uniform or 0.0), rtol,
+                                                       int(max_iter), _dptr(rho), C.byref(info)))
+        return rho, dict(info.as_dict(), status=st)
+
+    def get_rho_m(self):
+        out = self._empty(self.n_nodes)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_get_rho_m(self._ctx, _dptr(out)))
+        return out
+
+    def solve(self, g=None, phi0=None, rtol=1e-10, max_iter=100000):
+        if g is not None:
+            _f64(g, self.n_bnd)
+        if phi0 is not None:
+            _f64(phi0, self.n_nodes)
+        phi = self._empty(self.n_nodes)
+        info = SolveInfo()
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_solve(self._ctx, _dptr(g), _dptr(phi0), rtol, int(max_iter),
+                                                     _dptr(phi), C.byref(info)))
+        return phi, dict(info.as_dict(), status=st)
+
+    def gather_field(self, out=None):
+        if out is None:
+            out = tuple(self._empty(self.n) for _ in range(4))
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_gather_field(self._ctx, *[_dptr(t) for t in out]))
+        return out
+
+    def get_derivatives(self):
+        out = self._empty(self.n_int, NCOL)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_get_derivatives(self._ctx, _dptr(out)))
+        return out
+
+    def matvec(self, which, x):
+        _f64(x, self.n_nodes)
+        y = self._empty(self.n_nodes)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_matvec(self._ctx, 1 if which == "A" else 0, _dptr(x), _dptr(y)))
+        return y
+
+    def solve_system(self, which, b, x0=None, rtol=1e-10, max_iter=100000):
+        _f64(b, self.n_nodes)
+        x = torch.zeros(self.n_nodes, dtype=torch.float64, device=self.device) if x0 is None else x0.clone()
+        info = SolveInfo()
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_solve_system(self._ctx, 1 if which == "A" else 0, _dptr(b), _dptr(x),
+                                                            rtol, int(max_iter), C.byref(info)))
+        return x, dict(info.as_dict(), status=st)
+
+    def field_host(self, x, y, z, q=None, q_uniform=None, rtol=1e-10, max_iter=100000, out=None):
+        """Whole solve on host numpy arrays (pinned tensors are also accepted)."""
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()
+                return C.c_void_p(a.data_ptr())
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            return a.ctypes.data_as(C.c_void_p)
+        n = len(x)
+        if out is None:
+            out = tuple(np.empty(n) for _ in range(4))
+        if q is None and q_uniform is None:
+            q_uniform = 1.0 / max(1, n)
+        keep = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a for a in (x, y, z, q)]
+        ir, ip = SolveInfo(), SolveInfo()
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_field_host(self._ctx, hp(keep[0]), hp(keep[1]), hp(keep[2]),
+                                                          hp(keep[3]), float(q_uniform or 0.0), n, rtol,
+                                                          int(max_iter), *[hp(o) for o in out], C.byref(ir),
+                                                          C.byref(ip)))
+        self.n = n
+        return out, {"rho": ir.as_dict(), "phi": ip.as_dict(), "status": st}
+
+    def set_timing(self, mask):
+        self._check(self._lib.apcloud_set_timing(self._ctx, int(mask)))
+
+    def get_timing(self, reset=True):
+        ms = np.zeros(NUM_KINDS)
+        cnt = np.zeros(NUM_KINDS, dtype=np.int64)
+        self._check(self._lib.apcloud_get_timing(self._ctx, ms.ctypes.data_as(C.c_void_p),
+                                                 cnt.ctypes.data_as(C.c_void_p), 1 if reset else 0))
+        return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(kernel_names())}
+
+    def launch_count(self):
+        return int(self._lib.apcloud_launch_count(self._ctx))

@@ -1,0 +1,108 @@
+// gather.cu -- Section 3.2 step 3: GFD gradient and Hessian of phi at every
+// interior node, and second-order Taylor interpolation of phi and E = grad phi
+// (Section 2) from the centre of each particle's own leaf.
+//
+// Node pass: one thread per node walks its ELL row (the stencil neighbours in
+// order) and the derivative operator stored with nodes fastest, so the loads
+// of a warp are contiguous.  Particle pass: one thread per particle in the
+// caller's order recomputes the particle's Morton key, finds its leaf by
+// binary search over the Morton-ordered leaf anchors (the leaves partition
+// the key space), and writes phi and E coalesced -- no permutation is read.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace apc {
+
+namespace {
+
+constexpr int NF = 12;  // per-node record: phi, 9 derivatives, 2 pad
+
+__global__ void k_derivs(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+                         const int32_t *__restrict__ col, const double *__restrict__ D, int64_t dstride,
+                         const double *__restrict__ phi, int n_int, double *__restrict__ nf) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_int) return;
+    const int sl = j >> 5, lane = j & 31;
+    const int w = (int)sw[sl];
+    const int64_t base = (int64_t)soff[sl] * 32 + lane;
+    const double p0 = phi[j];
+    double acc[NCOL];
+#pragma unroll
+    for (int r = 0; r < NCOL; ++r) acc[r] = 0.0;
+    for (int k = 1; k < w; ++k) {
+        const int cj = col[base + (int64_t)k * 32];
+        const double diff = phi[cj] - p0;
+#pragma unroll
+        for (int r = 0; r < NCOL; ++r) acc[r] = fma(D[((int64_t)r * MMAX + (k - 1)) * dstride + j], diff, acc[r]);
+    }
+    double *o = nf + (int64_t)j * NF;
+    o[0] = p0;
+#pragma unroll
+    for (int r = 0; r < NCOL; ++r) o[1 + r] = acc[r];
+    o[10] = 0.0;
+    o[11] = 0.0;
+}
+
+__device__ __forceinline__ int leaf_of(const uint64_t *anchor, int n, uint64_t v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (__ldg(anchor + mid) <= v) lo = mid + 1; else hi = mid;
+    }
+    return lo - 1;
+}
+
+__global__ void k_gather(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+                         int64_t n, double lo0, double lo1, double lo2, double s, int shift, double unit,
+                         const uint64_t *__restrict__ anchor, int n_int, const int4 *__restrict__ ic,
+                         const double *__restrict__ nf, double *__restrict__ php, double *__restrict__ ex,
+                         double *__restrict__ ey, double *__restrict__ ez) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double p[3] = {x[i], y[i], z[i]};
+    const double lo[3] = {lo0, lo1, lo2};
+    uint32_t cc[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double t = floor(__dmul_rn(__dsub_rn(p[d], lo[d]), s));
+        t = fmin(fmax(t, 0.0), (double)((1u << KEY_DEPTH) - 1u));
+        cc[d] = (uint32_t)t >> shift;
+    }
+    const int j = leaf_of(anchor, n_int, morton(cc[0], cc[1], cc[2]));
+    const int4 q = ic[j];
+    const double r0 = p[0] - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
+    const double r1 = p[1] - __dadd_rn(lo1, __dmul_rn((double)q.y, unit));
+    const double r2 = p[2] - __dadd_rn(lo2, __dmul_rn((double)q.z, unit));
+    const double2 *f2 = reinterpret_cast<const double2 *>(nf + (int64_t)j * NF);
+    const double2 a = f2[0], b = f2[1], c = f2[2], d = f2[3], e = f2[4];
+    // a = (phi, fx), b = (fy, fz), c = (fxx, fxy), d = (fxz, fyy), e = (fyz, fzz)
+    const double hr0 = c.x * r0 + c.y * r1 + d.x * r2;
+    const double hr1 = c.y * r0 + d.y * r1 + e.x * r2;
+    const double hr2 = d.x * r0 + e.x * r1 + e.y * r2;
+    const double g0 = a.y, g1 = b.x, g2 = b.y;
+    if (php) php[i] = a.x + (g0 * r0 + g1 * r1 + g2 * r2) + 0.5 * (r0 * hr0 + r1 * hr1 + r2 * hr2);
+    if (ex) ex[i] = g0 + hr0;
+    if (ey) ey[i] = g1 + hr1;
+    if (ez) ez[i] = g2 + hr2;
+}
+
+}  // namespace
+
+apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *ey, double *ez) {
+    const int n = c->n_int;
+    double *nf = ensure<double>(c, c->nodefield, (int64_t)n * NF);
+    if (!nf) return APCLOUD_E_NOMEM;
+    const int64_t dstride = ((int64_t)n + 31) / 32 * 32;
+    APC_LAUNCH(c, K_DERIV, div_up(n, 128), 128, 0, k_derivs, ptr<uint32_t>(c->slice_w), ptr<uint32_t>(c->slice_off),
+               ptr<int32_t>(c->ell_col), ptr<double>(c->D), dstride, ptr<double>(c->phi), n, nf);
+    const double ext = c->P.hi[0] - c->P.lo[0];
+    const double s = ldexp(1.0, KEY_DEPTH) / ext;
+    const double unit = ldexp(ext, -(KEY_DEPTH + 1));
+    APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather, c->px, c->py, c->pz, c->N, c->P.lo[0], c->P.lo[1],
+               c->P.lo[2], s, KEY_DEPTH - c->L, unit, ptr<uint64_t>(c->leaf_anchor), n, ptr<int4>(c->node_ic), nf,
+               phi_p, ex, ey, ez);
+    return cuda_check(c, cudaGetLastError(), "gather");
+}
+
+}  // namespace apc

@@ -1,0 +1,196 @@
+// internal.cuh -- shared declarations of the GB300 AP-Cloud library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "apcloud.h"
+
+namespace apc {
+
+constexpr int KEY_DEPTH = 21;   // 63-bit Morton keys (Section 4.3)
+constexpr int NCOL = 9;         // unknowns of the 3-D second-order GFD system (Section 3.1)
+constexpr int MMAX = 32;        // widest stencil, one warp lane per neighbour
+constexpr int MAXC = 768;       // ring candidates held per node in shared memory
+constexpr double RANK_TOL = 1e-6;
+constexpr int MAX_RESTART = 64;
+
+// kernel kinds for the event timers (bit k of the timing mask)
+enum Kind {
+    K_KEYS = 0, K_SORT, K_TREE, K_ADJ, K_STENCIL, K_ELL, K_DEPOSIT, K_SPMV,
+    K_DOT, K_UPDDOT, K_UPDNORM, K_CYCLE, K_DERIV, K_GATHER, K_VEC, K_COPY, NKIND
+};
+static_assert(NKIND == APCLOUD_NUM_KINDS, "kind count");
+
+// device error word bits
+enum : unsigned { ERR_DOMAIN = 1u, ERR_STENCIL = 2u, ERR_BALANCE = 4u, ERR_OVERFLOW = 8u };
+
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+// GMRES bookkeeping kept on the device so that a whole restart cycle runs
+// without host round trips.
+struct GmresState {
+    double H[(MAX_RESTART + 1) * MAX_RESTART];  // Hessenberg, row-major [i][j], rotated in place
+    double cs[MAX_RESTART], sn[MAX_RESTART];
+    double g[MAX_RESTART + 1];
+    double y[MAX_RESTART];
+    double h1[MAX_RESTART + 1];   // first Gram-Schmidt projection of the current column
+    double h2[MAX_RESTART + 1];   // second projection
+    double bnorm;                 // ||b||
+    double beta;                  // ||r|| at cycle start
+    double inv_norm;              // 1 / ||w|| of the vector about to become V_{j+1}
+    double rtol;
+    int jend;                     // columns completed in this cycle
+    int done;                     // 1 once the cycle must stop (converged or breakdown)
+    unsigned ticket;              // grid-reduction ticket
+};
+
+struct Timer {
+    unsigned mask = 0;
+    std::vector<cudaEvent_t> ev;   // pairs
+    std::vector<int> kind;          // per pair
+    size_t used = 0;
+    double ms[NKIND] = {0};
+    int64_t launches[NKIND] = {0};
+};
+
+}  // namespace apc
+
+struct apcloud_ctx {
+    apcloud_params P;
+    apcloud_allocator A;
+    bool default_alloc = true;
+    cudaStream_t s = nullptr;
+    int stage = 0;  // 0 created, 1 octree, 2 stencils, 3 deposit, 4 solved, 5 gathered
+    char err[512] = {0};
+    int64_t launches = 0;
+    apc::Timer timer;
+
+    // particles (caller's device arrays, kept until the next build)
+    const double *px = nullptr, *py = nullptr, *pz = nullptr;
+    int64_t N = 0;
+
+    // sizes
+    int L = 0;
+    int n_int = 0, n_bnd = 0, n_tot = 0;
+    int n_slices = 0;
+    int64_t ell_entries = 0;
+
+    // sorted particle keys and permutation (result in key[kbuf], val[kbuf])
+    apc::DBuf key[2], val[2];
+    int kbuf = 0;
+    // tree temporaries
+    apc::DBuf ucell[2], ustart[2], opened, cand[2], cval[2], flags, scan, scan_blk, lkey, lval;
+    // nodes
+    apc::DBuf leaf_anchor, leaf_level, leaf_first, leaf_count, node_ic, bowner, bface, bidx, adj;
+    // stencils
+    apc::DBuf nbr, msz, ring, lap, lapd, D, rcond;
+    // matrices (sliced ELL, 32-row slices, column-major inside a slice)
+    apc::DBuf slice_w, slice_off, ell_col, ell_A, ell_B, dA, dB;
+    // solver
+    apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
+    // device staging for apcloud_field_host
+    apc::DBuf hx, hy, hz, hq, hphi, hex, hey, hez;
+    // error word, small host-visible values
+    apc::DBuf derr, dsmall;
+    unsigned *h_pinned = nullptr;  // pinned staging for small reads
+};
+
+namespace apc {
+
+// ---- context helpers (api.cu) ----
+apcloud_status fail(apcloud_ctx *c, apcloud_status st, const char *fmt, ...);
+apcloud_status cuda_check(apcloud_ctx *c, cudaError_t e, const char *what);
+void *raw_alloc(apcloud_ctx *c, size_t bytes);
+void raw_free(apcloud_ctx *c, void *p);
+bool ensure_bytes(apcloud_ctx *c, DBuf &b, size_t bytes, bool keep = false);
+template <class T>
+inline T *ensure(apcloud_ctx *c, DBuf &b, size_t count, bool keep = false) {
+    if (!ensure_bytes(c, b, count * sizeof(T) + 16, keep)) return nullptr;
+    return static_cast<T *>(b.p);
+}
+template <class T>
+inline T *ptr(DBuf &b) { return static_cast<T *>(b.p); }
+
+// event timers around launches of one kind
+void timer_begin(apcloud_ctx *c, int kind);
+void timer_end(apcloud_ctx *c, int kind);
+
+// read `bytes` from device to host on the context stream and synchronise
+apcloud_status read_back(apcloud_ctx *c, void *host, const void *dev, size_t bytes);
+apcloud_status check_device_errors(apcloud_ctx *c);
+
+// ---- primitives (prims.cu) ----
+// exclusive scan of n uint32 values; writes the total to *d_total if non-null
+apcloud_status scan_u32(apcloud_ctx *c, const uint32_t *in, uint32_t *out, int64_t n, uint32_t *d_total);
+// stable LSD radix sort of (key, value) pairs on key bits [0, nbits); returns
+// 0/1 = which of the two buffers holds the result
+apcloud_status radix_sort(apcloud_ctx *c, uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t n,
+                          int nbits, int *which);
+
+// ---- stages ----
+apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n);
+apcloud_status build_stencils(apcloud_ctx *c);
+apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform);
+apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x_inout_scaled, double rtol,
+                           int max_iter, apcloud_solve_info *info);
+apcloud_status spmv(apcloud_ctx *c, int which, const double *x, double *y, double scale, double *copy_out);
+apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *ey, double *ez);
+
+// ---- device helpers ----
+__host__ __device__ inline uint64_t spread3(uint32_t v) {
+    uint64_t x = v & 0x1fffffu;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+}
+__host__ __device__ inline uint32_t compact3(uint64_t x) {
+    x &= 0x1249249249249249ull;
+    x = (x ^ (x >> 2)) & 0x10c30c30c30c30c3ull;
+    x = (x ^ (x >> 4)) & 0x100f00f00f00f00full;
+    x = (x ^ (x >> 8)) & 0x1f0000ff0000ffull;
+    x = (x ^ (x >> 16)) & 0x1f00000000ffffull;
+    x = (x ^ (x >> 32)) & 0x1fffffull;
+    return (uint32_t)x;
+}
+// Morton key with x most significant in every 3-bit group
+__host__ __device__ inline uint64_t morton(uint32_t ix, uint32_t iy, uint32_t iz) {
+    return (spread3(ix) << 2) | (spread3(iy) << 1) | spread3(iz);
+}
+__host__ __device__ inline void unmorton(uint64_t k, uint32_t &ix, uint32_t &iy, uint32_t &iz) {
+    ix = compact3(k >> 2);
+    iy = compact3(k >> 1);
+    iz = compact3(k);
+}
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+#define APC_LAUNCH(c, kind, grid, block, smem, kern, ...)                       \
+    do {                                                                        \
+        if ((grid) > 0) {                                                       \
+            ::apc::timer_begin(c, kind);                                        \
+            kern<<<(grid), (block), (smem), (c)->s>>>(__VA_ARGS__);             \
+            ::apc::timer_end(c, kind);                                          \
+            (c)->launches++;                                                    \
+        }                                                                       \
+    } while (0)
+
+#define APC_TRY(expr)                          \
+    do {                                       \
+        apcloud_status _st = (expr);           \
+        if (_st < 0) return _st;               \
+    } while (0)
+
+#define APC_CUDA(c, expr) APC_TRY(::apc::cuda_check(c, (expr), #expr))
+
+}  // namespace apc

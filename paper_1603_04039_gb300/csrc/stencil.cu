@@ -1,0 +1,526 @@
+// stencil.cu -- Section 3.1 (WLS GFD operators) with the k-ring neighbour
+// search of Section 4.3, and assembly of the density matrix B and the
+// Poisson matrix A of Section 3.2 in sliced ELL.
+//
+// One warp per node.  The warp grows the k-ring (k = 2..ring_max) by BFS over
+// the face adjacency with the candidate set in shared memory, ranks the
+// candidates by (exact integer squared distance, node index), applies the
+// octant criterion, and builds the weighted scaled Vandermonde W V0 with one
+// lane per neighbour (lane j = row j, m <= 32).  The least-squares operator
+// P = (W V0)^+ W is formed by Cholesky QR applied twice (CholeskyQR2): the
+// 9x9 Gram matrices come from shared memory, Q = A R^-1 is lane-local, and
+// column j of P is R^-1 q_j^T W_j, again lane-local.  This replaces the
+// column-by-column Householder reductions of a CPU QR (9 dependent cross-lane
+// reductions) with two Gram products and lane-private triangular solves.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace apc {
+
+namespace {
+
+constexpr int SW = 4;           // warps (nodes) per block
+constexpr int ASTR = NCOL;      // row stride of the staged Vandermonde
+
+struct WarpSmem {
+    int32_t cand[MAXC];
+    long long d2[MAXC];
+    uint8_t oct[MAXC];
+    uint8_t pick[MAXC];   // octant picks
+    uint8_t fill[MAXC];   // nearest fill up to m_target
+    uint8_t tie[MAXC];    // ties at the cut distance
+    int32_t sel[MMAX];
+    long long seld2[MMAX];
+    double A[MMAX * ASTR];
+    double G[48];
+    double R1[NCOL * NCOL];
+    double R2[NCOL * NCOL];
+    double P[NCOL * MMAX];
+    int flag;
+    int cut_set;
+    long long cut;
+};
+
+struct BlockSmem {
+    WarpSmem w[SW];
+};
+
+__constant__ unsigned char c_pa[45], c_pb[45];
+
+__device__ __forceinline__ bool key_less(long long da, int ia, long long db, int ib) {
+    return da < db || (da == db && ia < ib);
+}
+
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        long long t = __shfl_xor_sync(0xffffffffu, v, o);
+        v = t > v ? t : v;
+    }
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Cholesky of the packed upper Gram matrix G into R (row-major 9x9, upper),
+// run by one lane.  Returns false on a non-positive pivot.
+__device__ bool cholesky9(const double *G, double *R) {
+    for (int i = 0; i < NCOL; ++i) {
+        for (int j = i; j < NCOL; ++j) {
+            int a = i, b = j;
+            int e = a * NCOL - a * (a - 1) / 2 + (b - a);  // packed upper index
+            double s = G[e];
+            for (int k = 0; k < i; ++k) s -= R[k * NCOL + i] * R[k * NCOL + j];
+            if (j == i) {
+                if (!(s > 0.0)) return false;
+                R[i * NCOL + i] = sqrt(s);
+            } else {
+                R[i * NCOL + j] = s / R[i * NCOL + i];
+            }
+        }
+        for (int j = 0; j < i; ++j) R[i * NCOL + j] = 0.0;
+    }
+    return true;
+}
+
+// solve q R = a for the row vector q (R upper), in place on v
+__device__ __forceinline__ void row_solve_upper(const double *R, double *v) {
+#pragma unroll
+    for (int c = 0; c < NCOL; ++c) {
+        double s = v[c];
+#pragma unroll
+        for (int k = 0; k < c; ++k) s -= v[k] * R[k * NCOL + c];
+        v[c] = s / R[c * NCOL + c];
+    }
+}
+
+// solve R z = v for the column vector z (R upper), in place
+__device__ __forceinline__ void col_solve_upper(const double *R, double *v) {
+#pragma unroll
+    for (int c = NCOL - 1; c >= 0; --c) {
+        double s = v[c];
+#pragma unroll
+        for (int k = c + 1; k < NCOL; ++k) s -= R[c * NCOL + k] * v[k];
+        v[c] = s / R[c * NCOL + c];
+    }
+}
+
+// Gram matrix of the staged rows: lane e < 45 owns entry (pa[e], pb[e])
+__device__ __forceinline__ void gram(const double *A, int m, double *G, int lane) {
+    for (int e = lane; e < 45; e += 32) {
+        int a = c_pa[e], b = c_pb[e];
+        double s = 0.0;
+        for (int j = 0; j < m; ++j) s = fma(A[j * ASTR + a], A[j * ASTR + b], s);
+        G[e] = s;
+    }
+}
+
+__global__ void __launch_bounds__(SW * 32) k_stencil(
+    const int4 *__restrict__ ic, const int32_t *__restrict__ adj, const int32_t *__restrict__ bowner, int n_int,
+    int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
+    int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,
+    double *__restrict__ lapd_out, double *__restrict__ D_out, int64_t dstride, double *__restrict__ rcond_out,
+    unsigned *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BlockSmem &S = *reinterpret_cast<BlockSmem *>(smem_raw);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    WarpSmem &W = S.w[wid];
+    const int y0 = blockIdx.x * SW + wid;
+    const unsigned FULL = 0xffffffffu;
+    const unsigned lt = (1u << lane) - 1u;
+    if (y0 >= n_int) return;
+
+    const int4 c0 = ic[y0];
+    int nc = 1;
+    if (lane == 0) W.cand[0] = y0;
+    __syncwarp();
+    int head = 0, tail = 1;
+    bool done = false, overflow = false;
+    int m = 0, ring = 0;
+    double rmin_over_rmax = 0.0;
+
+    for (int k = 1; k <= ring_max && !done; ++k) {
+        // ---- grow the ring by one layer (Section 4.3: (k+1)-ring = k-ring
+        // plus the face neighbours of its nodes)
+        const int nslots = (tail - head) * 24;
+        for (int base = 0; base < nslots; base += 32) {
+            int s = base + lane;
+            int v = -1;
+            if (s < nslots) {
+                int u = W.cand[head + s / 24];
+                int slot = s % 24;
+                if (u < n_int) v = adj[(int64_t)u * 24 + slot];
+                else if (slot == 0) v = bowner[u - n_int];
+            }
+            bool fresh = v >= 0;
+            for (int t = 0; fresh && t < nc; ++t)
+                if (W.cand[t] == v) fresh = false;
+            unsigned peers = __match_any_sync(FULL, fresh ? v : -2 - lane);
+            if (fresh && lane != __ffs(peers) - 1) fresh = false;
+            unsigned bal = __ballot_sync(FULL, fresh);
+            int p = nc + __popc(bal & lt);
+            if (fresh) {
+                if (p < MAXC) W.cand[p] = v;
+                else overflow = true;
+            }
+            nc += __popc(bal);
+            if (nc > MAXC) nc = MAXC;
+            __syncwarp();
+        }
+        if (__any_sync(FULL, overflow)) break;
+        head = tail;
+        tail = nc;
+        if (k < 2) continue;
+        const int ncand = nc - 1;
+        if (ncand < m_target && k < ring_max) continue;
+        if (ncand < NCOL) continue;
+
+        // ---- rank candidates (Section 3.1 quadrant criterion, octants in 3-D)
+        for (int t = 1 + lane; t < nc; t += 32) {
+            int4 q = ic[W.cand[t]];
+            long long dx = (long long)q.x - c0.x, dy = (long long)q.y - c0.y, dz = (long long)q.z - c0.z;
+            W.d2[t] = dx * dx + dy * dy + dz * dz;
+            W.oct[t] = (uint8_t)(((dx >= 0) << 2) | ((dy >= 0) << 1) | (dz >= 0));
+        }
+        __syncwarp();
+        int nA = 0;
+        for (int t = 1 + lane; t < nc; t += 32) {
+            long long dt = W.d2[t];
+            int it = W.cand[t], ot = W.oct[t], r = 0;
+            for (int u = 1; u < nc; ++u)
+                if (W.oct[u] == ot && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
+            W.pick[t] = (r < 2) ? 1 : 0;
+            nA += (r < 2);
+        }
+        nA = warp_sum_int(nA);
+        __syncwarp();
+        const int need = m_target - nA;
+        int nfill = 0;
+        if (lane == 0) W.cut_set = 0;
+        __syncwarp();
+        for (int t = 1 + lane; t < nc; t += 32) { W.fill[t] = 0; W.tie[t] = 0; }
+        __syncwarp();
+        if (need > 0) {
+            for (int t = 1 + lane; t < nc; t += 32) {
+                if (W.pick[t]) continue;
+                long long dt = W.d2[t];
+                int it = W.cand[t], r = 0;
+                for (int u = 1; u < nc; ++u)
+                    if (!W.pick[u] && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
+                if (r < need) {
+                    W.fill[t] = 1;
+                    ++nfill;
+                    if (r == need - 1) { W.cut = dt; W.cut_set = 1; }
+                }
+            }
+            nfill = warp_sum_int(nfill);
+        }
+        __syncwarp();
+        int ntie = 0;
+        if (W.cut_set) {
+            const long long cut = W.cut;
+            const int room = MMAX - nA - nfill;
+            for (int t = 1 + lane; t < nc; t += 32) {
+                if (W.pick[t] || W.fill[t] || W.d2[t] != cut) continue;
+                int it = W.cand[t], r = 0;
+                for (int u = 1; u < nc; ++u)
+                    if (!W.pick[u] && !W.fill[u] && W.d2[u] == cut && W.cand[u] < it) ++r;
+                if (r < room) { W.tie[t] = 1; ++ntie; }
+            }
+            ntie = warp_sum_int(ntie);
+        }
+        __syncwarp();
+        for (int t = 1 + lane; t < nc; t += 32) W.pick[t] = W.pick[t] | W.fill[t] | W.tie[t];
+        __syncwarp();
+        m = nA + nfill + ntie;
+        // final order by (d2, index)
+        for (int t = 1 + lane; t < nc; t += 32) {
+            if (!W.pick[t]) continue;
+            long long dt = W.d2[t];
+            int it = W.cand[t], r = 0;
+            for (int u = 1; u < nc; ++u)
+                if (W.pick[u] && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
+            if (r < MMAX) { W.sel[r] = it; W.seld2[r] = dt; }
+        }
+        __syncwarp();
+        if (m > MMAX) m = MMAX;
+
+        // ---- weighted scaled Vandermonde (Eq. regfd, normalized Gaussian weight)
+        long long off[3] = {0, 0, 0};
+        long long mydist = 0;
+        if (lane < m) {
+            int4 q = ic[W.sel[lane]];
+            off[0] = (long long)q.x - c0.x; off[1] = (long long)q.y - c0.y; off[2] = (long long)q.z - c0.z;
+            mydist = W.seld2[lane];
+        }
+        long long amax = 0;
+        if (lane < m) {
+            for (int d = 0; d < 3; ++d) { long long a = off[d] < 0 ? -off[d] : off[d]; amax = a > amax ? a : amax; }
+        }
+        const long long hint = warp_max_ll(amax);
+        const long long r2max = W.seld2[m - 1];
+        double wj = 0.0;
+        if (lane < MMAX) {
+            double row[NCOL];
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) row[e] = 0.0;
+            if (lane < m) {
+                double xi0 = (double)off[0] / (double)hint, xi1 = (double)off[1] / (double)hint,
+                       xi2 = (double)off[2] / (double)hint;
+                double ratio = (double)mydist / (double)r2max;
+                wj = __dmul_rn(__dsub_rn(exp(-ratio), ec), inv_1mec);
+                row[0] = xi0; row[1] = xi1; row[2] = xi2;
+                row[3] = __dmul_rn(__dmul_rn(0.5, xi0), xi0);
+                row[4] = __dmul_rn(xi0, xi1);
+                row[5] = __dmul_rn(xi0, xi2);
+                row[6] = __dmul_rn(__dmul_rn(0.5, xi1), xi1);
+                row[7] = __dmul_rn(xi1, xi2);
+                row[8] = __dmul_rn(__dmul_rn(0.5, xi2), xi2);
+#pragma unroll
+                for (int e = 0; e < NCOL; ++e) row[e] = __dmul_rn(wj, row[e]);
+            }
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) W.A[lane * ASTR + e] = row[e];
+        }
+        __syncwarp();
+
+        // ---- CholeskyQR2
+        gram(W.A, m, W.G, lane);
+        __syncwarp();
+        if (lane == 0) W.flag = cholesky9(W.G, W.R1) ? 1 : 0;
+        __syncwarp();
+        bool ok = W.flag != 0;
+        double q[NCOL];
+        if (ok) {
+            if (lane < m) {
+#pragma unroll
+                for (int e = 0; e < NCOL; ++e) q[e] = W.A[lane * ASTR + e];
+                row_solve_upper(W.R1, q);
+#pragma unroll
+                for (int e = 0; e < NCOL; ++e) W.A[lane * ASTR + e] = q[e];
+            }
+            __syncwarp();
+            gram(W.A, m, W.G, lane);
+            __syncwarp();
+            if (lane == 0) W.flag = cholesky9(W.G, W.R2) ? 1 : 0;
+            __syncwarp();
+            ok = W.flag != 0;
+        }
+        if (ok) {
+            double dmin = 1e300, dmax = 0.0;
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) {
+                double r = fabs(W.R1[e * NCOL + e] * W.R2[e * NCOL + e]);
+                dmin = fmin(dmin, r);
+                dmax = fmax(dmax, r);
+            }
+            rmin_over_rmax = dmin / dmax;
+            ok = dmin >= RANK_TOL * dmax;
+        }
+        if (!ok) {
+            if (k < ring_max) continue;
+            break;
+        }
+        // column j of P: R1^-1 R2^-1 q2_j^T W_j, unscaled by h and h^2
+        const double h = (double)hint * unit;
+        const double h2 = h * h;
+        double lapj = 0.0;
+        if (lane < m) {
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) q[e] = W.A[lane * ASTR + e];
+            row_solve_upper(W.R2, q);
+            col_solve_upper(W.R2, q);
+            col_solve_upper(W.R1, q);
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) q[e] = (q[e] * wj) / (e < 3 ? h : h2);
+            lapj = q[3] + q[6] + q[8];
+        }
+        if (lane < MMAX) {
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) W.P[e * MMAX + lane] = (lane < m) ? q[e] : 0.0;
+        }
+        const double lsum = warp_sum_d(lapj);
+        nbr_out[(int64_t)y0 * MMAX + lane] = (lane < m) ? W.sel[lane] : -1;
+        lap_out[(int64_t)y0 * MMAX + lane] = lapj;
+        if (lane == 0) {
+            lapd_out[y0] = -lsum;
+            m_out[y0] = m;
+            ring_out[y0] = k;
+            rcond_out[y0] = rmin_over_rmax;
+        }
+        __syncwarp();
+        // derivative operator, row-of-operator major with nodes fastest
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = W.P[e * MMAX + lane];
+        ring = k;
+        done = true;
+    }
+    if (!done) {
+        if (lane == 0) {
+            atomicOr(err, overflow ? (ERR_STENCIL | ERR_OVERFLOW) : ERR_STENCIL);
+            m_out[y0] = 0;
+            ring_out[y0] = -1;
+            lapd_out[y0] = 0.0;
+            rcond_out[y0] = 0.0;
+        }
+        nbr_out[(int64_t)y0 * MMAX + lane] = -1;
+        lap_out[(int64_t)y0 * MMAX + lane] = 0.0;
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = 0.0;
+    }
+    (void)ring;
+}
+
+// ---------------------------------------------------------------- matrices
+__global__ void k_diag(const int32_t *__restrict__ msz, const double *__restrict__ lapd, const int4 *__restrict__ ic,
+                       int n_int, int n_tot, double ext, double *__restrict__ dA, double *__restrict__ dB) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_tot) return;
+    if (r < n_int) {
+        double h = ldexp(ext, -ic[r].w);
+        double s = h * h / 24.0;
+        dA[r] = lapd[r];
+        dB[r] = 1.0 + s * lapd[r];
+    } else {
+        dA[r] = 1.0;
+        dB[r] = 1.0;
+    }
+}
+
+__global__ void k_slice_width(const int32_t *__restrict__ msz, int n_int, int n_tot, int nsl, uint32_t *__restrict__ w) {
+    int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (s >= nsl) return;
+    int r = s * 32 + lane;
+    int v = 0;
+    if (r < n_int) v = msz[r] + 1;
+    else if (r < n_tot) v = 1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) { int t = __shfl_xor_sync(0xffffffffu, v, o); v = t > v ? t : v; }
+    if (lane == 0) w[s] = (uint32_t)v;
+}
+
+// Row j of A: diag = -sum l, off-diagonals l_ji; row j of B: 1 + (h_j^2/24) A_jj
+// and (h_j^2/24) l_ji (Section 3.2 with the cell-indicator moments); boundary
+// rows are identity rows.  Values are stored right-scaled by the inverse
+// diagonal of the column (Jacobi preconditioning folded into the matrix).
+__global__ void k_ell_fill(const int32_t *__restrict__ msz, const int32_t *__restrict__ nbr,
+                           const double *__restrict__ lap, const double *__restrict__ lapd, const int4 *__restrict__ ic,
+                           const double *__restrict__ dA, const double *__restrict__ dB, int n_int, int n_tot,
+                           double ext, const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+                           int32_t *__restrict__ col, double *__restrict__ vA, double *__restrict__ vB) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    int s = r >> 5, lane = r & 31;
+    if (s * 32 >= n_tot) return;
+    int w = (int)sw[s];
+    int64_t base = (int64_t)soff[s] * 32 + lane;
+    if (r >= n_tot) {
+        for (int k = 0; k < w; ++k) { col[base + k * 32] = 0; vA[base + k * 32] = 0.0; vB[base + k * 32] = 0.0; }
+        return;
+    }
+    if (r >= n_int) {
+        col[base] = r; vA[base] = 1.0 / dA[r]; vB[base] = 1.0 / dB[r];
+        for (int k = 1; k < w; ++k) { col[base + k * 32] = r; vA[base + k * 32] = 0.0; vB[base + k * 32] = 0.0; }
+        return;
+    }
+    int m = msz[r];
+    double h = ldexp(ext, -ic[r].w);
+    double sc = h * h / 24.0;
+    col[base] = r;
+    vA[base] = lapd[r] / dA[r];
+    vB[base] = (1.0 + sc * lapd[r]) / dB[r];
+    for (int k = 1; k < w; ++k) {
+        int64_t e = base + (int64_t)k * 32;
+        if (k <= m) {
+            int cj = nbr[(int64_t)r * MMAX + k - 1];
+            double l = lap[(int64_t)r * MMAX + k - 1];
+            col[e] = cj;
+            vA[e] = l / dA[cj];
+            vB[e] = (sc * l) / dB[cj];
+        } else {
+            col[e] = r;
+            vA[e] = 0.0;
+            vB[e] = 0.0;
+        }
+    }
+}
+
+}  // namespace
+
+static bool g_pairs_set = false;
+
+apcloud_status build_stencils(apcloud_ctx *c) {
+    const int n = c->n_int, nt = c->n_tot;
+    if (!g_pairs_set) {
+        unsigned char pa[45], pb[45];
+        int e = 0;
+        for (int a = 0; a < NCOL; ++a)
+            for (int b = a; b < NCOL; ++b) { pa[e] = (unsigned char)a; pb[e] = (unsigned char)b; ++e; }
+        APC_CUDA(c, cudaMemcpyToSymbolAsync(c_pa, pa, sizeof pa, 0, cudaMemcpyHostToDevice, c->s));
+        APC_CUDA(c, cudaMemcpyToSymbolAsync(c_pb, pb, sizeof pb, 0, cudaMemcpyHostToDevice, c->s));
+        APC_CUDA(c, cudaStreamSynchronize(c->s));
+        g_pairs_set = true;
+    }
+    const int64_t dstride = ((int64_t)n + 31) / 32 * 32;
+    int32_t *nbr = ensure<int32_t>(c, c->nbr, (int64_t)n * MMAX);
+    int32_t *msz = ensure<int32_t>(c, c->msz, n + 1);
+    int32_t *ring = ensure<int32_t>(c, c->ring, n + 1);
+    double *lap = ensure<double>(c, c->lap, (int64_t)n * MMAX);
+    double *lapd = ensure<double>(c, c->lapd, n + 1);
+    double *D = ensure<double>(c, c->D, (int64_t)NCOL * MMAX * dstride);
+    double *rc = ensure<double>(c, c->rcond, n + 1);
+    if (!nbr || !msz || !ring || !lap || !lapd || !D || !rc) return APCLOUD_E_NOMEM;
+    unsigned *derr = ptr<unsigned>(c->derr);
+    APC_CUDA(c, cudaMemsetAsync(derr, 0, 4 * sizeof(unsigned), c->s));
+    const double ext = c->P.hi[0] - c->P.lo[0];
+    const double unit = ldexp(ext, -(KEY_DEPTH + 1));
+    const double ec = exp(-c->P.weight_c);
+    const double inv_1mec = 1.0 / (1.0 - ec);
+    size_t smem = sizeof(BlockSmem);
+    static bool attr = false;
+    if (!attr) {
+        APC_CUDA(c, cudaFuncSetAttribute(k_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    APC_LAUNCH(c, K_STENCIL, div_up(n, SW), SW * 32, smem, k_stencil, ptr<int4>(c->node_ic), ptr<int32_t>(c->adj),
+               ptr<int32_t>(c->bowner), n, c->P.m_target, c->P.ring_max, unit, ec, inv_1mec, nbr, msz, ring, lap,
+               lapd, D, dstride, rc, derr);
+    APC_CUDA(c, cudaGetLastError());
+    APC_TRY(check_device_errors(c));
+
+    // sliced ELL of A and B
+    const int nsl = div_up(nt, 32);
+    c->n_slices = nsl;
+    uint32_t *sw = ensure<uint32_t>(c, c->slice_w, nsl + 1);
+    uint32_t *so = ensure<uint32_t>(c, c->slice_off, nsl + 1);
+    double *dA = ensure<double>(c, c->dA, nt + 1);
+    double *dB = ensure<double>(c, c->dB, nt + 1);
+    if (!sw || !so || !dA || !dB) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_ELL, div_up(nt, 256), 256, 0, k_diag, msz, lapd, ptr<int4>(c->node_ic), n, nt, ext, dA, dB);
+    APC_LAUNCH(c, K_ELL, div_up(nsl, 8), 256, 0, k_slice_width, msz, n, nt, nsl, sw);
+    uint32_t *small = ptr<uint32_t>(c->dsmall);
+    APC_TRY(scan_u32(c, sw, so, nsl, small + 5));
+    uint32_t tot;
+    APC_TRY(read_back(c, &tot, small + 5, sizeof tot));
+    c->ell_entries = (int64_t)tot * 32;
+    int32_t *col = ensure<int32_t>(c, c->ell_col, c->ell_entries);
+    double *vA = ensure<double>(c, c->ell_A, c->ell_entries);
+    double *vB = ensure<double>(c, c->ell_B, c->ell_entries);
+    if (!col || !vA || !vB) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_ELL, div_up((int64_t)nsl * 32, 256), 256, 0, k_ell_fill, msz, nbr, lap, lapd,
+               ptr<int4>(c->node_ic), dA, dB, n, nt, ext, sw, so, col, vA, vB);
+    return cuda_check(c, cudaGetLastError(), "ell");
+}
+
+}  // namespace apc

@@ -1,0 +1,206 @@
+"""Parity of the CUDA path with the CPU oracle on the same seeded inputs.
+
+Integer results (node sets, leaf particle ranges, boundary nodes, stencil
+neighbour lists) must be bit-exact.  Floating-point results use tolerances
+derived from the arithmetic:
+  * stencil weights: both sides factor the same m x 9 weighted Vandermonde
+    (Householder on the CPU, CholeskyQR2 on the GPU); with column-scaled
+    conditions below 1e3 the operators agree to ~1e-13 relative, checked at
+    1e-11 of the row's largest weight;
+  * rho_M: a sum of at most N' charges in a different order, 1e-14;
+  * phi and E: both solved to a relative residual of 1e-13; with ||A^-1||
+    of order one the potentials agree to about 1e-12, checked at the stated
+    1e-10 relative L2 of the FP64 form.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1603_04039_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _setup(x, y, z, depth, c, m_target=20):
+    from paper_1603_04039_gb300 import APCloud
+    ap = APCloud(max_depth=depth, c_refine=c, m_target=m_target)
+    tx, ty, tz = _t(x), _t(y), _t(z)
+    ni, nb = ap.build_octree(tx, ty, tz)
+    o = oracle.Oracle(max_depth=depth, c_refine=c, m_target=m_target)
+    o.build(x, y, z)
+    return ap, o, (tx, ty, tz)
+
+
+CASES = [(100000, 6, 1.0, 1), (100000, 6, 0.5, 2), (20000, 5, 0.3, 3), (3000, 7, 0.2, 4), (777, 4, 0.05, 5)]
+
+
+@pytest.mark.parametrize("n,depth,c,seed", CASES)
+def test_octree_bit_exact(n, depth, c, seed):
+    x, y, z, q = inputs.beam_with_halo(n, seed)
+    ap, o, _ = _setup(x, y, z, depth, c)
+    assert (ap.n_int, ap.n_bnd) == (o.n_int, o.n_bnd)
+    g = ap.get_nodes()
+    w = o.nodes()
+    assert np.array_equal(g["level"].cpu().numpy(), w["level"])
+    assert np.array_equal(g["kind"].cpu().numpy(), w["kind"])
+    assert np.array_equal(g["xyz"].cpu().numpy(), w["xyz"])
+    gl = ap.get_leaves()
+    key, first, count = o.leaves()
+    assert np.array_equal(gl["key"].cpu().numpy().astype(np.uint64), key)
+    assert np.array_equal(gl["first"].cpu().numpy(), first)
+    assert np.array_equal(gl["count"].cpu().numpy(), count)
+
+
+@pytest.mark.parametrize("n,depth,c,seed", CASES[:4])
+def test_stencils_match_oracle(n, depth, c, seed):
+    x, y, z, q = inputs.beam_with_halo(n, seed)
+    ap, o, _ = _setup(x, y, z, depth, c)
+    ap.stencils()
+    g = {k: v.cpu().numpy() for k, v in ap.get_stencils().items()}
+    w = o.stencils()
+    assert np.array_equal(g["m"], w["m"])
+    assert np.array_equal(g["nbr"], w["nbr"])
+    scale = np.abs(w["lap"]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g["lap"] - w["lap"]) <= 1e-11 * scale)
+    assert np.all(np.abs(g["lapd"] - w["lapd"]) <= 1e-11 * scale[:, 0])
+    dscale = np.abs(w["D"]).max(axis=2, keepdims=True)
+    assert np.all(np.abs(g["D"] - w["D"]) <= 1e-11 * dscale)
+
+
+@pytest.mark.parametrize("n,depth,c,seed", CASES[:3])
+def test_matvec_matches_oracle(n, depth, c, seed):
+    x, y, z, q = inputs.beam_with_halo(n, seed)
+    ap, o, _ = _setup(x, y, z, depth, c)
+    ap.stencils()
+    o.stencils()
+    v = np.random.default_rng(seed).normal(size=o.n_nodes)
+    for which in ("A", "B"):
+        rp, col, val = o.matrix(which)
+        want = np.add.reduceat(val * v[col], rp[:-1])
+        got = ap.matvec(which, _t(v)).cpu().numpy()
+        assert np.allclose(got, want, rtol=1e-12, atol=1e-12 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("n,depth,c,seed", CASES[:4])
+def test_full_solve_matches_oracle(n, depth, c, seed):
+    x, y, z, q = inputs.beam_with_halo(n, seed)
+    ap, o, _ = _setup(x, y, z, depth, c)
+    ap.stencils()
+    rho, ir = ap.deposit(q_uniform=1.0 / n, rtol=1e-13)
+    phi, ip = ap.solve(rtol=1e-13)
+    php, ex, ey, ez = ap.gather_field()
+    assert ir["status"] == 0 and ip["status"] == 0 and ip["relres"] <= 1e-13
+    ref = o.run(x, y, z, q_uniform=1.0 / n, rtol=1e-13)
+    rm = ap.get_rho_m().cpu().numpy()
+    assert np.allclose(rm, ref["rhoM"], rtol=1e-14, atol=0)
+    def rel(a, b):
+        return np.linalg.norm(a - b) / np.linalg.norm(b)
+    assert rel(rho.cpu().numpy(), ref["rho"]) < 1e-10
+    assert rel(phi.cpu().numpy(), ref["phi"]) < 1e-10
+    assert rel(ap.get_derivatives().cpu().numpy(), ref["dphi"]) < 1e-10
+    assert rel(php.cpu().numpy(), ref["phi_p"]) < 1e-10
+    for a, b in ((ex, ref["ex"]), (ey, ref["ey"]), (ez, ref["ez"])):
+        assert rel(a.cpu().numpy(), b) < 1e-10
+
+
+def test_variable_charges_deposit():
+    n = 50000
+    x, y, z, _ = inputs.beam_with_halo(n, 9)
+    q = np.random.default_rng(9).uniform(0.0, 2.0 / n, n)
+    ap, o, _ = _setup(x, y, z, 6, 0.7)
+    ap.stencils()
+    o.stencils()
+    ap.deposit(q=_t(q), rtol=1e-12)
+    want, Qc, total = o.density_rhs(q)
+    got = ap.get_rho_m().cpu().numpy()
+    assert np.allclose(got, want, rtol=1e-14, atol=0)
+    h = 2.0 / 2.0 ** o.nodes()["level"][: o.n_int]
+    assert abs((got[: o.n_int] * h ** 3).sum() - q.sum()) < 1e-12 * q.sum()
+
+
+def test_field_host_matches_device_path():
+    from paper_1603_04039_gb300 import APCloud
+    n = 30000
+    x, y, z, q = inputs.beam_with_halo(n, 11)
+    ap = APCloud(max_depth=5, c_refine=0.8)
+    (php, ex, ey, ez), info = ap.field_host(x, y, z, q=q, rtol=1e-12)
+    o = oracle.Oracle(max_depth=5, c_refine=0.8)
+    ref = o.run(x, y, z, q=q, rtol=1e-12)
+    assert np.linalg.norm(php - ref["phi_p"]) / np.linalg.norm(ref["phi_p"]) < 1e-9
+    assert np.linalg.norm(ex - ref["ex"]) / np.linalg.norm(ref["ex"]) < 1e-9
+
+
+def test_solve_system_exact_for_quadratic():
+    """The GPU solves the oracle-pinned exactness problem: a quadratic phi with
+    constant Laplacian solves the GFD Poisson system exactly."""
+    x, y, z, q = inputs.beam_with_halo(20000, 7)
+    ap, o, _ = _setup(x, y, z, 5, 1.0)
+    ap.stencils()
+    xyz = ap.get_nodes()["xyz"].cpu().numpy()
+    H = np.array([[2.0, 0.3, -0.1], [0.3, -1.0, 0.2], [-0.1, 0.2, 0.5]])
+    f = 0.3 + xyz @ np.array([0.5, -1.0, 0.25]) + 0.5 * np.einsum("ni,ij,nj->n", xyz, H, xyz)
+    b = np.full(ap.n_nodes, np.trace(H))
+    b[ap.n_int:] = f[ap.n_int:]
+    sol, info = ap.solve_system("A", _t(b), rtol=1e-14, max_iter=20000)
+    assert np.allclose(sol.cpu().numpy(), f, atol=1e-9 * np.abs(f).max())
+
+
+# ---------------------------------------------------------------- edge cases
+def test_edge_cases():
+    from paper_1603_04039_gb300 import APCloud, APCloudError
+    ap = APCloud(max_depth=4, c_refine=1.0)
+    # call order
+    with pytest.raises(APCloudError) as e:
+        ap.stencils()
+    assert e.value.status == -7
+    # outside the domain and NaN
+    for bad in (1.5, float("nan")):
+        x = np.zeros(10)
+        x[3] = bad
+        with pytest.raises(APCloudError) as e:
+            ap.build_octree(_t(x), _t(np.zeros(10)), _t(np.zeros(10)))
+        assert e.value.status == -2
+    # empty input: the root is the only leaf, it has 6 boundary faces
+    ni, nb = ap.build_octree(_t(np.zeros(0)), _t(np.zeros(0)), _t(np.zeros(0)))
+    assert (ni, nb) == (1, 6)
+    with pytest.raises(APCloudError) as e:
+        ap.stencils()                     # 6 candidates < 9 unknowns
+    assert e.value.status == -3
+
+
+@pytest.mark.parametrize("layout", ["one_cell", "faces", "corners"])
+def test_degenerate_layouts_bit_exact(layout):
+    rng = np.random.default_rng(3)
+    if layout == "one_cell":                  # all particles in one depth-6 cell
+        p = 0.3 + rng.uniform(0, 2.0 / 64, size=(5000, 3))
+    elif layout == "faces":                   # exactly on cell faces and on the domain boundary
+        g = np.linspace(-1, 1, 17)
+        p = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    else:                                     # clustered at two opposite corners
+        p = np.concatenate([-1 + rng.uniform(0, 0.05, size=(3000, 3)), 1 - rng.uniform(0, 0.05, size=(3000, 3))])
+    x, y, z = (np.ascontiguousarray(p[:, d]) for d in range(3))
+    ap, o, _ = _setup(x, y, z, 6, 0.2)
+    assert (ap.n_int, ap.n_bnd) == (o.n_int, o.n_bnd)
+    assert np.array_equal(ap.get_nodes()["xyz"].cpu().numpy(), o.nodes()["xyz"])
+    ap.stencils()
+    w = o.stencils()
+    g = ap.get_stencils()
+    assert np.array_equal(g["nbr"].cpu().numpy(), w["nbr"])
+
+
+def test_m_target_variants():
+    x, y, z, q = inputs.beam_with_halo(30000, 12)
+    for m in (9, 16, 32):
+        ap, o, _ = _setup(x, y, z, 5, 0.5, m_target=m)
+        ap.stencils()
+        w = o.stencils()
+        g = ap.get_stencils()
+        assert np.array_equal(g["m"].cpu().numpy(), w["m"])
+        assert np.array_equal(g["nbr"].cpu().numpy(), w["nbr"])
