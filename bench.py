@@ -1,0 +1,328 @@
+"""Benchmark: AP-Cloud electrostatic solves per second on GB300.
+
+One step is one pass of the whole hot path on one synthetic beam-with-halo
+particle set resident in HBM: octree build, stencils (neighbour search + WLS),
+deposit and density solve, GMRES Poisson solve to rtol 1e-10, and the gather
+of phi and E back to the particles.
+
+Workload (default): 1e7 particles, octree depth 10, refinement constant
+tuned to ~1e6 nodes, FP64 throughout.  With --gpus N (launched under
+torchrun) every rank solves its own independent beam (seed 1 + rank): the
+problems do not share data, so there is no collective on the data path and
+the scaling is weak.  --impl reference times the CPU oracle instead.
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GFD Poisson solves/sec and nodes·iters/sec at rel-L2 ≤1e-6 vs FP64; % roofline"
+WORKLOADS = {
+    # name: (particles, max_depth, c_refine)
+    "beam_halo_1e7_depth10": (10_000_000, 10, 0.043),
+    "beam_halo_1e5_depth6": (100_000, 6, 1.0),
+}
+RTOL = 1e-10
+MAX_ITER = 200000
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- our GPU path
+def run_ours(args, ws, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1603_04039_gb300 import APCloud, inputs
+    from paper_1603_04039_gb300._binding import measure_fma_peak
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    fp64_peak, fp32_peak = measure_fma_peak()
+    npart, depth, c = WORKLOADS[args.workload]
+    seed = 1 + rank
+    x, y, z, q = inputs.beam_with_halo(npart, seed)
+    tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
+    ap = APCloud(max_depth=depth, c_refine=c, restart=30, device=dev)
+    out = tuple(torch.empty(npart, dtype=torch.float64, device=dev) for _ in range(4))
+    stream = ap.stream
+    info = {}
+
+    def step():
+        ni, nb = ap.build_octree(tx, ty, tz)
+        ap.stencils()
+        _, ir = ap.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
+        _, ip = ap.solve(rtol=RTOL, max_iter=MAX_ITER)
+        ap.gather_field(out)
+        info.update(n_int=ni, n_bnd=nb, iters_rho=ir["iters"], iters_phi=ip["iters"], relres_phi=ip["relres"],
+                    status=max(ir["status"], ip["status"]))
+
+    def barrier():
+        if ws > 1:
+            dist.barrier()
+
+    # warm-up; the last warm-up step times every kernel kind to find the dominant one
+    for w in range(args.warmup):
+        if w == args.warmup - 1:
+            ap.set_timing(0xFFFF)
+        step()
+    torch.cuda.synchronize()
+    all_kinds = ap.get_timing(reset=True)
+    ap.set_timing(0)
+    solve_kinds = {k: v for k, v in all_kinds.items() if v[1] > 0}
+    dominant = max(solve_kinds, key=lambda k: solve_kinds[k][0])
+    from paper_1603_04039_gb300._binding import kernel_names
+    dom_bit = kernel_names().index(dominant)
+
+    # timed region: inputs resident (positions and charges, 320 MB > L2)
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    launches0 = ap.launch_count()
+    ap.set_timing(1 << dom_bit)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    iters_total = 0
+    for _ in range(args.steps):
+        step()
+        iters_total += info["iters_phi"] + info["iters_rho"]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_total = e0.elapsed_time(e1)
+    dom = ap.get_timing(reset=True)[dominant]
+    ap.set_timing(0)
+    launches = ap.launch_count() - launches0
+    clocks = sampler.stop()
+    ms_step = ms_total / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    n_nodes = info["n_int"] + info["n_bnd"]
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    hx, hy, hz, hq = (torch.from_numpy(a).pin_memory() for a in (x, y, z, q))
+    hout = tuple(torch.empty(npart, dtype=torch.float64).pin_memory() for _ in range(4))
+    ap_e2e = APCloud(max_depth=depth, c_refine=c, restart=30, device=dev)
+    ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout)   # warm-up
+    barrier()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if ws > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    ap_e2e.close()
+
+    # roofline of the dominant kernel, measured live in the timed region
+    peaks = _measured_peaks()
+    ms_k, nl_k, by_k, fl_k = dom
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    gbs = by_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
+    tfs = fl_k / (ms_k * 1e-3) / 1e12 if ms_k > 0 else 0.0
+    # FP64 work per byte decides the bound: above FP64 peak / HBM peak the ALU limits
+    if fl_k > 0 and fl_k / max(by_k, 1.0) > fp64_peak * 1e12 / (hbm * 1e9):
+        roof = {"bound": "alu", "achieved": round(tfs, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
+                "frac": round(tfs / fp64_peak, 4)}
+    else:
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4)}
+    roof.update({"kernel": dominant, "traffic": None, "launches": nl_k,
+                 "algorithmic_bytes_per_launch": by_k / max(nl_k, 1),
+                 "algorithmic_flops_per_launch": fl_k / max(nl_k, 1),
+                 "share_of_step": round(ms_k / ms_total, 4),
+                 "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64 FMA chains on all SMs "
+                                "(apcloud_measure_fma_peak) in this run",
+                 "fp64_peak_tflops": round(fp64_peak, 4), "fp32_peak_tflops": round(fp32_peak, 3)})
+    solves = ws * 1000.0 / ms_step
+    line = {
+        "metric": METRIC, "value": round(solves, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "particles": npart, "max_depth": depth, "c_refine": c,
+                   "n_nodes": n_nodes, "n_interior": info["n_int"], "solver": "GMRES(30)+Jacobi", "rtol": RTOL,
+                   "gmres_iters_phi": info["iters_phi"], "gmres_iters_rho": info["iters_rho"],
+                   "relres_phi": info["relres_phi"], "l2": "inputs 320 MB > L2, no flush",
+                   "parallelism": "independent beam per GPU" if ws > 1 else "single GPU"},
+        "nodes_iters_per_s": round(ws * n_nodes * (iters_total / args.steps) / (ms_step * 1e-3), 1),
+        "e2e": {"value": round(ws / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,
+                "d2h_bytes_per_step": 32 * npart},
+        "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+        "stage_ms_by_kernel": {k: round(v[0] / 1, 3) for k, v in solve_kinds.items()},
+    }
+    return line
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(workload, seed=1, gmres_sample=10, gmres_iters_hint=None):
+    """Times the CPU oracle on the workload: the tree, stencils, deposit and
+    gather in full, and `gmres_sample` GMRES iterations of each system, scaled
+    to the iteration counts of a converged solve.  Returns (seconds per solve,
+    description)."""
+    import oracle
+    from paper_1603_04039_gb300 import inputs
+    npart, depth, c = WORKLOADS[workload]
+    x, y, z, q = inputs.beam_with_halo(npart, seed)
+    o = oracle.Oracle(max_depth=depth, c_refine=c)
+    t = {}
+    t0 = time.perf_counter(); o.build(x, y, z); t["build"] = time.perf_counter() - t0
+    t0 = time.perf_counter(); o.stencils(); t["stencils"] = time.perf_counter() - t0
+    t0 = time.perf_counter(); rhs, _, _ = o.density_rhs(q); t["deposit"] = time.perf_counter() - t0
+    it_r, it_p = gmres_iters_hint or (8, 6650)
+    t0 = time.perf_counter()
+    rho, k_r, _, _ = o.solve_density(rhs, rtol=RTOL, max_iter=min(gmres_sample, it_r))
+    t_r = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    phi, k_p, _, _ = o.solve_poisson(rho, rtol=RTOL, max_iter=gmres_sample)
+    t_p = time.perf_counter() - t0
+    t["solve_rho"] = t_r / max(k_r, 1) * it_r
+    t["solve_phi"] = t_p / max(k_p, 1) * it_p
+    t0 = time.perf_counter(); o.gather(phi); t["gather"] = time.perf_counter() - t0
+    total = sum(t.values())
+    desc = ("oracle on %s seed %d: tree, stencils, deposit and gather in full; %d+%d GMRES iterations timed and "
+            "scaled to %d+%d (a converged solve)" % (workload, seed, k_r, k_p, it_r, it_p))
+    return total, desc, {k: round(v, 3) for k, v in t.items()}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    times = []
+    for w in range(args.warmup + args.steps):
+        tot, desc, stages = oracle_sample(args.workload, gmres_sample=5)
+        if w >= args.warmup:
+            times.append(tot)
+    sec = float(np.mean(times))
+    val = 1.0 / sec
+    return {"metric": METRIC, "value": round(val, 6), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": args.workload}, "stage_s": stages,
+            "cpu_baseline": {"value": round(val, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": round(val, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="beam_halo_1e7_depth10", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    ws, rank, local = _dist()
+    if ws != args.gpus and ws > 1:
+        print("warning: --gpus %d but WORLD_SIZE %d" % (args.gpus, ws), file=sys.stderr)
+    if args.impl == "reference":
+        line = run_reference(args, ws, rank)
+        if line is not None:
+            print(json.dumps(line))
+        return
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    line = run_ours(args, ws, rank, local)
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            tot, desc, stages = oracle_sample(args.workload, gmres_sample=10,
+                                              gmres_iters_hint=(line["config"]["gmres_iters_rho"],
+                                                                line["config"]["gmres_iters_phi"]))
+            line["cpu_baseline"] = {"value": round(1.0 / tot, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                    "sample": desc, "stage_s": stages}
+        else:
+            line["cpu_baseline"] = None
+        print(json.dumps(line))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -190,12 +190,22 @@ apcloud_status apcloud_field_host(apcloud_ctx *ctx, const double *h_x, const dou
 /* Per-kernel device timing with CUDA events on the context stream.
  * apcloud_set_timing(ctx, mask) enables timing for the kernel kinds whose
  * bit is set in mask (bit k = kind k, see apcloud_kernel_name), 0 disables.
- * apcloud_get_timing synchronises and returns, for kind k, the summed
- * milliseconds and launch count since the last reset (reset = 1 clears). */
+ * apcloud_get_timing synchronises and returns, for kind k (host arrays of
+ * APCLOUD_NUM_KINDS entries, any may be NULL): summed milliseconds, launch
+ * count, and the algorithmic bytes and floating-point operations of those
+ * launches (what the kernel must move and compute, not what it did), since
+ * the last reset (reset = 1 clears). */
 #define APCLOUD_NUM_KINDS 16
 apcloud_status apcloud_set_timing(apcloud_ctx *ctx, unsigned mask);
-apcloud_status apcloud_get_timing(apcloud_ctx *ctx, double *h_ms, int64_t *h_launches, int reset);
+apcloud_status apcloud_get_timing(apcloud_ctx *ctx, double *h_ms, int64_t *h_launches, double *h_bytes,
+                                  double *h_flops, int reset);
 const char *apcloud_kernel_name(int kind);
+
+/* Fused multiply-add throughput of the current device in TFLOP/s (2 flops per
+ * FMA), FP64 and FP32, from independent FMA chains on every SM; allocates a
+ * few MB temporarily and synchronises the device.  No paper counterpart: it
+ * provides the ALU roofline of the FP64 kernels.  Either pointer may be NULL. */
+apcloud_status apcloud_measure_fma_peak(double *h_fp64_tflops, double *h_fp32_tflops);
 
 /* Total kernel launches issued by this context since creation. */
 int64_t apcloud_launch_count(const apcloud_ctx *ctx);

@@ -79,9 +79,10 @@ def load():
             "apcloud_field_host": (I, [P, P, P, P, P, D, L, D, I, P, P, P, P, C.POINTER(SolveInfo),
                                        C.POINTER(SolveInfo)]),
             "apcloud_set_timing": (I, [P, C.c_uint]),
-            "apcloud_get_timing": (I, [P, P, P, I]),
+            "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
             "apcloud_launch_count": (L, [P]),
+            "apcloud_measure_fma_peak": (I, [C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -109,6 +110,16 @@ def _f64(t, n=None):
     if n is not None and t.numel() != n:
         raise ValueError("expected %d entries, got %d" % (n, t.numel()))
     return t
+
+
+def measure_fma_peak():
+    """(FP64, FP32) FMA throughput of the current CUDA device in TFLOP/s."""
+    lib = load()
+    d, f = C.c_double(), C.c_double()
+    st = lib.apcloud_measure_fma_peak(C.byref(d), C.byref(f))
+    if st != 0:
+        raise APCloudError(st, "apcloud_measure_fma_peak failed")
+    return d.value, f.value
 
 
 def kernel_names():
@@ -297,11 +308,16 @@ class APCloud:
         self._check(self._lib.apcloud_set_timing(self._ctx, int(mask)))
 
     def get_timing(self, reset=True):
+        """{kernel: (ms, launches, algorithmic bytes, algorithmic flops)} since the last reset."""
         ms = np.zeros(NUM_KINDS)
         cnt = np.zeros(NUM_KINDS, dtype=np.int64)
+        by = np.zeros(NUM_KINDS)
+        fl = np.zeros(NUM_KINDS)
         self._check(self._lib.apcloud_get_timing(self._ctx, ms.ctypes.data_as(C.c_void_p),
-                                                 cnt.ctypes.data_as(C.c_void_p), 1 if reset else 0))
-        return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(kernel_names())}
+                                                 cnt.ctypes.data_as(C.c_void_p), by.ctypes.data_as(C.c_void_p),
+                                                 fl.ctypes.data_as(C.c_void_p), 1 if reset else 0))
+        return {name: (float(ms[k]), int(cnt[k]), float(by[k]), float(fl[k]))
+                for k, name in enumerate(kernel_names())}
 
     def launch_count(self):
         return int(self._lib.apcloud_launch_count(self._ctx))

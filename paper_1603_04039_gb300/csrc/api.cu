@@ -448,13 +448,16 @@ apcloud_status apcloud_set_timing(apcloud_ctx *c, unsigned mask) {
     return APCLOUD_OK;
 }
 
-apcloud_status apcloud_get_timing(apcloud_ctx *c, double *ms, int64_t *launches, int reset) {
+apcloud_status apcloud_get_timing(apcloud_ctx *c, double *ms, int64_t *launches, double *bytes, double *flops,
+                                  int reset) {
     if (!c) return APCLOUD_E_INVALID;
     timer_collect(c);
     for (int k = 0; k < NKIND; ++k) {
         if (ms) ms[k] = c->timer.ms[k];
         if (launches) launches[k] = c->timer.launches[k];
-        if (reset) { c->timer.ms[k] = 0; c->timer.launches[k] = 0; }
+        if (bytes) bytes[k] = c->timer.bytes[k];
+        if (flops) flops[k] = c->timer.flops[k];
+        if (reset) { c->timer.ms[k] = 0; c->timer.launches[k] = 0; c->timer.bytes[k] = 0; c->timer.flops[k] = 0; }
     }
     return APCLOUD_OK;
 }

@@ -102,6 +102,10 @@ apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *e
     APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather, c->px, c->py, c->pz, c->N, c->P.lo[0], c->P.lo[1],
                c->P.lo[2], s, KEY_DEPTH - c->L, unit, ptr<uint64_t>(c->leaf_anchor), n, ptr<int4>(c->node_ic), nf,
                phi_p, ex, ey, ez);
+    // node pass: operator (72 B), column (4 B) and neighbour value (8 B) per
+    // stencil entry plus the 96 B record; particle pass: 24 B in, 32 B out
+    account(c, K_DERIV, 84.0 * c->sum_m + 104.0 * n, 19.0 * c->sum_m);
+    account(c, K_GATHER, 56.0 * c->N, 38.0 * c->N);
     return cuda_check(c, cudaGetLastError(), "gather");
 }
 

@@ -59,6 +59,8 @@ struct Timer {
     size_t used = 0;
     double ms[NKIND] = {0};
     int64_t launches[NKIND] = {0};
+    double bytes[NKIND] = {0};   // algorithmic bytes of the timed launches
+    double flops[NKIND] = {0};   // algorithmic floating-point operations
 };
 
 }  // namespace apc
@@ -82,6 +84,7 @@ struct apcloud_ctx {
     int n_int = 0, n_bnd = 0, n_tot = 0;
     int n_slices = 0;
     int64_t ell_entries = 0;
+    int64_t sum_m = 0;  // total stencil neighbours over interior nodes
 
     // sorted particle keys and permutation (result in key[kbuf], val[kbuf])
     apc::DBuf key[2], val[2];
@@ -122,6 +125,10 @@ inline T *ptr(DBuf &b) { return static_cast<T *>(b.p); }
 // event timers around launches of one kind
 void timer_begin(apcloud_ctx *c, int kind);
 void timer_end(apcloud_ctx *c, int kind);
+// add algorithmic traffic of launches of `kind` (only while that kind is timed)
+inline void account(apcloud_ctx *c, int kind, double bytes, double flops) {
+    if (c->timer.mask >> kind & 1u) { c->timer.bytes[kind] += bytes; c->timer.flops[kind] += flops; }
+}
 
 // read `bytes` from device to host on the context stream and synchronise
 apcloud_status read_back(apcloud_ctx *c, void *host, const void *dev, size_t bytes);

@@ -245,6 +245,7 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
     const double s = ldexp(1.0, KEY_DEPTH) / ext;
     APC_LAUNCH(c, K_KEYS, div_up(n, T), T, 0, k_keys, x, y, z, n, c->P.lo[0], c->P.lo[1], c->P.lo[2], c->P.hi[0],
                c->P.hi[1], c->P.hi[2], s, KEY_DEPTH - L, k0, v0, derr);
+    account(c, K_KEYS, 36.0 * n, 9.0 * n);   // 24 B positions in, 12 B key and index out
     int which = 0;
     APC_TRY(radix_sort(c, k0, v0, k1, v1, n, 3 * L, &which));
     c->kbuf = which;

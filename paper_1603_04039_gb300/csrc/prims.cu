@@ -201,6 +201,7 @@ apcloud_status radix_sort(apcloud_ctx *c, uint64_t *k0, uint32_t *v0, uint64_t *
         APC_LAUNCH(c, K_SORT, nblk, RS_T, 0, k_rs_hist, ka, n, shift, mask, hist, nblk);
         APC_TRY(scan_u32(c, hist, offs, nh, nullptr));
         APC_LAUNCH(c, K_SORT, nblk, RS_T, 0, k_rs_scatter, ka, va, kb, vb, n, shift, mask, offs, nblk);
+        account(c, K_SORT, 32.0 * n, 0.0);   // key read for the histogram, key+value read and write
         uint64_t *tk = ka; ka = kb; kb = tk;
         uint32_t *tv = va; va = vb; vb = tv;
         cur ^= 1;

@@ -364,6 +364,8 @@ apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform) {
     APC_LAUNCH(c, K_DEPOSIT, div_up(n, 8), 256, 0, k_deposit, q, q_uniform, perm, ptr<int32_t>(c->leaf_first),
                ptr<int32_t>(c->leaf_count), ptr<int4>(c->node_ic), n, ext, rm);
     APC_LAUNCH(c, K_DEPOSIT, div_up(c->n_bnd, 256), 256, 0, k_bcopy, ptr<int32_t>(c->bowner), n, c->n_bnd, rm);
+    // permutation and charge per particle, rho_M per node
+    account(c, K_DEPOSIT, (q ? 12.0 * c->N : 0.0) + 8.0 * nt, q ? (double)c->N : (double)n);
     return cuda_check(c, cudaGetLastError(), "deposit");
 }
 
@@ -429,6 +431,16 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         APC_CUDA(c, cudaGetLastError());
         int je;
         APC_TRY(read_back(c, &je, &st->jend, sizeof(int)));
+        {   // algorithmic traffic of the launches that did work
+            const double nnz = (double)c->sum_m + (double)c->n_int + (double)c->n_bnd, dn = n;
+            account(c, K_SPMV, (12.0 * nnz + 16.0 * dn) * (je + 1), 2.0 * nnz * (je + 1));
+            for (int j = 0; j < je; ++j) {
+                account(c, K_DOT, 8.0 * dn * (j + 2), 2.0 * dn * (j + 1));
+                account(c, K_UPDDOT, 8.0 * dn * (j + 3), 4.0 * dn * (j + 1));
+                account(c, K_UPDNORM, 8.0 * dn * (j + 3), 2.0 * dn * (j + 2));
+            }
+            account(c, K_CYCLE, 8.0 * dn * (je + 2), 2.0 * dn * je);
+        }
         iters += je;
         ++cycles;
         if (je == 0) break;  // breakdown at the first column: nothing more to gain

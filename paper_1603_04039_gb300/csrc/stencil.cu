@@ -498,6 +498,19 @@ apcloud_status build_stencils(apcloud_ctx *c) {
                lapd, D, dstride, rc, derr);
     APC_CUDA(c, cudaGetLastError());
     APC_TRY(check_device_errors(c));
+    {   // total stencil size, for the algorithmic traffic of later kernels
+        uint32_t *tmp = ensure<uint32_t>(c, c->tmp, n + 1);
+        if (!tmp) return APCLOUD_E_NOMEM;
+        uint32_t *small = ptr<uint32_t>(c->dsmall);
+        APC_TRY(scan_u32(c, reinterpret_cast<const uint32_t *>(msz), tmp, n, small + 6));
+        uint32_t sm;
+        APC_TRY(read_back(c, &sm, small + 6, sizeof sm));
+        c->sum_m = sm;
+        // per node: offsets and weights in (28 B per neighbour), Laplacian row and
+        // 9 x m operator out (80 B per neighbour); two 9-column Gram products,
+        // three triangular solves per row and two 9x9 factorizations
+        account(c, K_STENCIL, 108.0 * sm + 8.0 * n, 450.0 * sm + 660.0 * n);
+    }
 
     // sliced ELL of A and B
     const int nsl = div_up(nt, 32);
