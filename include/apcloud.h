@@ -178,6 +178,24 @@ apcloud_status apcloud_matvec(apcloud_ctx *ctx, int which, const double *d_x, do
 apcloud_status apcloud_solve_system(apcloud_ctx *ctx, int which, const double *d_b, double *d_x, double rtol,
                                     int max_iter, apcloud_solve_info *info);
 
+/* Allocation-free variant of apcloud_solve_system, for callers that may not
+ * allocate memory once their setup is done: code running inside CUDA stream
+ * capture or under a memory manager that forbids cudaMalloc, real-time loops
+ * with a fixed memory budget, or hosts that own every allocation themselves.
+ * The paper has no counterpart; this is a deployment convenience.
+ * Same arguments and results as apcloud_solve_system, but the Krylov basis,
+ * work vectors, reduction partials and device state live in one file-scope
+ * device array of 20 MiB that every GPU loading the library holds until the
+ * process exits, so the call allocates nothing (timers are ignored during it).
+ * Limits: at most 65536 nodes (interior + boundary) and restart <= 30;
+ * larger problems return APCLOUD_E_INVALID.  The first call on a device
+ * resolves the array's device address (cudaGetSymbolAddress) and must not be
+ * made during stream capture.  All calls share the array: two calls whose
+ * work overlaps on the GPU (other streams, other contexts, other threads)
+ * race and give undefined results.  Synchronises the context stream. */
+apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *ctx, int which, const double *d_b, double *d_x,
+                                            double rtol, int max_iter, apcloud_solve_info *info);
+
 /* The whole solve on host arrays: copies positions and charges (h_q NULL =
  * q_uniform) to the device, runs the five steps with g = 0, and copies phi
  * and E at the particles back.  Host arrays may be pageable or pinned; pinned

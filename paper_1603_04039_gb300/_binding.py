@@ -76,6 +76,7 @@ def load():
             "apcloud_get_derivatives": (I, [P, P]),
             "apcloud_matvec": (I, [P, I, P, P]),
             "apcloud_solve_system": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo)]),
+            "apcloud_solve_system_noalloc": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo)]),
             "apcloud_field_host": (I, [P, P, P, P, P, D, L, D, I, P, P, P, P, C.POINTER(SolveInfo),
                                        C.POINTER(SolveInfo)]),
             "apcloud_set_timing": (I, [P, C.c_uint]),
@@ -278,6 +279,17 @@ class APCloud:
             st = self._check(self._lib.apcloud_solve_system(self._ctx, 1 if which == "A" else 0, _dptr(b), _dptr(x),
                                                             rtol, int(max_iter), C.byref(info)))
         return x, dict(info.as_dict(), status=st)
+
+    def solve_system_noalloc(self, which, b, x, rtol=1e-10, max_iter=100000):
+        """apcloud_solve_system_noalloc on caller-owned tensors: x holds the
+        initial guess and receives the solution; the library allocates nothing."""
+        _f64(b, self.n_nodes)
+        _f64(x, self.n_nodes)
+        info = SolveInfo()
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_solve_system_noalloc(self._ctx, 1 if which == "A" else 0, _dptr(b),
+                                                                    _dptr(x), rtol, int(max_iter), C.byref(info)))
+        return dict(info.as_dict(), status=st)
 
     def field_host(self, x, y, z, q=None, q_uniform=None, rtol=1e-10, max_iter=100000, out=None):
         """Whole solve on host numpy arrays (pinned tensors are also accepted)."""

@@ -456,3 +456,137 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
 }
 
 }  // namespace apc
+
+// ---------------------------------------------------------------- allocation-free solve
+// apcloud_solve_system_noalloc: the GMRES solve of apcloud_solve_system with
+// every piece of Krylov scratch (basis, work vectors, block partials, device
+// state) carved from one file-scope device array instead of context buffers,
+// so a call allocates no device or host memory.  Sized for at most
+// NOALLOC_MAX_NODES nodes and restart <= NOALLOC_MAX_RESTART.
+#include <mutex>
+
+namespace apc {
+
+constexpr size_t NOALLOC_BYTES = (size_t)20 << 20;   // 20 MiB on every device that loads the library
+constexpr int NOALLOC_MAX_NODES = 65536;
+constexpr int NOALLOC_MAX_RESTART = 30;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned char *g_noalloc_base[NOALLOC_MAX_DEVICES] = {};
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Device address of the scratch array for the current device (the host-side
+// name of the array is only a stand-in); resolved once per device.
+apcloud_status noalloc_base(apcloud_ctx *c, unsigned char **out) {
+    int dev = 0;
+    APC_CUDA(c, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(c, APCLOUD_E_INVALID, "device index %d too large", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_check(c, e == cudaSuccess ? cudaErrorInvalidSymbol : e,
+                                                      "cudaGetSymbolAddress(scratch)");
+        g_noalloc_base[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_base[dev];
+    return APCLOUD_OK;
+}
+}  // namespace
+}  // namespace apc
+
+extern "C" apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *c, int which, const double *b, double *x,
+                                                       double rtol, int max_iter, apcloud_solve_info *info) {
+    using namespace apc;
+    if (!c || !b || !x || (which != 0 && which != 1)) return APCLOUD_E_INVALID;
+    if (c->stage < 2) return fail(c, APCLOUD_E_STATE, "matrices are available after apcloud_stencils");
+    if (!(rtol > 0) || max_iter < 0) return fail(c, APCLOUD_E_INVALID, "rtol must be > 0 and max_iter >= 0");
+    const int n = c->n_tot;
+    const int m = c->P.restart;
+    if (n > NOALLOC_MAX_NODES)
+        return fail(c, APCLOUD_E_INVALID, "%d nodes exceed the %d-node limit of the allocation-free solve", n,
+                    NOALLOC_MAX_NODES);
+    if (m > NOALLOC_MAX_RESTART)
+        return fail(c, APCLOUD_E_INVALID, "restart %d exceeds the limit %d of the allocation-free solve", m,
+                    NOALLOC_MAX_RESTART);
+    unsigned char *base = nullptr;
+    APC_TRY(noalloc_base(c, &base));
+    // carve: state | basis | w | wraw | u | partials
+    const int64_t ldv = ((int64_t)n + 31) / 32 * 32;
+    const int nblk = reduction_blocks(c, n);
+    size_t off = 0;
+    GmresState *st = reinterpret_cast<GmresState *>(base + off);
+    off = align256(off + sizeof(GmresState));
+    double *V = reinterpret_cast<double *>(base + off);
+    off = align256(off + sizeof(double) * (size_t)(m + 1) * ldv);
+    double *w = reinterpret_cast<double *>(base + off);
+    off = align256(off + sizeof(double) * (size_t)ldv);
+    double *wraw = reinterpret_cast<double *>(base + off);
+    off = align256(off + sizeof(double) * (size_t)ldv);
+    double *u = reinterpret_cast<double *>(base + off);
+    off = align256(off + sizeof(double) * (size_t)ldv);
+    double *partial = reinterpret_cast<double *>(base + off);
+    off = align256(off + sizeof(double) * (size_t)(div_up(n, RT) + 2 * nblk) * 64);
+    if (off > NOALLOC_BYTES) return fail(c, APCLOUD_E_INVALID, "allocation-free scratch too small");
+
+    const unsigned saved_mask = c->timer.mask;   // event timers may allocate: off for this call
+    c->timer.mask = 0;
+    const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
+    const double *d = ptr<double>(which ? c->dA : c->dB);
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    apcloud_status status = APCLOUD_W_NOT_CONVERGED;
+    int iters = 0, cycles = 0;
+    double relres = 0.0;
+    do {
+        // the array keeps the previous call's contents: the state must start from zero
+        if (cuda_check(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s), "memset") < 0) { status = APCLOUD_E_CUDA; break; }
+        if (cuda_check(c, cudaMemcpyAsync(&st->rtol, &rtol, sizeof(double), cudaMemcpyHostToDevice, c->s), "rtol") < 0) {
+            status = APCLOUD_E_CUDA;
+            break;
+        }
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
+        APC_LAUNCH(c, K_VEC, nblk, RT, 0, k_norm2, b, n, st, partial);
+        for (;;) {
+            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<2>, sw, so, col, val, n, (const double *)u, wraw,
+                       (double *)nullptr, b, st, partial);
+            double tmp[2];
+            apcloud_status r = read_back(c, tmp, &st->bnorm, 2 * sizeof(double));
+            if (r < 0) { status = r; break; }
+            relres = tmp[0] > 0.0 ? tmp[1] / tmp[0] : 0.0;
+            if (tmp[0] == 0.0 || tmp[1] <= rtol * tmp[0]) { status = APCLOUD_OK; break; }
+            if (iters >= max_iter) break;
+            const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
+            for (int j = 0; j < jmax; ++j) {
+                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<1>, sw, so, col, val, n, (const double *)wraw, w,
+                           V + (int64_t)j * ldv, (const double *)nullptr, st, (double *)nullptr);
+                gs_dispatch(c, 0, nblk, V, ldv, n, j, w, wraw, st, partial);
+                gs_dispatch(c, 1, nblk, V, ldv, n, j, w, wraw, st, partial);
+                gs_dispatch(c, 2, nblk, V, ldv, n, j, w, wraw, st, partial);
+            }
+            cycle_end_dispatch(c, nblk, jmax, V, ldv, n, u, st);
+            int je = 0;
+            r = read_back(c, &je, &st->jend, sizeof(int));
+            if (r < 0) { status = r; break; }
+            iters += je;
+            ++cycles;
+            if (je == 0) break;
+        }
+        if (status < 0) break;
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_div, x, (const double *)u, d, n);
+        apcloud_status r = cuda_check(c, cudaStreamSynchronize(c->s), "solve_system_noalloc");
+        if (r < 0) status = r;
+    } while (0);
+    c->timer.mask = saved_mask;
+    if (info && status >= 0) {
+        info->iters = iters;
+        info->restarts = cycles;
+        info->relres = relres;
+    }
+    return status;
+}
