@@ -180,6 +180,7 @@ def run_ours(args, ws, rank, local):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     n_nodes = info["n_int"] + info["n_bnd"]
+    sz = ap.sizes()
 
     # end to end through the host-buffer entry point (pinned host memory)
     hx, hy, hz, hq = (torch.from_numpy(a).pin_memory() for a in (x, y, z, q))
@@ -226,6 +227,7 @@ def run_ours(args, ws, rank, local):
                    "n_nodes": n_nodes, "n_interior": info["n_int"], "solver": "GMRES(30)+Jacobi", "rtol": RTOL,
                    "gmres_iters_phi": info["iters_phi"], "gmres_iters_rho": info["iters_rho"],
                    "relres_phi": info["relres_phi"], "l2": "inputs 320 MB > L2, no flush",
+                   "nnz": sz["nnz"], "ell_fill": round(sz["nnz"] / max(1, sz["ell_entries"]), 4),
                    "parallelism": "independent beam per GPU" if ws > 1 else "single GPU"},
         "nodes_iters_per_s": round(ws * n_nodes * (iters_total / args.steps) / (ms_step * 1e-3), 1),
         "e2e": {"value": round(ws / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,

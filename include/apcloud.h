@@ -225,6 +225,12 @@ const char *apcloud_kernel_name(int kind);
  * provides the ALU roofline of the FP64 kernels.  Either pointer may be NULL. */
 apcloud_status apcloud_measure_fma_peak(double *h_fp64_tflops, double *h_fp32_tflops);
 
+/* Problem sizes after the last completed step (host array of 8 int64):
+ * particles, interior nodes, boundary nodes, matrix nonzeros (stencil
+ * entries + diagonals + boundary rows), stored sliced-ELL entries (with
+ * padding), sum of stencil sizes, ELL slices, octree depth. */
+apcloud_status apcloud_get_sizes(const apcloud_ctx *ctx, int64_t *h_sizes);
+
 /* Total kernel launches issued by this context since creation. */
 int64_t apcloud_launch_count(const apcloud_ctx *ctx);
 

@@ -42,10 +42,15 @@
  *   R6  density-system moments for the cell-indicator kernel with the Taylor
  *       1/l! factor: row j is rho~_j + (h_j^2/24) sum_i l_ji (rho~_i - rho~_j).
  *   R7  density-system boundary rows: rho~_b = rho_M of the owner leaf.
- *   R8  a stencil is widened to the next ring when it has fewer than m_target
- *       candidates or its weighted Vandermonde is rank deficient
- *       (min |R_ii| < 1e-6 max |R_ii|); at ring_max any full-rank stencil with
- *       at least 9 candidates is accepted, otherwise the build fails.
+ *   R8  a ring is searched only once it has m_target candidates (or it is the
+ *       last ring and has at least 9); a weighted Vandermonde with
+ *       min |R_ii| < 1e-6 max |R_ii| is rank deficient and not used.
+ *   R9  a stencil whose Laplacian diagonal (minus the sum of its weights) is
+ *       not negative is not used either: that row would have the wrong sign
+ *       and make the discrete Laplacian indefinite.  A node that gets an
+ *       unusable stencil retries with target sizes m_target + 2, + 4, ... (at
+ *       most 32) in the same ring, then widens the ring; after ring_max the
+ *       build fails.
  */
 #include <math.h>
 #include <stdint.h>
@@ -676,47 +681,55 @@ int or_stencils(or_ctx *c) {
                 cand[t - 1].oct = (int)((dd[0] >= 0) << 2 | (dd[1] >= 0) << 1 | (dd[2] >= 0));
             }
             qsort(cand, (size_t)nc, sizeof(cand_t), cmp_cand);
-            /* octant criterion (reading R4): two nearest per octant first, then
-             * the nearest remaining up to m_target, then every candidate tied
-             * with the last one filled (at most OR_MMAX in all) */
-            int taken[8] = {0}, m = 0;
-            int8_t pick[4096];
-            int8_t *pk = nc <= 4096 ? pick : (int8_t *)xcalloc((size_t)nc, 1);
-            for (int t = 0; t < nc; ++t) {
-                pk[t] = 0;
-                if (taken[cand[t].oct] < 2) { taken[cand[t].oct]++; pk[t] = 1; m++; }
+            /* target sizes m_target, m_target + 2, ... up to OR_MMAX (reading R9) */
+            int last_k = (k == c->ring_max);
+            for (int mt = M; mt <= OR_MMAX && !done; mt += 2) {
+                /* octant criterion (reading R4): two nearest per octant first, then
+                 * the nearest remaining up to mt, then every candidate tied with
+                 * the last one filled (at most OR_MMAX in all) */
+                int taken[8] = {0}, m = 0;
+                int8_t pick[4096];
+                int8_t *pk = nc <= 4096 ? pick : (int8_t *)xcalloc((size_t)nc, 1);
+                for (int t = 0; t < nc; ++t) {
+                    pk[t] = 0;
+                    if (taken[cand[t].oct] < 2) { taken[cand[t].oct]++; pk[t] = 1; m++; }
+                }
+                int64_t cut = -1;
+                for (int t = 0; t < nc && m < mt; ++t) if (!pk[t]) { pk[t] = 1; m++; cut = cand[t].d2; }
+                for (int t = 0; t < nc && m < OR_MMAX; ++t) if (!pk[t] && cand[t].d2 == cut) { pk[t] = 1; m++; }
+                int64_t dint[OR_MMAX * 3];
+                int32_t ids[OR_MMAX];
+                int s = 0;
+                for (int t = 0; t < nc && s < m; ++t) {
+                    if (!pk[t]) continue;
+                    ids[s] = cand[t].idx;
+                    for (int d = 0; d < 3; ++d)
+                        dint[3 * s + d] = (int64_t)c->icoord[3 * ids[s] + d] - (int64_t)c->icoord[3 * y0 + d];
+                    ++s;
+                }
+                if (pk != pick) free(pk);
+                double P[OR_NCOL * OR_MMAX], lp[OR_MMAX], ld, rr;
+                int bad = or_wls(m, dint, unit, c->weight_c, P, lp, &ld, &rr);
+                /* R8: rank deficient, R9: Laplacian diagonal not negative */
+                if (bad || !(ld < 0.0)) {
+                    if (m >= nc) break;          /* no more candidates in this ring */
+                    continue;
+                }
+                for (int i = 0; i < m; ++i) {
+                    c->nbr[(size_t)y0 * W + i] = ids[i];
+                    c->lap[(size_t)y0 * W + i] = lp[i];
+                    for (int r = 0; r < OR_NCOL; ++r) c->D[((size_t)y0 * OR_NCOL + r) * W + i] = P[r * m + i];
+                }
+                c->lapd[y0] = ld;
+                c->msz[y0] = m;
+                c->ring[y0] = k;
+                done = 1;
             }
-            int64_t cut = -1;
-            for (int t = 0; t < nc && m < M; ++t) if (!pk[t]) { pk[t] = 1; m++; cut = cand[t].d2; }
-            for (int t = 0; t < nc && m < OR_MMAX; ++t) if (!pk[t] && cand[t].d2 == cut) { pk[t] = 1; m++; }
-            int64_t dint[OR_MMAX * 3];
-            int32_t ids[OR_MMAX];
-            int s = 0;
-            for (int t = 0; t < nc && s < m; ++t) {
-                if (!pk[t]) continue;
-                ids[s] = cand[t].idx;
-                for (int d = 0; d < 3; ++d)
-                    dint[3 * s + d] = (int64_t)c->icoord[3 * ids[s] + d] - (int64_t)c->icoord[3 * y0 + d];
-                ++s;
-            }
-            if (pk != pick) free(pk);
-            double P[OR_NCOL * OR_MMAX], lp[OR_MMAX], ld, rr;
-            int bad = or_wls(m, dint, unit, c->weight_c, P, lp, &ld, &rr);
-            if (bad) {
-                if (k < c->ring_max) continue;
-                snprintf(c->err, sizeof c->err, "node %d: no full-rank stencil within ring %d", y0, c->ring_max);
+            if (!done && last_k) {
+                snprintf(c->err, sizeof c->err, "node %d: no usable stencil within ring %d", y0, c->ring_max);
                 status = OR_E_STENCIL;
                 break;
             }
-            for (int i = 0; i < m; ++i) {
-                c->nbr[(size_t)y0 * W + i] = ids[i];
-                c->lap[(size_t)y0 * W + i] = lp[i];
-                for (int r = 0; r < OR_NCOL; ++r) c->D[((size_t)y0 * OR_NCOL + r) * W + i] = P[r * m + i];
-            }
-            c->lapd[y0] = ld;
-            c->msz[y0] = m;
-            c->ring[y0] = k;
-            done = 1;
         }
         if (!done && status == OR_OK) {
             snprintf(c->err, sizeof c->err, "node %d: fewer than 9 candidates within ring %d", y0, c->ring_max);

@@ -83,6 +83,7 @@ def load():
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
             "apcloud_launch_count": (L, [P]),
+            "apcloud_get_sizes": (I, [P, P]),
             "apcloud_measure_fma_peak": (I, [C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
@@ -330,6 +331,12 @@ class APCloud:
                                                  fl.ctypes.data_as(C.c_void_p), 1 if reset else 0))
         return {name: (float(ms[k]), int(cnt[k]), float(by[k]), float(fl[k]))
                 for k, name in enumerate(kernel_names())}
+
+    def sizes(self):
+        h = np.zeros(8, dtype=np.int64)
+        self._check(self._lib.apcloud_get_sizes(self._ctx, h.ctypes.data_as(C.c_void_p)))
+        keys = ("particles", "n_interior", "n_boundary", "nnz", "ell_entries", "sum_m", "slices", "depth")
+        return dict(zip(keys, (int(v) for v in h)))
 
     def launch_count(self):
         return int(self._lib.apcloud_launch_count(self._ctx))

@@ -472,4 +472,17 @@ const char *apcloud_kernel_name(int kind) {
 
 int64_t apcloud_launch_count(const apcloud_ctx *c) { return c ? c->launches : 0; }
 
+apcloud_status apcloud_get_sizes(const apcloud_ctx *c, int64_t *h) {
+    if (!c || !h) return APCLOUD_E_INVALID;
+    h[0] = c->N;
+    h[1] = c->n_int;
+    h[2] = c->n_bnd;
+    h[3] = c->sum_m + c->n_int + c->n_bnd;
+    h[4] = c->ell_entries;
+    h[5] = c->sum_m;
+    h[6] = c->n_slices;
+    h[7] = c->L;
+    return APCLOUD_OK;
+}
+
 }  // extern "C"

@@ -173,62 +173,150 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
 }
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
-// PASS 0: h1 = V^T w
-// PASS 1: w -= V h1 ; h2 = V^T w
-// PASS 2: wraw = w - V h2 ; ||wraw||^2 ; Givens update (last block)
-template <int NJ, int PASS>
-__global__ void __launch_bounds__(RT) k_gs(const double *__restrict__ V, int64_t ldv, int n, int j,
-                                           double *__restrict__ w, double *__restrict__ wraw, GmresState *st,
-                                           double *__restrict__ partial) {
-    extern __shared__ double sm[];
+// GB300 executes FP64 at 1/58 of its FP32 rate and charges a warp-wide FP64
+// instruction in full even when lanes are predicated off, so every FP64
+// instruction here does useful work on 32 lanes:
+//   * dot products V_k^T w: one warp per basis vector over a tile of w staged
+//     in shared memory (lanes over rows, coalesced, no padding terms);
+//   * updates w -= V h: one thread per row with a runtime loop over k (four
+//     rows per thread for independent FMA chains).
+constexpr int GT = 256;                    // threads per block (8 warps)
+constexpr int GW = GT / 32;
+constexpr int TILE = 512;                  // rows staged per tile
+constexpr int KPW = MAX_RESTART / GW;      // basis vectors per warp (<= 8)
+
+__device__ __forceinline__ void tile_dots(const double *__restrict__ V, int64_t ldv, int base, int lim, int j1,
+                                          const double *ws, double (&acc)[KPW]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int kk = 0; kk < KPW; ++kk) {
+        const int k = wid + GW * kk;
+        if (k < j1) {   // uniform across the warp
+            const double *vk = V + (int64_t)k * ldv + base;
+            double a = acc[kk];
+#pragma unroll 4
+            for (int i = lane; i < lim; i += 32) a = fma(vk[i], ws[i], a);
+            acc[kk] = a;
+        }
+    }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.
+template <int PASS>
+__global__ void __launch_bounds__(GT) k_gs_dots(const double *__restrict__ V, int64_t ldv, int n, int j,
+                                                double *__restrict__ w, GmresState *st, double *__restrict__ partial) {
+    __shared__ double ws[TILE];
+    __shared__ double hs[MAX_RESTART];
+    __shared__ double red[MAX_RESTART];
+    __shared__ double sm[RT + RT / 32 + 8];
+    __shared__ double fs[64];
     if (st->done) return;
-    const int j1 = j + 1;
-    __shared__ double hs[NJ];
-    if (PASS >= 1 && threadIdx.x < j1) hs[threadIdx.x] = (PASS == 1) ? st->h1[threadIdx.x] : st->h2[threadIdx.x];
+    const int j1 = j + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (PASS == 1 && tid < j1) hs[tid] = st->h1[tid];
     __syncthreads();
-    double acc[NJ];
+    double acc[KPW];
 #pragma unroll
-    for (int k = 0; k < NJ; ++k) acc[k] = 0.0;
-    double sq = 0.0;
-    for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
-        double vk[NJ];
-#pragma unroll
-        for (int k = 0; k < NJ; ++k) vk[k] = (k < j1) ? V[(int64_t)k * ldv + i] : 0.0;
-        double wi = w[i];
+    for (int kk = 0; kk < KPW; ++kk) acc[kk] = 0.0;
+    for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
+        const int lim = (int)((n - base) < TILE ? (n - base) : TILE);
         if (PASS == 0) {
-#pragma unroll
-            for (int k = 0; k < NJ; ++k) if (k < j1) acc[k] = fma(vk[k], wi, acc[k]);
+            for (int t = tid; t < TILE; t += GT) ws[t] = (t < lim) ? w[base + t] : 0.0;
         } else {
+            double wi[TILE / GT];
 #pragma unroll
-            for (int k = 0; k < NJ; ++k) if (k < j1) wi = fma(-vk[k], hs[k], wi);
-            if (PASS == 1) {
-                w[i] = wi;
+            for (int r = 0; r < TILE / GT; ++r) {
+                int t = tid + GT * r;
+                wi[r] = (t < lim) ? w[base + t] : 0.0;
+            }
+            for (int k = 0; k < j1; ++k) {
+                const double hk = hs[k];
+                const double *vk = V + (int64_t)k * ldv + base;
 #pragma unroll
-                for (int k = 0; k < NJ; ++k) if (k < j1) acc[k] = fma(vk[k], wi, acc[k]);
-            } else {
-                wraw[i] = wi;
-                sq = fma(wi, wi, sq);
+                for (int r = 0; r < TILE / GT; ++r) {
+                    int t = tid + GT * r;
+                    if (t < lim) wi[r] = fma(-vk[t], hk, wi[r]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < TILE / GT; ++r) {
+                int t = tid + GT * r;
+                if (t < lim) w[base + t] = wi[r];
+                ws[t] = (t < lim) ? wi[r] : 0.0;
+            }
+        }
+        __syncthreads();
+        tile_dots(V, ldv, (int)base, lim, j1, ws, acc);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int kk = 0; kk < KPW; ++kk) {
+        const int k = wid + GW * kk;
+        if (k < j1) {
+            double v = warp_sum(acc[kk]);
+            if (lane == 0) red[k] = v;
+        }
+    }
+    __syncthreads();
+    if (tid < j1) partial[(int64_t)blockIdx.x * 64 + tid] = red[tid];
+    if (!last_block(&st->ticket)) return;
+    final_sums(partial, gridDim.x, j1, sm, fs);
+    if (tid < j1) {
+        if (PASS == 0) st->h1[tid] = fs[tid];
+        else st->h2[tid] = fs[tid];
+    }
+    if (tid == 0) st->ticket = 0;
+}
+
+// wraw = w - V h2 ; ||wraw||^2 ; Hessenberg column, Givens rotation and
+// convergence test in the last block (Saad, Algorithms 6.9 / 6.10)
+__global__ void __launch_bounds__(GT) k_gs_norm(const double *__restrict__ V, int64_t ldv, int n, int j,
+                                                const double *__restrict__ w, double *__restrict__ wraw,
+                                                GmresState *st, double *__restrict__ partial) {
+    __shared__ double hs[MAX_RESTART];
+    __shared__ double sm[RT + RT / 32 + 8];
+    __shared__ double fs[1];
+    if (st->done) return;
+    const int j1 = j + 1, tid = threadIdx.x;
+    if (tid < j1) hs[tid] = st->h2[tid];
+    __syncthreads();
+    double sq = 0.0;
+    constexpr int R = 4;
+    for (int64_t base = (int64_t)blockIdx.x * GT * R; base < n; base += (int64_t)gridDim.x * GT * R) {
+        double wi[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t i = base + tid + GT * r;
+            wi[r] = (i < n) ? w[i] : 0.0;
+        }
+        for (int k = 0; k < j1; ++k) {
+            const double hk = hs[k];
+            const double *vk = V + (int64_t)k * ldv + base + tid;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (base + tid + GT * r < n) wi[r] = fma(-vk[GT * r], hk, wi[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            int64_t i = base + tid + GT * r;
+            if (i < n) {
+                wraw[i] = wi[r];
+                sq = fma(wi[r], wi[r], sq);
             }
         }
     }
-    const int nred = (PASS == 2) ? 1 : j1;
+    double a1[1] = {sq};
     double tot = 0.0;
-    if (PASS == 2) {
-        double a1[1] = {sq};
-        block_reduce_many<1>(a1, 1, sm, &tot);
-    } else {
-        block_reduce_many<NJ>(acc, j1, sm, &tot);
-    }
-    if (threadIdx.x < nred) partial[(int64_t)blockIdx.x * 64 + threadIdx.x] = tot;
+    block_reduce_many<1>(a1, 1, sm, &tot);
+    if (tid == 0) partial[(int64_t)blockIdx.x * 64] = tot;
     if (!last_block(&st->ticket)) return;
-    __shared__ double fs[64];
-    final_sums(partial, gridDim.x, nred, sm, fs);
-    if (PASS == 0) {
-        if (threadIdx.x < j1) st->h1[threadIdx.x] = fs[threadIdx.x];
-    } else if (PASS == 1) {
-        if (threadIdx.x < j1) st->h2[threadIdx.x] = fs[threadIdx.x];
-    } else if (threadIdx.x == 0) {
-        // Hessenberg column j, previous rotations, new rotation (Saad Alg. 6.9 / 6.10)
+    final_sums(partial, gridDim.x, 1, sm, fs);
+    if (tid == 0) {
         const int M = MAX_RESTART;
         double hn = sqrt(fs[0]);
         for (int i = 0; i <= j; ++i) st->H[i * M + j] = st->h1[i] + st->h2[i];
@@ -249,15 +337,14 @@ __global__ void __launch_bounds__(RT) k_gs(const double *__restrict__ V, int64_t
         st->jend = j + 1;
         if (fabs(st->g[j + 1]) <= st->rtol * st->bnorm || hn == 0.0) st->done = 1;
         st->inv_norm = hn > 0.0 ? 1.0 / hn : 0.0;
+        st->ticket = 0;
     }
-    if (threadIdx.x == 0) st->ticket = 0;
 }
 
 // u += V y with H y = g solved (upper triangular, jend x jend) in every block
-template <int NJ>
-__global__ void __launch_bounds__(RT) k_cycle_end(const double *__restrict__ V, int64_t ldv, int n,
+__global__ void __launch_bounds__(GT) k_cycle_end(const double *__restrict__ V, int64_t ldv, int n,
                                                   double *__restrict__ u, const GmresState *__restrict__ st) {
-    __shared__ double ys[NJ];
+    __shared__ double ys[MAX_RESTART];
     const int je = st->jend;
     if (threadIdx.x == 0) {
         const int M = MAX_RESTART;
@@ -269,10 +356,9 @@ __global__ void __launch_bounds__(RT) k_cycle_end(const double *__restrict__ V, 
     }
     __syncthreads();
     if (je == 0) return;
-    for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) {
+    for (int64_t i = (int64_t)blockIdx.x * GT + threadIdx.x; i < n; i += (int64_t)gridDim.x * GT) {
         double s = 0.0;
-#pragma unroll
-        for (int k = 0; k < NJ; ++k) if (k < je) s = fma(V[(int64_t)k * ldv + i], ys[k], s);
+        for (int k = 0; k < je; ++k) s = fma(V[(int64_t)k * ldv + i], ys[k], s);
         u[i] += s;
     }
 }
@@ -306,38 +392,17 @@ __global__ void k_div(double *__restrict__ out, const double *__restrict__ a, co
     if (i < n) out[i] = a[i] / d[i];
 }
 
-template <int NJ>
-void launch_gs(apcloud_ctx *c, int pass, int nblk, const double *V, int64_t ldv, int n, int j, double *w,
-               double *wraw, GmresState *st, double *partial) {
-    size_t smem = (size_t)(RT * NJ + NJ * (RT / 32) + 8) * sizeof(double);
-    if (pass == 0) {
-        cudaFuncSetAttribute(k_gs<NJ, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        APC_LAUNCH(c, K_DOT, nblk, RT, smem, (k_gs<NJ, 0>), V, ldv, n, j, w, wraw, st, partial);
-    } else if (pass == 1) {
-        cudaFuncSetAttribute(k_gs<NJ, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        APC_LAUNCH(c, K_UPDDOT, nblk, RT, smem, (k_gs<NJ, 1>), V, ldv, n, j, w, wraw, st, partial);
-    } else {
-        size_t s1 = (size_t)(RT + RT / 32 + 8) * sizeof(double);
-        APC_LAUNCH(c, K_UPDNORM, nblk, RT, s1, (k_gs<NJ, 2>), V, ldv, n, j, w, wraw, st, partial);
-    }
-}
-
 void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const double *V, int64_t ldv, int n, int j, double *w,
                  double *wraw, GmresState *st, double *partial) {
-    int j1 = j + 1;
-    if (j1 <= 4) launch_gs<4>(c, pass, nblk, V, ldv, n, j, w, wraw, st, partial);
-    else if (j1 <= 8) launch_gs<8>(c, pass, nblk, V, ldv, n, j, w, wraw, st, partial);
-    else if (j1 <= 16) launch_gs<16>(c, pass, nblk, V, ldv, n, j, w, wraw, st, partial);
-    else if (j1 <= 32) launch_gs<32>(c, pass, nblk, V, ldv, n, j, w, wraw, st, partial);
-    else launch_gs<64>(c, pass, nblk, V, ldv, n, j, w, wraw, st, partial);
+    if (pass == 0) APC_LAUNCH(c, K_DOT, nblk, GT, 0, k_gs_dots<0>, V, ldv, n, j, w, st, partial);
+    else if (pass == 1) APC_LAUNCH(c, K_UPDDOT, nblk, GT, 0, k_gs_dots<1>, V, ldv, n, j, w, st, partial);
+    else APC_LAUNCH(c, K_UPDNORM, nblk, GT, 0, k_gs_norm, V, ldv, n, j, (const double *)w, wraw, st, partial);
 }
 
 void cycle_end_dispatch(apcloud_ctx *c, int nblk, int jmax, const double *V, int64_t ldv, int n, double *u,
                         GmresState *st) {
-    if (jmax <= 8) APC_LAUNCH(c, K_CYCLE, nblk, RT, 0, k_cycle_end<8>, V, ldv, n, u, st);
-    else if (jmax <= 16) APC_LAUNCH(c, K_CYCLE, nblk, RT, 0, k_cycle_end<16>, V, ldv, n, u, st);
-    else if (jmax <= 32) APC_LAUNCH(c, K_CYCLE, nblk, RT, 0, k_cycle_end<32>, V, ldv, n, u, st);
-    else APC_LAUNCH(c, K_CYCLE, nblk, RT, 0, k_cycle_end<64>, V, ldv, n, u, st);
+    (void)jmax;
+    APC_LAUNCH(c, K_CYCLE, nblk, GT, 0, k_cycle_end, V, ldv, n, u, st);
 }
 
 int reduction_blocks(apcloud_ctx *c, int n) {
@@ -346,7 +411,7 @@ int reduction_blocks(apcloud_ctx *c, int n) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 152;
-    int nb = div_up(n, RT * 4);
+    int nb = div_up(n, TILE);
     int cap = 2 * sms;
     if (nb > cap) nb = cap;
     if (nb < 1) nb = 1;

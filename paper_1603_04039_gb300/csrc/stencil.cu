@@ -205,10 +205,12 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
         }
         nA = warp_sum_int(nA);
         __syncwarp();
-        const int need = m_target - nA;
+        // target sizes m_target, m_target + 2, ... (a rank-deficient stencil or
+        // one whose Laplacian diagonal is not negative is not used)
+        for (int mt = m_target; mt <= MMAX && !done; mt += 2) {
+        const int need = mt - nA;
         int nfill = 0;
         if (lane == 0) W.cut_set = 0;
-        __syncwarp();
         for (int t = 1 + lane; t < nc; t += 32) { W.fill[t] = 0; W.tie[t] = 0; }
         __syncwarp();
         if (need > 0) {
@@ -241,16 +243,14 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
             ntie = warp_sum_int(ntie);
         }
         __syncwarp();
-        for (int t = 1 + lane; t < nc; t += 32) W.pick[t] = W.pick[t] | W.fill[t] | W.tie[t];
-        __syncwarp();
         m = nA + nfill + ntie;
         // final order by (d2, index)
         for (int t = 1 + lane; t < nc; t += 32) {
-            if (!W.pick[t]) continue;
+            if (!(W.pick[t] | W.fill[t] | W.tie[t])) continue;
             long long dt = W.d2[t];
             int it = W.cand[t], r = 0;
             for (int u = 1; u < nc; ++u)
-                if (W.pick[u] && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
+                if ((W.pick[u] | W.fill[u] | W.tie[u]) && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
             if (r < MMAX) { W.sel[r] = it; W.seld2[r] = dt; }
         }
         __syncwarp();
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
         const long long hint = warp_max_ll(amax);
         const long long r2max = W.seld2[m - 1];
         double wj = 0.0;
-        if (lane < MMAX) {
+        {
             double row[NCOL];
 #pragma unroll
             for (int e = 0; e < NCOL; ++e) row[e] = 0.0;
@@ -328,29 +328,29 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
             rmin_over_rmax = dmin / dmax;
             ok = dmin >= RANK_TOL * dmax;
         }
-        if (!ok) {
-            if (k < ring_max) continue;
-            break;
-        }
-        // column j of P: R1^-1 R2^-1 q2_j^T W_j, unscaled by h and h^2
-        const double h = (double)hint * unit;
-        const double h2 = h * h;
         double lapj = 0.0;
-        if (lane < m) {
+        if (ok) {
+            // column j of P: R1^-1 R2^-1 q2_j^T W_j, unscaled by h and h^2
+            const double h = (double)hint * unit;
+            const double h2 = h * h;
+            if (lane < m) {
 #pragma unroll
-            for (int e = 0; e < NCOL; ++e) q[e] = W.A[lane * ASTR + e];
-            row_solve_upper(W.R2, q);
-            col_solve_upper(W.R2, q);
-            col_solve_upper(W.R1, q);
+                for (int e = 0; e < NCOL; ++e) q[e] = W.A[lane * ASTR + e];
+                row_solve_upper(W.R2, q);
+                col_solve_upper(W.R2, q);
+                col_solve_upper(W.R1, q);
 #pragma unroll
-            for (int e = 0; e < NCOL; ++e) q[e] = (q[e] * wj) / (e < 3 ? h : h2);
-            lapj = q[3] + q[6] + q[8];
-        }
-        if (lane < MMAX) {
-#pragma unroll
-            for (int e = 0; e < NCOL; ++e) W.P[e * MMAX + lane] = (lane < m) ? q[e] : 0.0;
+                for (int e = 0; e < NCOL; ++e) q[e] = (q[e] * wj) / (e < 3 ? h : h2);
+                lapj = q[3] + q[6] + q[8];
+            }
         }
         const double lsum = warp_sum_d(lapj);
+        if (!ok || !(-lsum < 0.0)) {       // unusable: more neighbours, then a wider ring
+            if (m >= nc - 1) break;
+            continue;
+        }
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) W.P[e * MMAX + lane] = (lane < m) ? q[e] : 0.0;
         nbr_out[(int64_t)y0 * MMAX + lane] = (lane < m) ? W.sel[lane] : -1;
         lap_out[(int64_t)y0 * MMAX + lane] = lapj;
         if (lane == 0) {
@@ -365,6 +365,7 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
         for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = W.P[e * MMAX + lane];
         ring = k;
         done = true;
+        }   // target sizes
     }
     if (!done) {
         if (lane == 0) {

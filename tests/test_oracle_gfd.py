@@ -170,6 +170,17 @@ def test_poisson_exact_for_quadratic(small_problem):
     assert np.allclose(np.stack([ex, ey, ez], 1), grad, atol=1e-8 * np.abs(grad).max())
 
 
+def test_every_stencil_has_negative_diagonal():
+    """Reading R9: no stored stencil has a Laplacian diagonal >= 0 (a wrong-sign
+    row would make the discrete Laplacian indefinite)."""
+    x, y, z, q = inputs.beam_with_halo(200000, 3)
+    o = oracle.Oracle(max_depth=7, c_refine=0.2)
+    o.build(x, y, z)
+    st = o.stencils()
+    assert np.all(st["lapd"] < 0)
+    assert np.all(st["m"] >= 20) and np.all(st["m"] <= 32)
+
+
 def test_charge_conservation():
     """Leaves partition the domain, so the deposit conserves charge (Sec. 2, N q = 1)."""
     x, y, z, q = inputs.beam_with_halo(30000, 3)
