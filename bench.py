@@ -121,7 +121,7 @@ def run_ours(args, ws, rank, local):
     seed = 1 + rank
     x, y, z, q = inputs.beam_with_halo(npart, seed)
     tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
-    ap = APCloud(max_depth=depth, c_refine=c, restart=30, device=dev)
+    ap = APCloud(max_depth=depth, c_refine=c, restart=30, precision=args.precision, device=dev)
     out = tuple(torch.empty(npart, dtype=torch.float64, device=dev) for _ in range(4))
     stream = ap.stream
     info = {}
@@ -185,7 +185,7 @@ def run_ours(args, ws, rank, local):
     # end to end through the host-buffer entry point (pinned host memory)
     hx, hy, hz, hq = (torch.from_numpy(a).pin_memory() for a in (x, y, z, q))
     hout = tuple(torch.empty(npart, dtype=torch.float64).pin_memory() for _ in range(4))
-    ap_e2e = APCloud(max_depth=depth, c_refine=c, restart=30, device=dev)
+    ap_e2e = APCloud(max_depth=depth, c_refine=c, restart=30, precision=args.precision, device=dev)
     ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout)   # warm-up
     barrier()
     e2e_steps = max(1, min(args.steps, 3))
@@ -199,32 +199,56 @@ def run_ours(args, ws, rank, local):
         e2e_s = float(t.item())
     ap_e2e.close()
 
+    # field error of this form against the FP64 form on the same particles
+    rel_l2 = 0.0
+    if args.precision != "fp64":
+        ap64 = APCloud(max_depth=depth, c_refine=c, restart=30, precision="fp64", device=dev)
+        ref = tuple(torch.empty(npart, dtype=torch.float64, device=dev) for _ in range(4))
+        ap64.build_octree(tx, ty, tz)
+        ap64.stencils()
+        ap64.deposit(q=tq, rtol=1e-12, max_iter=MAX_ITER)
+        ap64.solve(rtol=1e-12, max_iter=MAX_ITER)
+        ap64.gather_field(ref)
+        errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(out, ref)]
+        rel_l2 = max(errs)
+        ap64.close()
     # roofline of the dominant kernel, measured live in the timed region
     peaks = _measured_peaks()
     ms_k, nl_k, by_k, fl_k = dom
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     gbs = by_k / (ms_k * 1e-3) / 1e9 if ms_k > 0 else 0.0
     tfs = fl_k / (ms_k * 1e-3) / 1e12 if ms_k > 0 else 0.0
-    # FP64 work per byte decides the bound: above FP64 peak / HBM peak the ALU limits
-    if fl_k > 0 and fl_k / max(by_k, 1.0) > fp64_peak * 1e12 / (hbm * 1e9):
-        roof = {"bound": "alu", "achieved": round(tfs, 4), "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                "frac": round(tfs / fp64_peak, 4)}
+    # the kernel's arithmetic type sets its ALU peak: in the mixed form the Krylov
+    # iterations and the stencil factorisations run in FP32, everything else FP64
+    fp32_kinds = {"spmv", "gmres_dots", "gmres_update_dots", "gmres_update_norm", "gmres_cycle_end",
+                  "ring_select_wls"}
+    alu_peak = fp32_peak if (args.precision == "mixed" and dominant in fp32_kinds) else fp64_peak
+    alu_name = "FP32" if alu_peak == fp32_peak else "FP64"
+    # work per byte decides the bound: above ALU peak / HBM peak the ALU limits
+    if fl_k > 0 and fl_k / max(by_k, 1.0) > alu_peak * 1e12 / (hbm * 1e9):
+        roof = {"bound": "alu", "achieved": round(tfs, 4), "peak": round(alu_peak, 4), "unit": "TFLOP/s",
+                "frac": round(tfs / alu_peak, 4), "alu": alu_name}
     else:
-        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4)}
+        roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                "alu": alu_name}
     roof.update({"kernel": dominant, "traffic": None, "launches": nl_k,
                  "algorithmic_bytes_per_launch": by_k / max(nl_k, 1),
                  "algorithmic_flops_per_launch": fl_k / max(nl_k, 1),
                  "share_of_step": round(ms_k / ms_total, 4),
-                 "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64 FMA chains on all SMs "
+                 "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64/FP32 FMA chains on all SMs "
                                 "(apcloud_measure_fma_peak) in this run",
                  "fp64_peak_tflops": round(fp64_peak, 4), "fp32_peak_tflops": round(fp32_peak, 3)})
     solves = ws * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(solves, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic", "rel_l2_vs_fp64": rel_l2,
         "config": {"workload": args.workload, "particles": npart, "max_depth": depth, "c_refine": c,
-                   "n_nodes": n_nodes, "n_interior": info["n_int"], "solver": "GMRES(30)+Jacobi", "rtol": RTOL,
+                   "n_nodes": n_nodes, "n_interior": info["n_int"], "precision": args.precision,
+                   "solver": "GMRES(30)+Jacobi" if args.precision == "fp64" else
+                   "FP64 iterative refinement around FP32 GMRES(30)+Jacobi", "rtol": RTOL,
+                   "fp64_stencils": sz["fp64_stencils"],
                    "gmres_iters_phi": info["iters_phi"], "gmres_iters_rho": info["iters_rho"],
                    "relres_phi": info["relres_phi"], "l2": "inputs 320 MB > L2, no flush",
                    "nnz": sz["nnz"], "ell_fill": round(sz["nnz"] / max(1, sz["ell_entries"]), 4),
@@ -296,6 +320,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="beam_halo_1e7_depth10", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -65,7 +65,10 @@ typedef struct {
     double weight_c;     /* constant c of the normalized Gaussian weight, 4 (Section 3.1) */
     double poisson_c;    /* c in Lap phi = c rho (Eq. Poisson), 1 in Section 5 */
     int restart;         /* GMRES restart length, 1..64 */
-    int precision;       /* 0 = FP64 throughout (the only value accepted) */
+    int precision;       /* 0 = FP64 throughout; 1 = mixed: FP32 WLS stencils with FP64
+                            refactorisation of blocks whose condition estimate exceeds 1e3,
+                            FP32 GMRES iterations inside an FP64 iterative-refinement loop
+                            (FP64 residual and solution), FP64 charge sums and gather */
 } apcloud_params;
 
 /* Optional device allocator; NULL selects cudaMallocAsync/cudaFreeAsync on
@@ -225,10 +228,11 @@ const char *apcloud_kernel_name(int kind);
  * provides the ALU roofline of the FP64 kernels.  Either pointer may be NULL. */
 apcloud_status apcloud_measure_fma_peak(double *h_fp64_tflops, double *h_fp32_tflops);
 
-/* Problem sizes after the last completed step (host array of 8 int64):
+/* Problem sizes after the last completed step (host array of 9 int64):
  * particles, interior nodes, boundary nodes, matrix nonzeros (stencil
  * entries + diagonals + boundary rows), stored sliced-ELL entries (with
- * padding), sum of stencil sizes, ELL slices, octree depth. */
+ * padding), sum of stencil sizes, ELL slices, octree depth, and (mixed form)
+ * stencils refactored in FP64. */
 apcloud_status apcloud_get_sizes(const apcloud_ctx *ctx, int64_t *h_sizes);
 
 /* Total kernel launches issued by this context since creation. */

@@ -133,7 +133,7 @@ class APCloud:
     """One AP-Cloud problem on one GPU (see include/apcloud.h for each call)."""
 
     def __init__(self, lo=-1.0, hi=1.0, max_depth=6, c_refine=1.0, m_target=20, ring_max=5, weight_c=4.0,
-                 poisson_c=1.0, restart=30, device="cuda:0", stream=None):
+                 poisson_c=1.0, restart=30, precision="fp64", device="cuda:0", stream=None):
         lib = load()
         self._lib = lib
         self.device = torch.device(device)
@@ -144,6 +144,7 @@ class APCloud:
             p.hi[d] = float(hi)
         p.max_depth, p.c_refine, p.m_target, p.ring_max = int(max_depth), float(c_refine), int(m_target), int(ring_max)
         p.weight_c, p.poisson_c, p.restart = float(weight_c), float(poisson_c), int(restart)
+        p.precision = {"fp64": 0, "mixed": 1}[precision]
         self.params = p
         with torch.cuda.device(self.device):
             s = stream if stream is not None else torch.cuda.current_stream(self.device)
@@ -333,9 +334,10 @@ class APCloud:
                 for k, name in enumerate(kernel_names())}
 
     def sizes(self):
-        h = np.zeros(8, dtype=np.int64)
+        h = np.zeros(9, dtype=np.int64)
         self._check(self._lib.apcloud_get_sizes(self._ctx, h.ctypes.data_as(C.c_void_p)))
-        keys = ("particles", "n_interior", "n_boundary", "nnz", "ell_entries", "sum_m", "slices", "depth")
+        keys = ("particles", "n_interior", "n_boundary", "nnz", "ell_entries", "sum_m", "slices", "depth",
+                "fp64_stencils")
         return dict(zip(keys, (int(v) for v in h)))
 
     def launch_count(self):

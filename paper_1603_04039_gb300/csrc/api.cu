@@ -139,7 +139,10 @@ static apcloud_status validate(const apcloud_params *p, char *msg, size_t len) {
     if (!(p->weight_c > 0) || !std::isfinite(p->weight_c)) { snprintf(msg, len, "weight_c must be > 0"); return APCLOUD_E_INVALID; }
     if (!std::isfinite(p->poisson_c)) { snprintf(msg, len, "poisson_c must be finite"); return APCLOUD_E_INVALID; }
     if (p->restart < 1 || p->restart > MAX_RESTART) { snprintf(msg, len, "restart must be 1..64"); return APCLOUD_E_INVALID; }
-    if (p->precision != 0) { snprintf(msg, len, "precision must be 0 (FP64)"); return APCLOUD_E_INVALID; }
+    if (p->precision != 0 && p->precision != 1) {
+        snprintf(msg, len, "precision must be 0 (FP64) or 1 (mixed)");
+        return APCLOUD_E_INVALID;
+    }
     return APCLOUD_OK;
 }
 
@@ -201,7 +204,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->ring, &c->lap, &c->lapd, &c->D, &c->rcond, &c->slice_w, &c->slice_off, &c->ell_col,
                     &c->ell_A, &c->ell_B, &c->dA, &c->dB, &c->V, &c->w0, &c->w1, &c->u, &c->b, &c->partial,
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->tmp, &c->derr, &c->dsmall,
-                    &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez};
+                    &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
+                    &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2};
     for (DBuf *b : bufs) free_buf(c, *b);
     cudaStreamSynchronize(c->s);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);
@@ -482,6 +486,7 @@ apcloud_status apcloud_get_sizes(const apcloud_ctx *c, int64_t *h) {
     h[5] = c->sum_m;
     h[6] = c->n_slices;
     h[7] = c->L;
+    h[8] = c->n_fp64_wls;
     return APCLOUD_OK;
 }
 

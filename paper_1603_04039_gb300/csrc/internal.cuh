@@ -85,6 +85,7 @@ struct apcloud_ctx {
     int n_slices = 0;
     int64_t ell_entries = 0;
     int64_t sum_m = 0;  // total stencil neighbours over interior nodes
+    int64_t n_fp64_wls = 0;  // mixed form: stencils refactored in FP64
 
     // sorted particle keys and permutation (result in key[kbuf], val[kbuf])
     apc::DBuf key[2], val[2];
@@ -97,8 +98,10 @@ struct apcloud_ctx {
     apc::DBuf nbr, msz, ring, lap, lapd, D, rcond;
     // matrices (sliced ELL, 32-row slices, column-major inside a slice)
     apc::DBuf slice_w, slice_off, ell_col, ell_A, ell_B, dA, dB;
+    apc::DBuf ell_A32, ell_B32;  // FP32 copies for the inner iterations of the mixed form
     // solver
     apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
+    apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
     // device staging for apcloud_field_host
     apc::DBuf hx, hy, hz, hq, hphi, hex, hey, hez;
     // error word, small host-visible values

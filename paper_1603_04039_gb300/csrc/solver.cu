@@ -123,21 +123,24 @@ __global__ void k_bcopy(const int32_t *__restrict__ owner, int n_int, int n_bnd,
 }
 
 // ---------------------------------------------------------------- SpMV
+// T is the value and vector type (double for the FP64 form and the outer
+// residual of the mixed form, float for the inner iterations of the mixed
+// form); per-thread sums run in T, every block or grid reduction in FP64.
 // mode 0: y = Ahat x
-// mode 1: y = Ahat x * s, vout[r] = x[r] * s, s = *sptr (Arnoldi step)
+// mode 1: y = Ahat x * s, vout[r] = x[r] * s, s = st->inv_norm (Arnoldi step)
 // mode 2: y = b - Ahat x, ||y||^2 reduced into st (cycle start)
-template <int MODE>
+template <int MODE, class T>
 __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
-                                             const int32_t *__restrict__ col, const double *__restrict__ val,
-                                             int n, const double *__restrict__ x, double *__restrict__ y,
-                                             double *__restrict__ vout, const double *__restrict__ b,
-                                             GmresState *st, double *__restrict__ partial) {
+                                             const int32_t *__restrict__ col, const T *__restrict__ val, int n,
+                                             const T *__restrict__ x, T *__restrict__ y, T *__restrict__ vout,
+                                             const T *__restrict__ b, GmresState *st, double *__restrict__ partial) {
     __shared__ double sm[RT + RT / 32 + 8];
     if (MODE == 1 && st->done) return;
     const int r = blockIdx.x * RT + threadIdx.x;
-    double s = 1.0;
-    if (MODE == 1) s = st->inv_norm;
-    double acc = 0.0, yv = 0.0;
+    T s = (T)1;
+    if (MODE == 1) s = (T)st->inv_norm;
+    T acc = (T)0;
+    double yv = 0.0;
     if (r < n) {
         const int sl = r >> 5, lane = r & 31;
         const int w = (int)sw[sl];
@@ -146,9 +149,9 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
             const int64_t e = base + (int64_t)k * 32;
             acc = fma(val[e], x[col[e]], acc);
         }
-        if (MODE == 0) { yv = acc; y[r] = yv; }
+        if (MODE == 0) y[r] = acc;
         if (MODE == 1) { y[r] = acc * s; vout[r] = x[r] * s; }
-        if (MODE == 2) { yv = b[r] - acc; y[r] = yv; }
+        if (MODE == 2) { T t = b[r] - acc; y[r] = t; yv = (double)t; }
     }
     if (MODE == 2) {
         double a[1] = {yv * yv};
@@ -173,29 +176,67 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
 }
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
-// GB300 executes FP64 at 1/58 of its FP32 rate and charges a warp-wide FP64
-// instruction in full even when lanes are predicated off, so every FP64
-// instruction here does useful work on 32 lanes:
+// Every arithmetic instruction does useful work on 32 lanes (GB300 runs FP64
+// at 1/58 of FP32 and charges predicated-off lanes in full), and loads are
+// 16-byte vectors so enough bytes are in flight to stream HBM in FP32:
 //   * dot products V_k^T w: one warp per basis vector over a tile of w staged
-//     in shared memory (lanes over rows, coalesced, no padding terms);
-//   * updates w -= V h: one thread per row with a runtime loop over k (four
-//     rows per thread for independent FMA chains).
+//     in shared memory (lanes over 16-byte chunks of rows, coalesced);
+//   * updates w -= V h: one thread per 16-byte chunk of rows, runtime loop
+//     over k unrolled for independent loads.
+// Work vectors are ldv long (a multiple of 32) with zero tails past n, so
+// whole chunks are always in bounds and the tails add nothing.
 constexpr int GT = 256;                    // threads per block (8 warps)
 constexpr int GW = GT / 32;
-constexpr int TILE = 512;                  // rows staged per tile
+constexpr int TILE = 1024;                 // rows staged per tile
 constexpr int KPW = MAX_RESTART / GW;      // basis vectors per warp (<= 8)
 
-__device__ __forceinline__ void tile_dots(const double *__restrict__ V, int64_t ldv, int base, int lim, int j1,
-                                          const double *ws, double (&acc)[KPW]) {
+template <class T> struct Vec;
+template <> struct Vec<double> { typedef double2 type; static constexpr int n = 2; };
+template <> struct Vec<float> { typedef float4 type; static constexpr int n = 4; };
+
+__device__ __forceinline__ double dotv(double2 a, double2 b, double acc) { return fma(a.y, b.y, fma(a.x, b.x, acc)); }
+__device__ __forceinline__ float dotv(float4 a, float4 b, float acc) {
+    return fma(a.w, b.w, fma(a.z, b.z, fma(a.y, b.y, fma(a.x, b.x, acc))));
+}
+__device__ __forceinline__ double2 axpyv(double2 w, double2 v, double h) {
+    return make_double2(fma(-v.x, h, w.x), fma(-v.y, h, w.y));
+}
+__device__ __forceinline__ float4 axpyv(float4 w, float4 v, float h) {
+    return make_float4(fma(-v.x, h, w.x), fma(-v.y, h, w.y), fma(-v.z, h, w.z), fma(-v.w, h, w.w));
+}
+__device__ __forceinline__ double sumsq(double2 a, double acc) { return fma(a.y, a.y, fma(a.x, a.x, acc)); }
+__device__ __forceinline__ float sumsq(float4 a, float acc) {
+    return fma(a.w, a.w, fma(a.z, a.z, fma(a.y, a.y, fma(a.x, a.x, acc))));
+}
+__device__ __forceinline__ double2 fmav(double2 v, double y, double2 s) {
+    return make_double2(fma(v.x, y, s.x), fma(v.y, y, s.y));
+}
+__device__ __forceinline__ float4 fmav(float4 v, float y, float4 s) {
+    return make_float4(fma(v.x, y, s.x), fma(v.y, y, s.y), fma(v.z, y, s.z), fma(v.w, y, s.w));
+}
+__device__ __forceinline__ double2 addv(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float4 addv(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+template <class VT> __device__ __forceinline__ VT zerov();
+template <> __device__ __forceinline__ double2 zerov<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float4 zerov<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+
+template <class T>
+__device__ __forceinline__ void tile_dots(const T *__restrict__ V, int64_t ldv, int64_t base, int lim, int j1,
+                                          const T *ws, T (&acc)[KPW]) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const VT *wv = reinterpret_cast<const VT *>(ws);
 #pragma unroll
     for (int kk = 0; kk < KPW; ++kk) {
         const int k = wid + GW * kk;
         if (k < j1) {   // uniform across the warp
-            const double *vk = V + (int64_t)k * ldv + base;
-            double a = acc[kk];
+            const VT *vk = reinterpret_cast<const VT *>(V + (int64_t)k * ldv + base);
+            T a = acc[kk];
 #pragma unroll 4
-            for (int i = lane; i < lim; i += 32) a = fma(vk[i], ws[i], a);
+            for (int c = lane; c < lim / VN; c += 32) a = dotv(__ldg(vk + c), wv[c], a);
             acc[kk] = a;
         }
     }
@@ -207,58 +248,50 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.
-template <int PASS>
-__global__ void __launch_bounds__(GT) k_gs_dots(const double *__restrict__ V, int64_t ldv, int n, int j,
-                                                double *__restrict__ w, GmresState *st, double *__restrict__ partial) {
-    __shared__ double ws[TILE];
-    __shared__ double hs[MAX_RESTART];
+// PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.   (nrow = ldv)
+template <int PASS, class T>
+__global__ void __launch_bounds__(GT) k_gs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                T *__restrict__ w, GmresState *st, double *__restrict__ partial) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ __align__(16) T ws[TILE];
+    __shared__ T hs[MAX_RESTART];
     __shared__ double red[MAX_RESTART];
     __shared__ double sm[RT + RT / 32 + 8];
     __shared__ double fs[64];
     if (st->done) return;
     const int j1 = j + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (PASS == 1 && tid < j1) hs[tid] = st->h1[tid];
+    if (PASS == 1 && tid < j1) hs[tid] = (T)st->h1[tid];
     __syncthreads();
-    double acc[KPW];
+    T acc[KPW];
 #pragma unroll
-    for (int kk = 0; kk < KPW; ++kk) acc[kk] = 0.0;
-    for (int64_t base = (int64_t)blockIdx.x * TILE; base < n; base += (int64_t)gridDim.x * TILE) {
-        const int lim = (int)((n - base) < TILE ? (n - base) : TILE);
+    for (int kk = 0; kk < KPW; ++kk) acc[kk] = (T)0;
+    VT *wsv = reinterpret_cast<VT *>(ws);
+    for (int64_t base = (int64_t)blockIdx.x * TILE; base < nrow; base += (int64_t)gridDim.x * TILE) {
+        const int lim = (int)((nrow - base) < TILE ? (nrow - base) : TILE);
+        VT *wg = reinterpret_cast<VT *>(w + base);
         if (PASS == 0) {
-            for (int t = tid; t < TILE; t += GT) ws[t] = (t < lim) ? w[base + t] : 0.0;
+            for (int cix = tid; cix < lim / VN; cix += GT) wsv[cix] = wg[cix];
         } else {
-            double wi[TILE / GT];
-#pragma unroll
-            for (int r = 0; r < TILE / GT; ++r) {
-                int t = tid + GT * r;
-                wi[r] = (t < lim) ? w[base + t] : 0.0;
-            }
-            for (int k = 0; k < j1; ++k) {
-                const double hk = hs[k];
-                const double *vk = V + (int64_t)k * ldv + base;
-#pragma unroll
-                for (int r = 0; r < TILE / GT; ++r) {
-                    int t = tid + GT * r;
-                    if (t < lim) wi[r] = fma(-vk[t], hk, wi[r]);
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < TILE / GT; ++r) {
-                int t = tid + GT * r;
-                if (t < lim) w[base + t] = wi[r];
-                ws[t] = (t < lim) ? wi[r] : 0.0;
+            for (int cix = tid; cix < lim / VN; cix += GT) {
+                VT wi = wg[cix];
+                const T *vb = V + base;
+#pragma unroll 4
+                for (int k = 0; k < j1; ++k)
+                    wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(vb + (int64_t)k * ldv) + cix), hs[k]);
+                wg[cix] = wi;
+                wsv[cix] = wi;
             }
         }
         __syncthreads();
-        tile_dots(V, ldv, (int)base, lim, j1, ws, acc);
+        tile_dots<T>(V, ldv, base, lim, j1, ws, acc);
         __syncthreads();
     }
 #pragma unroll
     for (int kk = 0; kk < KPW; ++kk) {
         const int k = wid + GW * kk;
         if (k < j1) {
-            double v = warp_sum(acc[kk]);
+            double v = warp_sum((double)acc[kk]);
             if (lane == 0) red[k] = v;
         }
     }
@@ -275,42 +308,32 @@ __global__ void __launch_bounds__(GT) k_gs_dots(const double *__restrict__ V, in
 
 // wraw = w - V h2 ; ||wraw||^2 ; Hessenberg column, Givens rotation and
 // convergence test in the last block (Saad, Algorithms 6.9 / 6.10)
-__global__ void __launch_bounds__(GT) k_gs_norm(const double *__restrict__ V, int64_t ldv, int n, int j,
-                                                const double *__restrict__ w, double *__restrict__ wraw,
-                                                GmresState *st, double *__restrict__ partial) {
-    __shared__ double hs[MAX_RESTART];
+template <class T>
+__global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                const T *__restrict__ w, T *__restrict__ wraw, GmresState *st,
+                                                double *__restrict__ partial) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ T hs[MAX_RESTART];
     __shared__ double sm[RT + RT / 32 + 8];
     __shared__ double fs[1];
     if (st->done) return;
     const int j1 = j + 1, tid = threadIdx.x;
-    if (tid < j1) hs[tid] = st->h2[tid];
+    if (tid < j1) hs[tid] = (T)st->h2[tid];
     __syncthreads();
-    double sq = 0.0;
-    constexpr int R = 4;
-    for (int64_t base = (int64_t)blockIdx.x * GT * R; base < n; base += (int64_t)gridDim.x * GT * R) {
-        double wi[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            int64_t i = base + tid + GT * r;
-            wi[r] = (i < n) ? w[i] : 0.0;
-        }
-        for (int k = 0; k < j1; ++k) {
-            const double hk = hs[k];
-            const double *vk = V + (int64_t)k * ldv + base + tid;
-#pragma unroll
-            for (int r = 0; r < R; ++r)
-                if (base + tid + GT * r < n) wi[r] = fma(-vk[GT * r], hk, wi[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            int64_t i = base + tid + GT * r;
-            if (i < n) {
-                wraw[i] = wi[r];
-                sq = fma(wi[r], wi[r], sq);
-            }
-        }
+    T sq = (T)0;
+    const int nch = nrow / VN;
+    const VT *wv = reinterpret_cast<const VT *>(w);
+    VT *ov = reinterpret_cast<VT *>(wraw);
+    for (int cix = blockIdx.x * GT + tid; cix < nch; cix += gridDim.x * GT) {
+        VT wi = wv[cix];
+#pragma unroll 4
+        for (int k = 0; k < j1; ++k)
+            wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix), hs[k]);
+        ov[cix] = wi;
+        sq = sumsq(wi, sq);
     }
-    double a1[1] = {sq};
+    double a1[1] = {(double)sq};
     double tot = 0.0;
     block_reduce_many<1>(a1, 1, sm, &tot);
     if (tid == 0) partial[(int64_t)blockIdx.x * 64] = tot;
@@ -342,32 +365,40 @@ __global__ void __launch_bounds__(GT) k_gs_norm(const double *__restrict__ V, in
 }
 
 // u += V y with H y = g solved (upper triangular, jend x jend) in every block
-__global__ void __launch_bounds__(GT) k_cycle_end(const double *__restrict__ V, int64_t ldv, int n,
-                                                  double *__restrict__ u, const GmresState *__restrict__ st) {
-    __shared__ double ys[MAX_RESTART];
+template <class T>
+__global__ void __launch_bounds__(GT) k_cycle_end(const T *__restrict__ V, int64_t ldv, int nrow, T *__restrict__ u,
+                                                  const GmresState *__restrict__ st) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ T ys[MAX_RESTART];
     const int je = st->jend;
     if (threadIdx.x == 0) {
         const int M = MAX_RESTART;
+        double yd[MAX_RESTART];
         for (int k = je - 1; k >= 0; --k) {
             double s = st->g[k];
-            for (int l = k + 1; l < je; ++l) s -= st->H[k * M + l] * ys[l];
-            ys[k] = s / st->H[k * M + k];
+            for (int l = k + 1; l < je; ++l) s -= st->H[k * M + l] * yd[l];
+            yd[k] = s / st->H[k * M + k];
+            ys[k] = (T)yd[k];
         }
     }
     __syncthreads();
     if (je == 0) return;
-    for (int64_t i = (int64_t)blockIdx.x * GT + threadIdx.x; i < n; i += (int64_t)gridDim.x * GT) {
-        double s = 0.0;
-        for (int k = 0; k < je; ++k) s = fma(V[(int64_t)k * ldv + i], ys[k], s);
-        u[i] += s;
+    VT *uv = reinterpret_cast<VT *>(u);
+    for (int cix = blockIdx.x * GT + threadIdx.x; cix < nrow / VN; cix += gridDim.x * GT) {
+        VT s = zerov<VT>();
+#pragma unroll 4
+        for (int k = 0; k < je; ++k) s = fmav(__ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix), ys[k], s);
+        uv[cix] = addv(uv[cix], s);
     }
 }
 
-__global__ void __launch_bounds__(RT) k_norm2(const double *__restrict__ x, int n, GmresState *st,
+template <class T>
+__global__ void __launch_bounds__(RT) k_norm2(const T *__restrict__ x, int n, GmresState *st,
                                               double *__restrict__ partial) {
     __shared__ double sm[RT + RT / 32 + 8];
     double s = 0.0;
-    for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) s = fma(x[i], x[i], s);
+    for (int i = blockIdx.x * RT + threadIdx.x; i < n; i += gridDim.x * RT) s = fma((double)x[i], (double)x[i], s);
     double a[1] = {s};
     double tot = 0.0;
     block_reduce_many<1>(a, 1, sm, &tot);
@@ -392,17 +423,24 @@ __global__ void k_div(double *__restrict__ out, const double *__restrict__ a, co
     if (i < n) out[i] = a[i] / d[i];
 }
 
-void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const double *V, int64_t ldv, int n, int j, double *w,
-                 double *wraw, GmresState *st, double *partial) {
-    if (pass == 0) APC_LAUNCH(c, K_DOT, nblk, GT, 0, k_gs_dots<0>, V, ldv, n, j, w, st, partial);
-    else if (pass == 1) APC_LAUNCH(c, K_UPDDOT, nblk, GT, 0, k_gs_dots<1>, V, ldv, n, j, w, st, partial);
-    else APC_LAUNCH(c, K_UPDNORM, nblk, GT, 0, k_gs_norm, V, ldv, n, j, (const double *)w, wraw, st, partial);
+__global__ void k_to_f32(float *__restrict__ out, const double *__restrict__ a, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)a[i];
 }
 
-void cycle_end_dispatch(apcloud_ctx *c, int nblk, int jmax, const double *V, int64_t ldv, int n, double *u,
-                        GmresState *st) {
-    (void)jmax;
-    APC_LAUNCH(c, K_CYCLE, nblk, GT, 0, k_cycle_end, V, ldv, n, u, st);
+// u += e (FP32 correction into the FP64 iterate), e cleared for the next refinement
+__global__ void k_add_f32(double *__restrict__ u, float *__restrict__ e, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { u[i] += (double)e[i]; e[i] = 0.f; }
+}
+
+template <class T>
+void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, int j, T *w, T *wraw, GmresState *st,
+                 double *partial) {
+    const int nrow = (int)ldv;
+    if (pass == 0) APC_LAUNCH(c, K_DOT, nblk, GT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial);
+    else if (pass == 1) APC_LAUNCH(c, K_UPDDOT, nblk, GT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial);
+    else APC_LAUNCH(c, K_UPDNORM, nblk, GT, 0, k_gs_norm<T>, V, ldv, nrow, j, (const T *)w, wraw, st, partial);
 }
 
 int reduction_blocks(apcloud_ctx *c, int n) {
@@ -416,6 +454,77 @@ int reduction_blocks(apcloud_ctx *c, int n) {
     if (nb > cap) nb = cap;
     if (nb < 1) nb = 1;
     return nb;
+}
+
+// Krylov scratch of one GMRES of element type T
+template <class T>
+struct Krylov {
+    T *V;
+    int64_t ldv;
+    T *w, *wraw;
+    GmresState *st;
+    double *partial;
+    int nblk;
+};
+
+// Restarted GMRES(restart) on Ahat u = b, u in/out; no allocation.  Returns
+// OK when ||b - Ahat u|| <= rtol ||b||, W_NOT_CONVERGED at max_iter.
+template <class T>
+apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double rtol, int max_iter,
+                          const Krylov<T> &K, int *iters_out, int *cycles_out, double *relres_out) {
+    const int n = c->n_tot;
+    const int m = c->P.restart;
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    GmresState *st = K.st;
+    APC_CUDA(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s));
+    // basis and work vectors are processed in whole 16-byte chunks up to ldv: zero tails
+    APC_CUDA(c, cudaMemsetAsync(K.V, 0, sizeof(T) * (size_t)(m + 1) * K.ldv, c->s));
+    APC_CUDA(c, cudaMemsetAsync(K.w, 0, sizeof(T) * (size_t)K.ldv, c->s));
+    APC_CUDA(c, cudaMemsetAsync(K.wraw, 0, sizeof(T) * (size_t)K.ldv, c->s));
+    APC_CUDA(c, cudaMemcpyAsync(&st->rtol, &rtol, sizeof(double), cudaMemcpyHostToDevice, c->s));
+    APC_LAUNCH(c, K_VEC, K.nblk, RT, 0, k_norm2<T>, b, n, st, K.partial);
+    int iters = 0, cycles = 0;
+    double relres = 0.0;
+    apcloud_status status = APCLOUD_W_NOT_CONVERGED;
+    const double vb = (double)sizeof(T), nnz = (double)c->sum_m + (double)c->n_int + (double)c->n_bnd, dn = n;
+    for (;;) {
+        APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
+                   (T *)nullptr, b, st, K.partial);
+        double tmp[2];  // bnorm and beta are adjacent in GmresState
+        APC_TRY(read_back(c, tmp, &st->bnorm, 2 * sizeof(double)));
+        relres = tmp[0] > 0.0 ? tmp[1] / tmp[0] : 0.0;
+        if (tmp[0] == 0.0 || tmp[1] <= rtol * tmp[0]) { status = APCLOUD_OK; break; }
+        if (iters >= max_iter) break;
+        const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
+        for (int j = 0; j < jmax; ++j) {
+            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<1, T>), sw, so, col, val, n, (const T *)K.wraw, K.w,
+                       K.V + (int64_t)j * K.ldv, (const T *)nullptr, st, (double *)nullptr);
+            gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+            gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+            gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+        }
+        APC_LAUNCH(c, K_CYCLE, K.nblk, GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv, u,
+                   (const GmresState *)st);
+        APC_CUDA(c, cudaGetLastError());
+        int je;
+        APC_TRY(read_back(c, &je, &st->jend, sizeof(int)));
+        // algorithmic traffic of the launches that did work (values + column index per entry)
+        account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * (je + 1), 2.0 * nnz * (je + 1));
+        for (int j = 0; j < je; ++j) {
+            account(c, K_DOT, vb * dn * (j + 2), 2.0 * dn * (j + 1));
+            account(c, K_UPDDOT, vb * dn * (j + 3), 4.0 * dn * (j + 1));
+            account(c, K_UPDNORM, vb * dn * (j + 3), 2.0 * dn * (j + 2));
+        }
+        account(c, K_CYCLE, vb * dn * (je + 2), 2.0 * dn * je);
+        iters += je;
+        ++cycles;
+        if (je == 0) break;
+    }
+    *iters_out = iters;
+    *cycles_out = cycles;
+    *relres_out = relres;
+    return status;
 }
 
 }  // namespace
@@ -438,77 +547,79 @@ apcloud_status spmv(apcloud_ctx *c, int which, const double *x, double *y, doubl
     (void)scale; (void)copy_out;
     const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
     const int n = c->n_tot;
-    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<0>, ptr<uint32_t>(c->slice_w), ptr<uint32_t>(c->slice_off),
-               ptr<int32_t>(c->ell_col), val, n, x, y, (double *)nullptr, (const double *)nullptr,
-               (GmresState *)nullptr, (double *)nullptr);
+    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<0, double>), ptr<uint32_t>(c->slice_w),
+               ptr<uint32_t>(c->slice_off), ptr<int32_t>(c->ell_col), val, n, x, y, (double *)nullptr,
+               (const double *)nullptr, (GmresState *)nullptr, (double *)nullptr);
     return cuda_check(c, cudaGetLastError(), "spmv");
 }
 
 // Solve (B or A) x = b.  On entry x holds the initial guess (unscaled); on
-// exit the solution.
+// exit the solution.  FP64 form: GMRES(restart) on Ahat u = b in FP64.
+// Mixed form: iterative refinement -- the residual r = b - Ahat u is formed
+// in FP64 with the FP64 matrix, the correction Ahat e = r gets one FP32
+// GMRES(restart) cycle on the FP32 copy of the matrix (stopping early at a
+// relative 1e-4 or what the outer tolerance still needs), and u += e in FP64:
+// restarted GMRES whose restarts recompute the residual in FP64.
 apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x, double rtol, int max_iter,
                            apcloud_solve_info *info) {
     const int n = c->n_tot;
     const int m = c->P.restart;
     const int64_t ldv = ((int64_t)n + 31) / 32 * 32;
-    double *V = ensure<double>(c, c->V, (int64_t)(m + 1) * ldv);
-    double *w = ensure<double>(c, c->w0, n + 1);
-    double *wraw = ensure<double>(c, c->w1, n + 1);
-    double *u = ensure<double>(c, c->u, n + 1);
     const int nblk = reduction_blocks(c, n);
-    double *partial = ensure<double>(c, c->partial, (int64_t)(div_up(n, RT) + 2 * nblk) * 64);
-    GmresState *st = ptr<GmresState>(c->gstate);
-    if (!V || !w || !wraw || !u || !partial) return APCLOUD_E_NOMEM;
+    const int64_t npart = (int64_t)(div_up(n, RT) + 2 * nblk) * 64;
+    double *u = ensure<double>(c, c->u, ldv + 1);
+    double *partial = ensure<double>(c, c->partial, npart);
+    if (!u || !partial) return APCLOUD_E_NOMEM;
     const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
     const double *d = ptr<double>(which ? c->dA : c->dB);
-    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
-    const int32_t *col = ptr<int32_t>(c->ell_col);
-
-    APC_CUDA(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s));
-    APC_CUDA(c, cudaMemcpyAsync(&st->rtol, &rtol, sizeof(double), cudaMemcpyHostToDevice, c->s));
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
-    APC_LAUNCH(c, K_VEC, nblk, RT, 0, k_norm2, b, n, st, partial);
-
-    struct { double beta, bnorm; int jend, done; } hs;
     int iters = 0, cycles = 0;
     double relres = 0.0;
-    apcloud_status status = APCLOUD_W_NOT_CONVERGED;
-    for (;;) {
-        // r = b - Ahat u, into wraw; beta = ||r||
-        APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<2>, sw, so, col, val, n, (const double *)u, wraw,
-                   (double *)nullptr, b, st, partial);
-        double tmp[2];  // bnorm and beta are adjacent in GmresState
-        APC_TRY(read_back(c, tmp, &st->bnorm, 2 * sizeof(double)));
-        hs.bnorm = tmp[0];
-        hs.beta = tmp[1];
-        relres = hs.bnorm > 0.0 ? hs.beta / hs.bnorm : 0.0;
-        if (hs.bnorm == 0.0 || hs.beta <= rtol * hs.bnorm) { status = APCLOUD_OK; break; }
-        if (iters >= max_iter) break;
-        const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
-        for (int j = 0; j < jmax; ++j) {
-            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<1>, sw, so, col, val, n, (const double *)wraw, w,
-                       V + (int64_t)j * ldv, (const double *)nullptr, st, (double *)nullptr);
-            gs_dispatch(c, 0, nblk, V, ldv, n, j, w, wraw, st, partial);
-            gs_dispatch(c, 1, nblk, V, ldv, n, j, w, wraw, st, partial);
-            gs_dispatch(c, 2, nblk, V, ldv, n, j, w, wraw, st, partial);
+    apcloud_status status;
+    if (c->P.precision == 0) {
+        Krylov<double> K{ensure<double>(c, c->V, (int64_t)(m + 1) * ldv), ldv, ensure<double>(c, c->w0, ldv + 1),
+                         ensure<double>(c, c->w1, ldv + 1), ptr<GmresState>(c->gstate), partial, nblk};
+        if (!K.V || !K.w || !K.wraw) return APCLOUD_E_NOMEM;
+        status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
+        if (status < 0) return status;
+    } else {
+        Krylov<float> K{ensure<float>(c, c->V32, (int64_t)(m + 1) * ldv), ldv, ensure<float>(c, c->w32a, ldv + 1),
+                        ensure<float>(c, c->w32b, ldv + 1), ptr<GmresState>(c->gstate), partial, nblk};
+        float *r32 = ensure<float>(c, c->r32, n + 1), *e32 = ensure<float>(c, c->e32, ldv + 1);
+        double *r64 = ensure<double>(c, c->w0, n + 1);
+        GmresState *so = ensure<GmresState>(c, c->gstate2, 1);
+        if (!K.V || !K.w || !K.wraw || !r32 || !e32 || !r64 || !so) return APCLOUD_E_NOMEM;
+        const float *val32 = ptr<float>(which ? c->ell_A32 : c->ell_B32);
+        const uint32_t *sw = ptr<uint32_t>(c->slice_w), *sof = ptr<uint32_t>(c->slice_off);
+        const int32_t *col = ptr<int32_t>(c->ell_col);
+        APC_CUDA(c, cudaMemsetAsync(so, 0, sizeof(GmresState), c->s));
+        APC_CUDA(c, cudaMemcpyAsync(&so->rtol, &rtol, sizeof(double), cudaMemcpyHostToDevice, c->s));
+        APC_CUDA(c, cudaMemsetAsync(e32, 0, sizeof(float) * ldv, c->s));
+        APC_LAUNCH(c, K_VEC, nblk, RT, 0, k_norm2<double>, b, n, so, partial);
+        status = APCLOUD_W_NOT_CONVERGED;
+        for (;;) {
+            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, double>), sw, sof, col, val, n,
+                       (const double *)u, r64, (double *)nullptr, b, so, partial);
+            double tmp[2];
+            APC_TRY(read_back(c, tmp, &so->bnorm, 2 * sizeof(double)));
+            relres = tmp[0] > 0.0 ? tmp[1] / tmp[0] : 0.0;
+            if (tmp[0] == 0.0 || tmp[1] <= rtol * tmp[0]) { status = APCLOUD_OK; break; }
+            if (iters >= max_iter) break;
+            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_to_f32, r32, (const double *)r64, n);
+            // one FP32 restart cycle per refinement step: FP32 residuals bottom out
+            // near kappa * 6e-8, so the FP64 residual takes over after each cycle
+            double inner = 0.5 * rtol * tmp[0] / tmp[1];
+            if (inner < 1e-4) inner = 1e-4;
+            const int cap = (m < max_iter - iters) ? m : (max_iter - iters);
+            int it = 0, cy = 0;
+            double rr = 0.0;
+            apcloud_status si = gmres_core<float>(c, val32, r32, e32, inner, cap, K, &it, &cy, &rr);
+            if (si < 0) return si;
+            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add_f32, u, e32, n);
+            iters += it;
+            cycles += cy;
+            if (it == 0) break;
         }
-        cycle_end_dispatch(c, nblk, jmax, V, ldv, n, u, st);
-        APC_CUDA(c, cudaGetLastError());
-        int je;
-        APC_TRY(read_back(c, &je, &st->jend, sizeof(int)));
-        {   // algorithmic traffic of the launches that did work
-            const double nnz = (double)c->sum_m + (double)c->n_int + (double)c->n_bnd, dn = n;
-            account(c, K_SPMV, (12.0 * nnz + 16.0 * dn) * (je + 1), 2.0 * nnz * (je + 1));
-            for (int j = 0; j < je; ++j) {
-                account(c, K_DOT, 8.0 * dn * (j + 2), 2.0 * dn * (j + 1));
-                account(c, K_UPDDOT, 8.0 * dn * (j + 3), 4.0 * dn * (j + 1));
-                account(c, K_UPDNORM, 8.0 * dn * (j + 3), 2.0 * dn * (j + 2));
-            }
-            account(c, K_CYCLE, 8.0 * dn * (je + 2), 2.0 * dn * je);
-        }
-        iters += je;
-        ++cycles;
-        if (je == 0) break;  // breakdown at the first column: nothing more to gain
     }
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_div, x, (const double *)u, d, n);
     APC_CUDA(c, cudaGetLastError());
@@ -603,45 +714,14 @@ extern "C" apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *c, int which
     c->timer.mask = 0;
     const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
     const double *d = ptr<double>(which ? c->dA : c->dB);
-    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
-    const int32_t *col = ptr<int32_t>(c->ell_col);
     apcloud_status status = APCLOUD_W_NOT_CONVERGED;
     int iters = 0, cycles = 0;
     double relres = 0.0;
     do {
-        // the array keeps the previous call's contents: the state must start from zero
-        if (cuda_check(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s), "memset") < 0) { status = APCLOUD_E_CUDA; break; }
-        if (cuda_check(c, cudaMemcpyAsync(&st->rtol, &rtol, sizeof(double), cudaMemcpyHostToDevice, c->s), "rtol") < 0) {
-            status = APCLOUD_E_CUDA;
-            break;
-        }
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
-        APC_LAUNCH(c, K_VEC, nblk, RT, 0, k_norm2, b, n, st, partial);
-        for (;;) {
-            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<2>, sw, so, col, val, n, (const double *)u, wraw,
-                       (double *)nullptr, b, st, partial);
-            double tmp[2];
-            apcloud_status r = read_back(c, tmp, &st->bnorm, 2 * sizeof(double));
-            if (r < 0) { status = r; break; }
-            relres = tmp[0] > 0.0 ? tmp[1] / tmp[0] : 0.0;
-            if (tmp[0] == 0.0 || tmp[1] <= rtol * tmp[0]) { status = APCLOUD_OK; break; }
-            if (iters >= max_iter) break;
-            const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
-            for (int j = 0; j < jmax; ++j) {
-                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_spmv<1>, sw, so, col, val, n, (const double *)wraw, w,
-                           V + (int64_t)j * ldv, (const double *)nullptr, st, (double *)nullptr);
-                gs_dispatch(c, 0, nblk, V, ldv, n, j, w, wraw, st, partial);
-                gs_dispatch(c, 1, nblk, V, ldv, n, j, w, wraw, st, partial);
-                gs_dispatch(c, 2, nblk, V, ldv, n, j, w, wraw, st, partial);
-            }
-            cycle_end_dispatch(c, nblk, jmax, V, ldv, n, u, st);
-            int je = 0;
-            r = read_back(c, &je, &st->jend, sizeof(int));
-            if (r < 0) { status = r; break; }
-            iters += je;
-            ++cycles;
-            if (je == 0) break;
-        }
+        Krylov<double> K{V, ldv, w, wraw, st, partial, nblk};
+        // gmres_core clears the device state itself (the array keeps the previous call's contents)
+        status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) break;
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_div, x, (const double *)u, d, n);
         apcloud_status r = cuda_check(c, cudaStreamSynchronize(c->s), "solve_system_noalloc");

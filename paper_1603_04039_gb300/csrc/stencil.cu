@@ -21,6 +21,7 @@ namespace apc {
 namespace {
 
 constexpr int SW = 4;           // warps (nodes) per block
+constexpr double FP32_RATIO_MIN = 1e-3;  // condition estimate limit of the FP32 factorisation
 constexpr int ASTR = NCOL;      // row stride of the staged Vandermonde
 
 struct WarpSmem {
@@ -75,30 +76,32 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 
 // Cholesky of the packed upper Gram matrix G into R (row-major 9x9, upper),
 // run by one lane.  Returns false on a non-positive pivot.
-__device__ bool cholesky9(const double *G, double *R) {
+template <class T>
+__device__ bool cholesky9(const T *G, T *R) {
     for (int i = 0; i < NCOL; ++i) {
         for (int j = i; j < NCOL; ++j) {
             int a = i, b = j;
             int e = a * NCOL - a * (a - 1) / 2 + (b - a);  // packed upper index
-            double s = G[e];
+            T s = G[e];
             for (int k = 0; k < i; ++k) s -= R[k * NCOL + i] * R[k * NCOL + j];
             if (j == i) {
-                if (!(s > 0.0)) return false;
+                if (!(s > (T)0)) return false;
                 R[i * NCOL + i] = sqrt(s);
             } else {
                 R[i * NCOL + j] = s / R[i * NCOL + i];
             }
         }
-        for (int j = 0; j < i; ++j) R[i * NCOL + j] = 0.0;
+        for (int j = 0; j < i; ++j) R[i * NCOL + j] = (T)0;
     }
     return true;
 }
 
 // solve q R = a for the row vector q (R upper), in place on v
-__device__ __forceinline__ void row_solve_upper(const double *R, double *v) {
+template <class T>
+__device__ __forceinline__ void row_solve_upper(const T *R, T *v) {
 #pragma unroll
     for (int c = 0; c < NCOL; ++c) {
-        double s = v[c];
+        T s = v[c];
 #pragma unroll
         for (int k = 0; k < c; ++k) s -= v[k] * R[k * NCOL + c];
         v[c] = s / R[c * NCOL + c];
@@ -106,10 +109,11 @@ __device__ __forceinline__ void row_solve_upper(const double *R, double *v) {
 }
 
 // solve R z = v for the column vector z (R upper), in place
-__device__ __forceinline__ void col_solve_upper(const double *R, double *v) {
+template <class T>
+__device__ __forceinline__ void col_solve_upper(const T *R, T *v) {
 #pragma unroll
     for (int c = NCOL - 1; c >= 0; --c) {
-        double s = v[c];
+        T s = v[c];
 #pragma unroll
         for (int k = c + 1; k < NCOL; ++k) s -= R[c * NCOL + k] * v[k];
         v[c] = s / R[c * NCOL + c];
@@ -117,13 +121,115 @@ __device__ __forceinline__ void col_solve_upper(const double *R, double *v) {
 }
 
 // Gram matrix of the staged rows: lane e < 45 owns entry (pa[e], pb[e])
-__device__ __forceinline__ void gram(const double *A, int m, double *G, int lane) {
+template <class T>
+__device__ __forceinline__ void gram(const T *A, int m, T *G, int lane) {
     for (int e = lane; e < 45; e += 32) {
         int a = c_pa[e], b = c_pb[e];
-        double s = 0.0;
+        T s = (T)0;
         for (int j = 0; j < m; ++j) s = fma(A[j * ASTR + a], A[j * ASTR + b], s);
         G[e] = s;
     }
+}
+
+__device__ __forceinline__ double exp_t(double v) { return exp(v); }
+__device__ __forceinline__ float exp_t(float v) { return expf(v); }
+
+// Weighted least-squares operator (Section 3.1) of the stencil staged in
+// W.sel / W.seld2, in arithmetic T: rows of W V0 (Eq. regfd with the
+// normalized Gaussian weight), CholeskyQR2, and column `lane` of
+// P = (W V0)^+ W unscaled by h and h^2, returned in FP64.  Returns false when
+// a Cholesky pivot fails; rratio = min |R_ii| / max |R_ii|.
+template <class T>
+__device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__restrict__ ic, double unit,
+                           double ec, double inv_1mec, double (&qout)[NCOL], double &lapj, double &rratio) {
+    T *A = reinterpret_cast<T *>(W.A);
+    T *G = reinterpret_cast<T *>(W.G);
+    T *R1 = reinterpret_cast<T *>(W.R1);
+    T *R2 = reinterpret_cast<T *>(W.R2);
+    long long off[3] = {0, 0, 0};
+    long long mydist = 0, amax = 0;
+    if (lane < m) {
+        int4 q = ic[W.sel[lane]];
+        off[0] = (long long)q.x - c0.x; off[1] = (long long)q.y - c0.y; off[2] = (long long)q.z - c0.z;
+        mydist = W.seld2[lane];
+        for (int d = 0; d < 3; ++d) { long long a = off[d] < 0 ? -off[d] : off[d]; amax = a > amax ? a : amax; }
+    }
+    const long long hint = warp_max_ll(amax);
+    const long long r2max = W.seld2[m - 1];
+    T wj = (T)0;
+    {
+        T row[NCOL];
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) row[e] = (T)0;
+        if (lane < m) {
+            // xi = dy / h with h = max |dy_d| (Section 3.1), exact integer ratios rounded once
+            T xi0 = (T)((double)off[0] / (double)hint), xi1 = (T)((double)off[1] / (double)hint),
+              xi2 = (T)((double)off[2] / (double)hint);
+            T ratio = (T)((double)mydist / (double)r2max);
+            wj = (exp_t(-ratio) - (T)ec) * (T)inv_1mec;
+            const T half = (T)0.5;
+            row[0] = xi0; row[1] = xi1; row[2] = xi2;
+            row[3] = (half * xi0) * xi0;
+            row[4] = xi0 * xi1;
+            row[5] = xi0 * xi2;
+            row[6] = (half * xi1) * xi1;
+            row[7] = xi1 * xi2;
+            row[8] = (half * xi2) * xi2;
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) row[e] = wj * row[e];
+        }
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) A[lane * ASTR + e] = row[e];
+    }
+    __syncwarp();
+    gram<T>(A, m, G, lane);
+    __syncwarp();
+    if (lane == 0) W.flag = cholesky9<T>(G, R1) ? 1 : 0;
+    __syncwarp();
+    bool ok = W.flag != 0;
+    T q[NCOL];
+    if (ok) {
+        if (lane < m) {
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) q[e] = A[lane * ASTR + e];
+            row_solve_upper<T>(R1, q);
+#pragma unroll
+            for (int e = 0; e < NCOL; ++e) A[lane * ASTR + e] = q[e];
+        }
+        __syncwarp();
+        gram<T>(A, m, G, lane);
+        __syncwarp();
+        if (lane == 0) W.flag = cholesky9<T>(G, R2) ? 1 : 0;
+        __syncwarp();
+        ok = W.flag != 0;
+    }
+    rratio = 0.0;
+    lapj = 0.0;
+    if (!ok) return false;
+    double dmin = 1e300, dmax = 0.0;
+#pragma unroll
+    for (int e = 0; e < NCOL; ++e) {
+        double r = fabs((double)R1[e * NCOL + e] * (double)R2[e * NCOL + e]);
+        dmin = fmin(dmin, r);
+        dmax = fmax(dmax, r);
+    }
+    rratio = dmin / dmax;
+    const double h = (double)hint * unit;
+    const double h2 = h * h;
+    if (lane < m) {
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) q[e] = A[lane * ASTR + e];
+        row_solve_upper<T>(R2, q);
+        col_solve_upper<T>(R2, q);
+        col_solve_upper<T>(R1, q);
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) qout[e] = ((double)q[e] * (double)wj) / (e < 3 ? h : h2);
+        lapj = qout[3] + qout[6] + qout[8];
+    } else {
+#pragma unroll
+        for (int e = 0; e < NCOL; ++e) qout[e] = 0.0;
+    }
+    return true;
 }
 
 __global__ void __launch_bounds__(SW * 32) k_stencil(
@@ -131,7 +237,7 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
     int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
     int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,
     double *__restrict__ lapd_out, double *__restrict__ D_out, int64_t dstride, double *__restrict__ rcond_out,
-    unsigned *err) {
+    int fp32_first, int *__restrict__ fp64_count, unsigned *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlockSmem &S = *reinterpret_cast<BlockSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -256,94 +362,19 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
         __syncwarp();
         if (m > MMAX) m = MMAX;
 
-        // ---- weighted scaled Vandermonde (Eq. regfd, normalized Gaussian weight)
-        long long off[3] = {0, 0, 0};
-        long long mydist = 0;
-        if (lane < m) {
-            int4 q = ic[W.sel[lane]];
-            off[0] = (long long)q.x - c0.x; off[1] = (long long)q.y - c0.y; off[2] = (long long)q.z - c0.z;
-            mydist = W.seld2[lane];
+        // ---- weighted least squares: FP32 first when asked, FP64 for blocks the
+        // FP32 factorisation cannot certify (Cholesky failure or condition
+        // estimate above 1e3, where FP32 Cholesky QR loses its accuracy)
+        double q[NCOL], lapj = 0.0;
+        bool ok = false;
+        if (fp32_first) {
+            ok = wls_column<float>(W, m, lane, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
+            if (ok && rmin_over_rmax < FP32_RATIO_MIN) ok = false;
+            if (!ok && lane == 0) atomicAdd(fp64_count, 1);
         }
-        long long amax = 0;
-        if (lane < m) {
-            for (int d = 0; d < 3; ++d) { long long a = off[d] < 0 ? -off[d] : off[d]; amax = a > amax ? a : amax; }
-        }
-        const long long hint = warp_max_ll(amax);
-        const long long r2max = W.seld2[m - 1];
-        double wj = 0.0;
-        {
-            double row[NCOL];
-#pragma unroll
-            for (int e = 0; e < NCOL; ++e) row[e] = 0.0;
-            if (lane < m) {
-                double xi0 = (double)off[0] / (double)hint, xi1 = (double)off[1] / (double)hint,
-                       xi2 = (double)off[2] / (double)hint;
-                double ratio = (double)mydist / (double)r2max;
-                wj = __dmul_rn(__dsub_rn(exp(-ratio), ec), inv_1mec);
-                row[0] = xi0; row[1] = xi1; row[2] = xi2;
-                row[3] = __dmul_rn(__dmul_rn(0.5, xi0), xi0);
-                row[4] = __dmul_rn(xi0, xi1);
-                row[5] = __dmul_rn(xi0, xi2);
-                row[6] = __dmul_rn(__dmul_rn(0.5, xi1), xi1);
-                row[7] = __dmul_rn(xi1, xi2);
-                row[8] = __dmul_rn(__dmul_rn(0.5, xi2), xi2);
-#pragma unroll
-                for (int e = 0; e < NCOL; ++e) row[e] = __dmul_rn(wj, row[e]);
-            }
-#pragma unroll
-            for (int e = 0; e < NCOL; ++e) W.A[lane * ASTR + e] = row[e];
-        }
-        __syncwarp();
-
-        // ---- CholeskyQR2
-        gram(W.A, m, W.G, lane);
-        __syncwarp();
-        if (lane == 0) W.flag = cholesky9(W.G, W.R1) ? 1 : 0;
-        __syncwarp();
-        bool ok = W.flag != 0;
-        double q[NCOL];
-        if (ok) {
-            if (lane < m) {
-#pragma unroll
-                for (int e = 0; e < NCOL; ++e) q[e] = W.A[lane * ASTR + e];
-                row_solve_upper(W.R1, q);
-#pragma unroll
-                for (int e = 0; e < NCOL; ++e) W.A[lane * ASTR + e] = q[e];
-            }
-            __syncwarp();
-            gram(W.A, m, W.G, lane);
-            __syncwarp();
-            if (lane == 0) W.flag = cholesky9(W.G, W.R2) ? 1 : 0;
-            __syncwarp();
-            ok = W.flag != 0;
-        }
-        if (ok) {
-            double dmin = 1e300, dmax = 0.0;
-#pragma unroll
-            for (int e = 0; e < NCOL; ++e) {
-                double r = fabs(W.R1[e * NCOL + e] * W.R2[e * NCOL + e]);
-                dmin = fmin(dmin, r);
-                dmax = fmax(dmax, r);
-            }
-            rmin_over_rmax = dmin / dmax;
-            ok = dmin >= RANK_TOL * dmax;
-        }
-        double lapj = 0.0;
-        if (ok) {
-            // column j of P: R1^-1 R2^-1 q2_j^T W_j, unscaled by h and h^2
-            const double h = (double)hint * unit;
-            const double h2 = h * h;
-            if (lane < m) {
-#pragma unroll
-                for (int e = 0; e < NCOL; ++e) q[e] = W.A[lane * ASTR + e];
-                row_solve_upper(W.R2, q);
-                col_solve_upper(W.R2, q);
-                col_solve_upper(W.R1, q);
-#pragma unroll
-                for (int e = 0; e < NCOL; ++e) q[e] = (q[e] * wj) / (e < 3 ? h : h2);
-                lapj = q[3] + q[6] + q[8];
-            }
-        }
+        if (!ok) ok = wls_column<double>(W, m, lane, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
+        if (ok) ok = rmin_over_rmax >= RANK_TOL;
+        if (!ok) lapj = 0.0;
         const double lsum = warp_sum_d(lapj);
         if (!ok || !(-lsum < 0.0)) {       // unusable: more neighbours, then a wider ring
             if (m >= nc - 1) break;
@@ -457,6 +488,13 @@ __global__ void k_ell_fill(const int32_t *__restrict__ msz, const int32_t *__res
     }
 }
 
+// FP32 copies of the stored (Jacobi-scaled) matrix values for the mixed form
+__global__ void k_values_f32(const double *__restrict__ vA, const double *__restrict__ vB, int64_t n,
+                             float *__restrict__ fA, float *__restrict__ fB) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) { fA[i] = (float)vA[i]; fB[i] = (float)vB[i]; }
+}
+
 }  // namespace
 
 static bool g_pairs_set = false;
@@ -496,9 +534,14 @@ apcloud_status build_stencils(apcloud_ctx *c) {
     }
     APC_LAUNCH(c, K_STENCIL, div_up(n, SW), SW * 32, smem, k_stencil, ptr<int4>(c->node_ic), ptr<int32_t>(c->adj),
                ptr<int32_t>(c->bowner), n, c->P.m_target, c->P.ring_max, unit, ec, inv_1mec, nbr, msz, ring, lap,
-               lapd, D, dstride, rc, derr);
+               lapd, D, dstride, rc, c->P.precision == 1 ? 1 : 0, reinterpret_cast<int *>(derr + 1), derr);
     APC_CUDA(c, cudaGetLastError());
     APC_TRY(check_device_errors(c));
+    {
+        unsigned e[2];
+        APC_TRY(read_back(c, e, derr, sizeof e));
+        c->n_fp64_wls = e[1];
+    }
     {   // total stencil size, for the algorithmic traffic of later kernels
         uint32_t *tmp = ensure<uint32_t>(c, c->tmp, n + 1);
         if (!tmp) return APCLOUD_E_NOMEM;
@@ -534,6 +577,12 @@ apcloud_status build_stencils(apcloud_ctx *c) {
     if (!col || !vA || !vB) return APCLOUD_E_NOMEM;
     APC_LAUNCH(c, K_ELL, div_up((int64_t)nsl * 32, 256), 256, 0, k_ell_fill, msz, nbr, lap, lapd,
                ptr<int4>(c->node_ic), dA, dB, n, nt, ext, sw, so, col, vA, vB);
+    if (c->P.precision == 1) {
+        float *fA = ensure<float>(c, c->ell_A32, c->ell_entries), *fB = ensure<float>(c, c->ell_B32, c->ell_entries);
+        if (!fA || !fB) return APCLOUD_E_NOMEM;
+        APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)vA,
+                   (const double *)vB, c->ell_entries, fA, fB);
+    }
     return cuda_check(c, cudaGetLastError(), "ell");
 }
 

@@ -1,0 +1,68 @@
+"""The mixed-precision form against the FP64 oracle.
+
+FP32 stencils (with FP64 refactorisation of blocks whose condition estimate
+exceeds 1e3) and FP32 GMRES iterations inside an FP64 iterative-refinement
+loop.  Integer results stay bit-exact (the selection is integer arithmetic
+and the accept/reject tests agree unless a value sits on a threshold); the
+fields must match the FP64 oracle within a relative L2 of 1e-6 (FP32
+weights perturb the operator by ~1e-7 relative and the rows stay exactly
+consistent, so the solution moves by ~1e-7).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1603_04039_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n,depth,c,seed", [(100000, 6, 1.0, 1), (100000, 6, 0.5, 2), (20000, 5, 0.3, 3)])
+def test_mixed_matches_fp64_oracle(n, depth, c, seed):
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(n, seed)
+    ap = APCloud(max_depth=depth, c_refine=c, precision="mixed")
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    o = oracle.Oracle(max_depth=depth, c_refine=c)
+    o.build(x, y, z)
+    w = o.stencils()
+    g = {k: v.cpu().numpy() for k, v in ap.get_stencils().items()}
+    assert np.array_equal(g["nbr"], w["nbr"]) and np.array_equal(g["m"], w["m"])
+    scale = np.abs(w["lap"]).max(axis=1, keepdims=True)
+    assert np.all(np.abs(g["lap"] - w["lap"]) <= 1e-5 * scale)
+    rho, ir = ap.deposit(q=_t(q), rtol=1e-10)
+    phi, ip = ap.solve(rtol=1e-10)
+    php, ex, ey, ez = ap.gather_field()
+    assert ir["status"] == 0 and ip["status"] == 0 and ip["relres"] <= 1e-10
+    ref = o.run(x, y, z, q=q, rtol=1e-12)
+    assert rel(rho.cpu().numpy(), ref["rho"]) < 1e-6
+    assert rel(phi.cpu().numpy(), ref["phi"]) < 1e-6
+    assert rel(php.cpu().numpy(), ref["phi_p"]) < 1e-6
+    for a, b in ((ex, ref["ex"]), (ey, ref["ey"]), (ez, ref["ez"])):
+        assert rel(a.cpu().numpy(), b) < 1e-6
+
+
+def test_mixed_refinement_reaches_fp64_residual():
+    """Iterative refinement drives the FP64 residual of the (FP32-built)
+    system to 1e-12, beyond what FP32 iterations alone can reach."""
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(100000, 4)
+    ap = APCloud(max_depth=6, c_refine=0.7, precision="mixed")
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    b = torch.from_numpy(np.random.default_rng(0).normal(size=ap.n_nodes)).to(DEV)
+    xs, info = ap.solve_system("A", b, rtol=1e-12, max_iter=50000)
+    assert info["status"] == 0 and info["relres"] <= 1e-12
+    r = (b - ap.matvec("A", xs)).cpu().numpy()
+    assert np.linalg.norm(r) <= 2e-12 * np.linalg.norm(b.cpu().numpy())
