@@ -69,6 +69,10 @@ typedef struct {
                             refactorisation of blocks whose condition estimate exceeds 1e3,
                             FP32 GMRES iterations inside an FP64 iterative-refinement loop
                             (FP64 residual and solution), FP64 charge sums and gather */
+    int poly_degree;     /* right preconditioner of GMRES: 1 = Jacobi; d > 1 = Jacobi-Neumann
+                            polynomial omega sum_{i<d} (I - omega D^-1 A)^i, i.e. d damped
+                            Jacobi sweeps per Arnoldi step (1..32) */
+    double poly_omega;   /* damping omega of those sweeps, 0 < omega < 2 */
 } apcloud_params;
 
 /* Optional device allocator; NULL selects cudaMallocAsync/cudaFreeAsync on
@@ -88,7 +92,8 @@ typedef struct {
 typedef struct apcloud_ctx apcloud_ctx;
 
 /* Fills *p with the defaults: domain [-1,1]^3, max_depth 6, c_refine 1,
- * m_target 20, ring_max 5, weight_c 4, poisson_c 1, restart 30, FP64. */
+ * m_target 20, ring_max 5, weight_c 4, poisson_c 1, restart 30, FP64,
+ * Jacobi preconditioning (poly_degree 1, poly_omega 0.7). */
 void apcloud_default_params(apcloud_params *p);
 
 /* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy

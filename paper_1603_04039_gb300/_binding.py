@@ -38,7 +38,8 @@ class APCloudError(RuntimeError):
 class Params(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("max_depth", C.c_int), ("c_refine", C.c_double),
                 ("m_target", C.c_int), ("ring_max", C.c_int), ("weight_c", C.c_double),
-                ("poisson_c", C.c_double), ("restart", C.c_int), ("precision", C.c_int)]
+                ("poisson_c", C.c_double), ("restart", C.c_int), ("precision", C.c_int),
+                ("poly_degree", C.c_int), ("poly_omega", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -133,7 +134,8 @@ class APCloud:
     """One AP-Cloud problem on one GPU (see include/apcloud.h for each call)."""
 
     def __init__(self, lo=-1.0, hi=1.0, max_depth=6, c_refine=1.0, m_target=20, ring_max=5, weight_c=4.0,
-                 poisson_c=1.0, restart=30, precision="fp64", device="cuda:0", stream=None):
+                 poisson_c=1.0, restart=30, precision="fp64", poly_degree=1, poly_omega=0.7, device="cuda:0",
+                 stream=None):
         lib = load()
         self._lib = lib
         self.device = torch.device(device)
@@ -145,6 +147,7 @@ class APCloud:
         p.max_depth, p.c_refine, p.m_target, p.ring_max = int(max_depth), float(c_refine), int(m_target), int(ring_max)
         p.weight_c, p.poisson_c, p.restart = float(weight_c), float(poisson_c), int(restart)
         p.precision = {"fp64": 0, "mixed": 1}[precision]
+        p.poly_degree, p.poly_omega = int(poly_degree), float(poly_omega)
         self.params = p
         with torch.cuda.device(self.device):
             s = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -139,6 +139,8 @@ static apcloud_status validate(const apcloud_params *p, char *msg, size_t len) {
     if (!(p->weight_c > 0) || !std::isfinite(p->weight_c)) { snprintf(msg, len, "weight_c must be > 0"); return APCLOUD_E_INVALID; }
     if (!std::isfinite(p->poisson_c)) { snprintf(msg, len, "poisson_c must be finite"); return APCLOUD_E_INVALID; }
     if (p->restart < 1 || p->restart > MAX_RESTART) { snprintf(msg, len, "restart must be 1..64"); return APCLOUD_E_INVALID; }
+    if (p->poly_degree < 1 || p->poly_degree > 32) { snprintf(msg, len, "poly_degree must be 1..32"); return APCLOUD_E_INVALID; }
+    if (!(p->poly_omega > 0 && p->poly_omega < 2)) { snprintf(msg, len, "poly_omega must be in (0, 2)"); return APCLOUD_E_INVALID; }
     if (p->precision != 0 && p->precision != 1) {
         snprintf(msg, len, "precision must be 0 (FP64) or 1 (mixed)");
         return APCLOUD_E_INVALID;
@@ -163,6 +165,8 @@ void apcloud_default_params(apcloud_params *p) {
     p->poisson_c = 1.0;
     p->restart = 30;
     p->precision = 0;
+    p->poly_degree = 1;
+    p->poly_omega = 0.7;
 }
 
 apcloud_status apcloud_create(const apcloud_params *params, const apcloud_allocator *alloc, void *stream,
@@ -205,7 +209,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->ell_A, &c->ell_B, &c->dA, &c->dB, &c->V, &c->w0, &c->w1, &c->u, &c->b, &c->partial,
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->tmp, &c->derr, &c->dsmall,
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
-                    &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2};
+                    &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
+                    &c->pz0, &c->pz1, &c->pt};
     for (DBuf *b : bufs) free_buf(c, *b);
     cudaStreamSynchronize(c->s);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);

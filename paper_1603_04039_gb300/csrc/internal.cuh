@@ -47,6 +47,7 @@ struct GmresState {
     double beta;                  // ||r|| at cycle start
     double inv_norm;              // 1 / ||w|| of the vector about to become V_{j+1}
     double rtol;
+    double omega;                 // damping of the polynomial preconditioner sweeps
     int jend;                     // columns completed in this cycle
     int done;                     // 1 once the cycle must stop (converged or breakdown)
     unsigned ticket;              // grid-reduction ticket
@@ -102,6 +103,7 @@ struct apcloud_ctx {
     // solver
     apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
+    apc::DBuf pz0, pz1, pt;                         // polynomial preconditioner sweeps
     // device staging for apcloud_field_host
     apc::DBuf hx, hy, hz, hq, hphi, hex, hey, hez;
     // error word, small host-visible values

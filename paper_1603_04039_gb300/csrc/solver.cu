@@ -28,27 +28,26 @@ constexpr int RT = 256;  // threads of the reduction kernels
 // of the block (returned in `out`, valid for threadIdx.x < nj).
 template <int NJ>
 __device__ __forceinline__ void block_reduce_many(const double (&acc)[NJ], int nj, double *sm, double *out) {
-    // sm: RT * NJ doubles laid out [k][t]
-    const int t = threadIdx.x;
+    // sm: blockDim * NJ doubles laid out [k][t], then NJ * (blockDim / 32) segment sums
+    const int t = threadIdx.x, B = blockDim.x;
 #pragma unroll
     for (int k = 0; k < NJ; ++k)
-        if (k < nj) sm[k * RT + t] = acc[k];
+        if (k < nj) sm[k * B + t] = acc[k];
     __syncthreads();
-    // nj * 8 threads each sum a segment of 32
-    const int seg = RT / 32;
-    for (int q = t; q < nj * seg; q += RT) {
+    // nj * (B / 32) threads each sum a segment of 32
+    const int seg = B / 32;
+    for (int q = t; q < nj * seg; q += B) {
         int k = q / seg, s = q % seg;
-        const double *p = sm + k * RT + s * 32;
+        const double *p = sm + k * B + s * 32;
         double v = 0.0;
 #pragma unroll 8
         for (int i = 0; i < 32; ++i) v += p[i];
-        sm[NJ * RT + q] = v;
+        sm[NJ * B + q] = v;
     }
     __syncthreads();
     if (t < nj) {
         double v = 0.0;
-#pragma unroll
-        for (int s = 0; s < seg; ++s) v += sm[NJ * RT + t * seg + s];
+        for (int s = 0; s < seg; ++s) v += sm[NJ * B + t * seg + s];
         *out = v;
     }
     __syncthreads();
@@ -74,19 +73,33 @@ __device__ void final_sums(const double *partial, int nblk, int nk, double *sm, 
     const int t = threadIdx.x;
     if (nk == 1) {
         double v = 0.0;
-        for (int b = t; b < nblk; b += RT) v += __ldcg(&partial[(int64_t)b * 64]);
+        for (int b = t; b < nblk; b += blockDim.x) v += __ldcg(&partial[(int64_t)b * 64]);
         double a[1] = {v};
         double tot = 0.0;
         block_reduce_many<1>(a, 1, sm, &tot);
         if (t == 0) out[0] = tot;
     } else {
-        const int k = t & 63, part = t >> 6;
-        double v = 0.0;
-        if (k < nk)
-            for (int b = part; b < nblk; b += RT / 64) v += __ldcg(&partial[(int64_t)b * 64 + k]);
-        sm[t] = v;
+        // thread t: value k = t % 64 over blocks part, part + P, ... (P = blockDim / 64),
+        // four independent partial sums so several loads are in flight
+        const int k = t & 63, part = t >> 6, P = blockDim.x >> 6;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        if (k < nk) {
+            int b = part;
+            for (; b + 3 * P < nblk; b += 4 * P) {
+                v0 += __ldcg(&partial[(int64_t)b * 64 + k]);
+                v1 += __ldcg(&partial[(int64_t)(b + P) * 64 + k]);
+                v2 += __ldcg(&partial[(int64_t)(b + 2 * P) * 64 + k]);
+                v3 += __ldcg(&partial[(int64_t)(b + 3 * P) * 64 + k]);
+            }
+            for (; b < nblk; b += P) v0 += __ldcg(&partial[(int64_t)b * 64 + k]);
+        }
+        sm[t] = (v0 + v1) + (v2 + v3);
         __syncthreads();
-        if (t < nk) out[t] = (sm[t] + sm[t + 64]) + (sm[t + 128] + sm[t + 192]);
+        if (t < nk) {
+            double s = 0.0;
+            for (int q = 0; q < P; ++q) s += sm[t + 64 * q];
+            out[t] = s;
+        }
     }
     __syncthreads();
 }
@@ -129,16 +142,20 @@ __global__ void k_bcopy(const int32_t *__restrict__ owner, int n_int, int n_bnd,
 // mode 0: y = Ahat x
 // mode 1: y = Ahat x * s, vout[r] = x[r] * s, s = st->inv_norm (Arnoldi step)
 // mode 2: y = b - Ahat x, ||y||^2 reduced into st (cycle start)
+// mode 3: y = x + omega (b - Ahat x)   (damped Jacobi sweep of the polynomial
+//         preconditioner, Ahat already carries the Jacobi scaling)
+// mode 4: y = Ahat x, skipped once the cycle is done
 template <int MODE, class T>
 __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                              const int32_t *__restrict__ col, const T *__restrict__ val, int n,
                                              const T *__restrict__ x, T *__restrict__ y, T *__restrict__ vout,
                                              const T *__restrict__ b, GmresState *st, double *__restrict__ partial) {
     __shared__ double sm[RT + RT / 32 + 8];
-    if (MODE == 1 && st->done) return;
+    if ((MODE == 1 || MODE == 3 || MODE == 4) && st->done) return;
     const int r = blockIdx.x * RT + threadIdx.x;
     T s = (T)1;
     if (MODE == 1) s = (T)st->inv_norm;
+    if (MODE == 3) s = (T)st->omega;
     T acc = (T)0;
     double yv = 0.0;
     if (r < n) {
@@ -149,8 +166,9 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
             const int64_t e = base + (int64_t)k * 32;
             acc = fma(val[e], x[col[e]], acc);
         }
-        if (MODE == 0) y[r] = acc;
+        if (MODE == 0 || MODE == 4) y[r] = acc;
         if (MODE == 1) { y[r] = acc * s; vout[r] = x[r] * s; }
+        if (MODE == 3) y[r] = fma(s, b[r] - acc, x[r]);
         if (MODE == 2) { T t = b[r] - acc; y[r] = t; yv = (double)t; }
     }
     if (MODE == 2) {
@@ -185,10 +203,11 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
 //     over k unrolled for independent loads.
 // Work vectors are ldv long (a multiple of 32) with zero tails past n, so
 // whole chunks are always in bounds and the tails add nothing.
-constexpr int GT = 256;                    // threads per block (8 warps)
-constexpr int GW = GT / 32;
-constexpr int TILE = 1024;                 // rows staged per tile
-constexpr int KPW = MAX_RESTART / GW;      // basis vectors per warp (<= 8)
+constexpr int GT = 256;                    // threads per block of the row-parallel kernels
+constexpr int DT = 512;                    // threads per block of the dot kernels (16 warps)
+constexpr int GW = DT / 32;
+constexpr int TILE = 2048;                 // rows staged per tile
+constexpr int KPW = MAX_RESTART / GW;      // basis vectors per warp (<= 4)
 
 template <class T> struct Vec;
 template <> struct Vec<double> { typedef double2 type; static constexpr int n = 2; };
@@ -250,14 +269,14 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.   (nrow = ldv)
 template <int PASS, class T>
-__global__ void __launch_bounds__(GT) k_gs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+__global__ void __launch_bounds__(DT) k_gs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
                                                 T *__restrict__ w, GmresState *st, double *__restrict__ partial) {
     typedef typename Vec<T>::type VT;
     constexpr int VN = Vec<T>::n;
     __shared__ __align__(16) T ws[TILE];
     __shared__ T hs[MAX_RESTART];
     __shared__ double red[MAX_RESTART];
-    __shared__ double sm[RT + RT / 32 + 8];
+    __shared__ double sm[DT + DT / 32 + 8];
     __shared__ double fs[64];
     if (st->done) return;
     const int j1 = j + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -271,9 +290,9 @@ __global__ void __launch_bounds__(GT) k_gs_dots(const T *__restrict__ V, int64_t
         const int lim = (int)((nrow - base) < TILE ? (nrow - base) : TILE);
         VT *wg = reinterpret_cast<VT *>(w + base);
         if (PASS == 0) {
-            for (int cix = tid; cix < lim / VN; cix += GT) wsv[cix] = wg[cix];
+            for (int cix = tid; cix < lim / VN; cix += DT) wsv[cix] = wg[cix];
         } else {
-            for (int cix = tid; cix < lim / VN; cix += GT) {
+            for (int cix = tid; cix < lim / VN; cix += DT) {
                 VT wi = wg[cix];
                 const T *vb = V + base;
 #pragma unroll 4
@@ -423,6 +442,55 @@ __global__ void k_div(double *__restrict__ out, const double *__restrict__ a, co
     if (i < n) out[i] = a[i] / d[i];
 }
 
+// V_j = wraw / ||wraw||, z = omega V_j (first sweep of the polynomial from z = 0)
+template <class T>
+__global__ void k_normalize_first(const T *__restrict__ wraw, T *__restrict__ vj, T *__restrict__ z, int n,
+                                  const GmresState *__restrict__ st) {
+    if (st->done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        T v = wraw[i] * (T)st->inv_norm;
+        vj[i] = v;
+        z[i] = (T)st->omega * v;
+    }
+}
+
+// t = V y with H y = g (the combination the cycle end adds, before preconditioning)
+template <class T>
+__global__ void __launch_bounds__(256) k_combine(const T *__restrict__ V, int64_t ldv, int nrow, T *__restrict__ t,
+                                                 const GmresState *__restrict__ st) {
+    __shared__ T ys[MAX_RESTART];
+    const int je = st->jend;
+    if (threadIdx.x == 0) {
+        const int M = MAX_RESTART;
+        double yd[MAX_RESTART];
+        for (int k = je - 1; k >= 0; --k) {
+            double s = st->g[k];
+            for (int l = k + 1; l < je; ++l) s -= st->H[k * M + l] * yd[l];
+            yd[k] = s / st->H[k * M + k];
+            ys[k] = (T)yd[k];
+        }
+    }
+    __syncthreads();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nrow; i += gridDim.x * blockDim.x) {
+        T s = (T)0;
+        for (int k = 0; k < je; ++k) s = fma(V[(int64_t)k * ldv + i], ys[k], s);
+        t[i] = s;
+    }
+}
+
+template <class T>
+__global__ void k_axpy_first(const T *__restrict__ t, T *__restrict__ z, int n, const GmresState *__restrict__ st) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) z[i] = (T)st->omega * t[i];
+}
+
+template <class T>
+__global__ void k_add(T *__restrict__ u, const T *__restrict__ z, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) u[i] += z[i];
+}
+
 __global__ void k_to_f32(float *__restrict__ out, const double *__restrict__ a, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = (float)a[i];
@@ -434,26 +502,45 @@ __global__ void k_add_f32(double *__restrict__ u, float *__restrict__ e, int n) 
     if (i < n) { u[i] += (double)e[i]; e[i] = 0.f; }
 }
 
-template <class T>
-void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, int j, T *w, T *wraw, GmresState *st,
-                 double *partial) {
-    const int nrow = (int)ldv;
-    if (pass == 0) APC_LAUNCH(c, K_DOT, nblk, GT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial);
-    else if (pass == 1) APC_LAUNCH(c, K_UPDDOT, nblk, GT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial);
-    else APC_LAUNCH(c, K_UPDNORM, nblk, GT, 0, k_gs_norm<T>, V, ldv, nrow, j, (const T *)w, wraw, st, partial);
-}
-
-int reduction_blocks(apcloud_ctx *c, int n) {
-    (void)c;
+int sm_count() {
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 152;
-    int nb = div_up(n, TILE);
-    int cap = 2 * sms;
-    if (nb > cap) nb = cap;
-    if (nb < 1) nb = 1;
-    return nb;
+    return sms > 0 ? sms : 152;
+}
+
+// dot kernels: 2 fat blocks per SM (few partials for the last block to sum)
+int dot_blocks(int64_t ldv) {
+    int nb = div_up(ldv, TILE), cap = 2 * sm_count();
+    return nb < 1 ? 1 : (nb > cap ? cap : nb);
+}
+
+// row-parallel kernels: up to 8 blocks per SM for memory parallelism
+int stream_blocks(int64_t nrow) {
+    int nb = div_up(nrow / 2, GT), cap = 8 * sm_count();
+    return nb < 1 ? 1 : (nb > cap ? cap : nb);
+}
+
+template <class T>
+void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, int j, T *w, T *wraw, GmresState *st,
+                 double *partial) {
+    (void)nblk;
+    const int nrow = (int)ldv;
+    if (pass == 0) APC_LAUNCH(c, K_DOT, dot_blocks(ldv), DT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial);
+    else if (pass == 1)
+        APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial);
+    else
+        APC_LAUNCH(c, K_UPDNORM, stream_blocks(ldv), GT, 0, k_gs_norm<T>, V, ldv, nrow, j, (const T *)w, wraw, st,
+                   partial);
+}
+
+// grid of the streaming reductions (norms, cycle end); the partial buffer
+// must hold (div_up(n, RT) + 2 * reduction_blocks) * 64 doubles
+int reduction_blocks(apcloud_ctx *c, int n) {
+    (void)c;
+    int64_t ldv = ((int64_t)n + 31) / 32 * 32;
+    int a = stream_blocks(ldv), b = dot_blocks(ldv);
+    return a > b ? a : b;
 }
 
 // Krylov scratch of one GMRES of element type T
@@ -465,7 +552,27 @@ struct Krylov {
     GmresState *st;
     double *partial;
     int nblk;
+    int pdeg = 1;                   // degree of the Jacobi-Neumann polynomial (1 = Jacobi)
+    double omega = 1.0;
+    T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
 };
+
+// z = p(Ahat) v with p(A) = omega sum_{i<d} (I - omega A)^i: d damped Jacobi
+// sweeps from z = 0 (the first one is z = omega v).  Returns the buffer
+// holding z.  v is read with a full row and the sweeps ping-pong z0/z1.
+template <class T>
+T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov<T> &K, GmresState *st) {
+    const int n = c->n_tot;
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    T *cur = z_first, *nxt = (z_first == K.z0) ? K.z1 : K.z0;
+    for (int i = 1; i < K.pdeg; ++i) {
+        APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<3, T>), sw, so, col, val, n, (const T *)cur, nxt,
+                   (T *)nullptr, v, st, (double *)nullptr);
+        T *tmp = cur; cur = nxt; nxt = tmp;
+    }
+    return cur;
+}
 
 // Restarted GMRES(restart) on Ahat u = b, u in/out; no allocation.  Returns
 // OK when ||b - Ahat u|| <= rtol ||b||, W_NOT_CONVERGED at max_iter.
@@ -483,6 +590,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
     APC_CUDA(c, cudaMemsetAsync(K.w, 0, sizeof(T) * (size_t)K.ldv, c->s));
     APC_CUDA(c, cudaMemsetAsync(K.wraw, 0, sizeof(T) * (size_t)K.ldv, c->s));
     APC_CUDA(c, cudaMemcpyAsync(&st->rtol, &rtol, sizeof(double), cudaMemcpyHostToDevice, c->s));
+    APC_CUDA(c, cudaMemcpyAsync(&st->omega, &K.omega, sizeof(double), cudaMemcpyHostToDevice, c->s));
     APC_LAUNCH(c, K_VEC, K.nblk, RT, 0, k_norm2<T>, b, n, st, K.partial);
     int iters = 0, cycles = 0;
     double relres = 0.0;
@@ -498,19 +606,46 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         if (iters >= max_iter) break;
         const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
         for (int j = 0; j < jmax; ++j) {
-            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<1, T>), sw, so, col, val, n, (const T *)K.wraw, K.w,
-                       K.V + (int64_t)j * K.ldv, (const T *)nullptr, st, (double *)nullptr);
+            if (K.pdeg <= 1) {
+                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<1, T>), sw, so, col, val, n, (const T *)K.wraw,
+                           K.w, K.V + (int64_t)j * K.ldv, (const T *)nullptr, st, (double *)nullptr);
+            } else {
+                // w = Ahat p(Ahat) v_j (right preconditioning)
+                T *vj = K.V + (int64_t)j * K.ldv;
+                APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_normalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
+                           (const GmresState *)st);
+                T *z = poly_apply<T>(c, val, vj, K.z0, K, st);
+                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<4, T>), sw, so, col, val, n, (const T *)z, K.w,
+                           (T *)nullptr, (const T *)nullptr, st, (double *)nullptr);
+            }
             gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
             gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
             gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
         }
-        APC_LAUNCH(c, K_CYCLE, K.nblk, GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv, u,
-                   (const GmresState *)st);
+        if (K.pdeg <= 1) {
+            APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv,
+                       u, (const GmresState *)st);
+        } else {
+            // u += p(Ahat) (V y)
+            APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), 256, 0, k_combine<T>, (const T *)K.V, K.ldv, n, K.t,
+                       (const GmresState *)st);
+            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_axpy_first<T>, (const T *)K.t, K.z0, n,
+                       (const GmresState *)st);
+            // the sweeps must run even though the cycle is done: clear the flag for them
+            GmresState *stp = st;
+            APC_CUDA(c, cudaMemsetAsync(&stp->done, 0, sizeof(int), c->s));
+            T *z = poly_apply<T>(c, val, K.t, K.z0, K, st);
+            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add<T>, u, (const T *)z, n);
+        }
         APC_CUDA(c, cudaGetLastError());
         int je;
         APC_TRY(read_back(c, &je, &st->jend, sizeof(int)));
         // algorithmic traffic of the launches that did work (values + column index per entry)
-        account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * (je + 1), 2.0 * nnz * (je + 1));
+        {
+            const double per = (double)(K.pdeg <= 1 ? 1 : K.pdeg);   // SpMV-like passes per Arnoldi step
+            const double cnt = per * je + 1.0 + (K.pdeg <= 1 ? 0.0 : K.pdeg - 1.0);
+            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * cnt, 2.0 * nnz * cnt);
+        }
         for (int j = 0; j < je; ++j) {
             account(c, K_DOT, vb * dn * (j + 2), 2.0 * dn * (j + 1));
             account(c, K_UPDDOT, vb * dn * (j + 3), 4.0 * dn * (j + 1));
@@ -580,6 +715,14 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         Krylov<double> K{ensure<double>(c, c->V, (int64_t)(m + 1) * ldv), ldv, ensure<double>(c, c->w0, ldv + 1),
                          ensure<double>(c, c->w1, ldv + 1), ptr<GmresState>(c->gstate), partial, nblk};
         if (!K.V || !K.w || !K.wraw) return APCLOUD_E_NOMEM;
+        if (c->P.poly_degree > 1) {
+            K.pdeg = c->P.poly_degree;
+            K.omega = c->P.poly_omega;
+            K.z0 = ensure<double>(c, c->pz0, ldv + 1);
+            K.z1 = ensure<double>(c, c->pz1, ldv + 1);
+            K.t = ensure<double>(c, c->pt, ldv + 1);
+            if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
+        }
         status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) return status;
     } else {
@@ -589,6 +732,14 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         double *r64 = ensure<double>(c, c->w0, n + 1);
         GmresState *so = ensure<GmresState>(c, c->gstate2, 1);
         if (!K.V || !K.w || !K.wraw || !r32 || !e32 || !r64 || !so) return APCLOUD_E_NOMEM;
+        if (c->P.poly_degree > 1) {
+            K.pdeg = c->P.poly_degree;
+            K.omega = c->P.poly_omega;
+            K.z0 = ensure<float>(c, c->pz0, ldv + 1);
+            K.z1 = ensure<float>(c, c->pz1, ldv + 1);
+            K.t = ensure<float>(c, c->pt, ldv + 1);
+            if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
+        }
         const float *val32 = ptr<float>(which ? c->ell_A32 : c->ell_B32);
         const uint32_t *sw = ptr<uint32_t>(c->slice_w), *sof = ptr<uint32_t>(c->slice_off);
         const int32_t *col = ptr<int32_t>(c->ell_col);

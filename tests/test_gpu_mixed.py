@@ -66,3 +66,31 @@ def test_mixed_refinement_reaches_fp64_residual():
     assert info["status"] == 0 and info["relres"] <= 1e-12
     r = (b - ap.matvec("A", xs)).cpu().numpy()
     assert np.linalg.norm(r) <= 2e-12 * np.linalg.norm(b.cpu().numpy())
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-10), ("mixed", 1e-6)])
+def test_polynomial_preconditioner_matches_oracle(precision, tol):
+    """The Jacobi-Neumann polynomial preconditioner changes the Krylov path, not
+    the solution: the fields still match the oracle's plain Jacobi solve."""
+    from paper_1603_04039_gb300 import APCloud
+    n = 100000
+    x, y, z, q = inputs.beam_with_halo(n, 5)
+    ap = APCloud(max_depth=6, c_refine=0.5, precision=precision, poly_degree=16, poly_omega=1.0)
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    rtol = 1e-13 if precision == "fp64" else 1e-10
+    rho, ir = ap.deposit(q=_t(q), rtol=rtol)
+    phi, ip = ap.solve(rtol=rtol)
+    php, ex, ey, ez = ap.gather_field()
+    assert ip["status"] == 0 and ip["relres"] <= rtol
+    ref = oracle.Oracle(max_depth=6, c_refine=0.5).run(x, y, z, q=q, rtol=1e-13)
+    assert rel(phi.cpu().numpy(), ref["phi"]) < tol
+    assert rel(php.cpu().numpy(), ref["phi_p"]) < tol
+    assert rel(ex.cpu().numpy(), ref["ex"]) < tol
+    # and it needs far fewer Arnoldi steps than Jacobi alone
+    ap1 = APCloud(max_depth=6, c_refine=0.5, precision=precision)
+    ap1.build_octree(_t(x), _t(y), _t(z))
+    ap1.stencils()
+    ap1.deposit(q=_t(q), rtol=rtol)
+    _, ip1 = ap1.solve(rtol=rtol)
+    assert ip["iters"] * 4 < ip1["iters"]
