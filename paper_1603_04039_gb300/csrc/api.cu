@@ -210,7 +210,7 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->tmp, &c->derr, &c->dsmall,
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
-                    &c->pz0, &c->pz1, &c->pt};
+                    &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16};
     for (DBuf *b : bufs) free_buf(c, *b);
     cudaStreamSynchronize(c->s);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);

@@ -100,6 +100,7 @@ struct apcloud_ctx {
     // matrices (sliced ELL, 32-row slices, column-major inside a slice)
     apc::DBuf slice_w, slice_off, ell_col, ell_A, ell_B, dA, dB;
     apc::DBuf ell_A32, ell_B32;  // FP32 copies for the inner iterations of the mixed form
+    apc::DBuf ell_A16, ell_B16;  // FP16 copies for the preconditioner sweeps of the mixed form
     // solver
     apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state

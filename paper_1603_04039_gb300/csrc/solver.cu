@@ -14,6 +14,8 @@
 // Grid reductions are finished by the last block to arrive (fixed summation
 // order, so results are deterministic).  The host synchronises once per
 // restart cycle.
+#include <cuda_fp16.h>
+
 #include <cmath>
 
 #include "internal.cuh"
@@ -191,6 +193,30 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
             }
         }
     }
+}
+
+// Damped Jacobi sweep of the polynomial preconditioner with FP16 matrix values
+// and FP32 vectors: y = x + omega (b - Ahat x).  The preconditioner only
+// steers the Krylov space (right preconditioning keeps the residual exact),
+// so its 11-bit values cost convergence at most, never accuracy; they cut the
+// sweep's traffic from 8 to 6 bytes per stored entry.
+__global__ void __launch_bounds__(RT) k_sweep_h(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+                                                const int32_t *__restrict__ col, const __half *__restrict__ val,
+                                                int n, const float *__restrict__ x, float *__restrict__ y,
+                                                const float *__restrict__ b, const GmresState *__restrict__ st) {
+    if (st->done) return;
+    const int r = blockIdx.x * RT + threadIdx.x;
+    if (r >= n) return;
+    const float om = (float)st->omega;
+    const int sl = r >> 5, lane = r & 31;
+    const int w = (int)sw[sl];
+    const int64_t base = (int64_t)soff[sl] * 32 + lane;
+    float acc = 0.f;
+    for (int k = 0; k < w; ++k) {
+        const int64_t e = base + (int64_t)k * 32;
+        acc = fmaf(__half2float(val[e]), x[col[e]], acc);
+    }
+    y[r] = fmaf(om, b[r] - acc, x[r]);
 }
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
@@ -554,6 +580,7 @@ struct Krylov {
     int nblk;
     int pdeg = 1;                   // degree of the Jacobi-Neumann polynomial (1 = Jacobi)
     double omega = 1.0;
+    const __half *hval = nullptr;   // FP16 copy of the matrix for the sweeps (FP32 vectors only)
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
 };
 
@@ -567,6 +594,14 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     const int32_t *col = ptr<int32_t>(c->ell_col);
     T *cur = z_first, *nxt = (z_first == K.z0) ? K.z1 : K.z0;
     for (int i = 1; i < K.pdeg; ++i) {
+        if constexpr (sizeof(T) == 4) {
+            if (K.hval) {
+                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_sweep_h, sw, so, col, K.hval, n, (const float *)cur,
+                           (float *)nxt, (const float *)v, (const GmresState *)st);
+                T *tmp = cur; cur = nxt; nxt = tmp;
+                continue;
+            }
+        }
         APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<3, T>), sw, so, col, val, n, (const T *)cur, nxt,
                    (T *)nullptr, v, st, (double *)nullptr);
         T *tmp = cur; cur = nxt; nxt = tmp;
@@ -642,9 +677,13 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         APC_TRY(read_back(c, &je, &st->jend, sizeof(int)));
         // algorithmic traffic of the launches that did work (values + column index per entry)
         {
-            const double per = (double)(K.pdeg <= 1 ? 1 : K.pdeg);   // SpMV-like passes per Arnoldi step
-            const double cnt = per * je + 1.0 + (K.pdeg <= 1 ? 0.0 : K.pdeg - 1.0);
-            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * cnt, 2.0 * nnz * cnt);
+            // per Arnoldi step: one product with the full matrix, pdeg - 1 sweeps (FP16
+            // values when available); the cycle end adds pdeg - 1 sweeps, the restart one product
+            const double sweeps = (K.pdeg <= 1) ? 0.0 : (double)(K.pdeg - 1) * (je + 1);
+            const double prods = je + 1.0;
+            const double sb = K.hval ? 2.0 : vb;
+            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods + ((sb + 4.0) * nnz + 3.0 * vb * dn) * sweeps,
+                    2.0 * nnz * (prods + sweeps));
         }
         for (int j = 0; j < je; ++j) {
             account(c, K_DOT, vb * dn * (j + 2), 2.0 * dn * (j + 1));
@@ -735,6 +774,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         if (c->P.poly_degree > 1) {
             K.pdeg = c->P.poly_degree;
             K.omega = c->P.poly_omega;
+            K.hval = ptr<__half>(which ? c->ell_A16 : c->ell_B16);
             K.z0 = ensure<float>(c, c->pz0, ldv + 1);
             K.z1 = ensure<float>(c, c->pz1, ldv + 1);
             K.t = ensure<float>(c, c->pt, ldv + 1);

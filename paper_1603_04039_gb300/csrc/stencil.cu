@@ -12,6 +12,8 @@
 // column j of P is R^-1 q_j^T W_j, again lane-local.  This replaces the
 // column-by-column Householder reductions of a CPU QR (9 dependent cross-lane
 // reductions) with two Gram products and lane-private triangular solves.
+#include <cuda_fp16.h>
+
 #include <cmath>
 
 #include "internal.cuh"
@@ -490,9 +492,15 @@ __global__ void k_ell_fill(const int32_t *__restrict__ msz, const int32_t *__res
 
 // FP32 copies of the stored (Jacobi-scaled) matrix values for the mixed form
 __global__ void k_values_f32(const double *__restrict__ vA, const double *__restrict__ vB, int64_t n,
-                             float *__restrict__ fA, float *__restrict__ fB) {
+                             float *__restrict__ fA, float *__restrict__ fB, __half *__restrict__ hA,
+                             __half *__restrict__ hB) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) { fA[i] = (float)vA[i]; fB[i] = (float)vB[i]; }
+    if (i < n) {
+        fA[i] = (float)vA[i];
+        fB[i] = (float)vB[i];
+        hA[i] = __double2half(vA[i]);
+        hB[i] = __double2half(vB[i]);
+    }
 }
 
 }  // namespace
@@ -579,9 +587,10 @@ apcloud_status build_stencils(apcloud_ctx *c) {
                ptr<int4>(c->node_ic), dA, dB, n, nt, ext, sw, so, col, vA, vB);
     if (c->P.precision == 1) {
         float *fA = ensure<float>(c, c->ell_A32, c->ell_entries), *fB = ensure<float>(c, c->ell_B32, c->ell_entries);
-        if (!fA || !fB) return APCLOUD_E_NOMEM;
+        __half *hA = ensure<__half>(c, c->ell_A16, c->ell_entries), *hB = ensure<__half>(c, c->ell_B16, c->ell_entries);
+        if (!fA || !fB || !hA || !hB) return APCLOUD_E_NOMEM;
         APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)vA,
-                   (const double *)vB, c->ell_entries, fA, fB);
+                   (const double *)vB, c->ell_entries, fA, fB, hA, hB);
     }
     return cuda_check(c, cudaGetLastError(), "ell");
 }
