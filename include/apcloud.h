@@ -213,6 +213,31 @@ apcloud_status apcloud_field_host(apcloud_ctx *ctx, const double *h_x, const dou
                                   double *h_phi, double *h_ex, double *h_ey, double *h_ez,
                                   apcloud_solve_info *info_rho, apcloud_solve_info *info_phi);
 
+/* ---- time stepping (Vlasov-Poisson, the setting of the paper's title) ----
+ * The paper gives no time integrator; these entry points support a leapfrog
+ * in which every step rebuilds the tree, stencils and systems (Section 4
+ * onward) for the moved particles. */
+
+/* phi at n arbitrary points (device FP64 SoA x, y, z inside the domain) from
+ * this context's last solution: second-order Taylor expansion about the
+ * centre of the point's leaf, as apcloud_gather_field does for particles.
+ * Used to warm-start the next step's solve on a new node set.  Requires
+ * apcloud_gather_field. */
+apcloud_status apcloud_interpolate_potential(apcloud_ctx *ctx, const double *d_x, const double *d_y,
+                                             const double *d_z, int64_t n, double *d_phi);
+
+/* One leapfrog half step on n particles (device FP64 arrays, updated in
+ * place): v += qm_dt * E if the field arrays are given (all three or none),
+ * then x += dt * v with specular reflection at the walls of the cubic domain.
+ * E = grad phi as in Section 2.  Does not need a solved context. */
+apcloud_status apcloud_push_particles(apcloud_ctx *ctx, double *d_x, double *d_y, double *d_z, double *d_vx,
+                                      double *d_vy, double *d_vz, int64_t n, const double *d_ex,
+                                      const double *d_ey, const double *d_ez, double qm_dt, double dt);
+
+/* Field energy 1/2 sum_j |grad phi_j|^2 h_j^3 over the leaves (node gradients
+ * from the last apcloud_gather_field times cell volumes), FP64, fixed order. */
+apcloud_status apcloud_field_energy(apcloud_ctx *ctx, double *h_energy);
+
 /* Per-kernel device timing with CUDA events on the context stream.
  * apcloud_set_timing(ctx, mask) enables timing for the kernel kinds whose
  * bit is set in mask (bit k = kind k, see apcloud_kernel_name), 0 disables.

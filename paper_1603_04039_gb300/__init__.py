@@ -13,4 +13,7 @@ def __getattr__(name):
     if name in ("APCloud", "APCloudError", "kernel_names", "load"):
         from . import _binding
         return getattr(_binding, name)
+    if name == "VlasovPoisson":
+        from .vlasov import VlasovPoisson
+        return VlasovPoisson
     raise AttributeError(name)

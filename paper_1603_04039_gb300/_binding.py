@@ -85,6 +85,9 @@ def load():
             "apcloud_kernel_name": (C.c_char_p, [I]),
             "apcloud_launch_count": (L, [P]),
             "apcloud_get_sizes": (I, [P, P]),
+            "apcloud_interpolate_potential": (I, [P, P, P, P, L, P]),
+            "apcloud_push_particles": (I, [P, P, P, P, P, P, P, L, P, P, P, D, D]),
+            "apcloud_field_energy": (I, [P, C.POINTER(D)]),
             "apcloud_measure_fma_peak": (I, [C.POINTER(D), C.POINTER(D)]),
         }
         for name, (res, args) in sig.items():
@@ -320,6 +323,28 @@ class APCloud:
                                                           C.byref(ip)))
         self.n = n
         return out, {"rho": ir.as_dict(), "phi": ip.as_dict(), "status": st}
+
+    def interpolate_potential(self, x, y, z, out=None):
+        n = x.numel()
+        out = self._empty(n) if out is None else out
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_interpolate_potential(self._ctx, _dptr(x), _dptr(y), _dptr(z), n,
+                                                                _dptr(out)))
+        return out
+
+    def push_particles(self, x, y, z, vx, vy, vz, field=None, qm_dt=0.0, dt=0.0):
+        n = x.numel()
+        ex, ey, ez = field if field is not None else (None, None, None)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_push_particles(self._ctx, _dptr(x), _dptr(y), _dptr(z), _dptr(vx),
+                                                         _dptr(vy), _dptr(vz), n, _dptr(ex), _dptr(ey), _dptr(ez),
+                                                         float(qm_dt), float(dt)))
+
+    def field_energy(self):
+        e = C.c_double()
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_field_energy(self._ctx, C.byref(e)))
+        return e.value
 
     def set_timing(self, mask):
         self._check(self._lib.apcloud_set_timing(self._ctx, int(mask)))

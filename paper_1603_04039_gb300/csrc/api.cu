@@ -450,6 +450,30 @@ apcloud_status apcloud_field_host(apcloud_ctx *c, const double *hx, const double
     return (s1 > 0 || s2 > 0) ? APCLOUD_W_NOT_CONVERGED : APCLOUD_OK;
 }
 
+apcloud_status apcloud_interpolate_potential(apcloud_ctx *c, const double *x, const double *y, const double *z,
+                                             int64_t n, double *phi) {
+    if (!c || n < 0 || (n > 0 && (!x || !y || !z || !phi))) return APCLOUD_E_INVALID;
+    if (c->stage < 5) return fail(c, APCLOUD_E_STATE, "interpolation needs apcloud_gather_field first");
+    if (n == 0) return APCLOUD_OK;
+    return interpolate_phi(c, x, y, z, n, phi);
+}
+
+apcloud_status apcloud_push_particles(apcloud_ctx *c, double *x, double *y, double *z, double *vx, double *vy,
+                                      double *vz, int64_t n, const double *ex, const double *ey, const double *ez,
+                                      double qm_dt, double dt) {
+    if (!c || n < 0 || (n > 0 && (!x || !y || !z || !vx || !vy || !vz))) return APCLOUD_E_INVALID;
+    if ((ex || ey || ez) && !(ex && ey && ez)) return fail(c, APCLOUD_E_INVALID, "field components: all or none");
+    if (!std::isfinite(qm_dt) || !std::isfinite(dt)) return fail(c, APCLOUD_E_INVALID, "non-finite step");
+    if (n == 0) return APCLOUD_OK;
+    return push(c, x, y, z, vx, vy, vz, n, ex, ey, ez, qm_dt, dt);
+}
+
+apcloud_status apcloud_field_energy(apcloud_ctx *c, double *h_energy) {
+    if (!c || !h_energy) return APCLOUD_E_INVALID;
+    if (c->stage < 5) return fail(c, APCLOUD_E_STATE, "field energy needs apcloud_gather_field first");
+    return field_energy(c, h_energy);
+}
+
 apcloud_status apcloud_set_timing(apcloud_ctx *c, unsigned mask) {
     if (!c) return APCLOUD_E_INVALID;
     timer_collect(c);

@@ -110,3 +110,79 @@ apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *e
 }
 
 }  // namespace apc
+
+// ---------------------------------------------------------------- time stepping support
+namespace apc {
+namespace {
+
+// Leapfrog half steps for particles with charge-to-mass ratio qm in the field
+// E = grad phi (Section 2): v += qm dt_kick E, then x += dt_drift v, with
+// specular reflection at the walls of the cubic domain.
+__global__ void k_push(double *__restrict__ x, double *__restrict__ y, double *__restrict__ z,
+                       double *__restrict__ vx, double *__restrict__ vy, double *__restrict__ vz, int64_t n,
+                       const double *__restrict__ ex, const double *__restrict__ ey, const double *__restrict__ ez,
+                       double qm_dt, double dt, double lo, double hi) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double p[3] = {x[i], y[i], z[i]}, v[3] = {vx[i], vy[i], vz[i]};
+    if (ex) { v[0] += qm_dt * ex[i]; v[1] += qm_dt * ey[i]; v[2] += qm_dt * ez[i]; }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        p[d] += dt * v[d];
+        if (p[d] > hi) { p[d] = 2.0 * hi - p[d]; v[d] = -v[d]; }
+        if (p[d] < lo) { p[d] = 2.0 * lo - p[d]; v[d] = -v[d]; }
+        p[d] = fmin(fmax(p[d], lo), hi);
+    }
+    x[i] = p[0]; y[i] = p[1]; z[i] = p[2];
+    vx[i] = v[0]; vy[i] = v[1]; vz[i] = v[2];
+}
+
+// W = 1/2 sum over leaves of |grad phi|^2 h^3 (node derivatives times cell volume),
+// one block, fixed summation order
+__global__ void k_field_energy(const double *__restrict__ nf, const int4 *__restrict__ ic, int n, double ext,
+                               double *__restrict__ out) {
+    __shared__ double sh[1024];
+    double s = 0.0;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double *f = nf + (int64_t)j * NF;
+        double h = ldexp(ext, -ic[j].w);
+        s += (f[1] * f[1] + f[2] * f[2] + f[3] * f[3]) * (h * h * h);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = 0.5 * sh[0];
+}
+
+}  // namespace
+
+apcloud_status interpolate_phi(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,
+                               double *phi) {
+    const double ext = c->P.hi[0] - c->P.lo[0];
+    const double s = ldexp(1.0, KEY_DEPTH) / ext;
+    const double unit = ldexp(ext, -(KEY_DEPTH + 1));
+    APC_LAUNCH(c, K_GATHER, div_up(n, 256), 256, 0, k_gather, x, y, z, n, c->P.lo[0], c->P.lo[1], c->P.lo[2], s,
+               KEY_DEPTH - c->L, unit, ptr<uint64_t>(c->leaf_anchor), c->n_int, ptr<int4>(c->node_ic),
+               ptr<double>(c->nodefield), phi, (double *)nullptr, (double *)nullptr, (double *)nullptr);
+    return cuda_check(c, cudaGetLastError(), "interpolate");
+}
+
+apcloud_status push(apcloud_ctx *c, double *x, double *y, double *z, double *vx, double *vy, double *vz, int64_t n,
+                    const double *ex, const double *ey, const double *ez, double qm_dt, double dt) {
+    APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_push, x, y, z, vx, vy, vz, n, ex, ey, ez, qm_dt, dt, c->P.lo[0],
+               c->P.hi[0]);
+    return cuda_check(c, cudaGetLastError(), "push");
+}
+
+apcloud_status field_energy(apcloud_ctx *c, double *h_out) {
+    double *tmp = ensure<double>(c, c->tmp, 2);
+    if (!tmp) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_VEC, 1, 1024, 0, k_field_energy, ptr<double>(c->nodefield), ptr<int4>(c->node_ic), c->n_int,
+               c->P.hi[0] - c->P.lo[0], tmp);
+    return read_back(c, h_out, tmp, sizeof(double));
+}
+
+}  // namespace apc

@@ -15,7 +15,7 @@ namespace apc {
 constexpr int KEY_DEPTH = 21;   // 63-bit Morton keys (Section 4.3)
 constexpr int NCOL = 9;         // unknowns of the 3-D second-order GFD system (Section 3.1)
 constexpr int MMAX = 32;        // widest stencil, one warp lane per neighbour
-constexpr int MAXC = 768;       // ring candidates held per node in shared memory
+constexpr int MAXC = 512;       // ring candidates held per node in shared memory
 constexpr double RANK_TOL = 1e-6;
 constexpr int MAX_RESTART = 64;
 
@@ -156,6 +156,11 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
                            int max_iter, apcloud_solve_info *info);
 apcloud_status spmv(apcloud_ctx *c, int which, const double *x, double *y, double scale, double *copy_out);
 apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *ey, double *ez);
+apcloud_status interpolate_phi(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,
+                               double *phi);
+apcloud_status push(apcloud_ctx *c, double *x, double *y, double *z, double *vx, double *vy, double *vz, int64_t n,
+                    const double *ex, const double *ey, const double *ez, double qm_dt, double dt);
+apcloud_status field_energy(apcloud_ctx *c, double *h_out);
 
 // ---- device helpers ----
 __host__ __device__ inline uint64_t spread3(uint32_t v) {

@@ -39,7 +39,6 @@ struct WarpSmem {
     double G[48];
     double R1[NCOL * NCOL];
     double R2[NCOL * NCOL];
-    double P[NCOL * MMAX];
     int flag;
     int cut_set;
     long long cut;
@@ -164,10 +163,9 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__
 #pragma unroll
         for (int e = 0; e < NCOL; ++e) row[e] = (T)0;
         if (lane < m) {
-            // xi = dy / h with h = max |dy_d| (Section 3.1), exact integer ratios rounded once
-            T xi0 = (T)((double)off[0] / (double)hint), xi1 = (T)((double)off[1] / (double)hint),
-              xi2 = (T)((double)off[2] / (double)hint);
-            T ratio = (T)((double)mydist / (double)r2max);
+            // xi = dy / h with h = max |dy_d| (Section 3.1): exact integers, one rounding in T
+            T xi0 = (T)off[0] / (T)hint, xi1 = (T)off[1] / (T)hint, xi2 = (T)off[2] / (T)hint;
+            T ratio = (T)mydist / (T)r2max;
             wj = (exp_t(-ratio) - (T)ec) * (T)inv_1mec;
             const T half = (T)0.5;
             row[0] = xi0; row[1] = xi1; row[2] = xi2;
@@ -208,25 +206,31 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__
     rratio = 0.0;
     lapj = 0.0;
     if (!ok) return false;
-    double dmin = 1e300, dmax = 0.0;
+    T dmin = (T)1e30, dmax = (T)0;
 #pragma unroll
     for (int e = 0; e < NCOL; ++e) {
-        double r = fabs((double)R1[e * NCOL + e] * (double)R2[e * NCOL + e]);
+        T r = fabs(R1[e * NCOL + e] * R2[e * NCOL + e]);
         dmin = fmin(dmin, r);
         dmax = fmax(dmax, r);
     }
-    rratio = dmin / dmax;
-    const double h = (double)hint * unit;
-    const double h2 = h * h;
+    rratio = (double)(dmin / dmax);
+    // unscale rows by 1/h and 1/h^2 (h = max |dy_d|), in T
+    const T h = (T)((double)hint * unit);
+    const T ih = (T)1 / h, ih2 = ih * ih;
     if (lane < m) {
 #pragma unroll
         for (int e = 0; e < NCOL; ++e) q[e] = A[lane * ASTR + e];
         row_solve_upper<T>(R2, q);
         col_solve_upper<T>(R2, q);
         col_solve_upper<T>(R1, q);
+        T lj = (T)0;
 #pragma unroll
-        for (int e = 0; e < NCOL; ++e) qout[e] = ((double)q[e] * (double)wj) / (e < 3 ? h : h2);
-        lapj = qout[3] + qout[6] + qout[8];
+        for (int e = 0; e < NCOL; ++e) {
+            const T v = (q[e] * wj) * (e < 3 ? ih : ih2);
+            qout[e] = (double)v;
+            if (e == 3 || e == 6 || e == 8) lj += v;
+        }
+        lapj = (double)lj;
     } else {
 #pragma unroll
         for (int e = 0; e < NCOL; ++e) qout[e] = 0.0;
@@ -234,7 +238,7 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__
     return true;
 }
 
-__global__ void __launch_bounds__(SW * 32) k_stencil(
+__global__ void __launch_bounds__(SW * 32, 3) k_stencil(
     const int4 *__restrict__ ic, const int32_t *__restrict__ adj, const int32_t *__restrict__ bowner, int n_int,
     int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
     int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,
@@ -382,8 +386,7 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
             if (m >= nc - 1) break;
             continue;
         }
-#pragma unroll
-        for (int e = 0; e < NCOL; ++e) W.P[e * MMAX + lane] = (lane < m) ? q[e] : 0.0;
+
         nbr_out[(int64_t)y0 * MMAX + lane] = (lane < m) ? W.sel[lane] : -1;
         lap_out[(int64_t)y0 * MMAX + lane] = lapj;
         if (lane == 0) {
@@ -395,7 +398,7 @@ __global__ void __launch_bounds__(SW * 32) k_stencil(
         __syncwarp();
         // derivative operator, row-of-operator major with nodes fastest
 #pragma unroll
-        for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = W.P[e * MMAX + lane];
+        for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = (lane < m) ? q[e] : 0.0;
         ring = k;
         done = true;
         }   // target sizes

@@ -109,3 +109,9 @@ def grid_points(depth: int, lo: float = -1.0, hi: float = 1.0):
     gx, gy, gz = np.meshgrid(c, c, c, indexing="ij")
     n = k ** 3
     return (gx.ravel().copy(), gy.ravel().copy(), gz.ravel().copy(), np.full(n, 1.0 / n))
+
+
+def thermal_velocities(n: int, seed: int, sigma_v: float = 0.01):
+    """(vx, vy, vz): independent N(0, sigma_v^2) components (stream 5)."""
+    g = _normals(seed, 5, 3 * int(n), 0).reshape(-1, 3) * sigma_v if n else np.zeros((0, 3))
+    return tuple(np.ascontiguousarray(g[:, d]) for d in range(3))
