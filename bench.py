@@ -36,6 +36,22 @@ WORKLOADS = {
     "beam_halo_1e7_depth10": (10_000_000, 10, 0.043),
     "beam_halo_1e5_depth6": (100_000, 6, 1.0),
 }
+BATCH_WORKLOADS = {
+    # name: (beams, max_depth, c_refine); particle counts log-uniform in [1e4, 1e6]
+    "beam_batch_64_depth9": (64, 9, 0.05),
+}
+
+
+def make_problem(workload, seed):
+    """(x, y, z, q, offsets or None, max_depth, c_refine, solves per step)"""
+    from paper_1603_04039_gb300 import inputs
+    if workload in BATCH_WORKLOADS:
+        nb, depth, c = BATCH_WORKLOADS[workload]
+        x, y, z, q, offs, _ = inputs.beam_batch(nb, seed)
+        return x, y, z, q, offs, depth, c, nb
+    npart, depth, c = WORKLOADS[workload]
+    x, y, z, q = inputs.beam_with_halo(npart, seed)
+    return x, y, z, q, None, depth, c, 1
 RTOL = 1e-10
 MAX_ITER = 200000
 
@@ -117,10 +133,15 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     fp64_peak, fp32_peak = measure_fma_peak()
-    npart, depth, c = WORKLOADS[args.workload]
     seed = 1 + rank
-    x, y, z, q = inputs.beam_with_halo(npart, seed)
+    x, y, z, q, offs, depth, c, nsolve = make_problem(args.workload, seed)
+    npart = len(x)
     tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
+
+    def build(a):
+        if offs is None:
+            return a.build_octree(tx, ty, tz)
+        return a.build_octree_batched(tx, ty, tz, offs)
     form = dict(max_depth=depth, c_refine=c, restart=30, precision=args.precision, poly_degree=args.poly_degree,
                 poly_omega=args.poly_omega, device=dev)
     ap = APCloud(**form)
@@ -129,7 +150,7 @@ def run_ours(args, ws, rank, local):
     info = {}
 
     def step():
-        ni, nb = ap.build_octree(tx, ty, tz)
+        ni, nb = build(ap)
         ap.stencils()
         _, ir = ap.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
         _, ip = ap.solve(rtol=RTOL, max_iter=MAX_ITER)
@@ -188,12 +209,12 @@ def run_ours(args, ws, rank, local):
     hx, hy, hz, hq = (torch.from_numpy(a).pin_memory() for a in (x, y, z, q))
     hout = tuple(torch.empty(npart, dtype=torch.float64).pin_memory() for _ in range(4))
     ap_e2e = APCloud(**form)
-    ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout)   # warm-up
+    ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout, offsets=offs)   # warm-up
     barrier()
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout)
+        ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout, offsets=offs)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if ws > 1:
         t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
@@ -211,7 +232,7 @@ def run_ours(args, ws, rank, local):
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(ap64.stream)
-        ap64.build_octree(tx, ty, tz)
+        build(ap64)
         ap64.stencils()
         _, pr = ap64.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
         _, pp = ap64.solve(rtol=RTOL, max_iter=MAX_ITER)
@@ -220,9 +241,34 @@ def run_ours(args, ws, rank, local):
         torch.cuda.synchronize()
         plain = {"ms_per_step": round(f0.elapsed_time(f1), 2), "iters_phi": pp["iters"], "iters_rho": pr["iters"],
                  "relres_phi": pp["relres"]}
-    errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(out, ref)]
+    if offs is None:
+        errs = [float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(out, ref)]
+    else:   # the worst beam
+        errs = [float(torch.linalg.norm(a[s:e] - b[s:e]) / torch.linalg.norm(b[s:e]))
+                for a, b in zip(out, ref) for s, e in zip(offs[:-1], offs[1:]) if e > s]
     rel_l2 = max(errs) if (args.precision != "fp64" or args.poly_degree > 1) else 0.0
     ap64.close()
+    unbatched = None
+    if offs is not None:
+        # the same form solving the beams one at a time (one context, same stream)
+        ap1 = APCloud(**form)
+        u0 = torch.cuda.Event(enable_timing=True)
+        u1 = torch.cuda.Event(enable_timing=True)
+        views = [(tx[s:e], ty[s:e], tz[s:e], tq[s:e]) for s, e in zip(offs[:-1], offs[1:])]
+        for rep in range(2):
+            u0.record(ap1.stream)
+            for bx, by, bz, bq in views:
+                ap1.build_octree(bx, by, bz)
+                ap1.stencils()
+                ap1.deposit(q=bq, rtol=RTOL, max_iter=MAX_ITER)
+                ap1.solve(rtol=RTOL, max_iter=MAX_ITER)
+                ap1.gather_field()
+            u1.record(ap1.stream)
+            torch.cuda.synchronize()
+        ms_u = u0.elapsed_time(u1)
+        unbatched = {"ms_per_batch": round(ms_u, 2), "solves_per_s": round(nsolve * 1000.0 / ms_u, 4),
+                     "speedup_of_batching": round(ms_u / ms_step, 2)}
+        ap1.close()
 
     # roofline of the dominant kernel, measured live in the timed region
     peaks = _measured_peaks()
@@ -250,13 +296,13 @@ def run_ours(args, ws, rank, local):
                  "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64/FP32 FMA chains on all SMs "
                                 "(apcloud_measure_fma_peak) in this run",
                  "fp64_peak_tflops": round(fp64_peak, 4), "fp32_peak_tflops": round(fp32_peak, 3)})
-    solves = ws * 1000.0 / ms_step
+    solves = ws * nsolve * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(solves, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic", "rel_l2_vs_fp64": rel_l2,
-        "config": {"workload": args.workload, "particles": npart, "max_depth": depth, "c_refine": c,
+        "config": {"workload": args.workload, "particles": npart, "beams": nsolve, "max_depth": depth, "c_refine": c,
                    "n_nodes": n_nodes, "n_interior": info["n_int"], "precision": args.precision,
                    "solver": ("GMRES(30), right preconditioner " +
                               ("Jacobi" if args.poly_degree <= 1 else
@@ -269,11 +315,12 @@ def run_ours(args, ws, rank, local):
                    "nnz": sz["nnz"], "ell_fill": round(sz["nnz"] / max(1, sz["ell_entries"]), 4),
                    "parallelism": "independent beam per GPU" if ws > 1 else "single GPU"},
         "nodes_iters_per_s": round(ws * n_nodes * (iters_total / args.steps) / (ms_step * 1e-3), 1),
-        "e2e": {"value": round(ws / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,
+        "e2e": {"value": round(ws * nsolve / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,
                 "d2h_bytes_per_step": 32 * npart},
         "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
-        "plain_fp64_form": dict(plain, solves_per_s=round(1000.0 / plain["ms_per_step"], 4),
-                                speedup_of_this_form=round((1000.0 / ms_step) / (1000.0 / plain["ms_per_step"]), 2)),
+        "plain_fp64_form": dict(plain, solves_per_s=round(nsolve * 1000.0 / plain["ms_per_step"], 4),
+                                speedup_of_this_form=round(plain["ms_per_step"] / ms_step, 2)),
+        "unbatched_same_form": unbatched,
         "stage_ms_by_kernel": {k: round(v[0] / 1, 3) for k, v in solve_kinds.items()},
     }
     return line
@@ -286,9 +333,9 @@ def oracle_sample(workload, seed=1, gmres_sample=10, gmres_iters_hint=None):
     to the iteration counts of a converged solve.  Returns (seconds per solve,
     description)."""
     import oracle
-    from paper_1603_04039_gb300 import inputs
-    npart, depth, c = WORKLOADS[workload]
-    x, y, z, q = inputs.beam_with_halo(npart, seed)
+    x, y, z, q, offs, depth, c, nsolve = make_problem(workload, seed)
+    if offs is not None:
+        return oracle_batch_sample(workload, x, y, z, q, offs, depth, c)
     o = oracle.Oracle(max_depth=depth, c_refine=c)
     t = {}
     t0 = time.perf_counter(); o.build(x, y, z); t["build"] = time.perf_counter() - t0
@@ -312,6 +359,33 @@ def oracle_sample(workload, seed=1, gmres_sample=10, gmres_iters_hint=None):
     return total, desc, {k: round(v, 3) for k, v in t.items()}
 
 
+def oracle_batch_sample(workload, x, y, z, q, offs, depth, c, n_sample=3):
+    """Batch workload: full oracle solves (GMRES to convergence) of the
+    n_sample smallest beams, scaled to the whole batch by particle count.  The
+    oracle's cost grows faster than the particle count (more nodes need more
+    iterations), so this underestimates its time on the larger beams."""
+    import oracle
+    sizes = np.diff(offs)
+    pick = np.argsort(sizes, kind="stable")[:n_sample]
+    t = {"build": 0.0, "stencils": 0.0, "deposit": 0.0, "solve_rho": 0.0, "solve_phi": 0.0, "gather": 0.0}
+    for b in pick:
+        s, e = offs[b], offs[b + 1]
+        o = oracle.Oracle(max_depth=depth, c_refine=c)
+        bx, by, bz, bq = (np.ascontiguousarray(a[s:e]) for a in (x, y, z, q))
+        t0 = time.perf_counter(); o.build(bx, by, bz); t["build"] += time.perf_counter() - t0
+        t0 = time.perf_counter(); o.stencils(); t["stencils"] += time.perf_counter() - t0
+        t0 = time.perf_counter(); rhs, _, _ = o.density_rhs(bq); t["deposit"] += time.perf_counter() - t0
+        t0 = time.perf_counter(); rho, _, _, _ = o.solve_density(rhs, rtol=RTOL); t["solve_rho"] += time.perf_counter() - t0
+        t0 = time.perf_counter(); phi, _, _, _ = o.solve_poisson(rho, rtol=RTOL); t["solve_phi"] += time.perf_counter() - t0
+        t0 = time.perf_counter(); o.gather(phi); t["gather"] += time.perf_counter() - t0
+    scale = float(sizes.sum()) / float(sizes[pick].sum())
+    total = sum(t.values()) * scale
+    desc = ("oracle on %s: full solves of the %d smallest beams (%d particles), scaled by particle count to the "
+            "batch's %d particles (%d beams)" % (workload, n_sample, int(sizes[pick].sum()), int(sizes.sum()),
+                                                 len(sizes)))
+    return total / len(sizes), desc, {k: round(v * scale, 3) for k, v in t.items()}
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return None
@@ -331,18 +405,103 @@ def run_reference(args, ws, rank):
             "e2e": {"value": round(val, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_vp(args):
+    """Time-dependent workload: leapfrog steps with a full rebuild and solve each
+    step (1e7 particles, thermal velocities sigma_v = 0.01, dt = 1e-3), warm
+    start from the previous potential.  Reports steps/s, the drift of the total
+    (field + kinetic) energy, and a 10-step comparison with the FP64 oracle on
+    a bounded sample (2e5 particles of the same law)."""
+    import torch
+
+    from paper_1603_04039_gb300 import VlasovPoisson, inputs
+    dev = torch.device("cuda", 0)
+    npart, depth, c = WORKLOADS["beam_halo_1e7_depth10"]
+    x, y, z, q = inputs.beam_with_halo(npart, 1)
+    vel = inputs.thermal_velocities(npart, 1, 0.01)
+    t = [torch.from_numpy(a).to(dev) for a in (x, y, z) + vel]
+    form = dict(max_depth=depth, c_refine=c, precision=args.precision, poly_degree=args.poly_degree,
+                poly_omega=args.poly_omega)
+    vp = VlasovPoisson(*t, qm=1.0, rtol=RTOL, **form)
+    dt = 1e-3
+    for _ in range(args.warmup):
+        vp.step(dt)
+    w0, k0 = vp.energies()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = 0
+    for _ in range(args.steps):
+        vp.step(dt)
+        iters += vp.info["iters_phi"]
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    w1, k1 = vp.energies()
+    # bounded oracle comparison: 10 steps on 2e5 particles, GPU vs oracle-driven leapfrog
+    import oracle
+    ns, ds, cs = 200000, 7, 0.2
+    xs, ys, zs, _ = inputs.beam_with_halo(ns, 2)
+    vs = inputs.thermal_velocities(ns, 2, 0.01)
+    ts = [torch.from_numpy(a.copy()).to(dev) for a in (xs, ys, zs) + vs]
+    vps = VlasovPoisson(*ts, qm=1.0, rtol=RTOL, max_depth=ds, c_refine=cs, precision=args.precision,
+                        poly_degree=args.poly_degree, poly_omega=args.poly_omega)
+    ws_gpu = [vps.energies()[0]]
+    for _ in range(10):
+        vps.step(dt)
+        ws_gpu.append(vps.energies()[0])
+    px, py, pz, pvx, pvy, pvz = (a.copy() for a in (xs, ys, zs) + vs)
+
+    def oracle_field():
+        o = oracle.Oracle(max_depth=ds, c_refine=cs)
+        r = o.run(px, py, pz, q_uniform=1.0 / ns, rtol=RTOL)
+        h = 2.0 / 2.0 ** o.nodes()["level"][: o.n_int].astype(float)
+        return (r["ex"], r["ey"], r["ez"]), 0.5 * float(((r["dphi"][:, :3] ** 2).sum(1) * h ** 3).sum())
+
+    t_or = time.perf_counter()
+    E, w = oracle_field()
+    ws_ref = [w]
+    for _ in range(10):                       # velocity Verlet, specular walls
+        for v, e in zip((pvx, pvy, pvz), E):
+            v += 0.5 * dt * e
+        for p_, v in zip((px, py, pz), (pvx, pvy, pvz)):
+            p_ += dt * v
+            hi, lo = p_ > 1.0, p_ < -1.0
+            p_[hi] = 2.0 - p_[hi]; v[hi] = -v[hi]
+            p_[lo] = -2.0 - p_[lo]; v[lo] = -v[lo]
+        E, w = oracle_field()
+        ws_ref.append(w)
+        for v, e in zip((pvx, pvy, pvz), E):
+            v += 0.5 * dt * e
+    t_or = time.perf_counter() - t_or
+    dw = np.max(np.abs(np.array(ws_gpu) - np.array(ws_ref)) / np.abs(ws_ref))
+    return {"metric": "Vlasov-Poisson leapfrog steps/sec (rebuild + solve every step)",
+            "value": round(args.steps / el, 4), "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "vp_beam_halo_1e7_depth10", "particles": npart, "dt": dt, "sigma_v": 0.01,
+                       "precision": args.precision, "poly_degree": args.poly_degree,
+                       "mean_gmres_iters": iters / args.steps},
+            "energy": {"field_start": w0, "kinetic_start": k0, "field_end": w1, "kinetic_end": k1,
+                       "total_drift_rel": (w1 + k1 - w0 - k0) / (w0 + k0)},
+            "oracle_10_steps": {"particles": ns, "max_rel_field_energy_diff": float(dw),
+                                "oracle_seconds": round(t_or, 1)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="beam_halo_1e7_depth10", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="beam_halo_1e7_depth10", choices=sorted(WORKLOADS) + sorted(BATCH_WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--poly-degree", type=int, default=16, help="1 = Jacobi")
     ap.add_argument("--poly-omega", type=float, default=1.0)
+    ap.add_argument("--vp", action="store_true", help="Vlasov-Poisson leapfrog workload instead of single solves")
     args = ap.parse_args()
+    if args.vp:
+        print(json.dumps(run_vp(args)))
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     ws, rank, local = _dist()

@@ -116,6 +116,29 @@ const char *apcloud_last_error(const apcloud_ctx *ctx);
 apcloud_status apcloud_build_octree(apcloud_ctx *ctx, const double *d_x, const double *d_y, const double *d_z,
                                     int64_t n, int64_t *n_interior, int64_t *n_boundary);
 
+/* Batch of independent problems ("beams"): n_beams particle sets that share
+ * the domain and the parameters, beam b holding particles
+ * h_offsets[b] .. h_offsets[b+1]-1 of d_x, d_y, d_z (h_offsets: host array of
+ * n_beams + 1 non-decreasing entries, h_offsets[0] = 0).  Each beam gets the
+ * octree, node set, stencils and linear systems it would get alone (Sections
+ * 3-4 per beam); the beams are laid out as one block-diagonal problem, so
+ * every later call (stencils, deposit, solve, gather) processes all beams in
+ * the same launches.  Interior nodes are ordered by beam, then Morton order;
+ * boundary nodes by face, then owner leaf.  Leaf keys (apcloud_get_leaves)
+ * carry the beam index above the 3*level Morton bits.  A solve in a batch
+ * stops when ||r|| <= rtol * min_b ||b_b||, which bounds every beam's own
+ * relative residual by rtol.  The paper treats one problem at a time; the
+ * batch is this library's.  Errors: APCLOUD_E_INVALID for bad offsets or
+ * when 3*max_depth plus the bits of n_beams - 1 exceed 63. */
+#define APCLOUD_MAX_BEAMS 65536
+apcloud_status apcloud_build_octree_batched(apcloud_ctx *ctx, const double *d_x, const double *d_y,
+                                            const double *d_z, const int64_t *h_offsets, int n_beams,
+                                            int64_t *n_interior, int64_t *n_boundary);
+
+/* Beam index of every node after an octree build (device int32, n_nodes
+ * entries; boundary nodes take their owner leaf's beam).  Synchronises. */
+apcloud_status apcloud_get_node_beams(apcloud_ctx *ctx, int32_t *d_beam);
+
 /* Node geometry after apcloud_build_octree, device outputs of n_nodes =
  * n_interior + n_boundary entries (any may be NULL): d_xyz FP64 [n_nodes][3]
  * centres, d_level int8 (owner's level for boundary nodes), d_kind int8
@@ -213,6 +236,15 @@ apcloud_status apcloud_field_host(apcloud_ctx *ctx, const double *h_x, const dou
                                   double *h_phi, double *h_ex, double *h_ey, double *h_ez,
                                   apcloud_solve_info *info_rho, apcloud_solve_info *info_phi);
 
+/* apcloud_field_host for a batch of beams (see apcloud_build_octree_batched):
+ * h_offsets (host, n_beams + 1 entries) splits the h_offsets[n_beams]
+ * particles into beams; outputs are in the input order. */
+apcloud_status apcloud_field_host_batched(apcloud_ctx *ctx, const double *h_x, const double *h_y,
+                                          const double *h_z, const double *h_q, double q_uniform,
+                                          const int64_t *h_offsets, int n_beams, double rtol, int max_iter,
+                                          double *h_phi, double *h_ex, double *h_ey, double *h_ez,
+                                          apcloud_solve_info *info_rho, apcloud_solve_info *info_phi);
+
 /* ---- time stepping (Vlasov-Poisson, the setting of the paper's title) ----
  * The paper gives no time integrator; these entry points support a leapfrog
  * in which every step rebuilds the tree, stencils and systems (Section 4
@@ -222,7 +254,8 @@ apcloud_status apcloud_field_host(apcloud_ctx *ctx, const double *h_x, const dou
  * this context's last solution: second-order Taylor expansion about the
  * centre of the point's leaf, as apcloud_gather_field does for particles.
  * Used to warm-start the next step's solve on a new node set.  Requires
- * apcloud_gather_field. */
+ * apcloud_gather_field on a single-beam context (APCLOUD_E_INVALID for a
+ * batch). */
 apcloud_status apcloud_interpolate_potential(apcloud_ctx *ctx, const double *d_x, const double *d_y,
                                              const double *d_z, int64_t n, double *d_phi);
 

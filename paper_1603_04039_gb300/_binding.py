@@ -66,6 +66,8 @@ def load():
             "apcloud_destroy": (None, [P]),
             "apcloud_last_error": (C.c_char_p, [P]),
             "apcloud_build_octree": (I, [P, P, P, P, L, C.POINTER(L), C.POINTER(L)]),
+            "apcloud_build_octree_batched": (I, [P, P, P, P, C.POINTER(L), I, C.POINTER(L), C.POINTER(L)]),
+            "apcloud_get_node_beams": (I, [P, P]),
             "apcloud_get_nodes": (I, [P, P, P, P]),
             "apcloud_get_leaves": (I, [P, P, P, P]),
             "apcloud_stencils": (I, [P]),
@@ -80,6 +82,8 @@ def load():
             "apcloud_solve_system_noalloc": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo)]),
             "apcloud_field_host": (I, [P, P, P, P, P, D, L, D, I, P, P, P, P, C.POINTER(SolveInfo),
                                        C.POINTER(SolveInfo)]),
+            "apcloud_field_host_batched": (I, [P, P, P, P, P, D, C.POINTER(L), I, D, I, P, P, P, P,
+                                               C.POINTER(SolveInfo), C.POINTER(SolveInfo)]),
             "apcloud_set_timing": (I, [P, C.c_uint]),
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
@@ -200,6 +204,29 @@ class APCloud:
         self.n, self.n_int, self.n_bnd = n, ni.value, nb.value
         return self.n_int, self.n_bnd
 
+    def build_octree_batched(self, x, y, z, offsets):
+        """Independent beams: beam b holds particles offsets[b]:offsets[b+1]."""
+        n = x.numel()
+        for t in (x, y, z):
+            _f64(t, n)
+        offs = [int(o) for o in offsets]
+        if len(offs) < 2 or offs[-1] != n:
+            raise ValueError("offsets must have n_beams + 1 entries ending at the particle count")
+        arr = (C.c_int64 * len(offs))(*offs)
+        self._pos = (x, y, z)
+        ni, nb = C.c_int64(), C.c_int64()
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_build_octree_batched(self._ctx, _dptr(x), _dptr(y), _dptr(z), arr,
+                                                               len(offs) - 1, C.byref(ni), C.byref(nb)))
+        self.n, self.n_int, self.n_bnd = n, ni.value, nb.value
+        return self.n_int, self.n_bnd
+
+    def get_node_beams(self):
+        out = self._empty(self.n_nodes, dtype=torch.int32)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_get_node_beams(self._ctx, _dptr(out)))
+        return out
+
     def get_nodes(self):
         xyz = self._empty(self.n_nodes, 3)
         lv = self._empty(self.n_nodes, dtype=torch.int8)
@@ -299,8 +326,9 @@ class APCloud:
                                                                     _dptr(x), rtol, int(max_iter), C.byref(info)))
         return dict(info.as_dict(), status=st)
 
-    def field_host(self, x, y, z, q=None, q_uniform=None, rtol=1e-10, max_iter=100000, out=None):
-        """Whole solve on host numpy arrays (pinned tensors are also accepted)."""
+    def field_host(self, x, y, z, q=None, q_uniform=None, rtol=1e-10, max_iter=100000, out=None, offsets=None):
+        """Whole solve on host numpy arrays (pinned tensors are also accepted);
+        ``offsets`` (n_beams + 1 entries) makes it a batch of beams."""
         def hp(a):
             if a is None:
                 return None
@@ -317,10 +345,19 @@ class APCloud:
         keep = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a for a in (x, y, z, q)]
         ir, ip = SolveInfo(), SolveInfo()
         with torch.cuda.device(self.device):
-            st = self._check(self._lib.apcloud_field_host(self._ctx, hp(keep[0]), hp(keep[1]), hp(keep[2]),
-                                                          hp(keep[3]), float(q_uniform or 0.0), n, rtol,
-                                                          int(max_iter), *[hp(o) for o in out], C.byref(ir),
-                                                          C.byref(ip)))
+            if offsets is None:
+                st = self._check(self._lib.apcloud_field_host(self._ctx, hp(keep[0]), hp(keep[1]), hp(keep[2]),
+                                                              hp(keep[3]), float(q_uniform or 0.0), n, rtol,
+                                                              int(max_iter), *[hp(o) for o in out], C.byref(ir),
+                                                              C.byref(ip)))
+            else:
+                offs = [int(o) for o in offsets]
+                if len(offs) < 2 or offs[0] != 0 or offs[-1] != n:
+                    raise ValueError("offsets must run from 0 to the particle count")
+                arr = (C.c_int64 * len(offs))(*offs)
+                st = self._check(self._lib.apcloud_field_host_batched(
+                    self._ctx, hp(keep[0]), hp(keep[1]), hp(keep[2]), hp(keep[3]), float(q_uniform or 0.0), arr,
+                    len(offs) - 1, rtol, int(max_iter), *[hp(o) for o in out], C.byref(ir), C.byref(ip)))
         self.n = n
         return out, {"rho": ir.as_dict(), "phi": ip.as_dict(), "status": st}
 

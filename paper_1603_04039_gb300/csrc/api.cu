@@ -210,7 +210,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->tmp, &c->derr, &c->dsmall,
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
-                    &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16};
+                    &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
+                    &c->beam_rng, &c->beam_norm};
     for (DBuf *b : bufs) free_buf(c, *b);
     cudaStreamSynchronize(c->s);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);
@@ -226,12 +227,41 @@ apcloud_status apcloud_build_octree(apcloud_ctx *c, const double *x, const doubl
     if (n < 0 || n > 2000000000LL) return fail(c, APCLOUD_E_INVALID, "particle count %lld out of range", (long long)n);
     if (n > 0 && (!x || !y || !z)) return fail(c, APCLOUD_E_INVALID, "null position array");
     c->stage = 0;
-    apcloud_status st = build_octree(c, x, y, z, n);
+    const int64_t off[2] = {0, n};
+    apcloud_status st = build_octree(c, x, y, z, n, off, 1);
     if (st < 0) return st;
     c->stage = 1;
     if (n_interior) *n_interior = c->n_int;
     if (n_boundary) *n_boundary = c->n_bnd;
     return APCLOUD_OK;
+}
+
+apcloud_status apcloud_build_octree_batched(apcloud_ctx *c, const double *x, const double *y, const double *z,
+                                            const int64_t *offsets, int n_beams, int64_t *n_interior,
+                                            int64_t *n_boundary) {
+    if (!c) return APCLOUD_E_INVALID;
+    if (n_beams < 1 || n_beams > APCLOUD_MAX_BEAMS || !offsets)
+        return fail(c, APCLOUD_E_INVALID, "n_beams must be in 1..%d with an offsets array", APCLOUD_MAX_BEAMS);
+    if (offsets[0] != 0) return fail(c, APCLOUD_E_INVALID, "offsets[0] must be 0");
+    for (int b = 0; b < n_beams; ++b)
+        if (offsets[b + 1] < offsets[b]) return fail(c, APCLOUD_E_INVALID, "offsets must not decrease (beam %d)", b);
+    const int64_t n = offsets[n_beams];
+    if (n > 2000000000LL) return fail(c, APCLOUD_E_INVALID, "particle count %lld out of range", (long long)n);
+    if (n > 0 && (!x || !y || !z)) return fail(c, APCLOUD_E_INVALID, "null position array");
+    c->stage = 0;
+    apcloud_status st = build_octree(c, x, y, z, n, offsets, n_beams);
+    if (st < 0) return st;
+    c->stage = 1;
+    if (n_interior) *n_interior = c->n_int;
+    if (n_boundary) *n_boundary = c->n_bnd;
+    return APCLOUD_OK;
+}
+
+apcloud_status apcloud_get_node_beams(apcloud_ctx *c, int32_t *beam) {
+    if (!c || !beam) return APCLOUD_E_INVALID;
+    if (c->stage < 1) return fail(c, APCLOUD_E_STATE, "node beams are available after apcloud_build_octree");
+    APC_TRY(node_beams(c, beam));
+    return cuda_check(c, cudaStreamSynchronize(c->s), "get_node_beams");
 }
 
 apcloud_status apcloud_get_nodes(apcloud_ctx *c, double *xyz, int8_t *level, int8_t *kind);
@@ -413,10 +443,10 @@ apcloud_status apcloud_solve_system(apcloud_ctx *c, int which, const double *b, 
     return gmres_solve(c, which, b, x, rtol, max_iter, info);
 }
 
-apcloud_status apcloud_field_host(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
-                                  const double *hq, double q_uniform, int64_t n, double rtol, int max_iter,
-                                  double *hphi, double *hex, double *hey, double *hez, apcloud_solve_info *ir,
-                                  apcloud_solve_info *ip) {
+static apcloud_status field_host(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
+                                 const double *hq, double q_uniform, int64_t n, const int64_t *offsets, int nbeams,
+                                 double rtol, int max_iter, double *hphi, double *hex, double *hey, double *hez,
+                                 apcloud_solve_info *ir, apcloud_solve_info *ip) {
     if (!c) return APCLOUD_E_INVALID;
     if (n < 0 || (n > 0 && (!hx || !hy || !hz))) return fail(c, APCLOUD_E_INVALID, "bad host particle arrays");
     size_t nb = (size_t)(n > 0 ? n : 1) * sizeof(double);
@@ -433,7 +463,8 @@ apcloud_status apcloud_field_host(apcloud_ctx *c, const double *hx, const double
         if (hq) APC_CUDA(c, cudaMemcpyAsync(dq, hq, nb, cudaMemcpyHostToDevice, c->s));
     }
     int64_t ni, nbd;
-    APC_TRY(apcloud_build_octree(c, dx, dy, dz, n, &ni, &nbd));
+    if (offsets) APC_TRY(apcloud_build_octree_batched(c, dx, dy, dz, offsets, nbeams, &ni, &nbd));
+    else APC_TRY(apcloud_build_octree(c, dx, dy, dz, n, &ni, &nbd));
     APC_TRY(apcloud_stencils(c));
     apcloud_status s1 = apcloud_deposit(c, dq, q_uniform, rtol, max_iter, nullptr, ir);
     if (s1 < 0) return s1;
@@ -450,10 +481,28 @@ apcloud_status apcloud_field_host(apcloud_ctx *c, const double *hx, const double
     return (s1 > 0 || s2 > 0) ? APCLOUD_W_NOT_CONVERGED : APCLOUD_OK;
 }
 
+apcloud_status apcloud_field_host(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
+                                  const double *hq, double q_uniform, int64_t n, double rtol, int max_iter,
+                                  double *hphi, double *hex, double *hey, double *hez, apcloud_solve_info *ir,
+                                  apcloud_solve_info *ip) {
+    return field_host(c, hx, hy, hz, hq, q_uniform, n, nullptr, 1, rtol, max_iter, hphi, hex, hey, hez, ir, ip);
+}
+
+apcloud_status apcloud_field_host_batched(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
+                                          const double *hq, double q_uniform, const int64_t *offsets, int n_beams,
+                                          double rtol, int max_iter, double *hphi, double *hex, double *hey,
+                                          double *hez, apcloud_solve_info *ir, apcloud_solve_info *ip) {
+    if (!c) return APCLOUD_E_INVALID;
+    if (!offsets || n_beams < 1) return fail(c, APCLOUD_E_INVALID, "a batch needs n_beams >= 1 and offsets");
+    return field_host(c, hx, hy, hz, hq, q_uniform, offsets[n_beams], offsets, n_beams, rtol, max_iter, hphi, hex,
+                      hey, hez, ir, ip);
+}
+
 apcloud_status apcloud_interpolate_potential(apcloud_ctx *c, const double *x, const double *y, const double *z,
                                              int64_t n, double *phi) {
     if (!c || n < 0 || (n > 0 && (!x || !y || !z || !phi))) return APCLOUD_E_INVALID;
     if (c->stage < 5) return fail(c, APCLOUD_E_STATE, "interpolation needs apcloud_gather_field first");
+    if (c->nbeams > 1) return fail(c, APCLOUD_E_INVALID, "interpolation needs a single-beam context");
     if (n == 0) return APCLOUD_OK;
     return interpolate_phi(c, x, y, z, n, phi);
 }

@@ -55,7 +55,7 @@ __device__ __forceinline__ int leaf_of(const uint64_t *anchor, int n, uint64_t v
 
 __global__ void k_gather(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                          int64_t n, double lo0, double lo1, double lo2, double s, int shift, double unit,
-                         const uint64_t *__restrict__ anchor, int n_int, const int4 *__restrict__ ic,
+                         const int64_t *__restrict__ offs, int nb, int L, const uint64_t *__restrict__ anchor, int n_int, const int4 *__restrict__ ic,
                          const double *__restrict__ nf, double *__restrict__ php, double *__restrict__ ex,
                          double *__restrict__ ey, double *__restrict__ ez) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,7 +69,16 @@ __global__ void k_gather(const double *__restrict__ x, const double *__restrict_
         t = fmin(fmax(t, 0.0), (double)((1u << KEY_DEPTH) - 1u));
         cc[d] = (uint32_t)t >> shift;
     }
-    const int j = leaf_of(anchor, n_int, morton(cc[0], cc[1], cc[2]));
+    uint64_t pre = 0;
+    if (nb > 1) {   // beam of particle i from the batch offsets
+        int lo = 0, hi = nb;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (offs[mid] <= i) lo = mid; else hi = mid;
+        }
+        pre = (uint64_t)lo << (3 * L);
+    }
+    const int j = leaf_of(anchor, n_int, pre | morton(cc[0], cc[1], cc[2]));
     const int4 q = ic[j];
     const double r0 = p[0] - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
     const double r1 = p[1] - __dadd_rn(lo1, __dmul_rn((double)q.y, unit));
@@ -100,8 +109,8 @@ apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *e
     const double s = ldexp(1.0, KEY_DEPTH) / ext;
     const double unit = ldexp(ext, -(KEY_DEPTH + 1));
     APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather, c->px, c->py, c->pz, c->N, c->P.lo[0], c->P.lo[1],
-               c->P.lo[2], s, KEY_DEPTH - c->L, unit, ptr<uint64_t>(c->leaf_anchor), n, ptr<int4>(c->node_ic), nf,
-               phi_p, ex, ey, ez);
+               c->P.lo[2], s, KEY_DEPTH - c->L, unit, ptr<int64_t>(c->beam_off), c->nbeams, c->L,
+               ptr<uint64_t>(c->leaf_anchor), n, ptr<int4>(c->node_ic), nf, phi_p, ex, ey, ez);
     // node pass: operator (72 B), column (4 B) and neighbour value (8 B) per
     // stencil entry plus the 96 B record; particle pass: 24 B in, 32 B out
     account(c, K_DERIV, 84.0 * c->sum_m + 104.0 * n, 19.0 * c->sum_m);
@@ -165,7 +174,8 @@ apcloud_status interpolate_phi(apcloud_ctx *c, const double *x, const double *y,
     const double s = ldexp(1.0, KEY_DEPTH) / ext;
     const double unit = ldexp(ext, -(KEY_DEPTH + 1));
     APC_LAUNCH(c, K_GATHER, div_up(n, 256), 256, 0, k_gather, x, y, z, n, c->P.lo[0], c->P.lo[1], c->P.lo[2], s,
-               KEY_DEPTH - c->L, unit, ptr<uint64_t>(c->leaf_anchor), c->n_int, ptr<int4>(c->node_ic),
+               KEY_DEPTH - c->L, unit, (const int64_t *)nullptr, 1, c->L, ptr<uint64_t>(c->leaf_anchor), c->n_int,
+               ptr<int4>(c->node_ic),
                ptr<double>(c->nodefield), phi, (double *)nullptr, (double *)nullptr, (double *)nullptr);
     return cuda_check(c, cudaGetLastError(), "interpolate");
 }

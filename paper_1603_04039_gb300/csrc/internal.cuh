@@ -80,6 +80,9 @@ struct apcloud_ctx {
     const double *px = nullptr, *py = nullptr, *pz = nullptr;
     int64_t N = 0;
 
+    // batch of independent problems (beams) sharing the domain and parameters
+    int nbeams = 1, beam_bits = 0;
+    std::vector<int64_t> h_beam_off;
     // sizes
     int L = 0;
     int n_int = 0, n_bnd = 0, n_tot = 0;
@@ -95,6 +98,7 @@ struct apcloud_ctx {
     apc::DBuf ucell[2], ustart[2], opened, cand[2], cval[2], flags, scan, scan_blk, lkey, lval;
     // nodes
     apc::DBuf leaf_anchor, leaf_level, leaf_first, leaf_count, node_ic, bowner, bface, bidx, adj;
+    apc::DBuf beam_off, leaf_beam, beam_rng, beam_norm;
     // stencils
     apc::DBuf nbr, msz, ring, lap, lapd, D, rcond;
     // matrices (sliced ELL, 32-row slices, column-major inside a slice)
@@ -149,7 +153,9 @@ apcloud_status radix_sort(apcloud_ctx *c, uint64_t *k0, uint32_t *v0, uint64_t *
                           int nbits, int *which);
 
 // ---- stages ----
-apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n);
+apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,
+                            const int64_t *h_offsets, int nbeams);
+apcloud_status node_beams(apcloud_ctx *c, int32_t *out);
 apcloud_status build_stencils(apcloud_ctx *c);
 apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform);
 apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x_inout_scaled, double rtol,

@@ -15,6 +15,11 @@
 // so O_l = Crit_l U parent(O_{l+1}) U parent(faces(O_{l+1})), a sort + unique
 // per level.  The result is the unique minimal balanced refinement, the set
 // the paper's deepest-level-first loop produces.
+//
+// Batches: several independent problems (beams) on the same cubic domain are
+// one tree whose cell keys carry the beam index above the 3l Morton bits of
+// level l, so one sort and one closure serve all beams and no neighbour
+// relation crosses from one beam to another.
 #include <cmath>
 
 #include "internal.cuh"
@@ -25,9 +30,20 @@ namespace {
 
 constexpr int T = 256;
 
+// beam of particle i from the batch offsets (nb + 1 entries, offs[0] = 0)
+__device__ __forceinline__ uint64_t beam_of(const int64_t *offs, int nb, int64_t i) {
+    int lo = 0, hi = nb;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (offs[mid] <= i) lo = mid; else hi = mid;
+    }
+    return (uint64_t)lo;
+}
+
 __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                        int64_t n, double lo0, double lo1, double lo2, double hi0, double hi1, double hi2, double s,
-                       int shift, uint64_t *__restrict__ key, uint32_t *__restrict__ idx, unsigned *err) {
+                       int shift, const int64_t *__restrict__ offs, int nb, int L, uint64_t *__restrict__ key,
+                       uint32_t *__restrict__ idx, unsigned *err) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     double p[3] = {x[i], y[i], z[i]};
@@ -43,7 +59,7 @@ __global__ void k_keys(const double *__restrict__ x, const double *__restrict__ 
         cc[d] = (uint32_t)t >> shift;
     }
     if (bad) atomicOr(err, ERR_DOMAIN);
-    key[i] = morton(cc[0], cc[1], cc[2]);
+    key[i] = (nb > 1 ? beam_of(offs, nb, i) << (3 * L) : 0ull) | morton(cc[0], cc[1], cc[2]);
     idx[i] = (uint32_t)i;
 }
 
@@ -88,8 +104,9 @@ __global__ void k_balance_gen(const uint64_t *__restrict__ op, int64_t n, int le
     if (i >= n) return;
     uint64_t k = op[i];
     uint64_t par = k >> 3;
+    const uint64_t pre = (k >> (3 * lev1)) << (3 * lev1);   // beam index bits
     uint32_t c[3];
-    unmorton(k, c[0], c[1], c[2]);
+    unmorton(k ^ pre, c[0], c[1], c[2]);
     const uint32_t lim = 1u << lev1;
     out[i * 7] = par;
 #pragma unroll
@@ -98,7 +115,7 @@ __global__ void k_balance_gen(const uint64_t *__restrict__ op, int64_t n, int le
         int d = f >> 1;
         bool inside = (f & 1) ? (t[d] + 1 < lim) : (t[d] > 0);
         t[d] = (f & 1) ? t[d] + 1 : t[d] - 1;
-        out[i * 7 + 1 + f] = inside ? (morton(t[0], t[1], t[2]) >> 3) : par;
+        out[i * 7 + 1 + f] = inside ? ((pre | morton(t[0], t[1], t[2])) >> 3) : par;
     }
 }
 
@@ -118,6 +135,20 @@ __global__ void k_leaf_flags(const uint64_t *__restrict__ par, int64_t npar, con
     if (i >= npar * 8) return;
     uint64_t ch = (par[i >> 3] << 3) | (uint64_t)(i & 7);
     f[i] = contains_sorted(op, nop, ch) ? 0u : 1u;
+}
+
+// level-0 cells (one root per beam) that are not opened are leaves
+__global__ void k_root_flags(int nb, const uint64_t *__restrict__ op, int64_t nop, uint32_t *__restrict__ f) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nb) f[i] = contains_sorted(op, nop, (uint64_t)i) ? 0u : 1u;
+}
+
+__global__ void k_root_emit(int nb, const uint32_t *__restrict__ f, const uint32_t *__restrict__ pos, int L,
+                            uint64_t *__restrict__ anchor, uint32_t *__restrict__ level) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb || !f[i]) return;
+    anchor[pos[i]] = (uint64_t)i << (3 * L);
+    level[pos[i]] = 0u;
 }
 
 __global__ void k_leaf_emit(const uint64_t *__restrict__ par, int64_t npar, const uint32_t *__restrict__ f,
@@ -153,7 +184,7 @@ __device__ __forceinline__ int64_t leaf_of(const uint64_t *anchor, int64_t n, ui
 __global__ void k_leaf_geom(const uint64_t *__restrict__ anchor, const uint32_t *__restrict__ lvl32, int64_t n,
                             int L, const uint64_t *__restrict__ skeys, int64_t npart, int8_t *__restrict__ level,
                             int32_t *__restrict__ first, int32_t *__restrict__ count, int4 *__restrict__ ic,
-                            uint32_t *__restrict__ bflag) {
+                            uint32_t *__restrict__ bflag, int32_t *__restrict__ beam) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     int lev = (int)lvl32[j];
@@ -163,8 +194,9 @@ __global__ void k_leaf_geom(const uint64_t *__restrict__ anchor, const uint32_t 
     first[j] = (int32_t)f0;
     count[j] = (int32_t)(f1 - f0);
     level[j] = (int8_t)lev;
+    if (beam) beam[j] = (int32_t)(a >> (3 * L));
     uint32_t c[3];
-    unmorton(a >> (3 * (L - lev)), c[0], c[1], c[2]);
+    unmorton((a >> (3 * (L - lev))) & ((1ull << (3 * lev)) - 1ull), c[0], c[1], c[2]);
     int sh = KEY_DEPTH - lev;
     ic[j] = make_int4((int)((2u * c[0] + 1u) << sh), (int)((2u * c[1] + 1u) << sh), (int)((2u * c[2] + 1u) << sh),
                       lev);
@@ -205,11 +237,12 @@ __global__ void k_adjacency(const uint64_t *__restrict__ anchor, const int8_t *_
         return;
     }
     int lev = level[j];
+    const uint64_t pre = (anchor[j] >> (3 * L)) << (3 * L);   // beam index bits
     uint32_t c[3];
-    unmorton(anchor[j] >> (3 * (L - lev)), c[0], c[1], c[2]);
+    unmorton((anchor[j] ^ pre) >> (3 * (L - lev)), c[0], c[1], c[2]);
     int d = f >> 1;
     c[d] = (f & 1) ? c[d] + 1 : c[d] - 1;
-    uint64_t a = morton(c[0], c[1], c[2]) << (3 * (L - lev));
+    uint64_t a = pre | (morton(c[0], c[1], c[2]) << (3 * (L - lev)));
     int64_t k = leaf_of(anchor, n, a);
     if (k < 0) { atomicOr(err, ERR_BALANCE); return; }
     if (level[k] <= lev) { out[0] = (int32_t)k; return; }
@@ -218,20 +251,63 @@ __global__ void k_adjacency(const uint64_t *__restrict__ anchor, const int8_t *_
     for (int o = 0; o < 8; ++o) {
         if (((o >> (2 - d)) & 1) != want) continue;
         uint32_t cc[3] = {2u * c[0] + ((o >> 2) & 1u), 2u * c[1] + ((o >> 1) & 1u), 2u * c[2] + (o & 1u)};
-        uint64_t ac = morton(cc[0], cc[1], cc[2]) << (3 * (L - lev - 1));
+        uint64_t ac = pre | (morton(cc[0], cc[1], cc[2]) << (3 * (L - lev - 1)));
         int64_t kk = leaf_of(anchor, n, ac);
         if (kk < 0 || anchor[kk] != ac || level[kk] != lev + 1) { atomicOr(err, ERR_BALANCE); return; }
         out[s++] = (int32_t)kk;
     }
 }
 
+// Node ranges of every beam: interior nodes [r[b], r[b+1]) (the leaves are
+// beam-sorted) and, per face f, boundary nodes [r[(1+f)(nb+1)+b], ...+1) (the
+// boundary nodes are face-major, leaf-ordered within a face).
+__global__ void k_beam_ranges(const int32_t *__restrict__ beam, int64_t n, int nb, const uint32_t *__restrict__ bpos,
+                              int64_t nbnd, int64_t *__restrict__ r) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nb) return;
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (beam[mid] < b) lo = mid + 1; else hi = mid;
+    }
+    r[b] = lo;
+    for (int f = 0; f < 6; ++f) {
+        int64_t t = (int64_t)f * n + lo;
+        r[(int64_t)(1 + f) * (nb + 1) + b] = n + (t < 6 * n ? (int64_t)bpos[t] : nbnd);
+    }
+}
+
+// beam index of every node (boundary nodes take their owner leaf's)
+__global__ void k_node_beam(const int32_t *__restrict__ leaf_beam, const int32_t *__restrict__ owner, int64_t n,
+                            int64_t nt, int32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    out[i] = i < n ? leaf_beam[i] : leaf_beam[owner[i - n]];
+}
+
 }  // namespace
 
-apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n) {
+apcloud_status node_beams(apcloud_ctx *c, int32_t *out) {
+    APC_LAUNCH(c, K_COPY, div_up(c->n_tot, T), T, 0, k_node_beam, ptr<int32_t>(c->leaf_beam),
+               ptr<int32_t>(c->bowner), (int64_t)c->n_int, (int64_t)c->n_tot, out);
+    return cuda_check(c, cudaGetLastError(), "node_beams");
+}
+
+apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,
+                            const int64_t *h_offsets, int nb) {
     const int L = c->P.max_depth;
+    int bb = 0;  // bits of the beam index above the tree bits
+    while ((1 << bb) < nb) ++bb;
+    if (3 * L + bb > 63) return fail(c, APCLOUD_E_INVALID, "%d beams need %d key bits above depth %d", nb, bb, L);
     c->L = L;
     c->N = n;
     c->px = x; c->py = y; c->pz = z;
+    c->nbeams = nb;
+    c->beam_bits = bb;
+    c->h_beam_off.assign(h_offsets, h_offsets + nb + 1);
+    int64_t *doff = ensure<int64_t>(c, c->beam_off, nb + 1);
+    if (!doff) return APCLOUD_E_NOMEM;
+    APC_CUDA(c, cudaMemcpyAsync(doff, h_offsets, sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, c->s));
     unsigned *derr = ptr<unsigned>(c->derr);
     APC_CUDA(c, cudaMemsetAsync(derr, 0, 4 * sizeof(unsigned), c->s));
     uint32_t *small = ptr<uint32_t>(c->dsmall);
@@ -244,10 +320,10 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
     const double ext = c->P.hi[0] - c->P.lo[0];
     const double s = ldexp(1.0, KEY_DEPTH) / ext;
     APC_LAUNCH(c, K_KEYS, div_up(n, T), T, 0, k_keys, x, y, z, n, c->P.lo[0], c->P.lo[1], c->P.lo[2], c->P.hi[0],
-               c->P.hi[1], c->P.hi[2], s, KEY_DEPTH - L, k0, v0, derr);
+               c->P.hi[1], c->P.hi[2], s, KEY_DEPTH - L, (const int64_t *)doff, nb, L, k0, v0, derr);
     account(c, K_KEYS, 36.0 * n, 9.0 * n);   // 24 B positions in, 12 B key and index out
     int which = 0;
-    APC_TRY(radix_sort(c, k0, v0, k1, v1, n, 3 * L, &which));
+    APC_TRY(radix_sort(c, k0, v0, k1, v1, n, 3 * L + bb, &which));
     c->kbuf = which;
     uint64_t *skeys = which ? k1 : k0;
 
@@ -310,7 +386,7 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
         int64_t nol = 0;
         if (ncand > 0) {
             int w = 0;
-            APC_TRY(radix_sort(c, ca0, cv0, ca1, cv1, ncand, 3 * l, &w));
+            APC_TRY(radix_sort(c, ca0, cv0, ca1, cv1, ncand, 3 * l + bb, &w));
             uint64_t *sc = w ? ca1 : ca0;
             uint32_t *f2 = ensure<uint32_t>(c, c->lval, ncand), *p2 = ensure<uint32_t>(c, c->lkey, ncand);
             if (!f2 || !p2) return APCLOUD_E_NOMEM;
@@ -333,69 +409,56 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
         if (U > 0) { cur = nxt; U = Ul; }
     }
 
-    // leaves: children of O_{l-1} not in O_l, l = 1..L (or the root alone)
-    int64_t nseg = 0;
+    // leaves: the roots (one per beam) that are not opened, and for l = 1..L the
+    // children of O_{l-1} not in O_l
+    int64_t nseg = nb;
     std::vector<int64_t> segoff(L + 2, 0);
     for (int l = 1; l <= L; ++l) { segoff[l] = nseg; nseg += 8 * ocount[l - 1]; }
-    int64_t nleaf = 0;
-    uint64_t *anc = nullptr;
-    uint32_t *alv = nullptr;
-    uint64_t *lk0 = nullptr;
-    uint32_t *lv0 = nullptr;
-    if (nseg == 0) {
-        nleaf = 1;
-        lk0 = ensure<uint64_t>(c, c->cand[0], 2);
-        lv0 = ensure<uint32_t>(c, c->cval[0], 2);
-        if (!lk0 || !lv0) return APCLOUD_E_NOMEM;
-        APC_CUDA(c, cudaMemsetAsync(lk0, 0, sizeof(uint64_t), c->s));
-        APC_CUDA(c, cudaMemsetAsync(lv0, 0, sizeof(uint32_t), c->s));
-        anc = lk0;
-        alv = lv0;
-    } else {
-        uint32_t *f3 = ensure<uint32_t>(c, c->lval, nseg), *p3 = ensure<uint32_t>(c, c->lkey, nseg);
-        if (!f3 || !p3) return APCLOUD_E_NOMEM;
-        const uint64_t *ob = ptr<uint64_t>(c->opened);
-        for (int l = 1; l <= L; ++l) {
-            int64_t np = ocount[l - 1];
-            if (np == 0) continue;
-            APC_LAUNCH(c, K_TREE, div_up(8 * np, T), T, 0, k_leaf_flags, ob + ooff[l - 1], np,
-                       l < L ? ob + ooff[l] : ob, l < L ? ocount[l] : 0, f3 + segoff[l]);
-        }
-        APC_TRY(scan_u32(c, f3, p3, nseg, small + 3));
-        uint32_t hl;
-        APC_TRY(read_back(c, &hl, small + 3, sizeof hl));
-        nleaf = hl;
-        lk0 = ensure<uint64_t>(c, c->cand[0], nleaf);
-        uint64_t *lk1 = ensure<uint64_t>(c, c->cand[1], nleaf);
-        lv0 = ensure<uint32_t>(c, c->cval[0], nleaf);
-        uint32_t *lv1 = ensure<uint32_t>(c, c->cval[1], nleaf);
-        if (!lk0 || !lk1 || !lv0 || !lv1) return APCLOUD_E_NOMEM;
-        for (int l = 1; l <= L; ++l) {
-            int64_t np = ocount[l - 1];
-            if (np == 0) continue;
-            APC_LAUNCH(c, K_TREE, div_up(8 * np, T), T, 0, k_leaf_emit, ob + ooff[l - 1], np, f3 + segoff[l],
-                       p3 + segoff[l], l, L, lk0, lv0);
-        }
-        int w = 0;
-        APC_TRY(radix_sort(c, lk0, lv0, lk1, lv1, nleaf, 3 * L, &w));
-        anc = w ? lk1 : lk0;
-        alv = w ? lv1 : lv0;
+    uint32_t *f3 = ensure<uint32_t>(c, c->lval, nseg), *p3 = ensure<uint32_t>(c, c->lkey, nseg);
+    if (!f3 || !p3) return APCLOUD_E_NOMEM;
+    const uint64_t *ob = ptr<uint64_t>(c->opened);
+    APC_LAUNCH(c, K_TREE, div_up(nb, T), T, 0, k_root_flags, nb, L > 0 ? ob + ooff[0] : ob, L > 0 ? ocount[0] : 0,
+               f3);
+    for (int l = 1; l <= L; ++l) {
+        int64_t np = ocount[l - 1];
+        if (np == 0) continue;
+        APC_LAUNCH(c, K_TREE, div_up(8 * np, T), T, 0, k_leaf_flags, ob + ooff[l - 1], np,
+                   l < L ? ob + ooff[l] : ob, l < L ? ocount[l] : 0, f3 + segoff[l]);
     }
+    APC_TRY(scan_u32(c, f3, p3, nseg, small + 3));
+    uint32_t hl;
+    APC_TRY(read_back(c, &hl, small + 3, sizeof hl));
+    const int64_t nleaf = hl;
+    uint64_t *lk0 = ensure<uint64_t>(c, c->cand[0], nleaf), *lk1 = ensure<uint64_t>(c, c->cand[1], nleaf);
+    uint32_t *lv0 = ensure<uint32_t>(c, c->cval[0], nleaf), *lv1 = ensure<uint32_t>(c, c->cval[1], nleaf);
+    if (!lk0 || !lk1 || !lv0 || !lv1) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_TREE, div_up(nb, T), T, 0, k_root_emit, nb, f3, p3, L, lk0, lv0);
+    for (int l = 1; l <= L; ++l) {
+        int64_t np = ocount[l - 1];
+        if (np == 0) continue;
+        APC_LAUNCH(c, K_TREE, div_up(8 * np, T), T, 0, k_leaf_emit, ob + ooff[l - 1], np, f3 + segoff[l],
+                   p3 + segoff[l], l, L, lk0, lv0);
+    }
+    int wl = 0;
+    APC_TRY(radix_sort(c, lk0, lv0, lk1, lv1, nleaf, 3 * L + bb, &wl));
+    uint64_t *anc = wl ? lk1 : lk0;
+    uint32_t *alv = wl ? lv1 : lv0;
     c->n_int = (int)nleaf;
 
     // leaf geometry, particle ranges, boundary faces
     uint64_t *la = ensure<uint64_t>(c, c->leaf_anchor, nleaf);
     int8_t *ll = ensure<int8_t>(c, c->leaf_level, nleaf);
+    int32_t *lb = ensure<int32_t>(c, c->leaf_beam, nleaf);
     int32_t *lf = ensure<int32_t>(c, c->leaf_first, nleaf);
     int32_t *lc = ensure<int32_t>(c, c->leaf_count, nleaf);
     uint32_t *bfl = ensure<uint32_t>(c, c->bidx, 12 * nleaf);  // flags then positions
-    if (!la || !ll || !lf || !lc || !bfl) return APCLOUD_E_NOMEM;
+    if (!la || !ll || !lf || !lc || !bfl || !lb) return APCLOUD_E_NOMEM;
     APC_CUDA(c, cudaMemcpyAsync(la, anc, nleaf * sizeof(uint64_t), cudaMemcpyDeviceToDevice, c->s));
     uint32_t *bpos = bfl + 6 * nleaf;
     // node coordinates need room for boundary nodes: at most 6 per leaf
     int4 *ic = ensure<int4>(c, c->node_ic, 7 * nleaf);
     if (!ic) return APCLOUD_E_NOMEM;
-    APC_LAUNCH(c, K_TREE, div_up(nleaf, T), T, 0, k_leaf_geom, la, alv, nleaf, L, skeys, n, ll, lf, lc, ic, bfl);
+    APC_LAUNCH(c, K_TREE, div_up(nleaf, T), T, 0, k_leaf_geom, la, alv, nleaf, L, skeys, n, ll, lf, lc, ic, bfl, lb);
     APC_TRY(scan_u32(c, bfl, bpos, 6 * nleaf, small + 4));
     uint32_t hb;
     APC_TRY(read_back(c, &hb, small + 4, sizeof hb));
@@ -407,6 +470,9 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
     if (!bo || !bf || !adj) return APCLOUD_E_NOMEM;
     APC_LAUNCH(c, K_TREE, div_up(6 * nleaf, T), T, 0, k_boundary, bfl, bpos, nleaf, ic, bo, bf);
     APC_LAUNCH(c, K_ADJ, div_up(6 * nleaf, T), T, 0, k_adjacency, la, ll, nleaf, L, bfl, bpos, adj, derr);
+    int64_t *rng = ensure<int64_t>(c, c->beam_rng, 7 * (nb + 1));
+    if (!rng) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_TREE, div_up(nb + 1, T), T, 0, k_beam_ranges, lb, nleaf, nb, bpos, (int64_t)hb, rng);
     APC_CUDA(c, cudaGetLastError());
     return check_device_errors(c);
 }

@@ -703,6 +703,25 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
 
 }  // namespace
 
+// squared norm of b over the nodes of each beam (one block per beam, fixed order)
+__global__ void k_beam_norm2(const double *__restrict__ b, const int64_t *__restrict__ rng, int nb,
+                             double *__restrict__ out) {
+    __shared__ double sh[256];
+    const int beam = blockIdx.x;
+    double s = 0.0;
+    for (int seg = 0; seg < 7; ++seg) {
+        const int64_t lo = rng[(int64_t)seg * (nb + 1) + beam], hi = rng[(int64_t)seg * (nb + 1) + beam + 1];
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(b[i], b[i], s);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[beam] = sh[0];
+}
+
 apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform) {
     const int n = c->n_int, nt = c->n_tot;
     double *rm = ensure<double>(c, c->rho_m, nt + 1);
@@ -746,6 +765,21 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
     if (!u || !partial) return APCLOUD_E_NOMEM;
     const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
     const double *d = ptr<double>(which ? c->dA : c->dB);
+    if (c->nbeams > 1) {
+        // batch: stop at ||r|| <= rtol min_b ||b_b||, so that ||r_b|| <= rtol ||b_b|| for every beam
+        const int nb = c->nbeams;
+        double *bn = ensure<double>(c, c->beam_norm, nb);
+        if (!bn) return APCLOUD_E_NOMEM;
+        APC_LAUNCH(c, K_VEC, nb, 256, 0, k_beam_norm2, b, (const int64_t *)ptr<int64_t>(c->beam_rng), nb, bn);
+        std::vector<double> h(nb);
+        APC_TRY(read_back(c, h.data(), bn, sizeof(double) * nb));
+        double tot = 0.0, mn = -1.0;
+        for (int i = 0; i < nb; ++i) {
+            tot += h[i];
+            if (h[i] > 0.0 && (mn < 0.0 || h[i] < mn)) mn = h[i];
+        }
+        if (mn > 0.0) rtol *= std::sqrt(mn / tot);
+    }
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
     int iters = 0, cycles = 0;
     double relres = 0.0;

@@ -115,3 +115,34 @@ def thermal_velocities(n: int, seed: int, sigma_v: float = 0.01):
     """(vx, vy, vz): independent N(0, sigma_v^2) components (stream 5)."""
     g = _normals(seed, 5, 3 * int(n), 0).reshape(-1, 3) * sigma_v if n else np.zeros((0, 3))
     return tuple(np.ascontiguousarray(g[:, d]) for d in range(3))
+
+
+def beam_batch_params(n_beams: int, seed: int = 1, n_lo: float = 1e4, n_hi: float = 1e6):
+    """Laws of a batch of independent beams (stream 6 of ``seed``, five uniforms
+    per beam): particle count log-uniform in [n_lo, n_hi], core sigma uniform
+    in [0.02, 0.1], halo fraction uniform in [0.01, 0.2], halo shell radii
+    uniform in [0.2, 0.8] (sorted).  Beam b draws its particles with seed b + 1.
+    """
+    u = uniforms(seed, 6, 5 * int(n_beams)).reshape(-1, 5)
+    out = []
+    for b in range(int(n_beams)):
+        r = sorted((0.2 + 0.6 * u[b, 3], 0.2 + 0.6 * u[b, 4]))
+        out.append(dict(n=int(round(n_lo * (n_hi / n_lo) ** u[b, 0])), sigma=0.02 + 0.08 * u[b, 1],
+                        halo_frac=0.01 + 0.19 * u[b, 2], r0=r[0], r1=r[1], seed=b + 1))
+    return out
+
+
+def beam_batch(n_beams: int, seed: int = 1, n_lo: float = 1e4, n_hi: float = 1e6):
+    """Concatenated particles of a beam batch: (x, y, z, q, offsets, params).
+    Beam b occupies offsets[b]:offsets[b+1] and carries charge 1/N_b per
+    particle, so every beam has total charge 1."""
+    params = beam_batch_params(n_beams, seed, n_lo, n_hi)
+    xs, ys, zs, qs = [], [], [], []
+    offsets = [0]
+    for p in params:
+        x, y, z, q = beam_with_halo(p["n"], p["seed"], sigma=p["sigma"], halo_frac=p["halo_frac"],
+                                    r0=p["r0"], r1=p["r1"])
+        xs.append(x); ys.append(y); zs.append(z); qs.append(q)
+        offsets.append(offsets[-1] + p["n"])
+    cat = lambda a: np.ascontiguousarray(np.concatenate(a)) if a else np.zeros(0)
+    return cat(xs), cat(ys), cat(zs), cat(qs), np.array(offsets, dtype=np.int64), params
