@@ -267,6 +267,36 @@ apcloud_status apcloud_push_particles(apcloud_ctx *ctx, double *d_x, double *d_y
                                       double *d_vy, double *d_vz, int64_t n, const double *d_ex,
                                       const double *d_ey, const double *d_ez, double qm_dt, double dt);
 
+/* CUDA graphs: every full GMRES restart cycle (its Arnoldi steps,
+ * Gram-Schmidt reductions, preconditioner sweeps, the update of the iterate
+ * and the residual that opens the next cycle) is captured once per set of
+ * buffers and sizes and replayed with one cudaGraphLaunch on the context
+ * stream; the host synchronises once per cycle for the convergence test.  On
+ * by default; enable = 0 launches every kernel directly (same results, the
+ * same kernels in the same order).  Synchronises the context stream.  The
+ * paper has no counterpart (launch mechanics). */
+apcloud_status apcloud_set_graphs(apcloud_ctx *ctx, int enable);
+
+/* Autotuner of the launch shapes (after apcloud_stencils): bit 0 of `what`
+ * times the preconditioner sweep (or the Arnoldi product under Jacobi) of the
+ * configured precision at 64, 128, 256 and 512 threads per block; bit 1 times
+ * the stencil build (neighbour search + WLS) at 2, 4 and 8 nodes (warps) per
+ * block on the current node set.  The fastest shapes are kept for later
+ * calls and written to *h_spmv_block and *h_wls_warps (either may be NULL);
+ * h_ms (NULL or 7 doubles) receives the measured milliseconds: four sweeps,
+ * then three stencil builds.  Results never depend on the shapes.  Runs the
+ * timed kernels on the context stream and synchronises.  The paper has no
+ * counterpart (launch mechanics). */
+apcloud_status apcloud_autotune(apcloud_ctx *ctx, unsigned what, int *h_spmv_block, int *h_wls_warps,
+                                double *h_ms);
+
+/* Sets the launch shapes directly: spmv_block in {64, 128, 256, 512},
+ * wls_warps in {2, 4, 8}; APCLOUD_E_INVALID otherwise. */
+apcloud_status apcloud_set_launch_shape(apcloud_ctx *ctx, int spmv_block, int wls_warps);
+
+/* Graph replays since the context was created and graphs currently cached. */
+apcloud_status apcloud_graph_stats(const apcloud_ctx *ctx, int64_t *h_replays, int64_t *h_cached);
+
 /* Field energy 1/2 sum_j |grad phi_j|^2 h_j^3 over the leaves (node gradients
  * from the last apcloud_gather_field times cell volumes), FP64, fixed order. */
 apcloud_status apcloud_field_energy(apcloud_ctx *ctx, double *h_energy);

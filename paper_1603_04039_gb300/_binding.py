@@ -85,6 +85,10 @@ def load():
             "apcloud_field_host_batched": (I, [P, P, P, P, P, D, C.POINTER(L), I, D, I, P, P, P, P,
                                                C.POINTER(SolveInfo), C.POINTER(SolveInfo)]),
             "apcloud_set_timing": (I, [P, C.c_uint]),
+            "apcloud_set_graphs": (I, [P, I]),
+            "apcloud_autotune": (I, [P, C.c_uint, C.POINTER(I), C.POINTER(I), P]),
+            "apcloud_set_launch_shape": (I, [P, I, I]),
+            "apcloud_graph_stats": (I, [P, C.POINTER(L), C.POINTER(L)]),
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
             "apcloud_launch_count": (L, [P]),
@@ -382,6 +386,30 @@ class APCloud:
         with torch.cuda.device(self.device):
             self._check(self._lib.apcloud_field_energy(self._ctx, C.byref(e)))
         return e.value
+
+    def autotune(self, spmv=True, stencils=True):
+        """Times the launch shapes and keeps the fastest; returns the choice and timings (ms)."""
+        bs, ww = C.c_int(), C.c_int()
+        ms = np.zeros(7)
+        what = (1 if spmv else 0) | (2 if stencils else 0)
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_autotune(self._ctx, what, C.byref(bs), C.byref(ww),
+                                                   ms.ctypes.data_as(C.c_void_p)))
+        return {"spmv_block": bs.value, "wls_warps": ww.value,
+                "spmv_ms": dict(zip((64, 128, 256, 512), ms[:4].round(4).tolist())) if spmv else None,
+                "wls_ms": dict(zip((2, 4, 8), ms[4:].round(3).tolist())) if stencils else None}
+
+    def set_launch_shape(self, spmv_block=256, wls_warps=4):
+        self._check(self._lib.apcloud_set_launch_shape(self._ctx, int(spmv_block), int(wls_warps)))
+
+    def set_graphs(self, enable):
+        with torch.cuda.device(self.device):
+            self._check(self._lib.apcloud_set_graphs(self._ctx, 1 if enable else 0))
+
+    def graph_stats(self):
+        r, g = C.c_int64(), C.c_int64()
+        self._check(self._lib.apcloud_graph_stats(self._ctx, C.byref(r), C.byref(g)))
+        return {"replays": r.value, "cached": g.value}
 
     def set_timing(self, mask):
         self._check(self._lib.apcloud_set_timing(self._ctx, int(mask)))

@@ -62,9 +62,21 @@ static void free_buf(apcloud_ctx *c, DBuf &b) {
     b.bytes = 0;
 }
 
+// inside a stream capture the timing pair becomes two event nodes of the graph,
+// owned by the graph entry and read after every replay
+static void capture_event(apcloud_ctx *c, int kind, bool begin) {
+    GraphEntry *g = c->capturing;
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    g->ev.push_back(e);
+    if (begin) g->kind.push_back(kind);
+    cudaEventRecordWithFlags(e, c->s, cudaEventRecordExternal);
+}
+
 void timer_begin(apcloud_ctx *c, int kind) {
     Timer &t = c->timer;
     if (!(t.mask >> kind & 1u)) return;
+    if (c->capturing) { capture_event(c, kind, true); return; }
     if (t.used * 2 + 2 > t.ev.size()) {
         size_t old = t.ev.size();
         size_t nn = old ? old * 2 : 512;
@@ -79,6 +91,7 @@ void timer_begin(apcloud_ctx *c, int kind) {
 void timer_end(apcloud_ctx *c, int kind) {
     Timer &t = c->timer;
     if (!(t.mask >> kind & 1u)) return;
+    if (c->capturing) { capture_event(c, kind, false); return; }
     cudaEventRecord(t.ev[t.used * 2 + 1], c->s);
     t.used++;
 }
@@ -95,6 +108,100 @@ static void timer_collect(apcloud_ctx *c) {
         }
     }
     t.used = 0;
+}
+
+// ---------------------------------------------------------------- CUDA graphs
+static void destroy_entry(GraphEntry *g) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+    delete g;
+}
+
+void free_graphs(apcloud_ctx *c) {
+    for (GraphEntry *g : c->graphs) destroy_entry(g);
+    c->graphs.clear();
+    c->last_replayed = nullptr;
+}
+
+GraphEntry *find_graph(apcloud_ctx *c, const GraphKey &key) {
+    for (GraphEntry *g : c->graphs)
+        if (memcmp(&g->key, &key, sizeof key) == 0) return g;
+    return nullptr;
+}
+
+GraphEntry *begin_capture(apcloud_ctx *c, const GraphKey &key) {
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        c->cap_stream = nullptr;
+        cudaGetLastError();
+        return nullptr;
+    }
+    GraphEntry *g = new GraphEntry;
+    g->key = key;
+    // capture on the context's own capture stream (the caller's may be the legacy
+    // default stream, which cannot be captured); replays run on the caller's stream
+    std::swap(c->s, c->cap_stream);
+    if (cudaStreamBeginCapture(c->s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        std::swap(c->s, c->cap_stream);
+        cudaGetLastError();
+        delete g;
+        return nullptr;
+    }
+    c->capturing = g;
+    return g;
+}
+
+GraphEntry *end_capture(apcloud_ctx *c, GraphEntry *g, apcloud_status st) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->s, &graph);
+    std::swap(c->s, c->cap_stream);
+    c->capturing = nullptr;
+    if (st >= 0 && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (st < 0 || e != cudaSuccess || !g->exec) {
+        cudaGetLastError();
+        destroy_entry(g);
+        c->err[0] = 0;
+        return nullptr;
+    }
+    // keep the 8 most recently used cycles
+    if (c->graphs.size() >= 8) {
+        size_t old = 0;
+        for (size_t i = 1; i < c->graphs.size(); ++i)
+            if (c->graphs[i]->last_use < c->graphs[old]->last_use) old = i;
+        destroy_entry(c->graphs[old]);
+        c->graphs.erase(c->graphs.begin() + old);
+    }
+    c->graphs.push_back(g);
+    return g;
+}
+
+apcloud_status launch_graph(apcloud_ctx *c, GraphEntry *g) {
+    g->last_use = ++c->graph_clock;
+    APC_CUDA(c, cudaGraphLaunch(g->exec, c->s));
+    c->launches += g->kernels;
+    c->graph_replays++;
+    c->last_replayed = g->ev.empty() ? nullptr : g;
+    return APCLOUD_OK;
+}
+
+// after the stream has synchronised: the replayed graph's timing pairs
+void harvest_graph_timing(apcloud_ctx *c) {
+    GraphEntry *g = c->last_replayed;
+    c->last_replayed = nullptr;
+    if (!g) return;
+    Timer &t = c->timer;
+    for (size_t i = 0; i < g->kind.size() && 2 * i + 1 < g->ev.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]) == cudaSuccess) {
+            t.ms[g->kind[i]] += ms;
+            t.launches[g->kind[i]]++;
+        } else {
+            // event nodes that cannot be timed: later timed cycles run without graphs
+            cudaGetLastError();
+            c->graph_timing_ok = false;
+            return;
+        }
+    }
 }
 
 apcloud_status read_back(apcloud_ctx *c, void *host, const void *dev, size_t bytes) {
@@ -214,6 +321,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->beam_rng, &c->beam_norm};
     for (DBuf *b : bufs) free_buf(c, *b);
     cudaStreamSynchronize(c->s);
+    free_graphs(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
@@ -553,6 +662,42 @@ const char *apcloud_kernel_name(int kind) {
 }
 
 int64_t apcloud_launch_count(const apcloud_ctx *c) { return c ? c->launches : 0; }
+
+apcloud_status apcloud_autotune(apcloud_ctx *c, unsigned what, int *spmv_block, int *wls_warps, double *ms) {
+    if (!c) return APCLOUD_E_INVALID;
+    if (c->stage < 2) return fail(c, APCLOUD_E_STATE, "apcloud_autotune needs apcloud_stencils first");
+    if (what & 1u) APC_TRY(tune_spmv(c, ms));
+    if (what & 2u) APC_TRY(tune_stencils(c, ms ? ms + 4 : nullptr));
+    if (spmv_block) *spmv_block = c->spmv_bs;
+    if (wls_warps) *wls_warps = c->wls_warps;
+    return APCLOUD_OK;
+}
+
+apcloud_status apcloud_set_launch_shape(apcloud_ctx *c, int spmv_block, int wls_warps) {
+    if (!c) return APCLOUD_E_INVALID;
+    if (spmv_block != 64 && spmv_block != 128 && spmv_block != 256 && spmv_block != 512)
+        return fail(c, APCLOUD_E_INVALID, "spmv_block must be 64, 128, 256 or 512");
+    if (wls_warps != 2 && wls_warps != 4 && wls_warps != 8)
+        return fail(c, APCLOUD_E_INVALID, "wls_warps must be 2, 4 or 8");
+    c->spmv_bs = spmv_block;
+    c->wls_warps = wls_warps;
+    return APCLOUD_OK;
+}
+
+apcloud_status apcloud_set_graphs(apcloud_ctx *c, int enable) {
+    if (!c) return APCLOUD_E_INVALID;
+    cudaStreamSynchronize(c->s);
+    c->graphs_on = enable != 0;
+    if (!c->graphs_on) free_graphs(c);
+    return APCLOUD_OK;
+}
+
+apcloud_status apcloud_graph_stats(const apcloud_ctx *c, int64_t *replays, int64_t *cached) {
+    if (!c) return APCLOUD_E_INVALID;
+    if (replays) *replays = c->graph_replays;
+    if (cached) *cached = (int64_t)c->graphs.size();
+    return APCLOUD_OK;
+}
 
 apcloud_status apcloud_get_sizes(const apcloud_ctx *c, int64_t *h) {
     if (!c || !h) return APCLOUD_E_INVALID;

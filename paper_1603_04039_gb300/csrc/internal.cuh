@@ -51,6 +51,25 @@ struct GmresState {
     int jend;                     // columns completed in this cycle
     int done;                     // 1 once the cycle must stop (converged or breakdown)
     unsigned ticket;              // grid-reduction ticket
+    int jlast;                    // columns completed by the previous cycle
+};
+
+// A captured restart cycle (CUDA graph), keyed by everything its launches
+// depend on: element size, sizes, timing mask and every buffer address.
+struct GraphKey {
+    int tsize, n, jmax, pdeg, nblk, spmv_bs;
+    unsigned mask;
+    int64_t ldv;
+    const void *p[16];
+};
+
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;             // kernel nodes per replay
+    std::vector<cudaEvent_t> ev;     // timing pairs recorded by event nodes
+    std::vector<int> kind;
+    uint64_t last_use = 0;
 };
 
 struct Timer {
@@ -75,6 +94,18 @@ struct apcloud_ctx {
     char err[512] = {0};
     int64_t launches = 0;
     apc::Timer timer;
+    // launch shapes chosen by apcloud_autotune
+    int spmv_bs = 256;     // threads per block of the Arnoldi products and sweeps
+    int wls_warps = 4;     // nodes (warps) per block of the stencil build
+    // CUDA graphs of GMRES restart cycles (captured on cap_stream, replayed on s)
+    bool graphs_on = true;
+    bool graph_timing_ok = true;
+    cudaStream_t cap_stream = nullptr;
+    apc::GraphEntry *capturing = nullptr;
+    apc::GraphEntry *last_replayed = nullptr;
+    std::vector<apc::GraphEntry *> graphs;
+    uint64_t graph_clock = 0;
+    int64_t graph_replays = 0;
 
     // particles (caller's device arrays, kept until the next build)
     const double *px = nullptr, *py = nullptr, *pz = nullptr;
@@ -156,6 +187,15 @@ apcloud_status radix_sort(apcloud_ctx *c, uint64_t *k0, uint32_t *v0, uint64_t *
 apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,
                             const int64_t *h_offsets, int nbeams);
 apcloud_status node_beams(apcloud_ctx *c, int32_t *out);
+apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out);      // ms per sweep at 64/128/256/512 threads
+apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out);  // ms per build at 2/4/8 warps
+// CUDA graphs of restart cycles
+GraphEntry *find_graph(apcloud_ctx *c, const GraphKey &key);
+GraphEntry *begin_capture(apcloud_ctx *c, const GraphKey &key);
+GraphEntry *end_capture(apcloud_ctx *c, GraphEntry *g, apcloud_status st);
+apcloud_status launch_graph(apcloud_ctx *c, GraphEntry *g);
+void harvest_graph_timing(apcloud_ctx *c);
+void free_graphs(apcloud_ctx *c);
 apcloud_status build_stencils(apcloud_ctx *c);
 apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform);
 apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x_inout_scaled, double rtol,
@@ -205,7 +245,8 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
             ::apc::timer_begin(c, kind);                                        \
             kern<<<(grid), (block), (smem), (c)->s>>>(__VA_ARGS__);             \
             ::apc::timer_end(c, kind);                                          \
-            (c)->launches++;                                                    \
+            if ((c)->capturing) (c)->capturing->kernels++;                      \
+            else (c)->launches++;                                               \
         }                                                                       \
     } while (0)
 

@@ -147,14 +147,17 @@ __global__ void k_bcopy(const int32_t *__restrict__ owner, int n_int, int n_bnd,
 // mode 3: y = x + omega (b - Ahat x)   (damped Jacobi sweep of the polynomial
 //         preconditioner, Ahat already carries the Jacobi scaling)
 // mode 4: y = Ahat x, skipped once the cycle is done
-template <int MODE, class T>
-__global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+// BS: threads per block (one row each); mode 2 runs with RT only, its block
+// partials are sized for div_up(n, RT) blocks.
+template <int MODE, class T, int BS = RT>
+__global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                              const int32_t *__restrict__ col, const T *__restrict__ val, int n,
                                              const T *__restrict__ x, T *__restrict__ y, T *__restrict__ vout,
                                              const T *__restrict__ b, GmresState *st, double *__restrict__ partial) {
-    __shared__ double sm[RT + RT / 32 + 8];
+    static_assert(MODE != 2 || BS == RT, "mode 2 partials are sized for RT-thread blocks");
+    __shared__ double sm[MODE == 2 ? RT + RT / 32 + 8 : 1];
     if ((MODE == 1 || MODE == 3 || MODE == 4) && st->done) return;
-    const int r = blockIdx.x * RT + threadIdx.x;
+    const int r = blockIdx.x * BS + threadIdx.x;
     T s = (T)1;
     if (MODE == 1) s = (T)st->inv_norm;
     if (MODE == 3) s = (T)st->omega;
@@ -200,12 +203,13 @@ __global__ void __launch_bounds__(RT) k_spmv(const uint32_t *__restrict__ sw, co
 // steers the Krylov space (right preconditioning keeps the residual exact),
 // so its 11-bit values cost convergence at most, never accuracy; they cut the
 // sweep's traffic from 8 to 6 bytes per stored entry.
-__global__ void __launch_bounds__(RT) k_sweep_h(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+template <int BS>
+__global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                                 const int32_t *__restrict__ col, const __half *__restrict__ val,
                                                 int n, const float *__restrict__ x, float *__restrict__ y,
                                                 const float *__restrict__ b, const GmresState *__restrict__ st) {
     if (st->done) return;
-    const int r = blockIdx.x * RT + threadIdx.x;
+    const int r = blockIdx.x * BS + threadIdx.x;
     if (r >= n) return;
     const float om = (float)st->omega;
     const int sl = r >> 5, lane = r & 31;
@@ -218,6 +222,22 @@ __global__ void __launch_bounds__(RT) k_sweep_h(const uint32_t *__restrict__ sw,
     }
     y[r] = fmaf(om, b[r] - acc, x[r]);
 }
+
+// Row-parallel products of the Arnoldi steps and sweeps at the block size the
+// autotuner chose (64, 128, 256 or 512 threads).
+#define APC_SPMV_BS(c, n, KERNEL_OF, ...)                                                              \
+    do {                                                                                               \
+        switch ((c)->spmv_bs) {                                                                        \
+        case 64: APC_LAUNCH(c, K_SPMV, div_up(n, 64), 64, 0, KERNEL_OF(64), __VA_ARGS__); break;       \
+        case 128: APC_LAUNCH(c, K_SPMV, div_up(n, 128), 128, 0, KERNEL_OF(128), __VA_ARGS__); break;   \
+        case 512: APC_LAUNCH(c, K_SPMV, div_up(n, 512), 512, 0, KERNEL_OF(512), __VA_ARGS__); break;   \
+        default: APC_LAUNCH(c, K_SPMV, div_up(n, 256), 256, 0, KERNEL_OF(256), __VA_ARGS__); break;    \
+        }                                                                                              \
+    } while (0)
+#define APC_SPMV1(B) (k_spmv<1, T, B>)
+#define APC_SPMV3(B) (k_spmv<3, T, B>)
+#define APC_SPMV4(B) (k_spmv<4, T, B>)
+#define APC_SWEEPH(B) (k_sweep_h<B>)
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
 // Every arithmetic instruction does useful work on 32 lanes (GB300 runs FP64
@@ -582,6 +602,7 @@ struct Krylov {
     double omega = 1.0;
     const __half *hval = nullptr;   // FP16 copy of the matrix for the sweeps (FP32 vectors only)
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
+    bool graphs = true;             // replay full restart cycles as CUDA graphs
 };
 
 // z = p(Ahat) v with p(A) = omega sum_{i<d} (I - omega A)^i: d damped Jacobi
@@ -596,17 +617,108 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     for (int i = 1; i < K.pdeg; ++i) {
         if constexpr (sizeof(T) == 4) {
             if (K.hval) {
-                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, k_sweep_h, sw, so, col, K.hval, n, (const float *)cur,
+                APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
                            (float *)nxt, (const float *)v, (const GmresState *)st);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
         }
-        APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<3, T>), sw, so, col, val, n, (const T *)cur, nxt,
-                   (T *)nullptr, v, st, (double *)nullptr);
+        APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, val, n, (const T *)cur, nxt, (T *)nullptr, v, st,
+                    (double *)nullptr);
         T *tmp = cur; cur = nxt; nxt = tmp;
     }
     return cur;
+}
+
+// bnorm .. jlast of GmresState, read back once per restart cycle; jlast is the
+// number of columns the cycle completed (the residual product that opens the
+// next cycle resets jend)
+struct StateTail {
+    double bnorm, beta, inv_norm, rtol, omega;
+    int jend, done;
+    unsigned ticket;
+    int jlast;
+};
+static_assert(sizeof(StateTail) == sizeof(GmresState) - offsetof(GmresState, bnorm), "GmresState tail layout");
+
+__global__ void k_save_jend(GmresState *st) {
+    if (threadIdx.x == 0) st->jlast = st->jend;
+}
+
+// One restart cycle of jmax Arnoldi steps, the update of u, and the residual
+// b - Ahat u that opens the next cycle (beta, g, done for it).
+template <class T>
+apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, const Krylov<T> &K, int jmax) {
+    const int n = c->n_tot;
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    GmresState *st = K.st;
+    for (int j = 0; j < jmax; ++j) {
+        if (K.pdeg <= 1) {
+            APC_SPMV_BS(c, n, APC_SPMV1, sw, so, col, val, n, (const T *)K.wraw, K.w, K.V + (int64_t)j * K.ldv,
+                        (const T *)nullptr, st, (double *)nullptr);
+        } else {
+            // w = Ahat p(Ahat) v_j (right preconditioning)
+            T *vj = K.V + (int64_t)j * K.ldv;
+            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_normalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
+                       (const GmresState *)st);
+            T *z = poly_apply<T>(c, val, vj, K.z0, K, st);
+            APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, (const T *)z, K.w, (T *)nullptr,
+                        (const T *)nullptr, st, (double *)nullptr);
+        }
+        gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+        gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+        gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+    }
+    if (K.pdeg <= 1) {
+        APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv, u,
+                   (const GmresState *)st);
+    } else {
+        // u += p(Ahat) (V y)
+        APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), 256, 0, k_combine<T>, (const T *)K.V, K.ldv, n, K.t,
+                   (const GmresState *)st);
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_axpy_first<T>, (const T *)K.t, K.z0, n,
+                   (const GmresState *)st);
+        // the sweeps must run even though the cycle is done: clear the flag for them
+        GmresState *stp = st;
+        APC_CUDA(c, cudaMemsetAsync(&stp->done, 0, sizeof(int), c->s));
+        T *z = poly_apply<T>(c, val, K.t, K.z0, K, st);
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add<T>, u, (const T *)z, n);
+    }
+    // the next cycle's residual keeps this cycle's column count: save it first
+    APC_LAUNCH(c, K_VEC, 1, 32, 0, k_save_jend, st);
+    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
+               (T *)nullptr, b, st, K.partial);
+    return cuda_check(c, cudaGetLastError(), "gmres cycle");
+}
+
+template <class T>
+apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const Krylov<T> &K, int jmax, bool graph) {
+    if (graph && c->graphs_on && (c->timer.mask == 0 || c->graph_timing_ok)) {
+        GraphKey key;
+        memset(&key, 0, sizeof key);
+        key.tsize = (int)sizeof(T);
+        key.n = c->n_tot;
+        key.jmax = jmax;
+        key.pdeg = K.pdeg;
+        key.nblk = K.nblk;
+        key.ldv = K.ldv;
+        key.mask = c->timer.mask;
+        key.spmv_bs = c->spmv_bs;
+        const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
+                           c->slice_w.p, c->slice_off.p, c->ell_col.p};
+        for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
+        GraphEntry *g = find_graph(c, key);
+        if (!g) {
+            g = begin_capture(c, key);
+            if (g) {
+                apcloud_status st = cycle_launches<T>(c, val, b, u, K, jmax);
+                g = end_capture(c, g, st);
+            }
+        }
+        if (g) return launch_graph(c, g);
+    }
+    return cycle_launches<T>(c, val, b, u, K, jmax);
 }
 
 // Restarted GMRES(restart) on Ahat u = b, u in/out; no allocation.  Returns
@@ -631,50 +743,21 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
     double relres = 0.0;
     apcloud_status status = APCLOUD_W_NOT_CONVERGED;
     const double vb = (double)sizeof(T), nnz = (double)c->sum_m + (double)c->n_int + (double)c->n_bnd, dn = n;
+    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
+               (T *)nullptr, b, st, K.partial);
+    StateTail tail;
+    APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
     for (;;) {
-        APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
-                   (T *)nullptr, b, st, K.partial);
-        double tmp[2];  // bnorm and beta are adjacent in GmresState
-        APC_TRY(read_back(c, tmp, &st->bnorm, 2 * sizeof(double)));
-        relres = tmp[0] > 0.0 ? tmp[1] / tmp[0] : 0.0;
-        if (tmp[0] == 0.0 || tmp[1] <= rtol * tmp[0]) { status = APCLOUD_OK; break; }
+        relres = tail.bnorm > 0.0 ? tail.beta / tail.bnorm : 0.0;
+        if (tail.bnorm == 0.0 || tail.beta <= rtol * tail.bnorm) { status = APCLOUD_OK; break; }
         if (iters >= max_iter) break;
         const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
-        for (int j = 0; j < jmax; ++j) {
-            if (K.pdeg <= 1) {
-                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<1, T>), sw, so, col, val, n, (const T *)K.wraw,
-                           K.w, K.V + (int64_t)j * K.ldv, (const T *)nullptr, st, (double *)nullptr);
-            } else {
-                // w = Ahat p(Ahat) v_j (right preconditioning)
-                T *vj = K.V + (int64_t)j * K.ldv;
-                APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_normalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
-                           (const GmresState *)st);
-                T *z = poly_apply<T>(c, val, vj, K.z0, K, st);
-                APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<4, T>), sw, so, col, val, n, (const T *)z, K.w,
-                           (T *)nullptr, (const T *)nullptr, st, (double *)nullptr);
-            }
-            gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
-            gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
-            gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
-        }
-        if (K.pdeg <= 1) {
-            APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv,
-                       u, (const GmresState *)st);
-        } else {
-            // u += p(Ahat) (V y)
-            APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), 256, 0, k_combine<T>, (const T *)K.V, K.ldv, n, K.t,
-                       (const GmresState *)st);
-            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_axpy_first<T>, (const T *)K.t, K.z0, n,
-                       (const GmresState *)st);
-            // the sweeps must run even though the cycle is done: clear the flag for them
-            GmresState *stp = st;
-            APC_CUDA(c, cudaMemsetAsync(&stp->done, 0, sizeof(int), c->s));
-            T *z = poly_apply<T>(c, val, K.t, K.z0, K, st);
-            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add<T>, u, (const T *)z, n);
-        }
-        APC_CUDA(c, cudaGetLastError());
-        int je;
-        APC_TRY(read_back(c, &je, &st->jend, sizeof(int)));
+        // one restart cycle and the next restart's residual: a CUDA graph replay
+        // when the cycle is a full one, otherwise direct launches
+        APC_TRY(run_cycle<T>(c, val, b, u, K, jmax, jmax == m && K.graphs));
+        APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
+        harvest_graph_timing(c);
+        const int je = tail.jlast;
         // algorithmic traffic of the launches that did work (values + column index per entry)
         {
             // per Arnoldi step: one product with the full matrix, pdeg - 1 sweeps (FP16
@@ -693,7 +776,11 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         account(c, K_CYCLE, vb * dn * (je + 2), 2.0 * dn * je);
         iters += je;
         ++cycles;
-        if (je == 0) break;
+        if (je == 0) {
+            relres = tail.bnorm > 0.0 ? tail.beta / tail.bnorm : 0.0;
+            if (tail.bnorm == 0.0 || tail.beta <= rtol * tail.bnorm) status = APCLOUD_OK;
+            break;
+        }
     }
     *iters_out = iters;
     *cycles_out = cycles;
@@ -856,6 +943,76 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
     return status;
 }
 
+// Times the preconditioner sweep of the active form (FP16 values and FP32
+// vectors in the mixed form, else the matrix's own type; the plain Arnoldi
+// product when the preconditioner is Jacobi) at each block size and keeps the
+// fastest.  Contents of the work vectors do not matter for the timing.
+apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
+    const int n = c->n_tot;
+    const int64_t ldv = ((int64_t)n + 31) / 32 * 32;
+    const bool mixed = c->P.precision == 1;
+    const size_t es = mixed ? sizeof(float) : sizeof(double);
+    void *x = ensure<unsigned char>(c, c->pz0, (ldv + 1) * 8), *y = ensure<unsigned char>(c, c->pz1, (ldv + 1) * 8),
+         *bv = ensure<unsigned char>(c, c->pt, (ldv + 1) * 8);
+    GmresState *st = ensure<GmresState>(c, c->gstate, 1);
+    if (!x || !y || !bv || !st) return APCLOUD_E_NOMEM;
+    APC_CUDA(c, cudaMemsetAsync(x, 0, es * ldv, c->s));
+    APC_CUDA(c, cudaMemsetAsync(y, 0, es * ldv, c->s));
+    APC_CUDA(c, cudaMemsetAsync(bv, 0, es * ldv, c->s));
+    APC_CUDA(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s));
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    const int sizes[4] = {64, 128, 256, 512};
+    cudaEvent_t e0, e1;
+    APC_CUDA(c, cudaEventCreate(&e0));
+    APC_CUDA(c, cudaEventCreate(&e1));
+    const unsigned mask = c->timer.mask;
+    c->timer.mask = 0;
+    const int saved = c->spmv_bs;
+    double best = 1e30;
+    int pick = saved;
+    apcloud_status rc = APCLOUD_OK;
+    for (int t = 0; t < 4 && rc == APCLOUD_OK; ++t) {
+        c->spmv_bs = sizes[t];
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // warm-up pass, then the timed pass
+            cudaEventRecord(e0, c->s);
+            for (int k = 0; k < 10; ++k) {
+                if (mixed && c->P.poly_degree > 1) {
+                    const __half *hv = ptr<__half>(c->ell_A16);
+                    APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, hv, n, (const float *)x, (float *)y,
+                                (const float *)bv, (const GmresState *)st);
+                } else if (mixed) {
+                    using T = float;
+                    APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, ptr<float>(c->ell_A32), n, (const float *)x,
+                                (float *)y, (float *)nullptr, (const float *)nullptr, st, (double *)nullptr);
+                } else {
+                    using T = double;
+                    const int m = c->P.poly_degree > 1 ? 3 : 4;
+                    if (m == 3)
+                        APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, ptr<double>(c->ell_A), n, (const double *)x,
+                                    (double *)y, (double *)nullptr, (const double *)bv, st, (double *)nullptr);
+                    else
+                        APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, ptr<double>(c->ell_A), n, (const double *)x,
+                                    (double *)y, (double *)nullptr, (const double *)nullptr, st, (double *)nullptr);
+                }
+            }
+            cudaEventRecord(e1, c->s);
+            rc = cuda_check(c, cudaEventSynchronize(e1), "autotune spmv");
+            if (rc != APCLOUD_OK) break;
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        const double per = ms / 10.0;
+        if (ms_out) ms_out[t] = per;
+        if (per < best) { best = per; pick = sizes[t]; }
+    }
+    c->timer.mask = mask;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->spmv_bs = (rc == APCLOUD_OK) ? pick : saved;
+    return rc;
+}
+
 }  // namespace apc
 
 // ---------------------------------------------------------------- allocation-free solve
@@ -945,6 +1102,7 @@ extern "C" apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *c, int which
     do {
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
         Krylov<double> K{V, ldv, w, wraw, st, partial, nblk};
+        K.graphs = false;   // instantiating a graph allocates
         // gmres_core clears the device state itself (the array keeps the previous call's contents)
         status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) break;

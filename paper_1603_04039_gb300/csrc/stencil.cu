@@ -22,7 +22,6 @@ namespace apc {
 
 namespace {
 
-constexpr int SW = 4;           // warps (nodes) per block
 constexpr double FP32_RATIO_MIN = 1e-3;  // condition estimate limit of the FP32 factorisation
 constexpr int ASTR = NCOL;      // row stride of the staged Vandermonde
 
@@ -44,9 +43,6 @@ struct WarpSmem {
     long long cut;
 };
 
-struct BlockSmem {
-    WarpSmem w[SW];
-};
 
 __constant__ unsigned char c_pa[45], c_pb[45];
 
@@ -238,16 +234,17 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__
     return true;
 }
 
-__global__ void __launch_bounds__(SW * 32, 3) k_stencil(
+// SW warps (nodes) per block, one WarpSmem each; the autotuner picks SW
+template <int SW>
+__global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stencil(
     const int4 *__restrict__ ic, const int32_t *__restrict__ adj, const int32_t *__restrict__ bowner, int n_int,
     int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
     int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,
     double *__restrict__ lapd_out, double *__restrict__ D_out, int64_t dstride, double *__restrict__ rcond_out,
     int fp32_first, int *__restrict__ fp64_count, unsigned *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    BlockSmem &S = *reinterpret_cast<BlockSmem *>(smem_raw);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem &W = S.w[wid];
+    WarpSmem &W = reinterpret_cast<WarpSmem *>(smem_raw)[wid];
     const int y0 = blockIdx.x * SW + wid;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
@@ -506,6 +503,23 @@ __global__ void k_values_f32(const double *__restrict__ vA, const double *__rest
     }
 }
 
+template <int SW>
+apcloud_status launch_stencil(apcloud_ctx *c, int n, double unit, double ec, double inv_1mec, int32_t *nbr,
+                              int32_t *msz, int32_t *ring, double *lap, double *lapd, double *D, int64_t dstride,
+                              double *rc, unsigned *derr) {
+    const size_t smem = SW * sizeof(WarpSmem);
+    static bool attr = false;
+    if (!attr) {
+        APC_CUDA(c, cudaFuncSetAttribute(k_stencil<SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    APC_LAUNCH(c, K_STENCIL, div_up(n, SW), SW * 32, smem, k_stencil<SW>, ptr<int4>(c->node_ic),
+               ptr<int32_t>(c->adj), ptr<int32_t>(c->bowner), n, c->P.m_target, c->P.ring_max, unit, ec, inv_1mec,
+               nbr, msz, ring, lap, lapd, D, dstride, rc, c->P.precision == 1 ? 1 : 0,
+               reinterpret_cast<int *>(derr + 1), derr);
+    return APCLOUD_OK;
+}
+
 }  // namespace
 
 static bool g_pairs_set = false;
@@ -537,15 +551,17 @@ apcloud_status build_stencils(apcloud_ctx *c) {
     const double unit = ldexp(ext, -(KEY_DEPTH + 1));
     const double ec = exp(-c->P.weight_c);
     const double inv_1mec = 1.0 / (1.0 - ec);
-    size_t smem = sizeof(BlockSmem);
-    static bool attr = false;
-    if (!attr) {
-        APC_CUDA(c, cudaFuncSetAttribute(k_stencil, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
+    switch (c->wls_warps) {
+    case 2:
+        APC_TRY(launch_stencil<2>(c, n, unit, ec, inv_1mec, nbr, msz, ring, lap, lapd, D, dstride, rc, derr));
+        break;
+    case 8:
+        APC_TRY(launch_stencil<8>(c, n, unit, ec, inv_1mec, nbr, msz, ring, lap, lapd, D, dstride, rc, derr));
+        break;
+    default:
+        APC_TRY(launch_stencil<4>(c, n, unit, ec, inv_1mec, nbr, msz, ring, lap, lapd, D, dstride, rc, derr));
+        break;
     }
-    APC_LAUNCH(c, K_STENCIL, div_up(n, SW), SW * 32, smem, k_stencil, ptr<int4>(c->node_ic), ptr<int32_t>(c->adj),
-               ptr<int32_t>(c->bowner), n, c->P.m_target, c->P.ring_max, unit, ec, inv_1mec, nbr, msz, ring, lap,
-               lapd, D, dstride, rc, c->P.precision == 1 ? 1 : 0, reinterpret_cast<int *>(derr + 1), derr);
     APC_CUDA(c, cudaGetLastError());
     APC_TRY(check_device_errors(c));
     {
@@ -596,6 +612,61 @@ apcloud_status build_stencils(apcloud_ctx *c) {
                    (const double *)vB, c->ell_entries, fA, fB, hA, hB);
     }
     return cuda_check(c, cudaGetLastError(), "ell");
+}
+
+}  // namespace apc
+
+namespace apc {
+
+// Times the stencil kernel at 2, 4 and 8 nodes per block on the current node
+// set (after build_stencils) and keeps the fastest.  Every node's outputs are
+// independent of the block shape, so the reruns rewrite identical values.
+apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out) {
+    const int n = c->n_int;
+    if (n == 0) return APCLOUD_OK;
+    const int64_t dstride = ((int64_t)n + 31) / 32 * 32;
+    int32_t *nbr = ptr<int32_t>(c->nbr), *msz = ptr<int32_t>(c->msz), *ring = ptr<int32_t>(c->ring);
+    double *lap = ptr<double>(c->lap), *lapd = ptr<double>(c->lapd), *D = ptr<double>(c->D);
+    double *rc = ptr<double>(c->rcond);
+    unsigned *derr = ptr<unsigned>(c->derr);
+    const double ext = c->P.hi[0] - c->P.lo[0];
+    const double unit = ldexp(ext, -(KEY_DEPTH + 1));
+    const double ec = exp(-c->P.weight_c);
+    const double inv_1mec = 1.0 / (1.0 - ec);
+    const int shapes[3] = {2, 4, 8};
+    cudaEvent_t e0, e1;
+    APC_CUDA(c, cudaEventCreate(&e0));
+    APC_CUDA(c, cudaEventCreate(&e1));
+    const unsigned mask = c->timer.mask;
+    c->timer.mask = 0;
+    double best = 1e30;
+    int pick = c->wls_warps;
+    apcloud_status st = APCLOUD_OK;
+    for (int t = 0; t < 3 && st == APCLOUD_OK; ++t) {
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == APCLOUD_OK; ++rep) {
+            st = cuda_check(c, cudaMemsetAsync(derr, 0, 4 * sizeof(unsigned), c->s), "autotune stencils");
+            if (st != APCLOUD_OK) break;
+            cudaEventRecord(e0, c->s);
+            if (shapes[t] == 2)
+                st = launch_stencil<2>(c, n, unit, ec, inv_1mec, nbr, msz, ring, lap, lapd, D, dstride, rc, derr);
+            else if (shapes[t] == 4)
+                st = launch_stencil<4>(c, n, unit, ec, inv_1mec, nbr, msz, ring, lap, lapd, D, dstride, rc, derr);
+            else
+                st = launch_stencil<8>(c, n, unit, ec, inv_1mec, nbr, msz, ring, lap, lapd, D, dstride, rc, derr);
+            cudaEventRecord(e1, c->s);
+            if (st == APCLOUD_OK) st = cuda_check(c, cudaEventSynchronize(e1), "autotune stencils");
+            if (st == APCLOUD_OK) cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (st == APCLOUD_OK) st = check_device_errors(c);
+        if (ms_out) ms_out[t] = ms;
+        if (st == APCLOUD_OK && ms < best) { best = ms; pick = shapes[t]; }
+    }
+    c->timer.mask = mask;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == APCLOUD_OK) c->wls_warps = pick;
+    return st;
 }
 
 }  // namespace apc

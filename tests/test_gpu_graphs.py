@@ -1,0 +1,104 @@
+"""GMRES restart cycles replayed as CUDA graphs give the same bits as direct
+launches, count their kernels, and keep the per-kernel timers working."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1603_04039_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("form", [dict(precision="fp64"), dict(precision="fp64", poly_degree=8, poly_omega=1.0),
+                                  dict(precision="mixed", poly_degree=16, poly_omega=1.0)])
+def test_graph_replay_is_bit_identical(form):
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(60000, 21)
+    res = []
+    for graphs in (False, True):
+        ap = APCloud(max_depth=6, c_refine=0.3, restart=12, **form)
+        ap.set_graphs(graphs)
+        ap.build_octree(_t(x), _t(y), _t(z))
+        ap.stencils()
+        ap.deposit(q_uniform=1.0 / len(x), rtol=1e-11)
+        l0 = ap.launch_count()
+        phi, info = ap.solve(rtol=1e-11)
+        launches = ap.launch_count() - l0
+        php, ex, ey, ez = ap.gather_field()
+        st = ap.graph_stats()
+        res.append((phi.cpu().numpy(), ex.cpu().numpy(), info["iters"], launches, st))
+    assert np.array_equal(res[0][0], res[1][0])
+    assert np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
+    assert res[0][4]["replays"] == 0
+    assert res[1][4]["replays"] > 0 and res[1][4]["cached"] >= 1
+    # a replay counts every kernel node: the same kernels ran either way
+    assert res[0][3] == res[1][3]
+
+
+def test_timers_inside_graphs():
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(40000, 22)
+    out = []
+    for graphs in (False, True):
+        ap = APCloud(max_depth=6, c_refine=0.4, restart=10)
+        ap.set_graphs(graphs)
+        ap.build_octree(_t(x), _t(y), _t(z))
+        ap.stencils()
+        ap.deposit(q_uniform=1.0 / len(x), rtol=1e-11)
+        ap.get_timing(reset=True)
+        ap.set_timing(0xFFFF)
+        ap.solve(rtol=1e-11)
+        t = ap.get_timing(reset=True)
+        ap.set_timing(0)
+        out.append(t)
+    for kind in ("spmv", "gmres_dots", "gmres_update_dots", "gmres_update_norm", "gmres_cycle_end"):
+        assert out[1][kind][1] == out[0][kind][1], kind     # timed launches
+        assert out[1][kind][0] > 0.0, kind                  # milliseconds
+        assert out[1][kind][2] == out[0][kind][2], kind     # algorithmic bytes
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_launch_shapes_do_not_change_results(precision):
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(50000, 23)
+    res = []
+    for bs, ww in ((256, 4), (64, 2), (512, 8), (128, 4)):
+        ap = APCloud(max_depth=6, c_refine=0.3, precision=precision, poly_degree=8, poly_omega=1.0)
+        ap.set_launch_shape(bs, ww)
+        ap.build_octree(_t(x), _t(y), _t(z))
+        ap.stencils()
+        ap.deposit(q_uniform=1.0 / len(x), rtol=1e-11)
+        phi, info = ap.solve(rtol=1e-11)
+        g = ap.get_stencils()
+        res.append((phi.cpu().numpy(), g["D"].cpu().numpy(), g["nbr"].cpu().numpy(), info["iters"]))
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+
+
+def test_autotune_choices_and_rejects():
+    from paper_1603_04039_gb300 import APCloud, APCloudError
+    x, y, z, q = inputs.beam_with_halo(80000, 24)
+    ap = APCloud(max_depth=6, c_refine=0.3, precision="mixed", poly_degree=16, poly_omega=1.0)
+    with pytest.raises(APCloudError) as e:
+        ap.autotune()
+    assert e.value.status == -7
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    before = ap.get_stencils()["D"].cpu().numpy()
+    t = ap.autotune()
+    assert t["spmv_block"] in (64, 128, 256, 512) and t["wls_warps"] in (2, 4, 8)
+    assert all(v > 0 for v in t["spmv_ms"].values()) and all(v > 0 for v in t["wls_ms"].values())
+    assert np.array_equal(ap.get_stencils()["D"].cpu().numpy(), before)
+    _, info = ap.deposit(q_uniform=1.0 / len(x), rtol=1e-10)
+    assert info["status"] == 0
+    for bad in ((100, 4), (256, 3)):
+        with pytest.raises(APCloudError):
+            ap.set_launch_shape(*bad)
