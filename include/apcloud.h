@@ -301,6 +301,68 @@ apcloud_status apcloud_graph_stats(const apcloud_ctx *ctx, int64_t *h_replays, i
  * from the last apcloud_gather_field times cell volumes), FP64, fixed order. */
 apcloud_status apcloud_field_energy(apcloud_ctx *ctx, double *h_energy);
 
+/* ---- learned preconditioner (no counterpart in the paper) ----
+ * A message-passing network over the GFD stencil graph proposes, for the
+ * Poisson system A phi = c rho of Section 3.2 step 2, a diagonal right
+ * preconditioner and an initial guess.  With Ahat = A D^-1 (D = diag A):
+ *   W = |Ahat_off| + |Ahat_off|^T, P = W normalised by its row sums;
+ *   H_0 = 16 node features (row and column sums of the WLS weights through
+ *   sign(f) log(1 + |f|), mean neighbour offset and level offset, b and P b
+ *   scaled by max|b|, degree);
+ *   H_{l+1} = relu([H_l | P H_l] W_l + b_l), l = 0, 1, 2, width 64;
+ *   t = H_3 W_o + b_o; s = exp(8 tanh t_0); gamma = exp(tanh t_1).
+ * The solve then runs GMRES on Ahat S (columns scaled by s) from the guess
+ * x0 = gamma b / D.  Training minimises L = Lp + Lg with
+ *   Lp = (1/n) ||I - Ahat S||_F^2 (approximate-inverse objective),
+ *   Lg = ||b - Ahat (gamma b)||^2 / ||b||^2 (initial residual of the guess).
+ * Dense layers and their gradients run on the tensor cores in BF16 with FP32
+ * accumulation; master weights are FP32.  Flat parameter layout (FP32):
+ *   W0 [32][64], b0 [64], W1 [128][64], b1 [64], W2 [128][64], b2 [64],
+ *   Wo [64][2], bo [2]  (apcloud_mpnn_num_params() values).
+ * A network object lives on the device that was current at creation and
+ * may be used with any context on that device. */
+typedef struct apcloud_mpnn apcloud_mpnn;
+
+int apcloud_mpnn_num_params(void);
+
+/* Creates a network with the given host parameters, or (h_theta NULL)
+ * Glorot-uniform layers drawn from SplitMix64(seed) with zero biases and a
+ * zero head, which is exactly Jacobi (s = 1) with the guess gamma = 1.
+ * Synchronises the device. */
+apcloud_status apcloud_mpnn_create(const float *h_theta, uint64_t seed, apcloud_mpnn **out);
+void apcloud_mpnn_destroy(apcloud_mpnn *net);
+
+/* Host copies of the parameters and of the last gradient (either NULL),
+ * and replacement of the parameters (which also clears the Adam moments).
+ * Both synchronise the device. */
+apcloud_status apcloud_mpnn_get_params(apcloud_mpnn *net, float *h_theta, float *h_grad);
+apcloud_status apcloud_mpnn_set_params(apcloud_mpnn *net, const float *h_theta);
+
+/* Loss of the network on ctx's current Poisson system (after
+ * apcloud_deposit; boundary data g = 0): h_loss[3] = {L, Lp, Lg}.  With
+ * backward != 0 also the gradient dL/dtheta (kept in the network for
+ * apcloud_mpnn_adam).  Synchronises.  APCLOUD_E_TIMEOUT if a tensor-core
+ * layer gave up waiting for its MMAs. */
+apcloud_status apcloud_mpnn_loss(apcloud_ctx *ctx, apcloud_mpnn *net, int backward, double *h_loss);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with learning rate lr on the
+ * last gradient, on ctx's stream. */
+apcloud_status apcloud_mpnn_adam(apcloud_ctx *ctx, apcloud_mpnn *net, float lr);
+
+/* Network outputs on ctx's current Poisson system (device FP32, n_nodes
+ * entries each, any NULL): column scaling s, guess factor gamma, and the
+ * n_nodes x 16 node features.  Synchronises. */
+apcloud_status apcloud_mpnn_outputs(apcloud_ctx *ctx, apcloud_mpnn *net, float *d_s, float *d_gamma,
+                                    float *d_features);
+
+/* apcloud_solve (g = 0) with the network's proposals: bit 0 of `use` scales
+ * the preconditioner columns by s, bit 1 starts from x0 = gamma b / D; use =
+ * 0 is plain apcloud_solve from phi = 0.  The stored matrix is restored
+ * afterwards.  The residual test is the same FP64 true residual, so the
+ * network can change the iteration count, never the accuracy. */
+apcloud_status apcloud_solve_learned(apcloud_ctx *ctx, apcloud_mpnn *net, unsigned use, double rtol, int max_iter,
+                                     double *d_phi_out, apcloud_solve_info *info);
+
 /* Per-kernel device timing with CUDA events on the context stream.
  * apcloud_set_timing(ctx, mask) enables timing for the kernel kinds whose
  * bit is set in mask (bit k = kind k, see apcloud_kernel_name), 0 disables.
@@ -309,7 +371,7 @@ apcloud_status apcloud_field_energy(apcloud_ctx *ctx, double *h_energy);
  * count, and the algorithmic bytes and floating-point operations of those
  * launches (what the kernel must move and compute, not what it did), since
  * the last reset (reset = 1 clears). */
-#define APCLOUD_NUM_KINDS 16
+#define APCLOUD_NUM_KINDS 18
 apcloud_status apcloud_set_timing(apcloud_ctx *ctx, unsigned mask);
 apcloud_status apcloud_get_timing(apcloud_ctx *ctx, double *h_ms, int64_t *h_launches, double *h_bytes,
                                   double *h_flops, int reset);

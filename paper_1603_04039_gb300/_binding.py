@@ -18,7 +18,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libapcloud.so")
 
-NUM_KINDS = 16
+NUM_KINDS = 18
 MMAX = 32
 NCOL = 9
 
@@ -97,6 +97,15 @@ def load():
             "apcloud_push_particles": (I, [P, P, P, P, P, P, P, L, P, P, P, D, D]),
             "apcloud_field_energy": (I, [P, C.POINTER(D)]),
             "apcloud_measure_fma_peak": (I, [C.POINTER(D), C.POINTER(D)]),
+            "apcloud_mpnn_num_params": (I, []),
+            "apcloud_mpnn_create": (I, [P, C.c_uint64, C.POINTER(P)]),
+            "apcloud_mpnn_destroy": (None, [P]),
+            "apcloud_mpnn_get_params": (I, [P, P, P]),
+            "apcloud_mpnn_set_params": (I, [P, P]),
+            "apcloud_mpnn_loss": (I, [P, P, I, P]),
+            "apcloud_mpnn_adam": (I, [P, P, C.c_float]),
+            "apcloud_mpnn_outputs": (I, [P, P, P, P, P]),
+            "apcloud_solve_learned": (I, [P, P, C.c_uint, D, I, P, C.POINTER(SolveInfo)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -402,6 +411,15 @@ class APCloud:
     def set_launch_shape(self, spmv_block=256, wls_warps=4):
         self._check(self._lib.apcloud_set_launch_shape(self._ctx, int(spmv_block), int(wls_warps)))
 
+    def solve_learned(self, net, use=3, rtol=1e-10, max_iter=100000):
+        """Poisson solve with the network's column scaling (use bit 0) and guess (bit 1)."""
+        phi = self._empty(self.n_nodes)
+        info = SolveInfo()
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_solve_learned(self._ctx, net._net, int(use), rtol, int(max_iter),
+                                                             _dptr(phi), C.byref(info)))
+        return phi, dict(info.as_dict(), status=st)
+
     def set_graphs(self, enable):
         with torch.cuda.device(self.device):
             self._check(self._lib.apcloud_set_graphs(self._ctx, 1 if enable else 0))
@@ -435,3 +453,73 @@ class APCloud:
 
     def launch_count(self):
         return int(self._lib.apcloud_launch_count(self._ctx))
+
+
+class MPNN:
+    """The learned preconditioner network (see include/apcloud.h)."""
+
+    def __init__(self, theta=None, seed=0, device="cuda:0"):
+        lib = load()
+        self._lib = lib
+        self.device = torch.device(device)
+        self.n_params = lib.apcloud_mpnn_num_params()
+        net = C.c_void_p()
+        arr = None
+        if theta is not None:
+            arr = np.ascontiguousarray(theta, dtype=np.float32)
+            assert arr.size == self.n_params
+        with torch.cuda.device(self.device):
+            st = lib.apcloud_mpnn_create(arr.ctypes.data_as(C.c_void_p) if arr is not None else None, int(seed),
+                                         C.byref(net))
+        if st != 0:
+            raise APCloudError(st, "apcloud_mpnn_create failed")
+        self._net = net
+
+    def close(self):
+        if getattr(self, "_net", None):
+            with torch.cuda.device(self.device):
+                self._lib.apcloud_mpnn_destroy(self._net)
+            self._net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        th = np.zeros(self.n_params, dtype=np.float32)
+        g = np.zeros(self.n_params, dtype=np.float32)
+        with torch.cuda.device(self.device):
+            st = self._lib.apcloud_mpnn_get_params(self._net, th.ctypes.data_as(C.c_void_p), g.ctypes.data_as(C.c_void_p))
+        if st != 0:
+            raise APCloudError(st, "apcloud_mpnn_get_params failed")
+        return th, g
+
+    def set_params(self, theta):
+        arr = np.ascontiguousarray(theta, dtype=np.float32)
+        with torch.cuda.device(self.device):
+            st = self._lib.apcloud_mpnn_set_params(self._net, arr.ctypes.data_as(C.c_void_p))
+        if st != 0:
+            raise APCloudError(st, "apcloud_mpnn_set_params failed")
+
+    def loss(self, ap, backward=False):
+        out = np.zeros(3)
+        with torch.cuda.device(self.device):
+            ap._check(self._lib.apcloud_mpnn_loss(ap._ctx, self._net, 1 if backward else 0,
+                                                  out.ctypes.data_as(C.c_void_p)))
+        return {"L": out[0], "Lp": out[1], "Lg": out[2]}
+
+    def adam(self, ap, lr=1e-3):
+        with torch.cuda.device(self.device):
+            ap._check(self._lib.apcloud_mpnn_adam(ap._ctx, self._net, C.c_float(lr)))
+
+    def outputs(self, ap):
+        n = ap.n_nodes
+        s = torch.empty(n, dtype=torch.float32, device=ap.device)
+        g = torch.empty(n, dtype=torch.float32, device=ap.device)
+        f = torch.empty(n, 16, dtype=torch.float32, device=ap.device)
+        with torch.cuda.device(self.device):
+            ap._check(self._lib.apcloud_mpnn_outputs(ap._ctx, self._net, _dptr(s), _dptr(g), _dptr(f)))
+        return {"s": s, "gamma": g, "features": f}
+

@@ -461,6 +461,15 @@ __global__ void k_copy_nf(const double *__restrict__ nf, int n, double *__restri
     o[t] = nf[j * 12 + 1 + r];
 }
 }  // namespace
+
+double *poisson_rhs(apcloud_ctx *c, const double *g) {
+    double *b = ensure<double>(c, c->b, c->n_tot + 1);
+    if (!b) return nullptr;
+    APC_LAUNCH(c, K_VEC, div_up(c->n_tot, 256), 256, 0, k_poisson_rhs, ptr<double>(c->rho), g, c->n_int, c->n_tot,
+               c->P.poisson_c, b);
+    return b;
+}
+
 }  // namespace apc
 
 extern "C" {
@@ -657,7 +666,7 @@ const char *apcloud_kernel_name(int kind) {
     static const char *names[NKIND] = {"morton_keys", "radix_sort", "tree", "face_adjacency", "ring_select_wls",
                                        "assemble_ell", "deposit", "spmv", "gmres_dots", "gmres_update_dots",
                                        "gmres_update_norm", "gmres_cycle_end", "derivatives", "gather",
-                                       "vector", "copy"};
+                                       "vector", "copy", "mpnn_dense_tc", "mpnn_graph"};
     return (kind >= 0 && kind < NKIND) ? names[kind] : "unknown";
 }
 

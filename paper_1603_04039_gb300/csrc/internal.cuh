@@ -22,7 +22,7 @@ constexpr int MAX_RESTART = 64;
 // kernel kinds for the event timers (bit k of the timing mask)
 enum Kind {
     K_KEYS = 0, K_SORT, K_TREE, K_ADJ, K_STENCIL, K_ELL, K_DEPOSIT, K_SPMV,
-    K_DOT, K_UPDDOT, K_UPDNORM, K_CYCLE, K_DERIV, K_GATHER, K_VEC, K_COPY, NKIND
+    K_DOT, K_UPDDOT, K_UPDNORM, K_CYCLE, K_DERIV, K_GATHER, K_VEC, K_COPY, K_MPNN_TC, K_MPNN_GRAPH, NKIND
 };
 static_assert(NKIND == APCLOUD_NUM_KINDS, "kind count");
 
@@ -130,6 +130,8 @@ struct apcloud_ctx {
     // nodes
     apc::DBuf leaf_anchor, leaf_level, leaf_first, leaf_count, node_ic, bowner, bface, bidx, adj;
     apc::DBuf beam_off, leaf_beam, beam_rng, beam_norm;
+    apc::DBuf mp[48];   // learned preconditioner: graph, activations, gradients (indices in mpnn.cu)
+    int mp_graph_n = -1; // node count the graph in mp was built for (-1: none)
     // stencils
     apc::DBuf nbr, msz, ring, lap, lapd, D, rcond;
     // matrices (sliced ELL, 32-row slices, column-major inside a slice)
@@ -187,6 +189,8 @@ apcloud_status radix_sort(apcloud_ctx *c, uint64_t *k0, uint32_t *v0, uint64_t *
 apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,
                             const int64_t *h_offsets, int nbeams);
 apcloud_status node_beams(apcloud_ctx *c, int32_t *out);
+apcloud_status refresh_lowp(apcloud_ctx *c);          // FP32/FP16 matrix copies from the FP64 values
+double *poisson_rhs(apcloud_ctx *c, const double *g);  // b of the Poisson system into c->b
 apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out);      // ms per sweep at 64/128/256/512 threads
 apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out);  // ms per build at 2/4/8 warps
 // CUDA graphs of restart cycles

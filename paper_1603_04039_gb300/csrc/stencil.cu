@@ -670,3 +670,16 @@ apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out) {
 }
 
 }  // namespace apc
+
+namespace apc {
+
+// FP32/FP16 copies of the stored values again (after the FP64 values changed)
+apcloud_status refresh_lowp(apcloud_ctx *c) {
+    if (c->P.precision != 1 || c->ell_entries == 0) return APCLOUD_OK;
+    APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)ptr<double>(c->ell_A),
+               (const double *)ptr<double>(c->ell_B), c->ell_entries, ptr<float>(c->ell_A32), ptr<float>(c->ell_B32),
+               ptr<__half>(c->ell_A16), ptr<__half>(c->ell_B16));
+    return cuda_check(c, cudaGetLastError(), "refresh_lowp");
+}
+
+}  // namespace apc
