@@ -128,7 +128,7 @@ def run_ours(args, ws, rank, local):
     import torch.distributed as dist
 
     from paper_1603_04039_gb300 import APCloud, inputs
-    from paper_1603_04039_gb300._binding import measure_fma_peak
+    from paper_1603_04039_gb300._binding import kernel_names, measure_fma_peak
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -169,14 +169,13 @@ def run_ours(args, ws, rank, local):
     # warm-up; the last warm-up step times every kernel kind to find the dominant one
     for w in range(args.warmup):
         if w == args.warmup - 1:
-            ap.set_timing(0xFFFF)
+            ap.set_timing((1 << len(kernel_names())) - 1)
         step()
     torch.cuda.synchronize()
     all_kinds = ap.get_timing(reset=True)
     ap.set_timing(0)
     solve_kinds = {k: v for k, v in all_kinds.items() if v[1] > 0}
     dominant = max(solve_kinds, key=lambda k: solve_kinds[k][0])
-    from paper_1603_04039_gb300._binding import kernel_names
     dom_bit = kernel_names().index(dominant)
 
     # timed region: inputs resident (positions and charges, 320 MB > L2)
@@ -426,7 +425,10 @@ def run_vp(args):
     t = [torch.from_numpy(a).to(dev) for a in (x, y, z) + vel]
     form = dict(max_depth=depth, c_refine=c, precision=args.precision, poly_degree=args.poly_degree,
                 poly_omega=args.poly_omega)
-    vp = VlasovPoisson(*t, qm=1.0, rtol=RTOL, **form)
+    net, t_train = None, 0.0
+    if args.learned:
+        net, t_train, _ = train_mpnn(args.train_systems)
+    vp = VlasovPoisson(*t, qm=1.0, rtol=RTOL, net=net, **form)
     dt = 1e-3
     for _ in range(args.warmup):
         vp.step(dt)
@@ -484,11 +486,104 @@ def run_vp(args):
             "data": "synthetic",
             "config": {"workload": "vp_beam_halo_1e7_depth10", "particles": npart, "dt": dt, "sigma_v": 0.01,
                        "precision": args.precision, "poly_degree": args.poly_degree,
+                       "learned_preconditioner": (None if net is None else
+                                                  {"train_systems": args.train_systems, "use": "column scaling",
+                                                   "train_seconds": round(t_train, 1)}),
                        "mean_gmres_iters": iters / args.steps},
             "energy": {"field_start": w0, "kinetic_start": k0, "field_end": w1, "kinetic_end": k1,
                        "total_drift_rel": (w1 + k1 - w0 - k0) / (w0 + k0)},
             "oracle_10_steps": {"particles": ns, "max_rel_field_energy_diff": float(dw),
                                 "oracle_seconds": round(t_or, 1)}}
+
+
+TRAIN_SIZES = ((20000, 6, 0.3), (100000, 8, 0.15))
+
+
+def train_mpnn(n_systems, seed0=10000, lr=2e-3, net_seed=7):
+    """Trains the learned preconditioner on the GPU: one Adam step on each of
+    n_systems fresh systems from the beam-with-halo law (seeds seed0, seed0 +
+    1, ...), alternating 2e4 particles at depth 6 and 1e5 at depth 8.
+    Returns the network, seconds spent and the loss curve."""
+    import torch
+    from paper_1603_04039_gb300 import APCloud, MPNN, inputs
+    dev = torch.device("cuda", 0)
+    net = MPNN(seed=net_seed)
+    aps = [APCloud(max_depth=d, c_refine=cc, device=dev) for _, d, cc in TRAIN_SIZES]
+    curve = []
+    t0 = time.perf_counter()
+    for k in range(n_systems):
+        npart = TRAIN_SIZES[k % len(TRAIN_SIZES)][0]
+        ap = aps[k % len(TRAIN_SIZES)]
+        x, y, z, q = inputs.beam_with_halo(npart, seed0 + k)
+        tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
+        ap.build_octree(tx, ty, tz)
+        ap.stencils()
+        ap.deposit(q=tq, rtol=1e-10)
+        lo = net.loss(ap, backward=True)
+        net.adam(ap, lr=lr)
+        if k % max(1, n_systems // 20) == 0 or k == n_systems - 1:
+            curve.append((k, round(lo["L"], 5), round(lo["Lp"], 5), round(lo["Lg"], 5)))
+    return net, time.perf_counter() - t0, curve
+
+
+def run_learned(args):
+    """Learned preconditioner: trained on the GPU on args.train_systems
+    beam-with-halo systems, evaluated on held-out seeds of the 1e7-particle
+    depth-10 workload: GMRES iterations and solve time to rtol 1e-10 with
+    Jacobi alone, with the network's column scaling (and guess), and with the
+    closed-form diagonal of the same objective, in the plain FP64 form; and
+    in the mixed form with the degree-16 polynomial."""
+    import torch
+    from paper_1603_04039_gb300 import APCloud, inputs
+    dev = torch.device("cuda", 0)
+    net, t_train, curve = train_mpnn(args.train_systems)
+    npart, depth, c = WORKLOADS["beam_halo_1e7_depth10"]
+    forms = {"fp64_jacobi": (dict(precision="fp64", poly_degree=1), (1, 3, 4)),
+             "mixed_poly16": (dict(precision="mixed", poly_degree=16, poly_omega=1.0), (1, 2, 4))}
+    names = {0: "jacobi", 1: "learned_scaling", 2: "learned_guess", 3: "learned_scaling_guess",
+             4: "closed_form_scaling"}
+    rows = []
+    for seed in args.eval_seeds:
+        x, y, z, q = inputs.beam_with_halo(npart, seed)
+        tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
+        for fname, (form, uses) in forms.items():
+            ap = APCloud(max_depth=depth, c_refine=c, device=dev, **form)
+            ap.build_octree(tx, ty, tz)
+            ap.stencils()
+            ap.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
+            lo = net.loss(ap)
+            res = {}
+            for use in (0,) + uses:
+                best = None
+                for rep in range(2):
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(ap.stream)
+                    phi, info = ap.solve_learned(net, use=use, rtol=RTOL, max_iter=args.learned_max_iter)
+                    e1.record(ap.stream)
+                    torch.cuda.synchronize()
+                    ms = e0.elapsed_time(e1)
+                    best = ms if best is None else min(best, ms)
+                res[names[use]] = {"iters": info["iters"], "ms": round(best, 2), "relres": info["relres"],
+                                   "status": info["status"], "phi": phi}
+            ref = res["jacobi"]["phi"]
+            for r in res.values():
+                r["rel_l2_phi_vs_jacobi"] = float(torch.linalg.norm(r.pop("phi") - ref) / torch.linalg.norm(ref))
+                r["speedup"] = round(res["jacobi"]["ms"] / r["ms"], 3)
+            rows.append({"seed": seed, "form": fname, "n_nodes": ap.n_nodes, "loss_learned": lo, **res})
+            ap.close()
+    fp = [r for r in rows if r["form"] == "fp64_jacobi"]
+    speed = float(np.mean([r["learned_scaling_guess"]["speedup"] for r in fp]))
+    return {"metric": "GMRES(30) time to rtol 1e-10 on held-out seeds, Jacobi / learned preconditioner",
+            "value": round(speed, 3), "unit": "x", "n_gpus": 1, "steps": len(args.eval_seeds), "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
+            "data": "synthetic",
+            "config": {"workload": "learned_preconditioner_beam_halo_1e7_depth10", "train_systems": args.train_systems,
+                       "train_law": "beam with halo, alternating 2e4 particles depth 6 c 0.3 and 1e5 "
+                                    "particles depth 8 c 0.15, seeds 10000..",
+                       "eval_seeds": args.eval_seeds, "net": "3 x 64 message passing, BF16 tcgen05 layers",
+                       "ilu0": "not built"},
+            "train_seconds": round(t_train, 1), "loss_curve": curve, "eval": rows}
 
 
 def main():
@@ -503,9 +598,18 @@ def main():
     ap.add_argument("--poly-degree", type=int, default=16, help="1 = Jacobi")
     ap.add_argument("--poly-omega", type=float, default=1.0)
     ap.add_argument("--vp", action="store_true", help="Vlasov-Poisson leapfrog workload instead of single solves")
+    ap.add_argument("--learned", action="store_true",
+                    help="train the learned preconditioner and compare it with Jacobi on held-out seeds "
+                         "(with --vp: use its column scaling in the leapfrog solves)")
+    ap.add_argument("--train-systems", type=int, default=10000)
+    ap.add_argument("--eval-seeds", type=int, nargs="+", default=[90001, 90002])
+    ap.add_argument("--learned-max-iter", type=int, default=20000)
     args = ap.parse_args()
     if args.vp:
         print(json.dumps(run_vp(args)))
+        return
+    if args.learned:
+        print(json.dumps(run_learned(args)))
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -310,10 +310,12 @@ apcloud_status apcloud_field_energy(apcloud_ctx *ctx, double *h_energy);
  *   sign(f) log(1 + |f|), mean neighbour offset and level offset, b and P b
  *   scaled by max|b|, degree);
  *   H_{l+1} = relu([H_l | P H_l] W_l + b_l), l = 0, 1, 2, width 64;
- *   t = H_3 W_o + b_o; s = exp(8 tanh t_0); gamma = exp(tanh t_1).
+ *   t = H_3 W_o + b_o; s = exp(ln 8 tanh t_0) on interior nodes, 1 on
+ *   boundary nodes (identity rows); gamma = exp(tanh t_1).
  * The solve then runs GMRES on Ahat S (columns scaled by s) from the guess
  * x0 = gamma b / D.  Training minimises L = Lp + Lg with
- *   Lp = (1/n) ||I - Ahat S||_F^2 (approximate-inverse objective),
+ *   Lp = (1/n_int) sum over interior columns of ||e_j - Ahat S e_j||^2
+ *   (approximate-inverse objective; its minimiser is s_j = 1/||Ahat e_j||^2),
  *   Lg = ||b - Ahat (gamma b)||^2 / ||b||^2 (initial residual of the guess).
  * Dense layers and their gradients run on the tensor cores in BF16 with FP32
  * accumulation; master weights are FP32.  Flat parameter layout (FP32):
@@ -356,12 +358,15 @@ apcloud_status apcloud_mpnn_outputs(apcloud_ctx *ctx, apcloud_mpnn *net, float *
                                     float *d_features);
 
 /* apcloud_solve (g = 0) with the network's proposals: bit 0 of `use` scales
- * the preconditioner columns by s, bit 1 starts from x0 = gamma b / D; use =
- * 0 is plain apcloud_solve from phi = 0.  The stored matrix is restored
- * afterwards.  The residual test is the same FP64 true residual, so the
- * network can change the iteration count, never the accuracy. */
-apcloud_status apcloud_solve_learned(apcloud_ctx *ctx, apcloud_mpnn *net, unsigned use, double rtol, int max_iter,
-                                     double *d_phi_out, apcloud_solve_info *info);
+ * the preconditioner columns by s, bit 1 starts from x0 = gamma b / D, bit 2
+ * scales by the closed-form minimiser 1/||Ahat e_j||^2 of the same objective
+ * instead of the network's s (the comparison baseline).  Without bit 1 the
+ * start is d_phi0 (device, n_nodes values) or 0 when it is NULL; use = 0 is
+ * plain apcloud_solve.  The stored matrix is restored afterwards.  The
+ * residual test is the same FP64 true residual, so the network can change the
+ * iteration count, never the accuracy. */
+apcloud_status apcloud_solve_learned(apcloud_ctx *ctx, apcloud_mpnn *net, unsigned use, const double *d_phi0,
+                                     double rtol, int max_iter, double *d_phi_out, apcloud_solve_info *info);
 
 /* Per-kernel device timing with CUDA events on the context stream.
  * apcloud_set_timing(ctx, mask) enables timing for the kernel kinds whose

@@ -23,14 +23,16 @@ learned part of the solver; the paper itself has no learned component):
     sum P_ji b_i / max|b|, and the W-degree / 64.
   * Layers l = 0, 1, 2: H_{l+1} = relu([H_l | P H_l] W_l + b_l), H_0 = F,
     width 64 (W_0: 32 x 64, W_1, W_2: 128 x 64).
-  * Head: t = H_3 W_o + b_o (64 x 2); s = exp(alpha tanh t_0), alpha = 8,
-    the learned column scaling of the preconditioner (Ahat S replaces
-    Ahat); gamma = exp(tanh t_1), the initial guess u0 = gamma * b of
-    Ahat u = b.
-  * Loss L = Lp + Lg.  Lp = (1/n) ||I - Ahat S||_F^2 (the approximate-inverse
-    objective for a diagonal right preconditioner; column j contributes
-    1 - 2 s_j + s_j^2 c_j with c_j = sum_i Ahat_ij^2), Lg = ||b - Ahat u0||^2
-    / ||b||^2 (the relative initial residual of the proposed guess).
+  * Head: t = H_3 W_o + b_o (64 x 2); s = exp(alpha tanh t_0), alpha = ln 8
+    (s in [1/8, 8]), on interior nodes, s = 1 on boundary nodes (their rows
+    are identity rows), the learned column scaling of the preconditioner
+    (Ahat S replaces Ahat); gamma = exp(tanh t_1), the initial guess
+    u0 = gamma * b of Ahat u = b.
+  * Loss L = Lp + Lg.  Lp = (1/n_int) sum over interior columns of
+    ||e_j - Ahat S e_j||^2 (the approximate-inverse objective for a diagonal
+    right preconditioner; column j contributes 1 - 2 s_j + s_j^2 c_j with
+    c_j = sum_i Ahat_ij^2), Lg = ||b - Ahat u0||^2 / ||b||^2 (the relative
+    initial residual of the proposed guess).
 
 Parameters travel as one flat FP32/FP64 vector in the order
 W0 (32x64, row-major), b0 (64), W1 (128x64), b1, W2 (128x64), b2,
@@ -43,7 +45,7 @@ import scipy.sparse as sp
 
 NF = 16
 WIDTH = 64
-ALPHA = 8.0
+ALPHA = float(np.log(8.0))
 SHAPES = [("W0", (2 * NF, WIDTH)), ("b0", (WIDTH,)), ("W1", (2 * WIDTH, WIDTH)), ("b1", (WIDTH,)),
           ("W2", (2 * WIDTH, WIDTH)), ("b2", (WIDTH,)), ("Wo", (WIDTH, 2)), ("bo", (2,))]
 N_PARAMS = int(sum(np.prod(s) for _, s in SHAPES))
@@ -107,6 +109,7 @@ def features(Ah, xyz, level, kind, b, ext):
 
 
 def forward(theta, F, P):
+    """Forward pass; F[:, 1] is the boundary flag."""
     p = unflatten(theta)
     H = [F]
     X = []
@@ -115,15 +118,15 @@ def forward(theta, F, P):
         X.append(x)
         H.append(np.maximum(x @ p["W%d" % l] + p["b%d" % l], 0.0))
     t = H[3] @ p["Wo"] + p["bo"]
-    s = np.exp(ALPHA * np.tanh(t[:, 0]))
+    interior = F[:, 1] == 0.0
+    s = np.where(interior, np.exp(ALPHA * np.tanh(t[:, 0])), 1.0)
     gamma = np.exp(np.tanh(t[:, 1]))
-    return dict(H=H, X=X, t=t, s=s, gamma=gamma)
+    return dict(H=H, X=X, t=t, s=s, gamma=gamma, interior=interior)
 
 
-def loss(Ah, b, s, gamma):
-    n = Ah.shape[0]
+def loss(Ah, b, s, gamma, interior):
     c = np.asarray(Ah.multiply(Ah).sum(axis=0)).ravel()   # 1 + the raw column feature
-    Lp = float(np.sum(1.0 - 2.0 * s + s * s * c)) / n
+    Lp = float(np.sum((1.0 - 2.0 * s + s * s * c)[interior])) / max(1, int(interior.sum()))
     u0 = gamma * b
     r = b - Ah @ u0
     Lg = float(r @ r) / float(b @ b)
@@ -132,12 +135,12 @@ def loss(Ah, b, s, gamma):
 
 def loss_and_grad(theta, Ah, F, P, b):
     """(L, Lp, Lg), flat gradient dL/dtheta, and the forward record."""
-    n = Ah.shape[0]
     p = unflatten(theta)
     fw = forward(theta, F, P)
-    L, Lp, Lg, c, r = loss(Ah, b, fw["s"], fw["gamma"])
+    interior = fw["interior"]
+    L, Lp, Lg, c, r = loss(Ah, b, fw["s"], fw["gamma"], interior)
     s, gamma, t = fw["s"], fw["gamma"], fw["t"]
-    ds = (2.0 / n) * (s * c - 1.0)
+    ds = np.where(interior, (2.0 / max(1, int(interior.sum()))) * (s * c - 1.0), 0.0)
     dgamma = -2.0 * b * (Ah.T @ r) / float(b @ b)
     dt = np.zeros_like(t)
     th0, th1 = np.tanh(t[:, 0]), np.tanh(t[:, 1])

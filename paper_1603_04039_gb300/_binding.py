@@ -105,7 +105,7 @@ def load():
             "apcloud_mpnn_loss": (I, [P, P, I, P]),
             "apcloud_mpnn_adam": (I, [P, P, C.c_float]),
             "apcloud_mpnn_outputs": (I, [P, P, P, P, P]),
-            "apcloud_solve_learned": (I, [P, P, C.c_uint, D, I, P, C.POINTER(SolveInfo)]),
+            "apcloud_solve_learned": (I, [P, P, C.c_uint, P, D, I, P, C.POINTER(SolveInfo)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -411,13 +411,16 @@ class APCloud:
     def set_launch_shape(self, spmv_block=256, wls_warps=4):
         self._check(self._lib.apcloud_set_launch_shape(self._ctx, int(spmv_block), int(wls_warps)))
 
-    def solve_learned(self, net, use=3, rtol=1e-10, max_iter=100000):
-        """Poisson solve with the network's column scaling (use bit 0) and guess (bit 1)."""
+    def solve_learned(self, net, use=3, rtol=1e-10, max_iter=100000, phi0=None):
+        """Poisson solve with the network's column scaling (use bit 0), guess (bit 1)
+        or the closed-form diagonal (bit 2); without bit 1 it starts from phi0 (or 0)."""
         phi = self._empty(self.n_nodes)
         info = SolveInfo()
+        if phi0 is not None:
+            _f64(phi0, self.n_nodes)
         with torch.cuda.device(self.device):
-            st = self._check(self._lib.apcloud_solve_learned(self._ctx, net._net, int(use), rtol, int(max_iter),
-                                                             _dptr(phi), C.byref(info)))
+            st = self._check(self._lib.apcloud_solve_learned(self._ctx, net._net, int(use), _dptr(phi0), rtol,
+                                                             int(max_iter), _dptr(phi), C.byref(info)))
         return phi, dict(info.as_dict(), status=st)
 
     def set_graphs(self, enable):

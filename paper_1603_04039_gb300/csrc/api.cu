@@ -379,6 +379,7 @@ apcloud_status apcloud_get_leaves(apcloud_ctx *c, uint64_t *key, int32_t *first,
 apcloud_status apcloud_stencils(apcloud_ctx *c) {
     if (!c) return APCLOUD_E_INVALID;
     if (c->stage < 1) return fail(c, APCLOUD_E_STATE, "apcloud_stencils before apcloud_build_octree");
+    c->mp_graph_n = -1;   // the learned preconditioner's graph belongs to the old matrix
     apcloud_status st = build_stencils(c);
     if (st < 0) { c->stage = 1; return st; }
     c->stage = 2;

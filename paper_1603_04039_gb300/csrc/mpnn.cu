@@ -8,8 +8,8 @@
 // accumulation):
 //   W = |Ahat_off| + |Ahat_off|^T (symmetric stencil graph), P = W / rowsum
 //   H_0 = F (16 node features), H_{l+1} = relu([H_l | P H_l] W_l + b_l)
-//   t = H_3 W_o + b_o;  s = exp(8 tanh t_0);  gamma = exp(tanh t_1)
-//   Lp = (1/n) ||I - Ahat S||_F^2 = (1/n) sum_j (1 - 2 s_j + s_j^2 c_j)
+//   t = H_3 W_o + b_o;  s = exp(ln8 tanh t_0) (1 on boundary nodes);  gamma = exp(tanh t_1)
+//   Lp = (1/n_int) sum over interior columns j of (1 - 2 s_j + s_j^2 c_j)
 //   Lg = ||b - Ahat (gamma * b)||^2 / ||b||^2
 // The dense layers, their data gradients and their weight gradients run on
 // the 5th-generation tensor cores: tcgen05.mma (kind::f16, BF16 inputs, FP32
@@ -39,7 +39,7 @@ namespace apc {
 namespace {
 
 constexpr int NF = 16, WD = 64;
-constexpr float ALPHA = 8.0f;
+constexpr float ALPHA = 2.0794415416798357f;   // ln 8: s in [1/8, 8]
 constexpr int K_L[3] = {2 * NF, 2 * WD, 2 * WD};
 // offsets into the flat parameter vector
 constexpr int OFF_W0 = 0, OFF_B0 = OFF_W0 + 2 * NF * WD, OFF_W1 = OFF_B0 + WD, OFF_B1 = OFF_W1 + 2 * WD * WD,
@@ -530,7 +530,7 @@ __global__ void k_agg_back(const int32_t *__restrict__ rp, const int32_t *__rest
 }
 
 // ---------------------------------------------------------------- head, loss, backward of the head
-__global__ void k_head(const __nv_bfloat16 *__restrict__ H3, const float *__restrict__ theta, int n,
+__global__ void k_head(const __nv_bfloat16 *__restrict__ H3, const float *__restrict__ theta, int n, int n_int,
                        float *__restrict__ t, float *__restrict__ s, float *__restrict__ gamma) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -543,7 +543,7 @@ __global__ void k_head(const __nv_bfloat16 *__restrict__ H3, const float *__rest
     }
     t[2 * j] = t0;
     t[2 * j + 1] = t1;
-    s[j] = expf(ALPHA * tanhf(t0));
+    s[j] = j < n_int ? expf(ALPHA * tanhf(t0)) : 1.f;   // boundary rows are identity rows
     gamma[j] = expf(tanhf(t1));
 }
 
@@ -552,7 +552,7 @@ __global__ void k_head(const __nv_bfloat16 *__restrict__ H3, const float *__rest
 __global__ void k_loss_terms(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                              const int32_t *__restrict__ col, const double *__restrict__ val,
                              const double *__restrict__ b, const float *__restrict__ gamma,
-                             const float *__restrict__ s, const float *__restrict__ ccol, int n,
+                             const float *__restrict__ s, const float *__restrict__ ccol, int n, int n_int,
                              float *__restrict__ r, double *__restrict__ part) {
     __shared__ double sh[3][256];
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -572,7 +572,7 @@ __global__ void k_loss_terms(const uint32_t *__restrict__ sw, const uint32_t *__
         rr = rj * rj;
         bb = b[j] * b[j];
         const double sj = s[j], cj = (double)ccol[j];
-        lp = 1.0 - 2.0 * sj + sj * sj * cj;
+        lp = j < n_int ? 1.0 - 2.0 * sj + sj * sj * cj : 0.0;
     }
     sh[0][threadIdx.x] = rr;
     sh[1][threadIdx.x] = bb;
@@ -587,7 +587,7 @@ __global__ void k_loss_terms(const uint32_t *__restrict__ sw, const uint32_t *__
         for (int q = 0; q < 3; ++q) part[(int64_t)blockIdx.x * 3 + q] = sh[q][0];
 }
 
-__global__ void k_loss_final(const double *__restrict__ part, int nblk, int n, double *__restrict__ out) {
+__global__ void k_loss_final(const double *__restrict__ part, int nblk, int n_int, double *__restrict__ out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double rr = 0.0, bb = 0.0, lp = 0.0;
     for (int k = 0; k < nblk; ++k) {
@@ -595,7 +595,7 @@ __global__ void k_loss_final(const double *__restrict__ part, int nblk, int n, d
         bb += part[3 * k + 1];
         lp += part[3 * k + 2];
     }
-    out[1] = lp / n;
+    out[1] = n_int > 0 ? lp / n_int : 0.0;
     out[2] = bb > 0.0 ? rr / bb : 0.0;
     out[0] = out[1] + out[2];
     out[3] = bb;
@@ -606,7 +606,7 @@ __global__ void k_loss_final(const double *__restrict__ part, int nblk, int n, d
 __global__ void k_head_back(const int32_t *__restrict__ rp, const int32_t *__restrict__ ecol,
                             const float *__restrict__ ain, const float *__restrict__ r, const double *__restrict__ b,
                             const float *__restrict__ s, const float *__restrict__ gamma, const float *__restrict__ t,
-                            const float *__restrict__ ccol, const double *__restrict__ lossv, int n,
+                            const float *__restrict__ ccol, const double *__restrict__ lossv, int n, int n_int,
                             float *__restrict__ dt) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -614,7 +614,7 @@ __global__ void k_head_back(const int32_t *__restrict__ rp, const int32_t *__res
     for (int e = rp[j]; e < rp[j + 1]; ++e) atr = fmaf(ain[e], r[ecol[e]], atr);
     const double bb = lossv[3];
     const float cj = ccol[j];
-    const float ds = (2.0f / n) * (s[j] * cj - 1.f);
+    const float ds = j < n_int ? (2.0f / n_int) * (s[j] * cj - 1.f) : 0.f;
     const float dg = bb > 0.0 ? (float)(-2.0 * b[j] * (double)atr / bb) : 0.f;
     const float th0 = tanhf(t[2 * j]), th1 = tanhf(t[2 * j + 1]);
     dt[2 * j] = ds * s[j] * ALPHA * (1.f - th0 * th0);
@@ -747,7 +747,8 @@ T *mp(apcloud_ctx *c, int i) { return ptr<T>(c->mp[i]); }
 
 constexpr int GT1 = 256;
 
-// symmetric stencil graph of the current system (built once per node set)
+// symmetric stencil graph of the current system (built once per matrix:
+// apcloud_stencils clears mp_graph_n)
 apcloud_status build_graph(apcloud_ctx *c) {
     const int n = c->n_tot;
     if (c->mp_graph_n == n) return APCLOUD_OK;
@@ -856,7 +857,7 @@ apcloud_status forward(apcloud_ctx *c, apcloud_mpnn *m, const double *b) {
         APC_TRY(tc_launch(c, 0, a, div_up(n, 128)));
     }
     APC_LAUNCH(c, K_MPNN_GRAPH, div_up(n, GT1), GT1, 0, k_head, (const __nv_bfloat16 *)H[3],
-               (const float *)m->theta, n, t, s, gm);
+               (const float *)m->theta, n, c->n_int, t, s, gm);
     return cuda_check(c, cudaGetLastError(), "mpnn forward");
 }
 
@@ -880,8 +881,8 @@ apcloud_status loss_grad(apcloud_ctx *c, apcloud_mpnn *m, const double *b, bool 
     const int nb = div_up(n, GT1);
     double *part = mp<double>(c, MB_PART);
     APC_LAUNCH(c, K_MPNN_GRAPH, nb, GT1, 0, k_loss_terms, sw, so, col, val, b, (const float *)mp<float>(c, MB_GAMMA),
-               (const float *)mp<float>(c, MB_SV), (const float *)mp<float>(c, MB_CCOL), n, r, part);
-    APC_LAUNCH(c, K_MPNN_GRAPH, 1, 32, 0, k_loss_final, (const double *)part, nb, n, lossv);
+               (const float *)mp<float>(c, MB_SV), (const float *)mp<float>(c, MB_CCOL), n, c->n_int, r, part);
+    APC_LAUNCH(c, K_MPNN_GRAPH, 1, 32, 0, k_loss_final, (const double *)part, nb, c->n_int, lossv);
     if (backward) {
         const int32_t *rp = mp<int32_t>(c, MB_RP), *ecol = mp<int32_t>(c, MB_ECOL);
         const float *ain = mp<float>(c, MB_AIN), *pb = mp<float>(c, MB_PB);
@@ -894,7 +895,7 @@ apcloud_status loss_grad(apcloud_ctx *c, apcloud_mpnn *m, const double *b, bool 
         APC_LAUNCH(c, K_MPNN_GRAPH, nb, GT1, 0, k_head_back, rp, ecol, ain, (const float *)r, b,
                    (const float *)mp<float>(c, MB_SV), (const float *)mp<float>(c, MB_GAMMA),
                    (const float *)mp<float>(c, MB_T), (const float *)mp<float>(c, MB_CCOL), (const double *)lossv, n,
-                   dt);
+                   c->n_int, dt);
         const __nv_bfloat16 *H3 = mp<__nv_bfloat16>(c, MB_H3);
         const int hb = nb < 1024 ? nb : 1024;
         APC_LAUNCH(c, K_MPNN_GRAPH, hb, GT1, 0, k_head_wgrad, H3, (const float *)dt, n, wpart);
@@ -948,6 +949,13 @@ __global__ void k_scale_cols(const uint32_t *__restrict__ sw, const uint32_t *__
         val[e] *= (double)s[col[e]];
     }
     d[r] /= (double)s[r];
+}
+
+// closed-form minimiser of the approximate-inverse objective: s_j = 1 / c_j
+// on interior columns, 1 on boundary ones
+__global__ void k_spai_diag(const float *__restrict__ ccol, int n, int n_int, float *__restrict__ s) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) s[j] = (j < n_int && ccol[j] > 0.f) ? 1.f / ccol[j] : 1.f;
 }
 
 __global__ void k_guess(const float *__restrict__ gamma, const double *__restrict__ b, const double *__restrict__ d,
@@ -1093,8 +1101,9 @@ extern "C" apcloud_status apcloud_mpnn_outputs(apcloud_ctx *c, apcloud_mpnn *m, 
     return cuda_check(c, cudaStreamSynchronize(c->s), "mpnn outputs");
 }
 
-extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m, unsigned use, double rtol,
-                                                int max_iter, double *d_phi_out, apcloud_solve_info *info) {
+extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m, unsigned use, const double *phi0,
+                                                double rtol, int max_iter, double *d_phi_out,
+                                                apcloud_solve_info *info) {
     if (!c || !m) return APCLOUD_E_INVALID;
     if (c->stage < 3) return fail(c, APCLOUD_E_STATE, "apcloud_solve_learned before apcloud_deposit");
     if (!(rtol > 0) || max_iter < 0) return fail(c, APCLOUD_E_INVALID, "rtol must be > 0 and max_iter >= 0");
@@ -1109,9 +1118,21 @@ extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m,
     if (use & 2u)
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_guess, (const float *)mp<float>(c, MB_GAMMA), (const double *)b,
                    (const double *)dA, n, phi);
+    else if (phi0)
+        APC_CUDA(c, cudaMemcpyAsync(phi, phi0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
     else
         APC_CUDA(c, cudaMemsetAsync(phi, 0, sizeof(double) * n, c->s));
     double *bk = nullptr, *dbk = nullptr;
+    const float *scale = mp<float>(c, MB_SV);
+    if (use & 4u) {
+        // the closed-form diagonal instead of the network's (comparison baseline)
+        float *sd = mb<float>(c, MB_PHI0, n);
+        if (!sd) return APCLOUD_E_NOMEM;
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_spai_diag, (const float *)mp<float>(c, MB_CCOL), n, c->n_int,
+                   sd);
+        scale = sd;
+        use |= 1u;
+    }
     if (use & 1u) {
         // Ahat S: scale the stored columns by s and the diagonal by 1/s; keep the originals
         bk = mb<double>(c, MB_BACKUP, c->ell_entries);
@@ -1120,8 +1141,7 @@ extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m,
         APC_CUDA(c, cudaMemcpyAsync(bk, ptr<double>(c->ell_A), sizeof(double) * c->ell_entries, cudaMemcpyDeviceToDevice, c->s));
         APC_CUDA(c, cudaMemcpyAsync(dbk, dA, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_scale_cols, ptr<uint32_t>(c->slice_w),
-                   ptr<uint32_t>(c->slice_off), ptr<int32_t>(c->ell_col), ptr<double>(c->ell_A),
-                   (const float *)mp<float>(c, MB_SV), n, dA);
+                   ptr<uint32_t>(c->slice_off), ptr<int32_t>(c->ell_col), ptr<double>(c->ell_A), scale, n, dA);
         APC_TRY(refresh_lowp(c));
     }
     apcloud_status st = gmres_solve(c, 1, b, phi, rtol, max_iter, info);

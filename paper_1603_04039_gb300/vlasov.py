@@ -23,13 +23,15 @@ class VlasovPoisson:
     Lap phi = c rho, E = grad phi, so the acceleration is qm * E."""
 
     def __init__(self, x, y, z, vx, vy, vz, q=None, q_uniform=None, qm=1.0, rtol=1e-10, max_iter=100000,
-                 warm_start=True, **params):
+                 warm_start=True, net=None, net_use=1, **params):
         self.x, self.y, self.z, self.vx, self.vy, self.vz = x, y, z, vx, vy, vz
         self.q = q
         self.q_uniform = (1.0 / x.numel()) if (q is None and q_uniform is None) else q_uniform
         self.qm = qm
         self.rtol, self.max_iter = rtol, max_iter
         self.warm_start = warm_start
+        # learned preconditioner for the Poisson solves (bits of apcloud_solve_learned's `use`)
+        self.net, self.net_use = net, net_use
         self.ctx = [APCloud(**params), APCloud(**params)]
         self.cur = 0
         n = x.numel()
@@ -53,7 +55,10 @@ class VlasovPoisson:
             px, py, pz = (xyz[:, d].contiguous() for d in range(3))
             phi0 = self.ctx[1 - self.cur].interpolate_potential(px, py, pz)
             phi0[ap.n_int:] = 0.0          # Dirichlet data g = 0 on the boundary nodes
-        _, ip = ap.solve(phi0=phi0, rtol=self.rtol, max_iter=self.max_iter)
+        if self.net is not None:
+            _, ip = ap.solve_learned(self.net, use=self.net_use, phi0=phi0, rtol=self.rtol, max_iter=self.max_iter)
+        else:
+            _, ip = ap.solve(phi0=phi0, rtol=self.rtol, max_iter=self.max_iter)
         ap.gather_field((self.phi_p,) + self.E)
         self.info = {"iters_rho": ir["iters"], "iters_phi": ip["iters"], "relres_phi": ip["relres"],
                      "n_nodes": ap.n_nodes}

@@ -46,26 +46,30 @@ def test_untrained_network_is_jacobi(system):
     theta = mpnn.init_params(3)
     fw = mpnn.forward(theta, F, P)
     assert np.all(fw["s"] == 1.0) and np.all(fw["gamma"] == 1.0)
-    L, Lp, Lg, c, r = mpnn.loss(Ah, b, fw["s"], fw["gamma"])
+    interior = nd["kind"] == 0
+    assert np.array_equal(fw["interior"], interior)
+    L, Lp, Lg, c, r = mpnn.loss(Ah, b, fw["s"], fw["gamma"], interior)
     n = Ah.shape[0]
     I = np.eye(n)
     dense = Ah.toarray()
-    assert np.isclose(Lp, np.linalg.norm(I - dense) ** 2 / n, rtol=1e-12)
+    assert np.isclose(Lp, np.linalg.norm((I - dense)[:, interior]) ** 2 / interior.sum(), rtol=1e-12)
     assert np.isclose(Lg, np.linalg.norm(b - dense @ b) ** 2 / np.linalg.norm(b) ** 2, rtol=1e-12)
 
 
 def test_closed_form_minimiser_of_lp(system):
     Ah, F, P, b, nd = system
     n = Ah.shape[0]
+    interior = nd["kind"] == 0
     dense = Ah.toarray()
     c = (dense ** 2).sum(axis=0)
-    s_opt = 1.0 / c
-    base = mpnn.loss(Ah, b, s_opt, np.ones(n))[1]
-    assert np.isclose(base, np.linalg.norm(np.eye(n) - dense * s_opt[None, :]) ** 2 / n, rtol=1e-12)
+    s_opt = np.where(interior, 1.0 / c, 1.0)
+    base = mpnn.loss(Ah, b, s_opt, np.ones(n), interior)[1]
+    resid = (np.eye(n) - dense * s_opt[None, :])[:, interior]
+    assert np.isclose(base, np.linalg.norm(resid) ** 2 / interior.sum(), rtol=1e-12)
     rng = np.random.default_rng(0)
     for _ in range(5):
-        s = s_opt * np.exp(0.05 * rng.normal(size=n))
-        assert mpnn.loss(Ah, b, s, np.ones(n))[1] > base
+        s = s_opt * np.where(interior, np.exp(0.05 * rng.normal(size=n)), 1.0)
+        assert mpnn.loss(Ah, b, s, np.ones(n), interior)[1] > base
 
 
 def test_backward_matches_finite_differences(system):
