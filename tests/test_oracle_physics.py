@@ -3,6 +3,8 @@
 Potentials solve Lap phi = rho (Eq. Poisson with c = 1, Section 5) so a point
 charge Q has phi = -Q / (4 pi r) and E = grad phi (Section 2).
 """
+import os
+
 import numpy as np
 import pytest
 from scipy.special import erf, ndtr
@@ -50,14 +52,27 @@ def _gaussian_errors(depth, sig):
 
 
 @pytest.mark.slow
+def _paper_orders():
+    """Orders of Table convergence_order (fixture tests/golden/convergence_order_table.txt)."""
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "convergence_order_table.txt")):
+        line = line.split("#")[0].split()
+        if line and line[3] != "-":
+            rows.append((float(line[3]), float(line[4])))
+    return np.array(rows)
+
+
 def test_second_order_convergence_without_mc_noise():
     """Sections 3.3 and 5: with exact cell integrals the second-order method
-    converges at order ~2 in both phi and grad phi (the paper reports
-    1.82-2.01 and 1.96-2.13)."""
+    converges at order ~2 in both phi and grad phi; every observed order must
+    reach the smallest one the paper prints (1.82 for phi, 1.96 for phi_x)
+    less 0.05."""
+    paper = _paper_orders()
+    assert paper.shape == (3, 2)
     errs = [_gaussian_errors(d, 0.15) for d in (4, 5, 6)]
     for (p0, e0), (p1, e1) in zip(errs[:-1], errs[1:]):
-        assert np.log2(p0 / p1) > 1.8, errs
-        assert np.log2(e0 / e1) > 1.8, errs
+        assert np.log2(p0 / p1) > paper[:, 0].min() - 0.05, errs
+        assert np.log2(e0 / e1) > paper[:, 1].min() - 0.05, errs
     assert errs[-1][0] < 2e-3 and errs[-1][1] < 6e-3
 
 

@@ -6,6 +6,8 @@ These tests rebuild that set with an independent fix-point iteration (refine
 any leaf that is two levels coarser than a face neighbour until nothing
 changes), and check face adjacency by brute force over all leaf pairs.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -186,12 +188,26 @@ def test_boundary_nodes_on_faces():
     assert np.all(nd["kind"][o.n_int:] == 1) and np.all(nd["kind"][: o.n_int] == 0)
 
 
+def _golden(name):
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (t.strip() for t in line.split("="))
+            vals[k] = float(v)
+    return vals
+
+
 def test_criterion_worked_example():
-    """Sec. 4.3: with c = 0.01 a depth-21 cell of [-1, 1] (edge 2 x 2^-21 = 2^-20)
-    would open only with 0.01^2 2^40 = 1.10e8 particles (depth cap lifted to 22
-    to exercise the arithmetic)."""
-    thr = 0.01 ** 2 * 2.0 ** 40
-    assert abs(thr - 1.10e8) < 0.005e8
+    """Sec. 4.3 (fixture tests/golden/criterion_worked_example.txt): with
+    c = 0.01 a depth-21 cell of [-1, 1] (edge 2 x 2^-21 = 2^-20) would open
+    only with 0.01^2 2^40 = 1.10e8 particles (depth cap lifted to 22 to
+    exercise the arithmetic)."""
+    g = _golden("criterion_worked_example.txt")
+    assert g["depth"] == 21 and (g["hi"] - g["lo"]) * 2.0 ** -g["depth"] == 2.0 ** g["leaf_edge_log2"]
+    thr = g["c"] ** 2 * 2.0 ** (-2 * g["leaf_edge_log2"])
+    half_ulp = 0.5 * 10 ** (np.floor(np.log10(g["particles_to_open"])) - g["printed_digits"] + 1)
+    assert abs(thr - g["particles_to_open"]) < half_ulp
     assert oracle.criterion_opens(109951163, 21, 22, -1.0, 1.0, 0.01)
     assert not oracle.criterion_opens(109951162, 21, 22, -1.0, 1.0, 0.01)
     # one level up the edge doubles and a quarter of the particles suffice
