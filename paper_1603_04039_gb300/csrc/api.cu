@@ -673,23 +673,27 @@ const char *apcloud_kernel_name(int kind) {
 
 int64_t apcloud_launch_count(const apcloud_ctx *c) { return c ? c->launches : 0; }
 
-apcloud_status apcloud_autotune(apcloud_ctx *c, unsigned what, int *spmv_block, int *wls_warps, double *ms) {
+apcloud_status apcloud_autotune(apcloud_ctx *c, unsigned what, int *spmv_block, int *spmv_unroll, int *wls_warps,
+                                double *ms) {
     if (!c) return APCLOUD_E_INVALID;
     if (c->stage < 2) return fail(c, APCLOUD_E_STATE, "apcloud_autotune needs apcloud_stencils first");
     if (what & 1u) APC_TRY(tune_spmv(c, ms));
-    if (what & 2u) APC_TRY(tune_stencils(c, ms ? ms + 4 : nullptr));
+    if (what & 2u) APC_TRY(tune_stencils(c, ms ? ms + 8 : nullptr));
     if (spmv_block) *spmv_block = c->spmv_bs;
+    if (spmv_unroll) *spmv_unroll = c->spmv_unroll;
     if (wls_warps) *wls_warps = c->wls_warps;
     return APCLOUD_OK;
 }
 
-apcloud_status apcloud_set_launch_shape(apcloud_ctx *c, int spmv_block, int wls_warps) {
+apcloud_status apcloud_set_launch_shape(apcloud_ctx *c, int spmv_block, int spmv_unroll, int wls_warps) {
     if (!c) return APCLOUD_E_INVALID;
     if (spmv_block != 64 && spmv_block != 128 && spmv_block != 256 && spmv_block != 512)
         return fail(c, APCLOUD_E_INVALID, "spmv_block must be 64, 128, 256 or 512");
+    if (spmv_unroll != 1 && spmv_unroll != 4) return fail(c, APCLOUD_E_INVALID, "spmv_unroll must be 1 or 4");
     if (wls_warps != 2 && wls_warps != 4 && wls_warps != 8)
         return fail(c, APCLOUD_E_INVALID, "wls_warps must be 2, 4 or 8");
     c->spmv_bs = spmv_block;
+    c->spmv_unroll = spmv_unroll;
     c->wls_warps = wls_warps;
     return APCLOUD_OK;
 }

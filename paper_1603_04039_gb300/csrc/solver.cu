@@ -147,9 +147,69 @@ __global__ void k_bcopy(const int32_t *__restrict__ owner, int n_int, int n_bnd,
 // mode 3: y = x + omega (b - Ahat x)   (damped Jacobi sweep of the polynomial
 //         preconditioner, Ahat already carries the Jacobi scaling)
 // mode 4: y = Ahat x, skipped once the cycle is done
+// One row of the sliced ELL product, sum_k val[e_k] x[col[e_k]] in stored
+// order.  U > 1 issues the column, value and gather loads of U entries
+// before their multiply-adds (more bytes in flight per thread) while keeping
+// the sequential summation order, so every U gives the same bits.
+template <int U, class V, class X>
+__device__ __forceinline__ X row_dot(const V *__restrict__ val, const int32_t *__restrict__ col,
+                                     const X *__restrict__ x, int64_t base, int w) {
+    X acc = (X)0;
+    int k = 0;
+    if (U > 1) {
+        for (; k + U <= w; k += U) {
+            int ci[U];
+            X vv[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = base + (int64_t)(k + u) * 32;
+                ci[u] = col[e];
+                vv[u] = (X)val[e];
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = x[ci[u]];
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc = fma(vv[u], xv[u], acc);
+        }
+    }
+    for (; k < w; ++k) {
+        const int64_t e = base + (int64_t)k * 32;
+        acc = fma((X)val[e], x[col[e]], acc);
+    }
+    return acc;
+}
+
+template <int U>
+__device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const int32_t *__restrict__ col,
+                                           const float *__restrict__ x, int64_t base, int w) {
+    float acc = 0.f;
+    int k = 0;
+    if (U > 1) {
+        for (; k + U <= w; k += U) {
+            int ci[U];
+            float vv[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int64_t e = base + (int64_t)(k + u) * 32;
+                ci[u] = col[e];
+                vv[u] = __half2float(val[e]);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) xv[u] = x[ci[u]];
+#pragma unroll
+            for (int u = 0; u < U; ++u) acc = fmaf(vv[u], xv[u], acc);
+        }
+    }
+    for (; k < w; ++k) {
+        const int64_t e = base + (int64_t)k * 32;
+        acc = fmaf(__half2float(val[e]), x[col[e]], acc);
+    }
+    return acc;
+}
+
 // BS: threads per block (one row each); mode 2 runs with RT only, its block
-// partials are sized for div_up(n, RT) blocks.
-template <int MODE, class T, int BS = RT>
+// partials are sized for div_up(n, RT) blocks.  U: loads issued ahead (row_dot).
+template <int MODE, class T, int BS = RT, int U = 1>
 __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                              const int32_t *__restrict__ col, const T *__restrict__ val, int n,
                                              const T *__restrict__ x, T *__restrict__ y, T *__restrict__ vout,
@@ -167,10 +227,7 @@ __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, co
         const int sl = r >> 5, lane = r & 31;
         const int w = (int)sw[sl];
         const int64_t base = (int64_t)soff[sl] * 32 + lane;
-        for (int k = 0; k < w; ++k) {
-            const int64_t e = base + (int64_t)k * 32;
-            acc = fma(val[e], x[col[e]], acc);
-        }
+        acc = row_dot<U, T, T>(val, col, x, base, w);
         if (MODE == 0 || MODE == 4) y[r] = acc;
         if (MODE == 1) { y[r] = acc * s; vout[r] = x[r] * s; }
         if (MODE == 3) y[r] = fma(s, b[r] - acc, x[r]);
@@ -203,7 +260,7 @@ __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, co
 // steers the Krylov space (right preconditioning keeps the residual exact),
 // so its 11-bit values cost convergence at most, never accuracy; they cut the
 // sweep's traffic from 8 to 6 bytes per stored entry.
-template <int BS>
+template <int BS, int U = 1>
 __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                                 const int32_t *__restrict__ col, const __half *__restrict__ val,
                                                 int n, const float *__restrict__ x, float *__restrict__ y,
@@ -215,29 +272,34 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
     const int sl = r >> 5, lane = r & 31;
     const int w = (int)sw[sl];
     const int64_t base = (int64_t)soff[sl] * 32 + lane;
-    float acc = 0.f;
-    for (int k = 0; k < w; ++k) {
-        const int64_t e = base + (int64_t)k * 32;
-        acc = fmaf(__half2float(val[e]), x[col[e]], acc);
-    }
+    const float acc = row_dot_h<U>(val, col, x, base, w);
     y[r] = fmaf(om, b[r] - acc, x[r]);
 }
 
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
 // autotuner chose (64, 128, 256 or 512 threads).
-#define APC_SPMV_BS(c, n, KERNEL_OF, ...)                                                              \
-    do {                                                                                               \
-        switch ((c)->spmv_bs) {                                                                        \
-        case 64: APC_LAUNCH(c, K_SPMV, div_up(n, 64), 64, 0, KERNEL_OF(64), __VA_ARGS__); break;       \
-        case 128: APC_LAUNCH(c, K_SPMV, div_up(n, 128), 128, 0, KERNEL_OF(128), __VA_ARGS__); break;   \
-        case 512: APC_LAUNCH(c, K_SPMV, div_up(n, 512), 512, 0, KERNEL_OF(512), __VA_ARGS__); break;   \
-        default: APC_LAUNCH(c, K_SPMV, div_up(n, 256), 256, 0, KERNEL_OF(256), __VA_ARGS__); break;    \
-        }                                                                                              \
+#define APC_SPMV_BS(c, n, KERNEL_OF, ...)                                                                   \
+    do {                                                                                                    \
+        if ((c)->spmv_unroll == 4) {                                                                        \
+            switch ((c)->spmv_bs) {                                                                         \
+            case 64: APC_LAUNCH(c, K_SPMV, div_up(n, 64), 64, 0, KERNEL_OF(64, 4), __VA_ARGS__); break;     \
+            case 128: APC_LAUNCH(c, K_SPMV, div_up(n, 128), 128, 0, KERNEL_OF(128, 4), __VA_ARGS__); break; \
+            case 512: APC_LAUNCH(c, K_SPMV, div_up(n, 512), 512, 0, KERNEL_OF(512, 4), __VA_ARGS__); break; \
+            default: APC_LAUNCH(c, K_SPMV, div_up(n, 256), 256, 0, KERNEL_OF(256, 4), __VA_ARGS__); break;  \
+            }                                                                                               \
+        } else {                                                                                            \
+            switch ((c)->spmv_bs) {                                                                         \
+            case 64: APC_LAUNCH(c, K_SPMV, div_up(n, 64), 64, 0, KERNEL_OF(64, 1), __VA_ARGS__); break;     \
+            case 128: APC_LAUNCH(c, K_SPMV, div_up(n, 128), 128, 0, KERNEL_OF(128, 1), __VA_ARGS__); break; \
+            case 512: APC_LAUNCH(c, K_SPMV, div_up(n, 512), 512, 0, KERNEL_OF(512, 1), __VA_ARGS__); break; \
+            default: APC_LAUNCH(c, K_SPMV, div_up(n, 256), 256, 0, KERNEL_OF(256, 1), __VA_ARGS__); break;  \
+            }                                                                                               \
+        }                                                                                                   \
     } while (0)
-#define APC_SPMV1(B) (k_spmv<1, T, B>)
-#define APC_SPMV3(B) (k_spmv<3, T, B>)
-#define APC_SPMV4(B) (k_spmv<4, T, B>)
-#define APC_SWEEPH(B) (k_sweep_h<B>)
+#define APC_SPMV1(B, U) (k_spmv<1, T, B, U>)
+#define APC_SPMV3(B, U) (k_spmv<3, T, B, U>)
+#define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
+#define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
 // Every arithmetic instruction does useful work on 32 lanes (GB300 runs FP64
@@ -704,7 +766,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
         key.nblk = K.nblk;
         key.ldv = K.ldv;
         key.mask = c->timer.mask;
-        key.spmv_bs = c->spmv_bs;
+        key.spmv_bs = c->spmv_bs * 8 + c->spmv_unroll;
         const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
                            c->slice_w.p, c->slice_off.p, c->ell_col.p};
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
@@ -962,7 +1024,9 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
     APC_CUDA(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s));
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
-    const int sizes[4] = {64, 128, 256, 512};
+    const int sizes[4] = {64, 128, 256, 512}, unrolls[2] = {1, 4};
+    const int saved_u = c->spmv_unroll;
+    int pick_u = saved_u;
     cudaEvent_t e0, e1;
     APC_CUDA(c, cudaEventCreate(&e0));
     APC_CUDA(c, cudaEventCreate(&e1));
@@ -972,8 +1036,10 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
     double best = 1e30;
     int pick = saved;
     apcloud_status rc = APCLOUD_OK;
-    for (int t = 0; t < 4 && rc == APCLOUD_OK; ++t) {
+    for (int tu = 0; tu < 8 && rc == APCLOUD_OK; ++tu) {
+        const int t = tu & 3;
         c->spmv_bs = sizes[t];
+        c->spmv_unroll = unrolls[tu >> 2];
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {   // warm-up pass, then the timed pass
             cudaEventRecord(e0, c->s);
@@ -1003,13 +1069,14 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
             cudaEventElapsedTime(&ms, e0, e1);
         }
         const double per = ms / 10.0;
-        if (ms_out) ms_out[t] = per;
-        if (per < best) { best = per; pick = sizes[t]; }
+        if (ms_out) ms_out[tu] = per;
+        if (per < best) { best = per; pick = sizes[t]; pick_u = unrolls[tu >> 2]; }
     }
     c->timer.mask = mask;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->spmv_bs = (rc == APCLOUD_OK) ? pick : saved;
+    c->spmv_unroll = (rc == APCLOUD_OK) ? pick_u : saved_u;
     return rc;
 }
 
