@@ -60,7 +60,7 @@ struct GraphKey {
     int tsize, n, jmax, pdeg, nblk, spmv_bs;
     unsigned mask;
     int64_t ldv;
-    const void *p[16];
+    const void *p[20];
 };
 
 struct GraphEntry {
@@ -130,7 +130,7 @@ struct apcloud_ctx {
     apc::DBuf ucell[2], ustart[2], opened, cand[2], cval[2], flags, scan, scan_blk, lkey, lval;
     // nodes
     apc::DBuf leaf_anchor, leaf_level, leaf_first, leaf_count, node_ic, bowner, bface, bidx, adj;
-    apc::DBuf beam_off, leaf_beam, beam_rng, beam_norm;
+    apc::DBuf beam_off, leaf_beam, beam_rng, beam_norm, beam_r2, beam_done, node_beam, tile_act;
     apc::DBuf mp[48];   // learned preconditioner: graph, activations, gradients (indices in mpnn.cu)
     int mp_graph_n = -1; // node count the graph in mp was built for (-1: none)
     // stencils

@@ -207,17 +207,30 @@ __device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const
     return acc;
 }
 
+// Rows of beams that have converged in a batch (both null outside batches):
+// their Krylov vectors are zero, so the products skip them.
+struct RowSkip {
+    const int32_t *nbo;   // beam of every node
+    const int *bdone;     // 1 once the beam has converged
+};
+
 // BS: threads per block (one row each); mode 2 runs with RT only, its block
 // partials are sized for div_up(n, RT) blocks.  U: loads issued ahead (row_dot).
 template <int MODE, class T, int BS = RT, int U = 1>
 __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                              const int32_t *__restrict__ col, const T *__restrict__ val, int n,
                                              const T *__restrict__ x, T *__restrict__ y, T *__restrict__ vout,
-                                             const T *__restrict__ b, GmresState *st, double *__restrict__ partial) {
+                                             const T *__restrict__ b, GmresState *st, double *__restrict__ partial,
+                                             RowSkip skip) {
     static_assert(MODE != 2 || BS == RT, "mode 2 partials are sized for RT-thread blocks");
     __shared__ double sm[MODE == 2 ? RT + RT / 32 + 8 : 1];
     if ((MODE == 1 || MODE == 3 || MODE == 4) && st->done) return;
     const int r = blockIdx.x * BS + threadIdx.x;
+    if ((MODE == 1 || MODE == 3 || MODE == 4) && skip.nbo && r < n && skip.bdone[skip.nbo[r]]) {
+        y[r] = (T)0;
+        if (MODE == 1) vout[r] = (T)0;
+        return;
+    }
     T s = (T)1;
     if (MODE == 1) s = (T)st->inv_norm;
     if (MODE == 3) s = (T)st->omega;
@@ -264,10 +277,15 @@ template <int BS, int U = 1>
 __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                                 const int32_t *__restrict__ col, const __half *__restrict__ val,
                                                 int n, const float *__restrict__ x, float *__restrict__ y,
-                                                const float *__restrict__ b, const GmresState *__restrict__ st) {
+                                                const float *__restrict__ b, const GmresState *__restrict__ st,
+                                                RowSkip skip) {
     if (st->done) return;
     const int r = blockIdx.x * BS + threadIdx.x;
     if (r >= n) return;
+    if (skip.nbo && skip.bdone[skip.nbo[r]]) {
+        y[r] = 0.f;
+        return;
+    }
     const float om = (float)st->omega;
     const int sl = r >> 5, lane = r & 31;
     const int w = (int)sw[sl];
@@ -378,7 +396,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.   (nrow = ldv)
 template <int PASS, class T>
 __global__ void __launch_bounds__(DT) k_gs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
-                                                T *__restrict__ w, GmresState *st, double *__restrict__ partial) {
+                                                T *__restrict__ w, GmresState *st, double *__restrict__ partial,
+                                                const uint8_t *__restrict__ tact) {
     typedef typename Vec<T>::type VT;
     constexpr int VN = Vec<T>::n;
     __shared__ __align__(16) T ws[TILE];
@@ -395,6 +414,7 @@ __global__ void __launch_bounds__(DT) k_gs_dots(const T *__restrict__ V, int64_t
     for (int kk = 0; kk < KPW; ++kk) acc[kk] = (T)0;
     VT *wsv = reinterpret_cast<VT *>(ws);
     for (int64_t base = (int64_t)blockIdx.x * TILE; base < nrow; base += (int64_t)gridDim.x * TILE) {
+        if (tact && !tact[base / TILE]) continue;   // every row of the tile is zero (converged beams)
         const int lim = (int)((nrow - base) < TILE ? (nrow - base) : TILE);
         VT *wg = reinterpret_cast<VT *>(w + base);
         if (PASS == 0) {
@@ -438,7 +458,7 @@ __global__ void __launch_bounds__(DT) k_gs_dots(const T *__restrict__ V, int64_t
 template <class T>
 __global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t ldv, int nrow, int j,
                                                 const T *__restrict__ w, T *__restrict__ wraw, GmresState *st,
-                                                double *__restrict__ partial) {
+                                                double *__restrict__ partial, const uint8_t *__restrict__ tact) {
     typedef typename Vec<T>::type VT;
     constexpr int VN = Vec<T>::n;
     __shared__ T hs[MAX_RESTART];
@@ -453,6 +473,7 @@ __global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t
     const VT *wv = reinterpret_cast<const VT *>(w);
     VT *ov = reinterpret_cast<VT *>(wraw);
     for (int cix = blockIdx.x * GT + tid; cix < nch; cix += gridDim.x * GT) {
+        if (tact && !tact[(int64_t)cix * VN / TILE]) continue;
         VT wi = wv[cix];
 #pragma unroll 4
         for (int k = 0; k < j1; ++k)
@@ -631,15 +652,16 @@ int stream_blocks(int64_t nrow) {
 
 template <class T>
 void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, int j, T *w, T *wraw, GmresState *st,
-                 double *partial) {
+                 double *partial, const uint8_t *tact) {
     (void)nblk;
     const int nrow = (int)ldv;
-    if (pass == 0) APC_LAUNCH(c, K_DOT, dot_blocks(ldv), DT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial);
+    if (pass == 0)
+        APC_LAUNCH(c, K_DOT, dot_blocks(ldv), DT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial, tact);
     else if (pass == 1)
-        APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial);
+        APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial, tact);
     else
         APC_LAUNCH(c, K_UPDNORM, stream_blocks(ldv), GT, 0, k_gs_norm<T>, V, ldv, nrow, j, (const T *)w, wraw, st,
-                   partial);
+                   partial, tact);
 }
 
 // grid of the streaming reductions (norms, cycle end); the partial buffer
@@ -649,6 +671,109 @@ int reduction_blocks(apcloud_ctx *c, int n) {
     int64_t ldv = ((int64_t)n + 31) / 32 * 32;
     int a = stream_blocks(ldv), b = dot_blocks(ldv);
     return a > b ? a : b;
+}
+
+// Per-beam convergence of a batch: at every restart the residual of each beam
+// is compared with rtol ||b_b||; converged beams are frozen (their residual
+// rows set to zero, so the block-diagonal Krylov vectors stay zero there and
+// the products skip them) and the cycle continues on the others.
+struct BeamMask {
+    int nb;
+    const int64_t *rng;   // 7 node ranges per beam
+    const double *b2;     // ||b_b||^2
+    double *r2;           // ||r_b||^2 scratch
+    int *bdone;
+    const int32_t *nbo;
+    uint8_t *tact;
+    int64_t ntile;
+    double rtol;
+};
+
+// squared norm of r over the nodes of each beam (one block per beam, fixed order)
+template <class T>
+__global__ void k_beam_sq(const T *__restrict__ r, const int64_t *__restrict__ rng, int nb, double *__restrict__ out) {
+    __shared__ double sh[256];
+    const int beam = blockIdx.x;
+    double s = 0.0;
+    for (int seg = 0; seg < 7; ++seg) {
+        const int64_t lo = rng[(int64_t)seg * (nb + 1) + beam], hi = rng[(int64_t)seg * (nb + 1) + beam + 1];
+        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma((double)r[i], (double)r[i], s);
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[beam] = sh[0];
+}
+
+// one block: mark converged beams, then restart the cycle on the others:
+// beta = ||r|| over unconverged beams, the in-cycle stopping threshold
+// rtol * min ||b_b|| over them (which implies every one of them converged)
+__global__ void __launch_bounds__(256) k_beam_mask(const double *__restrict__ r2, const double *__restrict__ b2, int nb,
+                                                   double rtol, int *__restrict__ bdone, GmresState *st) {
+    __shared__ double ssum[256], smin[256];
+    __shared__ int scnt[256];
+    double sum = 0.0, mn = 1e300;
+    int cnt = 0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int done = bdone[b] || b2[b] == 0.0 || r2[b] <= rtol * rtol * b2[b];
+        bdone[b] = done;
+        if (!done) {
+            sum += r2[b];
+            mn = fmin(mn, b2[b]);
+            ++cnt;
+        }
+    }
+    ssum[threadIdx.x] = sum;
+    smin[threadIdx.x] = mn;
+    scnt[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            ssum[threadIdx.x] += ssum[threadIdx.x + o];
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+            scnt[threadIdx.x] += scnt[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double beta = sqrt(ssum[0]);
+        st->beta = beta;
+        st->g[0] = beta;
+        st->inv_norm = beta > 0.0 ? 1.0 / beta : 0.0;
+        st->bnorm = scnt[0] > 0 ? sqrt(smin[0]) : 1.0;
+        st->done = scnt[0] == 0 ? 1 : 0;
+        st->jend = 0;
+    }
+}
+
+template <class T>
+__global__ void k_mask_rows(T *__restrict__ r, int n, const int32_t *__restrict__ nbo, const int *__restrict__ bdone) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && bdone[nbo[i]]) r[i] = (T)0;
+}
+
+// tile t (TILE rows) is active if one of its rows belongs to an unconverged beam
+__global__ void k_tile_active(const int32_t *__restrict__ nbo, const int *__restrict__ bdone, int n,
+                              uint8_t *__restrict__ tact) {
+    const int64_t lo = (int64_t)blockIdx.x * TILE;
+    int any = 0;
+    for (int64_t i = lo + threadIdx.x; i < lo + TILE && i < n; i += blockDim.x) any |= !bdone[nbo[i]];
+    any = __syncthreads_or(any);
+    if (threadIdx.x == 0) tact[blockIdx.x] = (uint8_t)any;
+}
+
+// after a residual product: freeze converged beams, restart on the others
+template <class T>
+apcloud_status mask_residual(apcloud_ctx *c, const BeamMask &bm, T *r, GmresState *st) {
+    const int n = c->n_tot;
+    APC_LAUNCH(c, K_VEC, bm.nb, 256, 0, k_beam_sq<T>, (const T *)r, bm.rng, bm.nb, bm.r2);
+    APC_LAUNCH(c, K_VEC, 1, 256, 0, k_beam_mask, (const double *)bm.r2, bm.b2, bm.nb, bm.rtol, bm.bdone, st);
+    APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mask_rows<T>, r, n, bm.nbo, (const int *)bm.bdone);
+    APC_LAUNCH(c, K_VEC, (int)bm.ntile, 256, 0, k_tile_active, bm.nbo, (const int *)bm.bdone, n, bm.tact);
+    return cuda_check(c, cudaGetLastError(), "beam mask");
 }
 
 // Krylov scratch of one GMRES of element type T
@@ -665,7 +790,11 @@ struct Krylov {
     const __half *hval = nullptr;   // FP16 copy of the matrix for the sweeps (FP32 vectors only)
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
     bool graphs = true;             // replay full restart cycles as CUDA graphs
+    RowSkip skip{nullptr, nullptr};         // batches: rows of converged beams
+    const uint8_t *tact = nullptr;          // batches: tiles holding a row of an unconverged beam
+    const BeamMask *mask = nullptr;         // batches: per-beam convergence at every restart
 };
+
 
 // z = p(Ahat) v with p(A) = omega sum_{i<d} (I - omega A)^i: d damped Jacobi
 // sweeps from z = 0 (the first one is z = omega v).  Returns the buffer
@@ -680,13 +809,13 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
         if constexpr (sizeof(T) == 4) {
             if (K.hval) {
                 APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
-                           (float *)nxt, (const float *)v, (const GmresState *)st);
+                           (float *)nxt, (const float *)v, (const GmresState *)st, K.skip);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
         }
         APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, val, n, (const T *)cur, nxt, (T *)nullptr, v, st,
-                    (double *)nullptr);
+                    (double *)nullptr, K.skip);
         T *tmp = cur; cur = nxt; nxt = tmp;
     }
     return cur;
@@ -718,7 +847,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     for (int j = 0; j < jmax; ++j) {
         if (K.pdeg <= 1) {
             APC_SPMV_BS(c, n, APC_SPMV1, sw, so, col, val, n, (const T *)K.wraw, K.w, K.V + (int64_t)j * K.ldv,
-                        (const T *)nullptr, st, (double *)nullptr);
+                        (const T *)nullptr, st, (double *)nullptr, K.skip);
         } else {
             // w = Ahat p(Ahat) v_j (right preconditioning)
             T *vj = K.V + (int64_t)j * K.ldv;
@@ -726,11 +855,11 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
                        (const GmresState *)st);
             T *z = poly_apply<T>(c, val, vj, K.z0, K, st);
             APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, (const T *)z, K.w, (T *)nullptr,
-                        (const T *)nullptr, st, (double *)nullptr);
+                        (const T *)nullptr, st, (double *)nullptr, K.skip);
         }
-        gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
-        gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
-        gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial);
+        gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
+        gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
+        gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
     }
     if (K.pdeg <= 1) {
         APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv, u,
@@ -750,7 +879,8 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     // the next cycle's residual keeps this cycle's column count: save it first
     APC_LAUNCH(c, K_VEC, 1, 32, 0, k_save_jend, st);
     APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
-               (T *)nullptr, b, st, K.partial);
+               (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
+    if (K.mask) APC_TRY(mask_residual<T>(c, *K.mask, K.wraw, st));
     return cuda_check(c, cudaGetLastError(), "gmres cycle");
 }
 
@@ -768,7 +898,8 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
         key.mask = c->timer.mask;
         key.spmv_bs = c->spmv_bs * 8 + c->spmv_unroll;
         const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
-                           c->slice_w.p, c->slice_off.p, c->ell_col.p};
+                           c->slice_w.p, c->slice_off.p, c->ell_col.p, K.skip.nbo, K.skip.bdone, K.tact,
+                           K.mask ? K.mask->r2 : nullptr};
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
         if (!g) {
@@ -806,7 +937,8 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
     apcloud_status status = APCLOUD_W_NOT_CONVERGED;
     const double vb = (double)sizeof(T), nnz = (double)c->sum_m + (double)c->n_int + (double)c->n_bnd, dn = n;
     APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
-               (T *)nullptr, b, st, K.partial);
+               (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
+    if (K.mask) APC_TRY(mask_residual<T>(c, *K.mask, K.wraw, st));
     StateTail tail;
     APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
     for (;;) {
@@ -852,25 +984,6 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
 
 }  // namespace
 
-// squared norm of b over the nodes of each beam (one block per beam, fixed order)
-__global__ void k_beam_norm2(const double *__restrict__ b, const int64_t *__restrict__ rng, int nb,
-                             double *__restrict__ out) {
-    __shared__ double sh[256];
-    const int beam = blockIdx.x;
-    double s = 0.0;
-    for (int seg = 0; seg < 7; ++seg) {
-        const int64_t lo = rng[(int64_t)seg * (nb + 1) + beam], hi = rng[(int64_t)seg * (nb + 1) + beam + 1];
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(b[i], b[i], s);
-    }
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[beam] = sh[0];
-}
-
 apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform) {
     const int n = c->n_int, nt = c->n_tot;
     double *rm = ensure<double>(c, c->rho_m, nt + 1);
@@ -891,7 +1004,7 @@ apcloud_status spmv(apcloud_ctx *c, int which, const double *x, double *y, doubl
     const int n = c->n_tot;
     APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<0, double>), ptr<uint32_t>(c->slice_w),
                ptr<uint32_t>(c->slice_off), ptr<int32_t>(c->ell_col), val, n, x, y, (double *)nullptr,
-               (const double *)nullptr, (GmresState *)nullptr, (double *)nullptr);
+               (const double *)nullptr, (GmresState *)nullptr, (double *)nullptr, RowSkip{nullptr, nullptr});
     return cuda_check(c, cudaGetLastError(), "spmv");
 }
 
@@ -914,20 +1027,24 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
     if (!u || !partial) return APCLOUD_E_NOMEM;
     const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
     const double *d = ptr<double>(which ? c->dA : c->dB);
+    // batch: every beam stops at its own rtol ||b_b|| (BeamMask)
+    BeamMask bmv{};
+    const BeamMask *bm = nullptr;
     if (c->nbeams > 1) {
-        // batch: stop at ||r|| <= rtol min_b ||b_b||, so that ||r_b|| <= rtol ||b_b|| for every beam
         const int nb = c->nbeams;
-        double *bn = ensure<double>(c, c->beam_norm, nb);
-        if (!bn) return APCLOUD_E_NOMEM;
-        APC_LAUNCH(c, K_VEC, nb, 256, 0, k_beam_norm2, b, (const int64_t *)ptr<int64_t>(c->beam_rng), nb, bn);
-        std::vector<double> h(nb);
-        APC_TRY(read_back(c, h.data(), bn, sizeof(double) * nb));
-        double tot = 0.0, mn = -1.0;
-        for (int i = 0; i < nb; ++i) {
-            tot += h[i];
-            if (h[i] > 0.0 && (mn < 0.0 || h[i] < mn)) mn = h[i];
-        }
-        if (mn > 0.0) rtol *= std::sqrt(mn / tot);
+        const int64_t ntile = div_up(ldv, TILE);
+        double *b2 = ensure<double>(c, c->beam_norm, nb), *r2 = ensure<double>(c, c->beam_r2, nb);
+        int *bdone = ensure<int>(c, c->beam_done, nb);
+        int32_t *nbo = ensure<int32_t>(c, c->node_beam, n);
+        uint8_t *tact = ensure<uint8_t>(c, c->tile_act, ntile);
+        if (!b2 || !r2 || !bdone || !nbo || !tact) return APCLOUD_E_NOMEM;
+        APC_TRY(node_beams(c, nbo));
+        APC_CUDA(c, cudaMemsetAsync(bdone, 0, sizeof(int) * nb, c->s));
+        APC_CUDA(c, cudaMemsetAsync(tact, 1, ntile, c->s));
+        const int64_t *rng = ptr<int64_t>(c->beam_rng);
+        APC_LAUNCH(c, K_VEC, nb, 256, 0, k_beam_sq<double>, b, rng, nb, b2);
+        bmv = BeamMask{nb, rng, b2, r2, bdone, nbo, tact, ntile, rtol};
+        bm = &bmv;
     }
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
     int iters = 0, cycles = 0;
@@ -944,6 +1061,11 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.z1 = ensure<double>(c, c->pz1, ldv + 1);
             K.t = ensure<double>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
+        }
+        if (bm) {
+            K.mask = bm;
+            K.skip = RowSkip{bm->nbo, bm->bdone};
+            K.tact = bm->tact;
         }
         status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) return status;
@@ -963,6 +1085,10 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.t = ensure<float>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
         }
+        if (bm) {   // the outer loop freezes converged beams; the inner cycles skip their rows
+            K.skip = RowSkip{bm->nbo, bm->bdone};
+            K.tact = bm->tact;
+        }
         const float *val32 = ptr<float>(which ? c->ell_A32 : c->ell_B32);
         const uint32_t *sw = ptr<uint32_t>(c->slice_w), *sof = ptr<uint32_t>(c->slice_off);
         const int32_t *col = ptr<int32_t>(c->ell_col);
@@ -973,7 +1099,8 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         status = APCLOUD_W_NOT_CONVERGED;
         for (;;) {
             APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, double>), sw, sof, col, val, n,
-                       (const double *)u, r64, (double *)nullptr, b, so, partial);
+                       (const double *)u, r64, (double *)nullptr, b, so, partial, RowSkip{nullptr, nullptr});
+            if (bm) APC_TRY(mask_residual<double>(c, *bm, r64, so));
             double tmp[2];
             APC_TRY(read_back(c, tmp, &so->bnorm, 2 * sizeof(double)));
             relres = tmp[0] > 0.0 ? tmp[1] / tmp[0] : 0.0;
@@ -1047,20 +1174,23 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
                 if (mixed && c->P.poly_degree > 1) {
                     const __half *hv = ptr<__half>(c->ell_A16);
                     APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, hv, n, (const float *)x, (float *)y,
-                                (const float *)bv, (const GmresState *)st);
+                                (const float *)bv, (const GmresState *)st, RowSkip{nullptr, nullptr});
                 } else if (mixed) {
                     using T = float;
                     APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, ptr<float>(c->ell_A32), n, (const float *)x,
-                                (float *)y, (float *)nullptr, (const float *)nullptr, st, (double *)nullptr);
+                                (float *)y, (float *)nullptr, (const float *)nullptr, st, (double *)nullptr,
+                                RowSkip{nullptr, nullptr});
                 } else {
                     using T = double;
                     const int m = c->P.poly_degree > 1 ? 3 : 4;
                     if (m == 3)
                         APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, ptr<double>(c->ell_A), n, (const double *)x,
-                                    (double *)y, (double *)nullptr, (const double *)bv, st, (double *)nullptr);
+                                    (double *)y, (double *)nullptr, (const double *)bv, st, (double *)nullptr,
+                                    RowSkip{nullptr, nullptr});
                     else
                         APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, ptr<double>(c->ell_A), n, (const double *)x,
-                                    (double *)y, (double *)nullptr, (const double *)nullptr, st, (double *)nullptr);
+                                    (double *)y, (double *)nullptr, (const double *)nullptr, st, (double *)nullptr,
+                                    RowSkip{nullptr, nullptr});
                 }
             }
             cudaEventRecord(e1, c->s);

@@ -3,9 +3,9 @@
 Every beam of a batch must come out exactly as the oracle computes it for that
 beam alone: node sets, leaf ranges and stencil neighbour lists bit-exact, and
 rho, phi, node derivatives and particle fields within the FP64 form's 1e-10
-relative L2.  The batch's stopping rule (||r|| <= rtol min_b ||b_b||) makes
-every beam's own relative residual at most rtol, so rtol = 1e-13 leaves the
-same margin as the single-beam parity tests.
+relative L2.  Every beam of a batch stops at its own relative residual rtol
+(converged beams are frozen at each restart), so rtol = 1e-13 leaves the same
+margin as the single-beam parity tests.
 """
 import numpy as np
 import pytest
