@@ -572,9 +572,10 @@ def run_learned(args):
                 r["speedup"] = round(res["jacobi"]["ms"] / r["ms"], 3)
             rows.append({"seed": seed, "form": fname, "n_nodes": ap.n_nodes, "loss_learned": lo, **res})
             ap.close()
-    fp = [r for r in rows if r["form"] == "fp64_jacobi"]
-    speed = float(np.mean([r["learned_scaling_guess"]["speedup"] for r in fp]))
-    return {"metric": "GMRES(30) time to rtol 1e-10 on held-out seeds, Jacobi / learned preconditioner",
+    mx = [r for r in rows if r["form"] == "mixed_poly16"]
+    speed = float(np.mean([r["learned_scaling"]["speedup"] for r in mx]))
+    return {"metric": "Poisson solve time to rtol 1e-10 on held-out seeds, without / with the learned column "
+                      "scaling (mixed form, polynomial degree 16)",
             "value": round(speed, 3), "unit": "x", "n_gpus": 1, "steps": len(args.eval_seeds), "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
             "data": "synthetic",
@@ -603,7 +604,7 @@ def main():
                          "(with --vp: use its column scaling in the leapfrog solves)")
     ap.add_argument("--train-systems", type=int, default=10000)
     ap.add_argument("--eval-seeds", type=int, nargs="+", default=[90001, 90002])
-    ap.add_argument("--learned-max-iter", type=int, default=20000)
+    ap.add_argument("--learned-max-iter", type=int, default=100000)
     args = ap.parse_args()
     if args.vp:
         print(json.dumps(run_vp(args)))

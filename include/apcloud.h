@@ -370,9 +370,12 @@ apcloud_status apcloud_mpnn_outputs(apcloud_ctx *ctx, apcloud_mpnn *net, float *
  * scales by the closed-form minimiser 1/||Ahat e_j||^2 of the same objective
  * instead of the network's s (the comparison baseline).  Without bit 1 the
  * start is d_phi0 (device, n_nodes values) or 0 when it is NULL; use = 0 is
- * plain apcloud_solve.  The stored matrix is restored afterwards.  The
- * residual test is the same FP64 true residual, so the network can change the
- * iteration count, never the accuracy. */
+ * plain apcloud_solve.  The scaled solve gets at most 1000 Arnoldi steps; if
+ * it has not converged by then, the solve continues from its iterate with the
+ * plain Jacobi scaling (the fallback; info counts both phases).  The stored
+ * matrix is restored afterwards.  The residual test is the same FP64 true
+ * residual, so the network can change the iteration count, never the
+ * accuracy. */
 apcloud_status apcloud_solve_learned(apcloud_ctx *ctx, apcloud_mpnn *net, unsigned use, const double *d_phi0,
                                      double rtol, int max_iter, double *d_phi_out, apcloud_solve_info *info);
 

@@ -47,6 +47,7 @@ constexpr int OFF_W0 = 0, OFF_B0 = OFF_W0 + 2 * NF * WD, OFF_W1 = OFF_B0 + WD, O
               N_PARAMS = OFF_BO + 2;
 constexpr int OFF_W[3] = {OFF_W0, OFF_W1, OFF_W2}, OFF_B[3] = {OFF_B0, OFF_B1, OFF_B2};
 constexpr unsigned ERR_TC_TIMEOUT = 1u;
+constexpr int LEARNED_STEPS = 1000;   // Arnoldi steps the scaled solve gets before the Jacobi fallback
 
 // ---------------------------------------------------------------- tcgen05 helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -1144,13 +1145,26 @@ extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m,
                    ptr<uint32_t>(c->slice_off), ptr<int32_t>(c->ell_col), ptr<double>(c->ell_A), scale, n, dA);
         APC_TRY(refresh_lowp(c));
     }
-    apcloud_status st = gmres_solve(c, 1, b, phi, rtol, max_iter, info);
+    // the scaled phase gets at most LEARNED_STEPS Arnoldi steps; a solve it has
+    // not finished continues with plain Jacobi from its iterate (the fallback)
+    const int budget = (use & 1u) && max_iter > LEARNED_STEPS ? LEARNED_STEPS : max_iter;
+    apcloud_solve_info i1{};
+    apcloud_status st = gmres_solve(c, 1, b, phi, rtol, budget, &i1);
     if (use & 1u) {
         APC_CUDA(c, cudaMemcpyAsync(ptr<double>(c->ell_A), bk, sizeof(double) * c->ell_entries, cudaMemcpyDeviceToDevice, c->s));
         APC_CUDA(c, cudaMemcpyAsync(dA, dbk, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
         APC_TRY(refresh_lowp(c));
     }
     if (st < 0) return st;
+    if (st == APCLOUD_W_NOT_CONVERGED && budget < max_iter) {
+        apcloud_solve_info i2{};
+        st = gmres_solve(c, 1, b, phi, rtol, max_iter - i1.iters, &i2);
+        if (st < 0) return st;
+        i1.iters += i2.iters;
+        i1.restarts += i2.restarts;
+        i1.relres = i2.relres;
+    }
+    if (info) *info = i1;
     if (d_phi_out) APC_CUDA(c, cudaMemcpyAsync(d_phi_out, phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
     c->stage = 4;
     return st;
