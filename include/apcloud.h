@@ -371,8 +371,8 @@ apcloud_status apcloud_mpnn_outputs(apcloud_ctx *ctx, apcloud_mpnn *net, float *
  * instead of the network's s (the comparison baseline).  Without bit 1 the
  * start is d_phi0 (device, n_nodes values) or 0 when it is NULL; use = 0 is
  * plain apcloud_solve.  The scaled solve gets at most 1000 Arnoldi steps; if
- * it has not converged by then, the solve continues from its iterate with the
- * plain Jacobi scaling (the fallback; info counts both phases).  The stored
+ * it has not converged by then, the plain Jacobi-scaled solve runs from the
+ * original start (the fallback; info counts both phases).  The stored
  * matrix is restored afterwards.  The residual test is the same FP64 true
  * residual, so the network can change the iteration count, never the
  * accuracy. */

@@ -737,7 +737,7 @@ enum MpBuf {
     MB_CNT = 0, MB_OFF, MB_KEY0, MB_KEY1, MB_REC0, MB_REC1, MB_FLAG, MB_POS, MB_ECOL, MB_AOUT, MB_AIN, MB_UKEY,
     MB_RP, MB_S, MB_PF, MB_PB, MB_F, MB_H0, MB_PH0, MB_H1, MB_PH1, MB_H2, MB_PH2, MB_H3, MB_T, MB_SV, MB_GAMMA,
     MB_R, MB_PART, MB_LOSS, MB_DT, MB_DZ, MB_DX, MB_DH, MB_WPART, MB_BMAX, MB_TICKET, MB_BACKUP, MB_DBACKUP,
-    MB_PHI0, MB_CCOL, MB_COUNT
+    MB_PHI0, MB_CCOL, MB_X0, MB_COUNT
 };
 static_assert(MB_COUNT <= 48, "buffer slots");
 
@@ -1148,6 +1148,12 @@ extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m,
     // the scaled phase gets at most LEARNED_STEPS Arnoldi steps; a solve it has
     // not finished continues with plain Jacobi from its iterate (the fallback)
     const int budget = (use & 1u) && max_iter > LEARNED_STEPS ? LEARNED_STEPS : max_iter;
+    double *x0 = nullptr;
+    if (budget < max_iter) {   // keep the start: the fallback begins from it, not from the scaled phase's iterate
+        x0 = mb<double>(c, MB_X0, n);
+        if (!x0) return APCLOUD_E_NOMEM;
+        APC_CUDA(c, cudaMemcpyAsync(x0, phi, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
+    }
     apcloud_solve_info i1{};
     apcloud_status st = gmres_solve(c, 1, b, phi, rtol, budget, &i1);
     if (use & 1u) {
@@ -1157,6 +1163,9 @@ extern "C" apcloud_status apcloud_solve_learned(apcloud_ctx *c, apcloud_mpnn *m,
     }
     if (st < 0) return st;
     if (st == APCLOUD_W_NOT_CONVERGED && budget < max_iter) {
+        // restarted GMRES can stall on the rough residual a failed scaled phase
+        // leaves, so the plain solve starts again from the original start
+        APC_CUDA(c, cudaMemcpyAsync(phi, x0, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->s));
         apcloud_solve_info i2{};
         st = gmres_solve(c, 1, b, phi, rtol, max_iter - i1.iters, &i2);
         if (st < 0) return st;
