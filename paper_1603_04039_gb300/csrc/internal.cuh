@@ -60,7 +60,7 @@ struct GraphKey {
     int tsize, n, jmax, pdeg, nblk, spmv_bs;
     unsigned mask;
     int64_t ldv;
-    const void *p[32];
+    const void *p[20];
 };
 
 struct GraphEntry {
@@ -139,11 +139,6 @@ struct apcloud_ctx {
     apc::DBuf slice_w, slice_off, ell_col, ell_A, ell_B, dA, dB;
     apc::DBuf ell_A32, ell_B32;  // FP32 copies for the inner iterations of the mixed form
     apc::DBuf ell_A16, ell_B16;  // FP16 copies for the preconditioner sweeps of the mixed form
-    // sweep matrix of the mixed form: FP16 values with 16-bit column offsets
-    // (near part) plus the few entries whose column is farther (far part)
-    apc::DBuf cs_w1, cs_o1, cs_w2, cs_o2, cs_dcol, cs_A, cs_B, cs_fcol, cs_fA, cs_fB, cs_cnt;
-    int64_t cs_near = 0, cs_far = 0;   // stored nonzeros of each part
-    bool cs_ok = false;
     // solver
     apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
@@ -196,7 +191,6 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
                             const int64_t *h_offsets, int nbeams);
 apcloud_status node_beams(apcloud_ctx *c, int32_t *out);
 apcloud_status refresh_lowp(apcloud_ctx *c);          // FP32/FP16 matrix copies from the FP64 values
-apcloud_status build_sweep_matrix(apcloud_ctx *c);    // compressed FP16 sweep matrix from the ELL
 double *poisson_rhs(apcloud_ctx *c, const double *g);  // b of the Poisson system into c->b
 apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out);      // ms per sweep at 64/128/256/512 threads
 apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out);  // ms per build at 2/4/8 warps

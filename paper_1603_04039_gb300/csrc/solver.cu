@@ -294,66 +294,6 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
     y[r] = fmaf(om, b[r] - acc, x[r]);
 }
 
-// The same sweep on the compressed sweep matrix: near entries hold a 16-bit
-// column offset from the row, far entries a 32-bit column (two sliced ELLs).
-struct SweepMat {
-    const uint32_t *w1, *o1, *w2, *o2;
-    const int16_t *dcol;
-    const __half *v1;
-    const int32_t *fcol;
-    const __half *v2;
-};
-
-template <int BS, int U = 1>
-__global__ void __launch_bounds__(BS) k_sweep_c(SweepMat M, int n, const float *__restrict__ x, float *__restrict__ y,
-                                                const float *__restrict__ b, const GmresState *__restrict__ st,
-                                                RowSkip skip) {
-    if (st->done) return;
-    const int r = blockIdx.x * BS + threadIdx.x;
-    if (r >= n) return;
-    if (skip.nbo && skip.bdone[skip.nbo[r]]) {
-        y[r] = 0.f;
-        return;
-    }
-    const float om = (float)st->omega;
-    const int sl = r >> 5, lane = r & 31;
-    float acc = 0.f;
-    {
-        const int w = (int)M.w1[sl];
-        const int64_t base = (int64_t)M.o1[sl] * 32 + lane;
-        int k = 0;
-        if (U > 1) {
-            for (; k + U <= w; k += U) {
-                int ci[U];
-                float vv[U], xv[U];
-#pragma unroll
-                for (int u = 0; u < U; ++u) {
-                    const int64_t e = base + (int64_t)(k + u) * 32;
-                    ci[u] = r + (int)M.dcol[e];
-                    vv[u] = __half2float(M.v1[e]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; ++u) xv[u] = x[ci[u]];
-#pragma unroll
-                for (int u = 0; u < U; ++u) acc = fmaf(vv[u], xv[u], acc);
-            }
-        }
-        for (; k < w; ++k) {
-            const int64_t e = base + (int64_t)k * 32;
-            acc = fmaf(__half2float(M.v1[e]), x[r + (int)M.dcol[e]], acc);
-        }
-    }
-    {
-        const int w = (int)M.w2[sl];
-        const int64_t base = (int64_t)M.o2[sl] * 32 + lane;
-        for (int k = 0; k < w; ++k) {
-            const int64_t e = base + (int64_t)k * 32;
-            acc = fmaf(__half2float(M.v2[e]), x[M.fcol[e]], acc);
-        }
-    }
-    y[r] = fmaf(om, b[r] - acc, x[r]);
-}
-
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
 // autotuner chose (64, 128, 256 or 512 threads).
 #define APC_SPMV_BS(c, n, KERNEL_OF, ...)                                                                   \
@@ -378,7 +318,6 @@ __global__ void __launch_bounds__(BS) k_sweep_c(SweepMat M, int n, const float *
 #define APC_SPMV3(B, U) (k_spmv<3, T, B, U>)
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
-#define APC_SWEEPC(B, U) (k_sweep_c<B, U>)
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
 // Every arithmetic instruction does useful work on 32 lanes (GB300 runs FP64
@@ -849,8 +788,6 @@ struct Krylov {
     int pdeg = 1;                   // degree of the Jacobi-Neumann polynomial (1 = Jacobi)
     double omega = 1.0;
     const __half *hval = nullptr;   // FP16 copy of the matrix for the sweeps (FP32 vectors only)
-    bool csw = false;               // sweeps on the compressed sweep matrix (cs)
-    SweepMat cs{};
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
     bool graphs = true;             // replay full restart cycles as CUDA graphs
     RowSkip skip{nullptr, nullptr};         // batches: rows of converged beams
@@ -870,12 +807,6 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     T *cur = z_first, *nxt = (z_first == K.z0) ? K.z1 : K.z0;
     for (int i = 1; i < K.pdeg; ++i) {
         if constexpr (sizeof(T) == 4) {
-            if (K.csw) {
-                APC_SPMV_BS(c, n, APC_SWEEPC, K.cs, n, (const float *)cur, (float *)nxt, (const float *)v,
-                            (const GmresState *)st, K.skip);
-                T *tmp = cur; cur = nxt; nxt = tmp;
-                continue;
-            }
             if (K.hval) {
                 APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
                            (float *)nxt, (const float *)v, (const GmresState *)st, K.skip);
@@ -968,8 +899,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
         key.spmv_bs = c->spmv_bs * 8 + c->spmv_unroll;
         const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
                            c->slice_w.p, c->slice_off.p, c->ell_col.p, K.skip.nbo, K.skip.bdone, K.tact,
-                           K.mask ? K.mask->r2 : nullptr, K.csw ? K.cs.dcol : nullptr, K.cs.v1, K.cs.fcol, K.cs.v2,
-                           K.cs.w1, K.cs.o1, K.cs.w2, K.cs.o2};
+                           K.mask ? K.mask->r2 : nullptr};
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
         if (!g) {
@@ -1029,9 +959,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             const double sweeps = (K.pdeg <= 1) ? 0.0 : (double)(K.pdeg - 1) * (je + 1);
             const double prods = je + 1.0;
             const double sb = K.hval ? 2.0 : vb;
-            // sweep bytes per stored nonzero: value + column (16-bit offsets on the compressed matrix)
-            const double swb = K.csw ? (4.0 * (double)c->cs_near + 6.0 * (double)c->cs_far) : (sb + 4.0) * nnz;
-            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods + (swb + 3.0 * vb * dn) * sweeps,
+            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods + ((sb + 4.0) * nnz + 3.0 * vb * dn) * sweeps,
                     2.0 * nnz * (prods + sweeps));
         }
         for (int j = 0; j < je; ++j) {
@@ -1152,13 +1080,6 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.pdeg = c->P.poly_degree;
             K.omega = c->P.poly_omega;
             K.hval = ptr<__half>(which ? c->ell_A16 : c->ell_B16);
-            if (c->cs_ok) {
-                K.csw = true;
-                K.cs = SweepMat{ptr<uint32_t>(c->cs_w1), ptr<uint32_t>(c->cs_o1), ptr<uint32_t>(c->cs_w2),
-                                ptr<uint32_t>(c->cs_o2), ptr<int16_t>(c->cs_dcol),
-                                ptr<__half>(which ? c->cs_A : c->cs_B), ptr<int32_t>(c->cs_fcol),
-                                ptr<__half>(which ? c->cs_fA : c->cs_fB)};
-            }
             K.z0 = ensure<float>(c, c->pz0, ldv + 1);
             K.z1 = ensure<float>(c, c->pz1, ldv + 1);
             K.t = ensure<float>(c, c->pt, ldv + 1);
@@ -1250,13 +1171,7 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
         for (int rep = 0; rep < 2; ++rep) {   // warm-up pass, then the timed pass
             cudaEventRecord(e0, c->s);
             for (int k = 0; k < 10; ++k) {
-                if (mixed && c->P.poly_degree > 1 && c->cs_ok) {
-                    const SweepMat M{ptr<uint32_t>(c->cs_w1), ptr<uint32_t>(c->cs_o1), ptr<uint32_t>(c->cs_w2),
-                                     ptr<uint32_t>(c->cs_o2), ptr<int16_t>(c->cs_dcol), ptr<__half>(c->cs_A),
-                                     ptr<int32_t>(c->cs_fcol), ptr<__half>(c->cs_fA)};
-                    APC_SPMV_BS(c, n, APC_SWEEPC, M, n, (const float *)x, (float *)y, (const float *)bv,
-                                (const GmresState *)st, RowSkip{nullptr, nullptr});
-                } else if (mixed && c->P.poly_degree > 1) {
+                if (mixed && c->P.poly_degree > 1) {
                     const __half *hv = ptr<__half>(c->ell_A16);
                     APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, hv, n, (const float *)x, (float *)y,
                                 (const float *)bv, (const GmresState *)st, RowSkip{nullptr, nullptr});

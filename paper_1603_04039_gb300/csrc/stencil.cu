@@ -610,7 +610,6 @@ apcloud_status build_stencils(apcloud_ctx *c) {
         if (!fA || !fB || !hA || !hB) return APCLOUD_E_NOMEM;
         APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)vA,
                    (const double *)vB, c->ell_entries, fA, fB, hA, hB);
-        APC_TRY(build_sweep_matrix(c));
     }
     return cuda_check(c, cudaGetLastError(), "ell");
 }
@@ -680,139 +679,7 @@ apcloud_status refresh_lowp(apcloud_ctx *c) {
     APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)ptr<double>(c->ell_A),
                (const double *)ptr<double>(c->ell_B), c->ell_entries, ptr<float>(c->ell_A32), ptr<float>(c->ell_B32),
                ptr<__half>(c->ell_A16), ptr<__half>(c->ell_B16));
-    APC_TRY(build_sweep_matrix(c));
     return cuda_check(c, cudaGetLastError(), "refresh_lowp");
-}
-
-namespace {
-
-constexpr int NEAR = 32767;   // largest |column - row| a 16-bit offset holds
-
-// per row: stored nonzeros whose column is within NEAR of the row (near) and the others (far)
-__global__ void k_split_count(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
-                              const int32_t *__restrict__ col, const __half *__restrict__ hA,
-                              const __half *__restrict__ hB, int n, uint32_t *__restrict__ cnt) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    const int sl = r >> 5, lane = r & 31;
-    const int w = (int)sw[sl];
-    const int64_t base = (int64_t)soff[sl] * 32 + lane;
-    uint32_t nr = 0, fr = 0;
-    for (int k = 0; k < w; ++k) {
-        const int64_t e = base + (int64_t)k * 32;
-        if (k > 0 && __half2float(hA[e]) == 0.f && __half2float(hB[e]) == 0.f) continue;
-        const int d = col[e] - r;
-        if (d >= -NEAR && d <= NEAR) ++nr; else ++fr;
-    }
-    cnt[r] = nr;
-    cnt[n + r] = fr;
-}
-
-// slice widths of both parts (max over the 32 rows)
-__global__ void k_split_width(const uint32_t *__restrict__ cnt, int n, int nsl, uint32_t *__restrict__ w1,
-                              uint32_t *__restrict__ w2) {
-    const int s = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (s >= nsl) return;
-    const int r = s * 32 + lane;
-    uint32_t a = r < n ? cnt[r] : 0u, b = r < n ? cnt[n + r] : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
-        b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
-    }
-    if (lane == 0) { w1[s] = a; w2[s] = b; }
-}
-
-__global__ void k_split_fill(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
-                             const int32_t *__restrict__ col, const __half *__restrict__ hA,
-                             const __half *__restrict__ hB, int n, int nsl, const uint32_t *__restrict__ w1,
-                             const uint32_t *__restrict__ o1, const uint32_t *__restrict__ w2,
-                             const uint32_t *__restrict__ o2, int16_t *__restrict__ dcol, __half *__restrict__ nA,
-                             __half *__restrict__ nB, int32_t *__restrict__ fcol, __half *__restrict__ fA,
-                             __half *__restrict__ fB) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int sl = r >> 5, lane = r & 31;
-    if (sl >= nsl) return;
-    const int64_t b1 = (int64_t)o1[sl] * 32 + lane, b2 = (int64_t)o2[sl] * 32 + lane;
-    int k1 = 0, k2 = 0;
-    if (r < n) {
-        const int w = (int)sw[sl];
-        const int64_t base = (int64_t)soff[sl] * 32 + lane;
-        for (int k = 0; k < w; ++k) {
-            const int64_t e = base + (int64_t)k * 32;
-            const __half a = hA[e], bb = hB[e];
-            if (k > 0 && __half2float(a) == 0.f && __half2float(bb) == 0.f) continue;
-            const int d = col[e] - r;
-            if (d >= -NEAR && d <= NEAR) {
-                const int64_t q = b1 + (int64_t)k1++ * 32;
-                dcol[q] = (int16_t)d;
-                nA[q] = a;
-                nB[q] = bb;
-            } else {
-                const int64_t q = b2 + (int64_t)k2++ * 32;
-                fcol[q] = col[e];
-                fA[q] = a;
-                fB[q] = bb;
-            }
-        }
-    }
-    // padding: offset 0 (the row itself) with value 0
-    for (; k1 < (int)w1[sl]; ++k1) {
-        const int64_t q = b1 + (int64_t)k1 * 32;
-        dcol[q] = 0;
-        nA[q] = __float2half(0.f);
-        nB[q] = __float2half(0.f);
-    }
-    for (; k2 < (int)w2[sl]; ++k2) {
-        const int64_t q = b2 + (int64_t)k2 * 32;
-        fcol[q] = r < n ? r : 0;
-        fA[q] = __float2half(0.f);
-        fB[q] = __float2half(0.f);
-    }
-}
-
-}  // namespace
-
-// The preconditioner sweeps of the mixed form read the matrix 15 times per
-// Arnoldi step; with FP16 values a 32-bit column index is two thirds of their
-// traffic.  Most stencil columns lie within 32767 rows of their row in the
-// Morton order, so those entries store a 16-bit offset (4 bytes per entry with
-// the value) and the rest go to a second, narrow sliced ELL with 32-bit
-// columns.  Built from the FP16 copies; the entry order within each part is the
-// stored order.
-apcloud_status build_sweep_matrix(apcloud_ctx *c) {
-    c->cs_ok = false;
-    const int n = c->n_tot;
-    if (n == 0) return APCLOUD_OK;
-    const int nsl = div_up(n, 32);
-    uint32_t *cnt = ensure<uint32_t>(c, c->cs_cnt, 2 * (int64_t)n);
-    uint32_t *w1 = ensure<uint32_t>(c, c->cs_w1, nsl), *o1 = ensure<uint32_t>(c, c->cs_o1, nsl);
-    uint32_t *w2 = ensure<uint32_t>(c, c->cs_w2, nsl), *o2 = ensure<uint32_t>(c, c->cs_o2, nsl);
-    if (!cnt || !w1 || !o1 || !w2 || !o2) return APCLOUD_E_NOMEM;
-    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
-    const int32_t *col = ptr<int32_t>(c->ell_col);
-    const __half *hA = ptr<__half>(c->ell_A16), *hB = ptr<__half>(c->ell_B16);
-    APC_LAUNCH(c, K_ELL, div_up(n, 256), 256, 0, k_split_count, sw, so, col, hA, hB, n, cnt);
-    APC_LAUNCH(c, K_ELL, div_up(nsl, 8), 256, 0, k_split_width, (const uint32_t *)cnt, n, nsl, w1, w2);
-    uint32_t *small = ptr<uint32_t>(c->dsmall);
-    APC_TRY(scan_u32(c, w1, o1, nsl, small + 10));
-    APC_TRY(scan_u32(c, w2, o2, nsl, small + 11));
-    APC_TRY(scan_u32(c, cnt + n, cnt, n, small + 12));   // total far nonzeros (near counts no longer needed)
-    uint32_t t[3];
-    APC_TRY(read_back(c, t, small + 10, sizeof t));
-    const int64_t e1 = (int64_t)t[0] * 32, e2 = (int64_t)t[1] * 32;
-    int16_t *dcol = ensure<int16_t>(c, c->cs_dcol, e1);
-    __half *nA = ensure<__half>(c, c->cs_A, e1), *nB = ensure<__half>(c, c->cs_B, e1);
-    int32_t *fcol = ensure<int32_t>(c, c->cs_fcol, e2 > 0 ? e2 : 1);
-    __half *fA = ensure<__half>(c, c->cs_fA, e2 > 0 ? e2 : 1), *fB = ensure<__half>(c, c->cs_fB, e2 > 0 ? e2 : 1);
-    if (!dcol || !nA || !nB || !fcol || !fA || !fB) return APCLOUD_E_NOMEM;
-    APC_LAUNCH(c, K_ELL, div_up((int64_t)nsl * 32, 256), 256, 0, k_split_fill, sw, so, col, hA, hB, n, nsl,
-               (const uint32_t *)w1, (const uint32_t *)o1, (const uint32_t *)w2, (const uint32_t *)o2, dcol, nA, nB,
-               fcol, fA, fB);
-    c->cs_far = t[2];
-    c->cs_near = (int64_t)c->sum_m + n - c->cs_far;
-    c->cs_ok = true;
-    return cuda_check(c, cudaGetLastError(), "sweep matrix");
 }
 
 }  // namespace apc
