@@ -258,19 +258,28 @@ def run_ours(args, ws, rank, local):
         u0 = torch.cuda.Event(enable_timing=True)
         u1 = torch.cuda.Event(enable_timing=True)
         views = [(tx[s:e], ty[s:e], tz[s:e], tq[s:e]) for s, e in zip(offs[:-1], offs[1:])]
+        per_beam = []
         for rep in range(2):
+            per_beam = []
             u0.record(ap1.stream)
             for bx, by, bz, bq in views:
                 ap1.build_octree(bx, by, bz)
                 ap1.stencils()
                 ap1.deposit(q=bq, rtol=RTOL, max_iter=MAX_ITER)
-                ap1.solve(rtol=RTOL, max_iter=MAX_ITER)
+                _, ib = ap1.solve(rtol=RTOL, max_iter=MAX_ITER)
                 ap1.gather_field()
+                per_beam.append((ap1.n_nodes, ib["iters"]))
             u1.record(ap1.stream)
             torch.cuda.synchronize()
         ms_u = u0.elapsed_time(u1)
+        # Arnoldi work (rows x steps) of the beams solved alone against the batch's
+        work_alone = sum(nn * it for nn, it in per_beam)
         unbatched = {"ms_per_batch": round(ms_u, 2), "solves_per_s": round(nsolve * 1000.0 / ms_u, 4),
-                     "speedup_of_batching": round(ms_u / ms_step, 2)}
+                     "speedup_of_batching": round(ms_u / ms_step, 2),
+                     "poisson_steps_alone": {"min": min(it for _, it in per_beam),
+                                             "max": max(it for _, it in per_beam),
+                                             "node_weighted_mean": round(work_alone / sum(nn for nn, _ in per_beam), 1)},
+                     "row_steps_alone_over_batch": round(work_alone / max(1, n_nodes * info["iters_phi"]), 3)}
         ap1.close()
 
     # roofline of the dominant kernel, measured live in the timed region
