@@ -318,7 +318,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
                     &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
-                    &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act};
+                    &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act,
+                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i};
     for (DBuf *b : bufs) free_buf(c, *b);
     for (DBuf &b : c->mp) free_buf(c, b);
     cudaStreamSynchronize(c->s);

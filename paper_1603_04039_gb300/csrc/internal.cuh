@@ -131,6 +131,7 @@ struct apcloud_ctx {
     // nodes
     apc::DBuf leaf_anchor, leaf_level, leaf_first, leaf_count, node_ic, bowner, bface, bidx, adj;
     apc::DBuf beam_off, leaf_beam, beam_rng, beam_norm, beam_r2, beam_done, node_beam, tile_act;
+    apc::DBuf bk_items, bk_ioff, bk_d, bk_i;   // per-beam Krylov spaces of a batch
     apc::DBuf mp[48];   // learned preconditioner: graph, activations, gradients (indices in mpnn.cu)
     int mp_graph_n = -1; // node count the graph in mp was built for (-1: none)
     // stencils

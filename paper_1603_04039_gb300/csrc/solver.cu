@@ -211,7 +211,8 @@ __device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const
 // their Krylov vectors are zero, so the products skip them.
 struct RowSkip {
     const int32_t *nbo;   // beam of every node
-    const int *bdone;     // 1 once the beam has converged
+    const int *bdone;     // 1 once the beam has converged (or finished its cycle)
+    const double *binv;   // per-beam Krylov spaces: 1 / ||w|| of each beam (null: st->inv_norm)
 };
 
 // BS: threads per block (one row each); mode 2 runs with RT only, its block
@@ -232,7 +233,7 @@ __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, co
         return;
     }
     T s = (T)1;
-    if (MODE == 1) s = (T)st->inv_norm;
+    if (MODE == 1) s = (skip.binv && r < n) ? (T)skip.binv[skip.nbo[r]] : (T)st->inv_norm;
     if (MODE == 3) s = (T)st->omega;
     T acc = (T)0;
     double yv = 0.0;
@@ -776,6 +777,263 @@ apcloud_status mask_residual(apcloud_ctx *c, const BeamMask &bm, T *r, GmresStat
     return cuda_check(c, cudaGetLastError(), "beam mask");
 }
 
+// ---------------------------------------------------------------- per-beam Krylov spaces
+// A batch of B independent beams is block-diagonal.  Instead of one Krylov
+// space for the whole vector (whose iteration count is set by all beams at
+// once), every beam runs its own GMRES(m): the row-parallel kernels (products,
+// sweeps, normalisation) look up the row's beam, and the Gram-Schmidt
+// reductions run over "items" -- chunks of at most BITEM rows inside one of a
+// beam's 7 node ranges -- whose partial sums are added per beam in a fixed
+// order.  Each beam has its own Hessenberg matrix, Givens rotations, residual
+// estimate and stopping test; a beam that has finished its cycle (or
+// converged) drops out of every later launch of the cycle.
+constexpr int BITEM = 1024;   // rows per item
+constexpr int BGT = 256;      // threads per item block (8 warps)
+
+struct BKry {
+    int nb, nitems, m;
+    const int4 *items;        // (beam, lo, hi, 0)
+    const int *item_off;      // items of beam b: item_off[b] .. item_off[b+1]-1
+    const int32_t *nbo;       // beam of every node
+    double *H, *cs, *sn, *g, *h1, *h2, *y;   // per beam: (m+1) x m, m, m, m+1, m+1, m+1, m
+    double *bnorm, *binv, *r2, *relres;
+    int *done;                // cycle finished (converged, breakdown or m steps)
+    int *conv;                // converged: frozen for the rest of the solve
+    int *jend;
+};
+
+template <class T>
+__global__ void k_bnormalize_first(const T *__restrict__ wraw, T *__restrict__ vj, T *__restrict__ z, int n,
+                                   const int32_t *__restrict__ nbo, const int *__restrict__ done,
+                                   const double *__restrict__ binv, const GmresState *__restrict__ st) {
+    if (st->done) return;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int b = nbo[i];
+    if (done[b]) return;
+    const T v = wraw[i] * (T)binv[b];
+    vj[i] = v;
+    z[i] = (T)st->omega * v;
+}
+
+// PASS 0: h1 = V^T w over the item's rows.  PASS 1: w -= V h1 there, then
+// h2 = V^T w.  Partial sums per item (64 per item).
+template <int PASS, class T>
+__global__ void __launch_bounds__(BGT) k_bgs_dots(const T *__restrict__ V, int64_t ldv, int j, T *__restrict__ w,
+                                                  BKry bk, const GmresState *__restrict__ st,
+                                                  double *__restrict__ partial) {
+    __shared__ T ws[BITEM];
+    __shared__ T hs[MAX_RESTART + 1];
+    if (st->done) return;
+    const int4 it = bk.items[blockIdx.x];
+    const int beam = it.x, lo = it.y, cnt = it.z - it.y;
+    if (bk.done[beam]) return;
+    const int j1 = j + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (PASS == 1 && tid < j1) hs[tid] = (T)bk.h1[(int64_t)beam * (bk.m + 1) + tid];
+    __syncthreads();
+    for (int r = tid; r < cnt; r += BGT) {
+        T wi = w[lo + r];
+        if (PASS == 1) {
+            for (int k = 0; k < j1; ++k) wi = fma(-V[(int64_t)k * ldv + lo + r], hs[k], wi);
+            w[lo + r] = wi;
+        }
+        ws[r] = wi;
+    }
+    __syncthreads();
+    for (int k = wid; k < j1; k += BGT / 32) {
+        const T *vk = V + (int64_t)k * ldv + lo;
+        T a = (T)0;
+        for (int r = lane; r < cnt; r += 32) a = fma(vk[r], ws[r], a);
+        const double sum = warp_sum((double)a);
+        if (lane == 0) partial[(int64_t)blockIdx.x * 64 + k] = sum;
+    }
+}
+
+// per beam: h = sum of its items' partials (fixed order)
+template <int PASS>
+__global__ void k_bfinal_h(int j, BKry bk, const GmresState *__restrict__ st, const double *__restrict__ partial) {
+    if (st->done) return;
+    const int beam = blockIdx.x, i = threadIdx.x;
+    if (bk.done[beam] || i > j) return;
+    double s = 0.0;
+    for (int q = bk.item_off[beam]; q < bk.item_off[beam + 1]; ++q) s += partial[(int64_t)q * 64 + i];
+    double *h = (PASS == 0 ? bk.h1 : bk.h2) + (int64_t)beam * (bk.m + 1);
+    h[i] = s;
+}
+
+// wraw = w - V h2 over the item's rows; partial = ||wraw||^2 there
+template <class T>
+__global__ void __launch_bounds__(BGT) k_bgs_norm(const T *__restrict__ V, int64_t ldv, int j,
+                                                  const T *__restrict__ w, T *__restrict__ wraw, BKry bk,
+                                                  const GmresState *__restrict__ st, double *__restrict__ partial) {
+    __shared__ T hs[MAX_RESTART + 1];
+    __shared__ double red[BGT / 32];
+    if (st->done) return;
+    const int4 it = bk.items[blockIdx.x];
+    const int beam = it.x, lo = it.y, cnt = it.z - it.y;
+    if (bk.done[beam]) return;
+    const int j1 = j + 1, tid = threadIdx.x;
+    if (tid < j1) hs[tid] = (T)bk.h2[(int64_t)beam * (bk.m + 1) + tid];
+    __syncthreads();
+    double sq = 0.0;
+    for (int r = tid; r < cnt; r += BGT) {
+        T wi = w[lo + r];
+        for (int k = 0; k < j1; ++k) wi = fma(-V[(int64_t)k * ldv + lo + r], hs[k], wi);
+        wraw[lo + r] = wi;
+        sq = fma((double)wi, (double)wi, sq);
+    }
+    sq = warp_sum(sq);
+    if ((tid & 31) == 0) red[tid >> 5] = sq;
+    __syncthreads();
+    if (tid == 0) {
+        double t = 0.0;
+        for (int q = 0; q < BGT / 32; ++q) t += red[q];
+        partial[(int64_t)blockIdx.x * 64] = t;
+    }
+}
+
+// per beam (one thread each): Hessenberg column j, Givens rotation, residual
+// estimate, stopping test; then (block 0 of a single-block launch) the
+// number of beams still in their cycle decides st->done
+__global__ void __launch_bounds__(256) k_bfinal_norm(int j, BKry bk, GmresState *st,
+                                                     const double *__restrict__ partial) {
+    __shared__ int act[256];
+    int a = 0;
+    if (!st->done) {
+        const int M = bk.m;
+        for (int beam = threadIdx.x; beam < bk.nb; beam += blockDim.x) {
+            if (bk.done[beam]) continue;
+            double s = 0.0;
+            for (int q = bk.item_off[beam]; q < bk.item_off[beam + 1]; ++q) s += partial[(int64_t)q * 64];
+            const double hn = sqrt(s);
+            double *H = bk.H + (int64_t)beam * (M + 1) * M, *cs = bk.cs + (int64_t)beam * M,
+                   *sn = bk.sn + (int64_t)beam * M, *g = bk.g + (int64_t)beam * (M + 1);
+            const double *h1 = bk.h1 + (int64_t)beam * (M + 1), *h2 = bk.h2 + (int64_t)beam * (M + 1);
+            for (int i = 0; i <= j; ++i) H[i * M + j] = h1[i] + h2[i];
+            H[(j + 1) * M + j] = hn;
+            for (int i = 0; i < j; ++i) {
+                const double x0 = H[i * M + j], x1 = H[(i + 1) * M + j];
+                H[i * M + j] = cs[i] * x0 + sn[i] * x1;
+                H[(i + 1) * M + j] = -sn[i] * x0 + cs[i] * x1;
+            }
+            const double x0 = H[j * M + j], x1 = H[(j + 1) * M + j];
+            const double den = sqrt(x0 * x0 + x1 * x1);
+            cs[j] = den != 0.0 ? x0 / den : 1.0;
+            sn[j] = den != 0.0 ? x1 / den : 0.0;
+            H[j * M + j] = den;
+            H[(j + 1) * M + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            bk.jend[beam] = j + 1;
+            const bool fin = fabs(g[j + 1]) <= st->rtol * bk.bnorm[beam] || hn == 0.0 || j + 1 >= M;
+            bk.done[beam] = fin ? 1 : 0;
+            bk.binv[beam] = hn > 0.0 ? 1.0 / hn : 0.0;
+            if (!fin) ++a;
+        }
+    }
+    act[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) act[threadIdx.x] += act[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !st->done && act[0] == 0) st->done = 1;
+}
+
+// per beam: y = H^-1 g (jend x jend, upper triangular after the rotations)
+__global__ void k_bsolve_y(BKry bk) {
+    const int beam = blockIdx.x * blockDim.x + threadIdx.x;
+    if (beam >= bk.nb) return;
+    const int M = bk.m, je = bk.jend[beam];
+    const double *H = bk.H + (int64_t)beam * (M + 1) * M, *g = bk.g + (int64_t)beam * (M + 1);
+    double *y = bk.y + (int64_t)beam * M;
+    for (int k = je - 1; k >= 0; --k) {
+        double t = g[k];
+        for (int l = k + 1; l < je; ++l) t -= H[k * M + l] * y[l];
+        y[k] = t / H[k * M + k];
+    }
+}
+
+// out (+)= V y over the item's rows (ADD: u += V y; else t = V y)
+template <bool ADD, class T>
+__global__ void __launch_bounds__(BGT) k_bcombine(const T *__restrict__ V, int64_t ldv, T *__restrict__ out,
+                                                  BKry bk) {
+    const int4 it = bk.items[blockIdx.x];
+    const int beam = it.x, lo = it.y, cnt = it.z - it.y;
+    const int je = bk.jend[beam];
+    const double *y = bk.y + (int64_t)beam * bk.m;
+    for (int r = threadIdx.x; r < cnt; r += BGT) {
+        T sum = (T)0;
+        for (int k = 0; k < je; ++k) sum = fma(V[(int64_t)k * ldv + lo + r], (T)y[k], sum);
+        if (ADD) out[lo + r] += sum;
+        else out[lo + r] = sum;
+    }
+}
+
+// per beam after the residual b - Ahat u of a restart: beta_b, the stopping
+// test against rtol ||b_b|| (converged beams stay frozen), the start of the
+// beam's next cycle; st->done once every beam has converged
+__global__ void __launch_bounds__(256) k_bstart(BKry bk, GmresState *st) {
+    __shared__ int act[256];
+    __shared__ double rmax[256];
+    int a = 0;
+    double rm = 0.0;
+    const int M = bk.m;
+    for (int beam = threadIdx.x; beam < bk.nb; beam += blockDim.x) {
+        const double beta = sqrt(bk.r2[beam]), bn = bk.bnorm[beam];
+        const bool conv = bk.conv[beam] || bn == 0.0 || beta <= st->rtol * bn;
+        bk.conv[beam] = conv ? 1 : 0;
+        bk.done[beam] = conv ? 1 : 0;
+        bk.jend[beam] = 0;
+        double *g = bk.g + (int64_t)beam * (M + 1);
+        g[0] = beta;
+        for (int i = 1; i <= M; ++i) g[i] = 0.0;
+        bk.binv[beam] = beta > 0.0 ? 1.0 / beta : 0.0;
+        if (bn > 0.0) rm = fmax(rm, beta / bn);
+        if (!conv) ++a;
+    }
+    act[threadIdx.x] = a;
+    rmax[threadIdx.x] = rm;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            act[threadIdx.x] += act[threadIdx.x + o];
+            rmax[threadIdx.x] = fmax(rmax[threadIdx.x], rmax[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        // the host's test beta <= rtol * bnorm holds exactly when every beam converged
+        st->bnorm = 1.0;
+        st->beta = act[0] > 0 ? 1.0 : 0.0;
+        st->done = act[0] == 0 ? 1 : 0;
+        st->jend = 0;
+        *bk.relres = rmax[0];
+    }
+}
+
+__global__ void k_bnorm_init(BKry bk) {
+    const int beam = blockIdx.x * blockDim.x + threadIdx.x;
+    if (beam < bk.nb) {
+        bk.bnorm[beam] = sqrt(bk.r2[beam]);
+        bk.conv[beam] = 0;
+    }
+}
+
+// st->jlast = the longest cycle of any beam (for the host's step count)
+__global__ void __launch_bounds__(256) k_bmax_jend(BKry bk, GmresState *st) {
+    __shared__ int mx[256];
+    int v = 0;
+    for (int beam = threadIdx.x; beam < bk.nb; beam += blockDim.x) v = max(v, bk.jend[beam]);
+    mx[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) mx[threadIdx.x] = max(mx[threadIdx.x], mx[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) st->jlast = mx[0];
+}
+
 // Krylov scratch of one GMRES of element type T
 template <class T>
 struct Krylov {
@@ -793,6 +1051,7 @@ struct Krylov {
     RowSkip skip{nullptr, nullptr};         // batches: rows of converged beams
     const uint8_t *tact = nullptr;          // batches: tiles holding a row of an unconverged beam
     const BeamMask *mask = nullptr;         // batches: per-beam convergence at every restart
+    const BKry *bk = nullptr;               // batches: an independent Krylov space per beam
 };
 
 
@@ -800,7 +1059,8 @@ struct Krylov {
 // sweeps from z = 0 (the first one is z = omega v).  Returns the buffer
 // holding z.  v is read with a full row and the sweeps ping-pong z0/z1.
 template <class T>
-T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov<T> &K, GmresState *st) {
+T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov<T> &K, GmresState *st,
+              RowSkip skip) {
     const int n = c->n_tot;
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
@@ -809,13 +1069,13 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
         if constexpr (sizeof(T) == 4) {
             if (K.hval) {
                 APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
-                           (float *)nxt, (const float *)v, (const GmresState *)st, K.skip);
+                           (float *)nxt, (const float *)v, (const GmresState *)st, skip);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
         }
         APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, val, n, (const T *)cur, nxt, (T *)nullptr, v, st,
-                    (double *)nullptr, K.skip);
+                    (double *)nullptr, skip);
         T *tmp = cur; cur = nxt; nxt = tmp;
     }
     return cur;
@@ -836,6 +1096,70 @@ __global__ void k_save_jend(GmresState *st) {
     if (threadIdx.x == 0) st->jlast = st->jend;
 }
 
+// Per-beam Krylov spaces: the residual that opens a cycle gives every beam its
+// own beta and stopping test (k_bstart).
+template <class T>
+apcloud_status bstart_launches(apcloud_ctx *c, const Krylov<T> &K) {
+    const BKry &bk = *K.bk;
+    APC_LAUNCH(c, K_VEC, bk.nb, 256, 0, k_beam_sq<T>, (const T *)K.wraw, (const int64_t *)ptr<int64_t>(c->beam_rng),
+               bk.nb, bk.r2);
+    APC_LAUNCH(c, K_VEC, 1, 256, 0, k_bstart, bk, K.st);
+    return cuda_check(c, cudaGetLastError(), "batched restart");
+}
+
+// One restart cycle with an independent Krylov space per beam (same launches
+// for every beam), the update of u and the residual that opens the next cycle.
+template <class T>
+apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, const Krylov<T> &K, int jmax) {
+    const int n = c->n_tot;
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    GmresState *st = K.st;
+    const BKry &bk = *K.bk;
+    const RowSkip active{bk.nbo, bk.done, bk.binv};
+    for (int j = 0; j < jmax; ++j) {
+        if (K.pdeg <= 1) {
+            APC_SPMV_BS(c, n, APC_SPMV1, sw, so, col, val, n, (const T *)K.wraw, K.w, K.V + (int64_t)j * K.ldv,
+                        (const T *)nullptr, st, (double *)nullptr, active);
+        } else {
+            T *vj = K.V + (int64_t)j * K.ldv;
+            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_bnormalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
+                       bk.nbo, (const int *)bk.done, (const double *)bk.binv, (const GmresState *)st);
+            T *z = poly_apply<T>(c, val, vj, K.z0, K, st, RowSkip{bk.nbo, bk.done, nullptr});
+            APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, (const T *)z, K.w, (T *)nullptr,
+                        (const T *)nullptr, st, (double *)nullptr, RowSkip{bk.nbo, bk.done, nullptr});
+        }
+        APC_LAUNCH(c, K_DOT, bk.nitems, BGT, 0, (k_bgs_dots<0, T>), (const T *)K.V, K.ldv, j, K.w, bk,
+                   (const GmresState *)st, K.partial);
+        APC_LAUNCH(c, K_DOT, bk.nb, 64, 0, k_bfinal_h<0>, j, bk, (const GmresState *)st, (const double *)K.partial);
+        APC_LAUNCH(c, K_UPDDOT, bk.nitems, BGT, 0, (k_bgs_dots<1, T>), (const T *)K.V, K.ldv, j, K.w, bk,
+                   (const GmresState *)st, K.partial);
+        APC_LAUNCH(c, K_UPDDOT, bk.nb, 64, 0, k_bfinal_h<1>, j, bk, (const GmresState *)st,
+                   (const double *)K.partial);
+        APC_LAUNCH(c, K_UPDNORM, bk.nitems, BGT, 0, k_bgs_norm<T>, (const T *)K.V, K.ldv, j, (const T *)K.w, K.wraw,
+                   bk, (const GmresState *)st, K.partial);
+        APC_LAUNCH(c, K_UPDNORM, 1, 256, 0, k_bfinal_norm, j, bk, st, (const double *)K.partial);
+    }
+    APC_LAUNCH(c, K_CYCLE, div_up(bk.nb, 64), 64, 0, k_bsolve_y, bk);
+    if (K.pdeg <= 1) {
+        APC_LAUNCH(c, K_CYCLE, bk.nitems, BGT, 0, (k_bcombine<true, T>), (const T *)K.V, K.ldv, u, bk);
+    } else {
+        // u += p(Ahat) (V y), beam by beam; beams converged before this cycle are skipped
+        APC_LAUNCH(c, K_CYCLE, bk.nitems, BGT, 0, (k_bcombine<false, T>), (const T *)K.V, K.ldv, K.t, bk);
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_axpy_first<T>, (const T *)K.t, K.z0, n,
+                   (const GmresState *)st);
+        GmresState *stp = st;
+        APC_CUDA(c, cudaMemsetAsync(&stp->done, 0, sizeof(int), c->s));
+        T *z = poly_apply<T>(c, val, K.t, K.z0, K, st, RowSkip{bk.nbo, bk.conv, nullptr});
+        APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add<T>, u, (const T *)z, n);
+    }
+    APC_LAUNCH(c, K_VEC, 1, 256, 0, k_bmax_jend, bk, st);
+    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
+               (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
+    APC_TRY(bstart_launches<T>(c, K));
+    return cuda_check(c, cudaGetLastError(), "batched gmres cycle");
+}
+
 // One restart cycle of jmax Arnoldi steps, the update of u, and the residual
 // b - Ahat u that opens the next cycle (beta, g, done for it).
 template <class T>
@@ -844,6 +1168,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
     GmresState *st = K.st;
+    if (K.bk) return bcycle_launches<T>(c, val, b, u, K, jmax);
     for (int j = 0; j < jmax; ++j) {
         if (K.pdeg <= 1) {
             APC_SPMV_BS(c, n, APC_SPMV1, sw, so, col, val, n, (const T *)K.wraw, K.w, K.V + (int64_t)j * K.ldv,
@@ -853,7 +1178,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
             T *vj = K.V + (int64_t)j * K.ldv;
             APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_normalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
                        (const GmresState *)st);
-            T *z = poly_apply<T>(c, val, vj, K.z0, K, st);
+            T *z = poly_apply<T>(c, val, vj, K.z0, K, st, K.skip);
             APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, (const T *)z, K.w, (T *)nullptr,
                         (const T *)nullptr, st, (double *)nullptr, K.skip);
         }
@@ -873,7 +1198,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
         // the sweeps must run even though the cycle is done: clear the flag for them
         GmresState *stp = st;
         APC_CUDA(c, cudaMemsetAsync(&stp->done, 0, sizeof(int), c->s));
-        T *z = poly_apply<T>(c, val, K.t, K.z0, K, st);
+        T *z = poly_apply<T>(c, val, K.t, K.z0, K, st, K.skip);
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add<T>, u, (const T *)z, n);
     }
     // the next cycle's residual keeps this cycle's column count: save it first
@@ -899,7 +1224,9 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
         key.spmv_bs = c->spmv_bs * 8 + c->spmv_unroll;
         const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
                            c->slice_w.p, c->slice_off.p, c->ell_col.p, K.skip.nbo, K.skip.bdone, K.tact,
-                           K.mask ? K.mask->r2 : nullptr};
+                           K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,
+                           K.bk ? K.bk->H : nullptr, K.bk ? K.bk->done : nullptr,
+                           K.bk ? (const void *)(intptr_t)K.bk->nitems : nullptr};
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
         if (!g) {
@@ -939,6 +1266,13 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
     APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
                (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
     if (K.mask) APC_TRY(mask_residual<T>(c, *K.mask, K.wraw, st));
+    if (K.bk) {
+        // per-beam ||b_b|| once, then every beam's first cycle
+        APC_LAUNCH(c, K_VEC, K.bk->nb, 256, 0, k_beam_sq<T>, b, (const int64_t *)ptr<int64_t>(c->beam_rng),
+                   K.bk->nb, K.bk->r2);
+        APC_LAUNCH(c, K_VEC, div_up(K.bk->nb, 64), 64, 0, k_bnorm_init, *K.bk);
+        APC_TRY(bstart_launches<T>(c, K));
+    }
     StateTail tail;
     APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
     for (;;) {
@@ -975,6 +1309,11 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             if (tail.bnorm == 0.0 || tail.beta <= rtol * tail.bnorm) status = APCLOUD_OK;
             break;
         }
+    }
+    if (K.bk) {   // largest relative residual over the beams
+        double rr;
+        APC_TRY(read_back(c, &rr, K.bk->relres, sizeof rr));
+        relres = rr;
     }
     *iters_out = iters;
     *cycles_out = cycles;
@@ -1027,9 +1366,13 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
     if (!u || !partial) return APCLOUD_E_NOMEM;
     const double *val = ptr<double>(which ? c->ell_A : c->ell_B);
     const double *d = ptr<double>(which ? c->dA : c->dB);
-    // batch: every beam stops at its own rtol ||b_b|| (BeamMask)
+    // batch: every beam has its own Krylov space and stops at its own
+    // rtol ||b_b|| (BKry); the FP64 refinement loop of the mixed form freezes
+    // converged beams (BeamMask)
     BeamMask bmv{};
     const BeamMask *bm = nullptr;
+    BKry bkv{};
+    const BKry *bk = nullptr;
     if (c->nbeams > 1) {
         const int nb = c->nbeams;
         const int64_t ntile = div_up(ldv, TILE);
@@ -1045,6 +1388,50 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         APC_LAUNCH(c, K_VEC, nb, 256, 0, k_beam_sq<double>, b, rng, nb, b2);
         bmv = BeamMask{nb, rng, b2, r2, bdone, nbo, tact, ntile, rtol};
         bm = &bmv;
+        // work items of the per-beam Krylov spaces: chunks of at most BITEM rows
+        // inside each beam's 7 node ranges, grouped by beam
+        std::vector<int64_t> hr(7 * (size_t)(nb + 1));
+        APC_TRY(read_back(c, hr.data(), rng, sizeof(int64_t) * hr.size()));
+        std::vector<int4> items;
+        std::vector<int> ioff(nb + 1, 0);
+        for (int bb = 0; bb < nb; ++bb) {
+            ioff[bb] = (int)items.size();
+            for (int seg = 0; seg < 7; ++seg) {
+                const int64_t lo = hr[(size_t)seg * (nb + 1) + bb], hi = hr[(size_t)seg * (nb + 1) + bb + 1];
+                for (int64_t a = lo; a < hi; a += BITEM)
+                    items.push_back(make_int4(bb, (int)a, (int)(a + BITEM < hi ? a + BITEM : hi), 0));
+            }
+        }
+        ioff[nb] = (int)items.size();
+        const int ni = (int)items.size();
+        int4 *ditems = ensure<int4>(c, c->bk_items, ni > 0 ? ni : 1);
+        int *dioff = ensure<int>(c, c->bk_ioff, nb + 1);
+        const int64_t per = (int64_t)(m + 1) * m + 2 * m + 3 * (m + 1) + m + 3;
+        double *dd = ensure<double>(c, c->bk_d, per * nb + 1);
+        int *di = ensure<int>(c, c->bk_i, 3 * (int64_t)nb);
+        double *part2 = ensure<double>(c, c->partial, std::max<int64_t>(npart, (int64_t)ni * 64), true);
+        if (!ditems || !dioff || !dd || !di || !part2) return APCLOUD_E_NOMEM;
+        partial = part2;
+        if (ni > 0)
+            APC_CUDA(c, cudaMemcpyAsync(ditems, items.data(), sizeof(int4) * ni, cudaMemcpyHostToDevice, c->s));
+        APC_CUDA(c, cudaMemcpyAsync(dioff, ioff.data(), sizeof(int) * (nb + 1), cudaMemcpyHostToDevice, c->s));
+        APC_CUDA(c, cudaStreamSynchronize(c->s));   // the host vectors go out of scope
+        double *q = dd;
+        bkv.nb = nb; bkv.nitems = ni; bkv.m = m;
+        bkv.items = ditems; bkv.item_off = dioff; bkv.nbo = nbo;
+        bkv.H = q; q += (int64_t)(m + 1) * m * nb;
+        bkv.cs = q; q += (int64_t)m * nb;
+        bkv.sn = q; q += (int64_t)m * nb;
+        bkv.g = q; q += (int64_t)(m + 1) * nb;
+        bkv.h1 = q; q += (int64_t)(m + 1) * nb;
+        bkv.h2 = q; q += (int64_t)(m + 1) * nb;
+        bkv.y = q; q += (int64_t)m * nb;
+        bkv.bnorm = q; q += nb;
+        bkv.binv = q; q += nb;
+        bkv.r2 = q; q += nb;
+        bkv.relres = q;
+        bkv.done = di; bkv.conv = di + nb; bkv.jend = di + 2 * nb;
+        bk = &bkv;
     }
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
     int iters = 0, cycles = 0;
@@ -1062,11 +1449,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.t = ensure<double>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
         }
-        if (bm) {
-            K.mask = bm;
-            K.skip = RowSkip{bm->nbo, bm->bdone};
-            K.tact = bm->tact;
-        }
+        K.bk = bk;
         status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) return status;
     } else {
@@ -1085,10 +1468,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.t = ensure<float>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
         }
-        if (bm) {   // the outer loop freezes converged beams; the inner cycles skip their rows
-            K.skip = RowSkip{bm->nbo, bm->bdone};
-            K.tact = bm->tact;
-        }
+        K.bk = bk;   // beams frozen by the outer loop have zero residual: their inner spaces stop at once
         const float *val32 = ptr<float>(which ? c->ell_A32 : c->ell_B32);
         const uint32_t *sw = ptr<uint32_t>(c->slice_w), *sof = ptr<uint32_t>(c->slice_off);
         const int32_t *col = ptr<int32_t>(c->ell_col);
