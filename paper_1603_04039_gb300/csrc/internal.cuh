@@ -60,7 +60,7 @@ struct GraphKey {
     int tsize, n, jmax, pdeg, nblk, spmv_bs;
     unsigned mask;
     int64_t ldv;
-    const void *p[20];
+    const void *p[32];
 };
 
 struct GraphEntry {

@@ -1227,6 +1227,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
                            K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,
                            K.bk ? K.bk->H : nullptr, K.bk ? K.bk->done : nullptr,
                            K.bk ? (const void *)(intptr_t)K.bk->nitems : nullptr};
+        static_assert(sizeof p <= sizeof key.p, "graph key holds every buffer address");
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
         if (!g) {
