@@ -126,12 +126,15 @@ apcloud_status apcloud_build_octree(apcloud_ctx *ctx, const double *d_x, const d
  * the same launches.  Interior nodes are ordered by beam, then Morton order;
  * boundary nodes by face, then owner leaf.  Leaf keys (apcloud_get_leaves)
  * carry the beam index above the 3*level Morton bits.  In a batch every
- * beam stops at its own ||r_b|| <= rtol ||b_b||: at each GMRES restart the
- * beams that meet it are frozen (their residual rows are zeroed, so the
- * block-diagonal Krylov vectors stay zero there and the products skip their
- * rows) and the iteration continues on the others; info.relres is then the
- * residual of the beams still running relative to their smallest ||b_b||
- * (0 once all have converged).  The paper treats one problem at a time; the
+ * beam stops at its own ||r_b|| <= rtol ||b_b||.  With the polynomial
+ * preconditioner (poly_degree > 1) every beam runs its own GMRES(restart) --
+ * own Krylov space, Hessenberg matrix and stopping test -- inside the same
+ * launches, and info.relres is the largest relative residual over the beams.
+ * With Jacobi alone the batch shares one Krylov space and freezes the beams
+ * that have converged at each restart (their residual rows are zeroed and
+ * skipped); info.relres is then 0 once all have converged.  In both cases
+ * info.iters counts the Arnoldi steps of the longest-running beam.  The
+ * paper treats one problem at a time; the
  * batch is this library's.  Errors: APCLOUD_E_INVALID for bad offsets or
  * when 3*max_depth plus the bits of n_beams - 1 exceed 63. */
 #define APCLOUD_MAX_BEAMS 65536

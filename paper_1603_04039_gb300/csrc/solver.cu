@@ -1450,7 +1450,16 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.t = ensure<double>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
         }
-        K.bk = bk;
+        if (bk && K.pdeg > 1) {
+            K.bk = bk;
+        } else if (bm) {
+            // Jacobi alone: restarted GMRES(30) on a single small beam can stall where the
+            // shared space of the whole batch does not, so the batch keeps one Krylov
+            // space and freezes converged beams at restarts
+            K.mask = bm;
+            K.skip = RowSkip{bm->nbo, bm->bdone, nullptr};
+            K.tact = bm->tact;
+        }
         status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) return status;
     } else {
@@ -1469,7 +1478,12 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.t = ensure<float>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
         }
-        K.bk = bk;   // beams frozen by the outer loop have zero residual: their inner spaces stop at once
+        if (bk && K.pdeg > 1) {
+            K.bk = bk;   // beams frozen by the outer loop have zero residual: their inner spaces stop at once
+        } else if (bm) {
+            K.skip = RowSkip{bm->nbo, bm->bdone, nullptr};
+            K.tact = bm->tact;
+        }
         const float *val32 = ptr<float>(which ? c->ell_A32 : c->ell_B32);
         const uint32_t *sw = ptr<uint32_t>(c->slice_w), *sof = ptr<uint32_t>(c->slice_off);
         const int32_t *col = ptr<int32_t>(c->ell_col);

@@ -46,9 +46,12 @@ def _split(ap):
     return out
 
 
-@pytest.mark.parametrize("nb,depth,c,seed", [(5, 6, 0.3, 1), (9, 5, 0.5, 2), (3, 7, 0.15, 3)])
-def test_batch_matches_oracle_per_beam(nb, depth, c, seed):
-    ap, (x, y, z, q, offs, params) = _batch(nb, depth, c, 2000, 30000, seed)
+@pytest.mark.parametrize("nb,depth,c,seed,pdeg", [(5, 6, 0.3, 1, 1), (9, 5, 0.5, 2, 1), (3, 7, 0.15, 3, 1),
+                                                  (5, 6, 0.3, 1, 8), (9, 5, 0.5, 2, 8)])
+def test_batch_matches_oracle_per_beam(nb, depth, c, seed, pdeg):
+    """pdeg 1: one shared Krylov space with converged beams frozen at restarts;
+    pdeg 8: an independent Krylov space per beam (FP64 polynomial form)."""
+    ap, (x, y, z, q, offs, params) = _batch(nb, depth, c, 2000, 30000, seed, poly_degree=pdeg, poly_omega=1.0)
     ap.stencils()
     rho, ir = ap.deposit(q=_t(q), rtol=1e-13)
     phi, ip = ap.solve(rtol=1e-13)
