@@ -290,8 +290,8 @@ def run_ours(args, ws, rank, local):
     tfs = fl_k / (ms_k * 1e-3) / 1e12 if ms_k > 0 else 0.0
     # the kernel's arithmetic type sets its ALU peak: in the mixed form the Krylov
     # iterations and the stencil factorisations run in FP32, everything else FP64
-    fp32_kinds = {"spmv", "gmres_dots", "gmres_update_dots", "gmres_update_norm", "gmres_cycle_end",
-                  "ring_select_wls"}
+    fp32_kinds = {"spmv", "precond_sweep", "gmres_dots", "gmres_update_dots", "gmres_update_norm",
+                  "gmres_cycle_end", "ring_select_wls"}
     alu_peak = fp32_peak if (args.precision == "mixed" and dominant in fp32_kinds) else fp64_peak
     alu_name = "FP32" if alu_peak == fp32_peak else "FP64"
     # work per byte decides the bound: above ALU peak / HBM peak the ALU limits

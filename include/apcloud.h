@@ -390,7 +390,7 @@ apcloud_status apcloud_solve_learned(apcloud_ctx *ctx, apcloud_mpnn *net, unsign
  * count, and the algorithmic bytes and floating-point operations of those
  * launches (what the kernel must move and compute, not what it did), since
  * the last reset (reset = 1 clears). */
-#define APCLOUD_NUM_KINDS 18
+#define APCLOUD_NUM_KINDS 19
 apcloud_status apcloud_set_timing(apcloud_ctx *ctx, unsigned mask);
 apcloud_status apcloud_get_timing(apcloud_ctx *ctx, double *h_ms, int64_t *h_launches, double *h_bytes,
                                   double *h_flops, int reset);

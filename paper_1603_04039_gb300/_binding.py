@@ -18,7 +18,7 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libapcloud.so")
 
-NUM_KINDS = 18
+NUM_KINDS = 19
 MMAX = 32
 NCOL = 9
 

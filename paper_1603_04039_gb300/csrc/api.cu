@@ -669,7 +669,7 @@ const char *apcloud_kernel_name(int kind) {
     static const char *names[NKIND] = {"morton_keys", "radix_sort", "tree", "face_adjacency", "ring_select_wls",
                                        "assemble_ell", "deposit", "spmv", "gmres_dots", "gmres_update_dots",
                                        "gmres_update_norm", "gmres_cycle_end", "derivatives", "gather",
-                                       "vector", "copy", "mpnn_dense_tc", "mpnn_graph"};
+                                       "vector", "copy", "mpnn_dense_tc", "mpnn_graph", "precond_sweep"};
     return (kind >= 0 && kind < NKIND) ? names[kind] : "unknown";
 }
 

@@ -22,7 +22,7 @@ constexpr int MAX_RESTART = 64;
 // kernel kinds for the event timers (bit k of the timing mask)
 enum Kind {
     K_KEYS = 0, K_SORT, K_TREE, K_ADJ, K_STENCIL, K_ELL, K_DEPOSIT, K_SPMV,
-    K_DOT, K_UPDDOT, K_UPDNORM, K_CYCLE, K_DERIV, K_GATHER, K_VEC, K_COPY, K_MPNN_TC, K_MPNN_GRAPH, NKIND
+    K_DOT, K_UPDDOT, K_UPDNORM, K_CYCLE, K_DERIV, K_GATHER, K_VEC, K_COPY, K_MPNN_TC, K_MPNN_GRAPH, K_SWEEP, NKIND
 };
 static_assert(NKIND == APCLOUD_NUM_KINDS, "kind count");
 

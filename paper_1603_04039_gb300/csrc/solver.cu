@@ -297,24 +297,26 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
 
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
 // autotuner chose (64, 128, 256 or 512 threads).
-#define APC_SPMV_BS(c, n, KERNEL_OF, ...)                                                                   \
+#define APC_ROWS_BS(c, kind, n, KERNEL_OF, ...)                                                                 \
     do {                                                                                                    \
         if ((c)->spmv_unroll == 4) {                                                                        \
             switch ((c)->spmv_bs) {                                                                         \
-            case 64: APC_LAUNCH(c, K_SPMV, div_up(n, 64), 64, 0, KERNEL_OF(64, 4), __VA_ARGS__); break;     \
-            case 128: APC_LAUNCH(c, K_SPMV, div_up(n, 128), 128, 0, KERNEL_OF(128, 4), __VA_ARGS__); break; \
-            case 512: APC_LAUNCH(c, K_SPMV, div_up(n, 512), 512, 0, KERNEL_OF(512, 4), __VA_ARGS__); break; \
-            default: APC_LAUNCH(c, K_SPMV, div_up(n, 256), 256, 0, KERNEL_OF(256, 4), __VA_ARGS__); break;  \
+            case 64: APC_LAUNCH(c, kind, div_up(n, 64), 64, 0, KERNEL_OF(64, 4), __VA_ARGS__); break;     \
+            case 128: APC_LAUNCH(c, kind, div_up(n, 128), 128, 0, KERNEL_OF(128, 4), __VA_ARGS__); break; \
+            case 512: APC_LAUNCH(c, kind, div_up(n, 512), 512, 0, KERNEL_OF(512, 4), __VA_ARGS__); break; \
+            default: APC_LAUNCH(c, kind, div_up(n, 256), 256, 0, KERNEL_OF(256, 4), __VA_ARGS__); break;  \
             }                                                                                               \
         } else {                                                                                            \
             switch ((c)->spmv_bs) {                                                                         \
-            case 64: APC_LAUNCH(c, K_SPMV, div_up(n, 64), 64, 0, KERNEL_OF(64, 1), __VA_ARGS__); break;     \
-            case 128: APC_LAUNCH(c, K_SPMV, div_up(n, 128), 128, 0, KERNEL_OF(128, 1), __VA_ARGS__); break; \
-            case 512: APC_LAUNCH(c, K_SPMV, div_up(n, 512), 512, 0, KERNEL_OF(512, 1), __VA_ARGS__); break; \
-            default: APC_LAUNCH(c, K_SPMV, div_up(n, 256), 256, 0, KERNEL_OF(256, 1), __VA_ARGS__); break;  \
+            case 64: APC_LAUNCH(c, kind, div_up(n, 64), 64, 0, KERNEL_OF(64, 1), __VA_ARGS__); break;     \
+            case 128: APC_LAUNCH(c, kind, div_up(n, 128), 128, 0, KERNEL_OF(128, 1), __VA_ARGS__); break; \
+            case 512: APC_LAUNCH(c, kind, div_up(n, 512), 512, 0, KERNEL_OF(512, 1), __VA_ARGS__); break; \
+            default: APC_LAUNCH(c, kind, div_up(n, 256), 256, 0, KERNEL_OF(256, 1), __VA_ARGS__); break;  \
             }                                                                                               \
         }                                                                                                   \
     } while (0)
+#define APC_SPMV_BS(c, n, KERNEL_OF, ...) APC_ROWS_BS(c, K_SPMV, n, KERNEL_OF, __VA_ARGS__)
+#define APC_SWEEP_BS(c, n, KERNEL_OF, ...) APC_ROWS_BS(c, K_SWEEP, n, KERNEL_OF, __VA_ARGS__)
 #define APC_SPMV1(B, U) (k_spmv<1, T, B, U>)
 #define APC_SPMV3(B, U) (k_spmv<3, T, B, U>)
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
@@ -1068,14 +1070,14 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     for (int i = 1; i < K.pdeg; ++i) {
         if constexpr (sizeof(T) == 4) {
             if (K.hval) {
-                APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
+                APC_SWEEP_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
                            (float *)nxt, (const float *)v, (const GmresState *)st, skip);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
         }
-        APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, val, n, (const T *)cur, nxt, (T *)nullptr, v, st,
-                    (double *)nullptr, skip);
+        APC_SWEEP_BS(c, n, APC_SPMV3, sw, so, col, val, n, (const T *)cur, nxt, (T *)nullptr, v, st,
+                     (double *)nullptr, skip);
         T *tmp = cur; cur = nxt; nxt = tmp;
     }
     return cur;
@@ -1294,8 +1296,8 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             const double sweeps = (K.pdeg <= 1) ? 0.0 : (double)(K.pdeg - 1) * (je + 1);
             const double prods = je + 1.0;
             const double sb = K.hval ? 2.0 : vb;
-            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods + ((sb + 4.0) * nnz + 3.0 * vb * dn) * sweeps,
-                    2.0 * nnz * (prods + sweeps));
+            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
+            account(c, K_SWEEP, ((sb + 4.0) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
         }
         for (int j = 0; j < je; ++j) {
             account(c, K_DOT, vb * dn * (j + 2), 2.0 * dn * (j + 1));
