@@ -97,6 +97,7 @@ struct apcloud_ctx {
     // launch shapes chosen by apcloud_autotune
     int spmv_bs = 256;     // threads per block of the Arnoldi products and sweeps
     int spmv_unroll = 1;   // stencil entries whose loads a thread issues ahead (1 or 4)
+    int jprev[2][2] = {{0, 0}, {0, 0}};   // Arnoldi steps of the last cycle, per system (B, A) and FP64/FP32
     int wls_warps = 4;     // nodes (warps) per block of the stencil build
     // CUDA graphs of GMRES restart cycles (captured on cap_stream, replayed on s)
     bool graphs_on = true;

@@ -16,6 +16,7 @@
 // restart cycle.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -1050,6 +1051,7 @@ struct Krylov {
     const __half *hval = nullptr;   // FP16 copy of the matrix for the sweeps (FP32 vectors only)
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
     bool graphs = true;             // replay full restart cycles as CUDA graphs
+    int *jhint = nullptr;           // Arnoldi steps the last cycle of this system used (cycle cap)
     RowSkip skip{nullptr, nullptr};         // batches: rows of converged beams
     const uint8_t *tact = nullptr;          // batches: tiles holding a row of an unconverged beam
     const BeamMask *mask = nullptr;         // batches: per-beam convergence at every restart
@@ -1282,10 +1284,16 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         relres = tail.bnorm > 0.0 ? tail.beta / tail.bnorm : 0.0;
         if (tail.bnorm == 0.0 || tail.beta <= rtol * tail.bnorm) { status = APCLOUD_OK; break; }
         if (iters >= max_iter) break;
-        const int jmax = (m < max_iter - iters) ? m : (max_iter - iters);
+        // A cycle ends at the stopping test or after m steps; its launches are
+        // fixed in advance (graph), so steps past the test are empty launches.
+        // Systems that converge in a few steps per cycle (the density system)
+        // get a cycle of at most 2 j + 2 steps after one that needed j.
+        int cap = m;
+        if (K.jhint && *K.jhint > 0) cap = std::min(m, std::max(4, 2 * *K.jhint + 2));
+        const int jmax = (cap < max_iter - iters) ? cap : (max_iter - iters);
         // one restart cycle and the next restart's residual: a CUDA graph replay
         // when the cycle is a full one, otherwise direct launches
-        APC_TRY(run_cycle<T>(c, val, b, u, K, jmax, jmax == m && K.graphs));
+        APC_TRY(run_cycle<T>(c, val, b, u, K, jmax, jmax == cap && K.graphs));
         APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
         harvest_graph_timing(c);
         const int je = tail.jlast;
@@ -1306,6 +1314,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         }
         account(c, K_CYCLE, vb * dn * (je + 2), 2.0 * dn * je);
         iters += je;
+        if (K.jhint) *K.jhint = je;
         ++cycles;
         if (je == 0) {
             relres = tail.bnorm > 0.0 ? tail.beta / tail.bnorm : 0.0;
@@ -1437,6 +1446,8 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         bk = &bkv;
     }
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mul, u, (const double *)x, d, n);
+    // cycle caps learn within this solve only: a solve does not depend on earlier ones
+    c->jprev[which][0] = c->jprev[which][1] = 0;
     int iters = 0, cycles = 0;
     double relres = 0.0;
     apcloud_status status;
@@ -1462,6 +1473,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.skip = RowSkip{bm->nbo, bm->bdone, nullptr};
             K.tact = bm->tact;
         }
+        K.jhint = &c->jprev[which][0];
         status = gmres_core<double>(c, val, b, u, rtol, max_iter, K, &iters, &cycles, &relres);
         if (status < 0) return status;
     } else {
@@ -1486,6 +1498,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.skip = RowSkip{bm->nbo, bm->bdone, nullptr};
             K.tact = bm->tact;
         }
+        K.jhint = &c->jprev[which][1];
         const float *val32 = ptr<float>(which ? c->ell_A32 : c->ell_B32);
         const uint32_t *sw = ptr<uint32_t>(c->slice_w), *sof = ptr<uint32_t>(c->slice_off);
         const int32_t *col = ptr<int32_t>(c->ell_col);
