@@ -63,6 +63,27 @@ def _dist():
     return ws, rank, local
 
 
+def _ncu_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary
+    (a line 'traffic: kernel=... workload=... bytes_per_launch=...'), else None."""
+    d = os.path.join(ROOT, "profiles")
+    try:
+        names = sorted(os.listdir(d))
+    except OSError:
+        return None
+    for fn in names:
+        if not fn.endswith(".md"):
+            continue
+        for line in open(os.path.join(d, fn)):
+            if not line.startswith("traffic:"):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("kernel") == kernel and kv.get("workload") == workload:
+                return {"file": "profiles/" + fn, "bytes_per_launch": float(kv["bytes_per_launch"]),
+                        "algorithmic_bytes_per_working_launch": float(kv["algorithmic_bytes_per_working_launch"])}
+    return None
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -322,6 +343,13 @@ def run_ours(args, ws, rank, local):
                  "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64/FP32 FMA chains on all SMs "
                                 "(apcloud_measure_fma_peak) in this run",
                  "fp64_peak_tflops": round(fp64_peak, 4), "fp32_peak_tflops": round(fp32_peak, 3)})
+    tr = _ncu_traffic(dominant, args.workload)
+    if tr:
+        roof["traffic"] = tr["bytes_per_launch"]
+        roof["traffic_note"] = ("DRAM read + write of one working launch from an ncu capture (%s); "
+                                "algorithmic bytes of a working launch %.4g; the per-launch average above also "
+                                "counts launches that exit at once after convergence" %
+                                (tr["file"], tr["algorithmic_bytes_per_working_launch"]))
     solves = ws * nsolve * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(solves, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
