@@ -288,22 +288,27 @@ apcloud_status apcloud_set_graphs(apcloud_ctx *ctx, int enable);
  * times the preconditioner sweep (or the Arnoldi product under Jacobi) of the
  * configured precision at 64, 128, 256 and 512 threads per block, each with
  * the loads of 1 or 4 stencil entries issued ahead of their multiply-adds
- * (the sum keeps its order either way); bit 1 times the stencil build
- * (neighbour search + WLS) at 2, 4 and 8 nodes (warps) per block on the
- * current node set.  The fastest shapes are kept for later calls and written
- * to *h_spmv_block, *h_spmv_unroll and *h_wls_warps (any may be NULL); h_ms
- * (NULL or 11 doubles) receives the measured milliseconds: eight sweeps
- * (block sizes with unroll 1, then with unroll 4), then three stencil builds.
+ * (the sum keeps its order either way), and -- for the FP16 sweeps of the
+ * mixed form -- on the sliced ELL and on its width-sorted copy (rows ordered
+ * by stencil width inside 256-row windows, so 32-row slices carry little
+ * padding; same entries in the same order per row); bit 1 times the stencil
+ * build (neighbour search + WLS) at 2, 4 and 8 nodes (warps) per block on
+ * the current node set.  The fastest shapes are kept for later calls and
+ * written to *h_spmv_block, *h_spmv_unroll, *h_sweep_sorted and *h_wls_warps
+ * (any may be NULL); h_ms (NULL or 19 doubles) receives the measured
+ * milliseconds: 16 sweep variants (index = block-size index + 4 * unroll-4 +
+ * 8 * sorted; variants not timed stay 0), then three stencil builds.
  * Results never depend on the shapes.  Runs the timed kernels on the context
  * stream and synchronises.  The paper has no counterpart (launch
  * mechanics). */
 apcloud_status apcloud_autotune(apcloud_ctx *ctx, unsigned what, int *h_spmv_block, int *h_spmv_unroll,
-                                int *h_wls_warps, double *h_ms);
+                                int *h_sweep_sorted, int *h_wls_warps, double *h_ms);
 
 /* Sets the launch shapes directly: spmv_block in {64, 128, 256, 512},
- * spmv_unroll in {1, 4}, wls_warps in {2, 4, 8}; APCLOUD_E_INVALID
- * otherwise. */
-apcloud_status apcloud_set_launch_shape(apcloud_ctx *ctx, int spmv_block, int spmv_unroll, int wls_warps);
+ * spmv_unroll in {1, 4}, sweep_sorted in {0, 1}, wls_warps in {2, 4, 8};
+ * APCLOUD_E_INVALID otherwise. */
+apcloud_status apcloud_set_launch_shape(apcloud_ctx *ctx, int spmv_block, int spmv_unroll, int sweep_sorted,
+                                        int wls_warps);
 
 /* Graph replays since the context was created and graphs currently cached. */
 apcloud_status apcloud_graph_stats(const apcloud_ctx *ctx, int64_t *h_replays, int64_t *h_cached);

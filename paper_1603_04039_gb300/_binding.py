@@ -86,8 +86,8 @@ def load():
                                                C.POINTER(SolveInfo), C.POINTER(SolveInfo)]),
             "apcloud_set_timing": (I, [P, C.c_uint]),
             "apcloud_set_graphs": (I, [P, I]),
-            "apcloud_autotune": (I, [P, C.c_uint, C.POINTER(I), C.POINTER(I), C.POINTER(I), P]),
-            "apcloud_set_launch_shape": (I, [P, I, I, I]),
+            "apcloud_autotune": (I, [P, C.c_uint, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), P]),
+            "apcloud_set_launch_shape": (I, [P, I, I, I, I]),
             "apcloud_graph_stats": (I, [P, C.POINTER(L), C.POINTER(L)]),
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
@@ -398,20 +398,21 @@ class APCloud:
 
     def autotune(self, spmv=True, stencils=True):
         """Times the launch shapes and keeps the fastest; returns the choice and timings (ms)."""
-        bs, un, ww = C.c_int(), C.c_int(), C.c_int()
-        ms = np.zeros(11)
+        bs, un, so, ww = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        ms = np.zeros(19)
         what = (1 if spmv else 0) | (2 if stencils else 0)
         with torch.cuda.device(self.device):
-            self._check(self._lib.apcloud_autotune(self._ctx, what, C.byref(bs), C.byref(un), C.byref(ww),
-                                                   ms.ctypes.data_as(C.c_void_p)))
-        keys = ["%d/u%d" % (b, u) for u in (1, 4) for b in (64, 128, 256, 512)]
-        return {"spmv_block": bs.value, "spmv_unroll": un.value, "wls_warps": ww.value,
-                "spmv_ms": dict(zip(keys, ms[:8].round(4).tolist())) if spmv else None,
-                "wls_ms": dict(zip((2, 4, 8), ms[8:].round(3).tolist())) if stencils else None}
+            self._check(self._lib.apcloud_autotune(self._ctx, what, C.byref(bs), C.byref(un), C.byref(so),
+                                                   C.byref(ww), ms.ctypes.data_as(C.c_void_p)))
+        keys = ["%s%d/u%d" % (lay, b, u) for lay in ("ell", "sorted") for u in (1, 4) for b in (64, 128, 256, 512)]
+        sp = {k: v for k, v in zip(keys, ms[:16].round(4).tolist()) if v > 0}
+        return {"spmv_block": bs.value, "spmv_unroll": un.value, "sweep_sorted": so.value, "wls_warps": ww.value,
+                "spmv_ms": sp if spmv else None,
+                "wls_ms": dict(zip((2, 4, 8), ms[16:].round(3).tolist())) if stencils else None}
 
-    def set_launch_shape(self, spmv_block=256, wls_warps=4, spmv_unroll=1):
+    def set_launch_shape(self, spmv_block=256, wls_warps=4, spmv_unroll=1, sweep_sorted=0):
         self._check(self._lib.apcloud_set_launch_shape(self._ctx, int(spmv_block), int(spmv_unroll),
-                                                       int(wls_warps)))
+                                                       int(sweep_sorted), int(wls_warps)))
 
     def solve_learned(self, net, use=3, rtol=1e-10, max_iter=100000, phi0=None):
         """Poisson solve with the network's column scaling (use bit 0), guess (bit 1)

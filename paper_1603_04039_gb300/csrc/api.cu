@@ -319,7 +319,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
                     &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
                     &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act,
-                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i};
+                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col,
+                    &c->ss_A, &c->ss_B};
     for (DBuf *b : bufs) free_buf(c, *b);
     for (DBuf &b : c->mp) free_buf(c, b);
     cudaStreamSynchronize(c->s);
@@ -675,27 +676,33 @@ const char *apcloud_kernel_name(int kind) {
 
 int64_t apcloud_launch_count(const apcloud_ctx *c) { return c ? c->launches : 0; }
 
-apcloud_status apcloud_autotune(apcloud_ctx *c, unsigned what, int *spmv_block, int *spmv_unroll, int *wls_warps,
-                                double *ms) {
+apcloud_status apcloud_autotune(apcloud_ctx *c, unsigned what, int *spmv_block, int *spmv_unroll,
+                                int *sweep_sorted, int *wls_warps, double *ms) {
     if (!c) return APCLOUD_E_INVALID;
     if (c->stage < 2) return fail(c, APCLOUD_E_STATE, "apcloud_autotune needs apcloud_stencils first");
+    if (ms)
+        for (int i = 0; i < 19; ++i) ms[i] = 0.0;
     if (what & 1u) APC_TRY(tune_spmv(c, ms));
-    if (what & 2u) APC_TRY(tune_stencils(c, ms ? ms + 8 : nullptr));
+    if (what & 2u) APC_TRY(tune_stencils(c, ms ? ms + 16 : nullptr));
     if (spmv_block) *spmv_block = c->spmv_bs;
     if (spmv_unroll) *spmv_unroll = c->spmv_unroll;
+    if (sweep_sorted) *sweep_sorted = c->sweep_sorted;
     if (wls_warps) *wls_warps = c->wls_warps;
     return APCLOUD_OK;
 }
 
-apcloud_status apcloud_set_launch_shape(apcloud_ctx *c, int spmv_block, int spmv_unroll, int wls_warps) {
+apcloud_status apcloud_set_launch_shape(apcloud_ctx *c, int spmv_block, int spmv_unroll, int sweep_sorted,
+                                        int wls_warps) {
     if (!c) return APCLOUD_E_INVALID;
     if (spmv_block != 64 && spmv_block != 128 && spmv_block != 256 && spmv_block != 512)
         return fail(c, APCLOUD_E_INVALID, "spmv_block must be 64, 128, 256 or 512");
     if (spmv_unroll != 1 && spmv_unroll != 4) return fail(c, APCLOUD_E_INVALID, "spmv_unroll must be 1 or 4");
+    if (sweep_sorted != 0 && sweep_sorted != 1) return fail(c, APCLOUD_E_INVALID, "sweep_sorted must be 0 or 1");
     if (wls_warps != 2 && wls_warps != 4 && wls_warps != 8)
         return fail(c, APCLOUD_E_INVALID, "wls_warps must be 2, 4 or 8");
     c->spmv_bs = spmv_block;
     c->spmv_unroll = spmv_unroll;
+    c->sweep_sorted = sweep_sorted;
     c->wls_warps = wls_warps;
     return APCLOUD_OK;
 }

@@ -97,6 +97,7 @@ struct apcloud_ctx {
     // launch shapes chosen by apcloud_autotune
     int spmv_bs = 256;     // threads per block of the Arnoldi products and sweeps
     int spmv_unroll = 1;   // stencil entries whose loads a thread issues ahead (1 or 4)
+    int sweep_sorted = 0;  // 1: FP16 sweeps on the width-sorted matrix (autotuner's choice)
     int jprev[2][2] = {{0, 0}, {0, 0}};   // Arnoldi steps of the last cycle, per system (B, A) and FP64/FP32
     int wls_warps = 4;     // nodes (warps) per block of the stencil build
     // CUDA graphs of GMRES restart cycles (captured on cap_stream, replayed on s)
@@ -141,6 +142,11 @@ struct apcloud_ctx {
     apc::DBuf slice_w, slice_off, ell_col, ell_A, ell_B, dA, dB;
     apc::DBuf ell_A32, ell_B32;  // FP32 copies for the inner iterations of the mixed form
     apc::DBuf ell_A16, ell_B16;  // FP16 copies for the preconditioner sweeps of the mixed form
+    // width-sorted copy of the FP16 sweep matrix: rows ordered by stencil width
+    // inside windows of 256 rows, so 32-row slices pad little (see build_sorted_sweep)
+    apc::DBuf ss_perm, ss_w, ss_o, ss_col, ss_A, ss_B;
+    bool ss_ok = false;
+    int64_t ss_entries = 0;
     // solver
     apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
@@ -193,6 +199,7 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
                             const int64_t *h_offsets, int nbeams);
 apcloud_status node_beams(apcloud_ctx *c, int32_t *out);
 apcloud_status refresh_lowp(apcloud_ctx *c);          // FP32/FP16 matrix copies from the FP64 values
+apcloud_status build_sorted_sweep(apcloud_ctx *c);    // width-sorted FP16 sweep matrix from the ELL
 double *poisson_rhs(apcloud_ctx *c, const double *g);  // b of the Poisson system into c->b
 apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out);      // ms per sweep at 64/128/256/512 threads
 apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out);  // ms per build at 2/4/8 warps

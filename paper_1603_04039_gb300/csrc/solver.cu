@@ -296,6 +296,33 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
     y[r] = fmaf(om, b[r] - acc, x[r]);
 }
 
+// The same sweep on the width-sorted copy: thread = slot of a 32-slot slice,
+// its row from the window's permutation (entries in the same order, so the
+// same bits as k_sweep_h).
+template <int BS, int U = 1>
+__global__ void __launch_bounds__(BS) k_sweep_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
+                                                const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
+                                                const __half *__restrict__ val, int64_t nslot,
+                                                const float *__restrict__ x, float *__restrict__ y,
+                                                const float *__restrict__ b, const GmresState *__restrict__ st,
+                                                RowSkip skip) {
+    if (st->done) return;
+    const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (sl_ >= nslot) return;
+    const int r = perm[sl_];
+    if (r < 0) return;
+    if (skip.nbo && skip.bdone[skip.nbo[r]]) {
+        y[r] = 0.f;
+        return;
+    }
+    const float om = (float)st->omega;
+    const int sl = (int)(sl_ >> 5), lane = (int)(sl_ & 31);
+    const int w = (int)sw[sl];
+    const int64_t base = (int64_t)soff[sl] * 32 + lane;
+    const float acc = row_dot_h<U>(val, col, x, base, w);
+    y[r] = fmaf(om, b[r] - acc, x[r]);
+}
+
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
 // autotuner chose (64, 128, 256 or 512 threads).
 #define APC_ROWS_BS(c, kind, n, KERNEL_OF, ...)                                                                 \
@@ -322,6 +349,7 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
 #define APC_SPMV3(B, U) (k_spmv<3, T, B, U>)
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
+#define APC_SWEEPS(B, U) (k_sweep_s<B, U>)
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
 // Every arithmetic instruction does useful work on 32 lanes (GB300 runs FP64
@@ -1049,6 +1077,11 @@ struct Krylov {
     int pdeg = 1;                   // degree of the Jacobi-Neumann polynomial (1 = Jacobi)
     double omega = 1.0;
     const __half *hval = nullptr;   // FP16 copy of the matrix for the sweeps (FP32 vectors only)
+    // width-sorted FP16 sweep matrix (null: sweep on the ELL)
+    const int32_t *sperm = nullptr, *scol = nullptr;
+    const uint32_t *ssw = nullptr, *sso = nullptr;
+    const __half *sval = nullptr;
+    int64_t nslot = 0;
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
     bool graphs = true;             // replay full restart cycles as CUDA graphs
     int *jhint = nullptr;           // Arnoldi steps the last cycle of this system used (cycle cap)
@@ -1071,6 +1104,12 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     T *cur = z_first, *nxt = (z_first == K.z0) ? K.z1 : K.z0;
     for (int i = 1; i < K.pdeg; ++i) {
         if constexpr (sizeof(T) == 4) {
+            if (K.hval && K.sperm) {
+                APC_SWEEP_BS(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                             (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip);
+                T *tmp = cur; cur = nxt; nxt = tmp;
+                continue;
+            }
             if (K.hval) {
                 APC_SWEEP_BS(c, n, APC_SWEEPH, sw, so, col, K.hval, n, (const float *)cur,
                            (float *)nxt, (const float *)v, (const GmresState *)st, skip);
@@ -1230,7 +1269,8 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
                            c->slice_w.p, c->slice_off.p, c->ell_col.p, K.skip.nbo, K.skip.bdone, K.tact,
                            K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,
                            K.bk ? K.bk->H : nullptr, K.bk ? K.bk->done : nullptr,
-                           K.bk ? (const void *)(intptr_t)K.bk->nitems : nullptr};
+                           K.bk ? (const void *)(intptr_t)K.bk->nitems : nullptr, K.sperm, K.sval, K.scol, K.ssw,
+                           K.sso};
         static_assert(sizeof p <= sizeof key.p, "graph key holds every buffer address");
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
@@ -1487,6 +1527,14 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.pdeg = c->P.poly_degree;
             K.omega = c->P.poly_omega;
             K.hval = ptr<__half>(which ? c->ell_A16 : c->ell_B16);
+            if (c->ss_ok && c->sweep_sorted) {
+                K.sperm = ptr<int32_t>(c->ss_perm);
+                K.ssw = ptr<uint32_t>(c->ss_w);
+                K.sso = ptr<uint32_t>(c->ss_o);
+                K.scol = ptr<int32_t>(c->ss_col);
+                K.sval = ptr<__half>(which ? c->ss_A : c->ss_B);
+                K.nslot = (int64_t)div_up(c->n_tot, 256) * 256;
+            }
             K.z0 = ensure<float>(c, c->pz0, ldv + 1);
             K.z1 = ensure<float>(c, c->pz1, ldv + 1);
             K.t = ensure<float>(c, c->pt, ldv + 1);
@@ -1562,8 +1610,10 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
     const int sizes[4] = {64, 128, 256, 512}, unrolls[2] = {1, 4};
-    const int saved_u = c->spmv_unroll;
-    int pick_u = saved_u;
+    const int saved_u = c->spmv_unroll, saved_s = c->sweep_sorted;
+    int pick_u = saved_u, pick_s = saved_s;
+    // the width-sorted sweep matrix is a third dimension when it exists
+    const int nvar = (mixed && c->P.poly_degree > 1 && c->ss_ok) ? 16 : 8;
     cudaEvent_t e0, e1;
     APC_CUDA(c, cudaEventCreate(&e0));
     APC_CUDA(c, cudaEventCreate(&e1));
@@ -1573,15 +1623,23 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
     double best = 1e30;
     int pick = saved;
     apcloud_status rc = APCLOUD_OK;
-    for (int tu = 0; tu < 8 && rc == APCLOUD_OK; ++tu) {
+    for (int tu = 0; tu < nvar && rc == APCLOUD_OK; ++tu) {
         const int t = tu & 3;
         c->spmv_bs = sizes[t];
-        c->spmv_unroll = unrolls[tu >> 2];
+        c->spmv_unroll = unrolls[(tu >> 2) & 1];
+        c->sweep_sorted = tu >> 3;
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {   // warm-up pass, then the timed pass
             cudaEventRecord(e0, c->s);
             for (int k = 0; k < 10; ++k) {
-                if (mixed && c->P.poly_degree > 1) {
+                if (mixed && c->P.poly_degree > 1 && c->sweep_sorted) {
+                    const int64_t ns = (int64_t)div_up(n, 256) * 256;
+                    APC_SWEEP_BS(c, ns, APC_SWEEPS, (const int32_t *)ptr<int32_t>(c->ss_perm),
+                                 (const uint32_t *)ptr<uint32_t>(c->ss_w), (const uint32_t *)ptr<uint32_t>(c->ss_o),
+                                 (const int32_t *)ptr<int32_t>(c->ss_col), (const __half *)ptr<__half>(c->ss_A), ns,
+                                 (const float *)x, (float *)y, (const float *)bv, (const GmresState *)st,
+                                 RowSkip{nullptr, nullptr, nullptr});
+                } else if (mixed && c->P.poly_degree > 1) {
                     const __half *hv = ptr<__half>(c->ell_A16);
                     APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, hv, n, (const float *)x, (float *)y,
                                 (const float *)bv, (const GmresState *)st, RowSkip{nullptr, nullptr});
@@ -1610,13 +1668,14 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
         }
         const double per = ms / 10.0;
         if (ms_out) ms_out[tu] = per;
-        if (per < best) { best = per; pick = sizes[t]; pick_u = unrolls[tu >> 2]; }
+        if (per < best) { best = per; pick = sizes[t]; pick_u = unrolls[(tu >> 2) & 1]; pick_s = tu >> 3; }
     }
     c->timer.mask = mask;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->spmv_bs = (rc == APCLOUD_OK) ? pick : saved;
     c->spmv_unroll = (rc == APCLOUD_OK) ? pick_u : saved_u;
+    c->sweep_sorted = (rc == APCLOUD_OK) ? pick_s : saved_s;
     return rc;
 }
 

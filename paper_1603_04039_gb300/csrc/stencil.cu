@@ -610,6 +610,7 @@ apcloud_status build_stencils(apcloud_ctx *c) {
         if (!fA || !fB || !hA || !hB) return APCLOUD_E_NOMEM;
         APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)vA,
                    (const double *)vB, c->ell_entries, fA, fB, hA, hB);
+        APC_TRY(build_sorted_sweep(c));
     }
     return cuda_check(c, cudaGetLastError(), "ell");
 }
@@ -679,7 +680,102 @@ apcloud_status refresh_lowp(apcloud_ctx *c) {
     APC_LAUNCH(c, K_ELL, div_up(c->ell_entries, 256), 256, 0, k_values_f32, (const double *)ptr<double>(c->ell_A),
                (const double *)ptr<double>(c->ell_B), c->ell_entries, ptr<float>(c->ell_A32), ptr<float>(c->ell_B32),
                ptr<__half>(c->ell_A16), ptr<__half>(c->ell_B16));
+    APC_TRY(build_sorted_sweep(c));
     return cuda_check(c, cudaGetLastError(), "refresh_lowp");
+}
+
+namespace {
+
+constexpr int SS_WIN = 256;   // rows per sorting window (8 slices)
+
+// one block per window: rank the window's rows by stored width (descending,
+// ties by row index), perm[slot] = row (-1 past the last row), and the width
+// of each of the window's 8 slices
+__global__ void __launch_bounds__(SS_WIN) k_ss_rank(const int32_t *__restrict__ msz, int n_int, int n_tot,
+                                                  int32_t *__restrict__ perm, uint32_t *__restrict__ w) {
+    __shared__ int wd[SS_WIN];
+    __shared__ int sorted_w[SS_WIN];
+    const int base = blockIdx.x * SS_WIN, t = threadIdx.x, r = base + t;
+    const int my = r < n_int ? msz[r] + 1 : (r < n_tot ? 1 : -1);
+    wd[t] = my;
+    __syncthreads();
+    int rank = 0;
+    for (int k = 0; k < SS_WIN; ++k) {
+        const int o = wd[k];
+        rank += (o > my) || (o == my && k < t);
+    }
+    perm[base + rank] = my >= 0 ? r : -1;
+    sorted_w[rank] = my > 0 ? my : 0;
+    __syncthreads();
+    if ((t & 31) == 0) w[blockIdx.x * (SS_WIN / 32) + (t >> 5)] = (uint32_t)sorted_w[t];   // max of the slice
+}
+
+// copy every row's stored entries (in their order) into its slot of the sorted layout
+__global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+                          const int32_t *__restrict__ col, const __half *__restrict__ hA, const __half *__restrict__ hB,
+                          const int32_t *__restrict__ perm, const uint32_t *__restrict__ w2,
+                          const uint32_t *__restrict__ o2, int64_t nslot, int32_t *__restrict__ col2,
+                          __half *__restrict__ A2, __half *__restrict__ B2) {
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nslot) return;
+    const int sl2 = (int)(s >> 5), lane2 = (int)(s & 31);
+    const int64_t b2 = (int64_t)o2[sl2] * 32 + lane2;
+    const int wid2 = (int)w2[sl2];
+    const int r = perm[s];
+    int k = 0;
+    if (r >= 0) {
+        const int sl = r >> 5, lane = r & 31;
+        const int w = (int)sw[sl];
+        const int64_t base = (int64_t)soff[sl] * 32 + lane;
+        for (; k < wid2 && k < w; ++k) {
+            const int64_t e = base + (int64_t)k * 32, q = b2 + (int64_t)k * 32;
+            col2[q] = col[e];
+            A2[q] = hA[e];
+            B2[q] = hB[e];
+        }
+    }
+    for (; k < wid2; ++k) {   // padding: the row itself (or row 0) with value 0
+        const int64_t q = b2 + (int64_t)k * 32;
+        col2[q] = r >= 0 ? r : 0;
+        A2[q] = __float2half(0.f);
+        B2[q] = __float2half(0.f);
+    }
+}
+
+}  // namespace
+
+// The FP16 preconditioner sweeps stream the whole matrix 15 times per Arnoldi
+// step; in 32-row slices of consecutive rows the slice width is that of its
+// widest stencil and 14% of the stored entries are padding.  This copy orders
+// the rows of every 256-row window by stored width (SELL-C-sigma, C = 32,
+// sigma = 256): slices then hold rows of nearly equal width.  Each row keeps
+// its entries in their stored order, so a sweep on this copy gives the same
+// bits as on the ELL.
+apcloud_status build_sorted_sweep(apcloud_ctx *c) {
+    c->ss_ok = false;
+    const int n = c->n_tot;
+    if (n == 0) return APCLOUD_OK;
+    const int nwin = div_up(n, SS_WIN);
+    const int64_t nslot = (int64_t)nwin * SS_WIN;
+    const int nsl2 = (int)(nslot / 32);
+    int32_t *perm = ensure<int32_t>(c, c->ss_perm, nslot);
+    uint32_t *w2 = ensure<uint32_t>(c, c->ss_w, nsl2 + 1), *o2 = ensure<uint32_t>(c, c->ss_o, nsl2 + 1);
+    if (!perm || !w2 || !o2) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_ELL, nwin, SS_WIN, 0, k_ss_rank, (const int32_t *)ptr<int32_t>(c->msz), c->n_int, n, perm, w2);
+    uint32_t *small = ptr<uint32_t>(c->dsmall);
+    APC_TRY(scan_u32(c, w2, o2, nsl2, small + 13));
+    uint32_t tot;
+    APC_TRY(read_back(c, &tot, small + 13, sizeof tot));
+    c->ss_entries = (int64_t)tot * 32;
+    int32_t *col2 = ensure<int32_t>(c, c->ss_col, c->ss_entries + 1);
+    __half *A2 = ensure<__half>(c, c->ss_A, c->ss_entries + 1), *B2 = ensure<__half>(c, c->ss_B, c->ss_entries + 1);
+    if (!col2 || !A2 || !B2) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_ELL, div_up(nslot, 256), 256, 0, k_ss_fill, (const uint32_t *)ptr<uint32_t>(c->slice_w),
+               (const uint32_t *)ptr<uint32_t>(c->slice_off), (const int32_t *)ptr<int32_t>(c->ell_col),
+               (const __half *)ptr<__half>(c->ell_A16), (const __half *)ptr<__half>(c->ell_B16),
+               (const int32_t *)perm, (const uint32_t *)w2, (const uint32_t *)o2, nslot, col2, A2, B2);
+    c->ss_ok = true;
+    return cuda_check(c, cudaGetLastError(), "sorted sweep matrix");
 }
 
 }  // namespace apc

@@ -69,9 +69,9 @@ def test_launch_shapes_do_not_change_results(precision):
     from paper_1603_04039_gb300 import APCloud
     x, y, z, q = inputs.beam_with_halo(50000, 23)
     res = []
-    for bs, ww, un in ((256, 4, 1), (64, 2, 4), (512, 8, 1), (128, 4, 4)):
+    for bs, ww, un, so in ((256, 4, 1, 0), (64, 2, 4, 1), (512, 8, 1, 1), (128, 4, 4, 0)):
         ap = APCloud(max_depth=6, c_refine=0.3, precision=precision, poly_degree=8, poly_omega=1.0)
-        ap.set_launch_shape(bs, ww, un)
+        ap.set_launch_shape(bs, ww, un, so)
         ap.build_octree(_t(x), _t(y), _t(z))
         ap.stencils()
         ap.deposit(q_uniform=1.0 / len(x), rtol=1e-11)
@@ -95,10 +95,11 @@ def test_autotune_choices_and_rejects():
     before = ap.get_stencils()["D"].cpu().numpy()
     t = ap.autotune()
     assert t["spmv_block"] in (64, 128, 256, 512) and t["wls_warps"] in (2, 4, 8) and t["spmv_unroll"] in (1, 4)
+    assert t["sweep_sorted"] in (0, 1) and len(t["spmv_ms"]) == 16
     assert all(v > 0 for v in t["spmv_ms"].values()) and all(v > 0 for v in t["wls_ms"].values())
     assert np.array_equal(ap.get_stencils()["D"].cpu().numpy(), before)
     _, info = ap.deposit(q_uniform=1.0 / len(x), rtol=1e-10)
     assert info["status"] == 0
-    for bad in ((100, 4, 1), (256, 3, 1), (256, 4, 2)):
+    for bad in ((100, 4, 1, 0), (256, 3, 1, 0), (256, 4, 2, 0), (256, 4, 1, 2)):
         with pytest.raises(APCloudError):
             ap.set_launch_shape(*bad)
