@@ -3,15 +3,17 @@
 // Poisson matrix A of Section 3.2 in sliced ELL.
 //
 // One warp per node.  The warp grows the k-ring (k = 2..ring_max) by BFS over
-// the face adjacency with the candidate set in shared memory, ranks the
-// candidates by (exact integer squared distance, node index), applies the
-// octant criterion, and builds the weighted scaled Vandermonde W V0 with one
-// lane per neighbour (lane j = row j, m <= 32).  The least-squares operator
+// the face adjacency with the candidate set in shared memory, sorts the
+// candidates once by (exact integer squared distance, node index), takes the
+// octant picks, the nearest fill and the ties as prefix counts (ballots) along
+// that order, and builds the weighted scaled Vandermonde W V0 with one lane per
+// neighbour (lane j = row j, m <= 32).  The least-squares operator
 // P = (W V0)^+ W is formed by Cholesky QR applied twice (CholeskyQR2): the
-// 9x9 Gram matrices come from shared memory, Q = A R^-1 is lane-local, and
-// column j of P is R^-1 q_j^T W_j, again lane-local.  This replaces the
-// column-by-column Householder reductions of a CPU QR (9 dependent cross-lane
-// reductions) with two Gram products and lane-private triangular solves.
+// 9x9 Gram matrices come from shared memory and are factored by the whole
+// warp, Q = A R^-1 is lane-local, and column j of P is R^-1 q_j^T W_j, again
+// lane-local.  This replaces the column-by-column Householder reductions of a
+// CPU QR (9 dependent cross-lane reductions) with two Gram products, two
+// 9-step warp factorisations and lane-private triangular solves.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -25,35 +27,24 @@ namespace {
 constexpr double FP32_RATIO_MIN = 1e-3;  // condition estimate limit of the FP32 factorisation
 constexpr int ASTR = NCOL;      // row stride of the staged Vandermonde
 
-struct WarpSmem {
-    int32_t cand[MAXC];
+struct __align__(16) WarpSmem {
+    int32_t cand[MAXC];   // read four at a time by the membership test
     long long d2[MAXC];
+    uint16_t srt[MAXC];   // candidate slots in (d2, index) order
     uint8_t oct[MAXC];
-    uint8_t pick[MAXC];   // octant picks
-    uint8_t fill[MAXC];   // nearest fill up to m_target
-    uint8_t tie[MAXC];    // ties at the cut distance
+    uint8_t pick[MAXC];   // octant picks, by sorted position
     int32_t sel[MMAX];
     long long seld2[MMAX];
     double A[MMAX * ASTR];
     double G[48];
     double R1[NCOL * NCOL];
     double R2[NCOL * NCOL];
-    int flag;
-    int cut_set;
-    long long cut;
+    double Ri1[NCOL], Ri2[NCOL];   // reciprocal diagonals of R1, R2
 };
 
 
-__constant__ unsigned char c_pa[45], c_pb[45];
-
 __device__ __forceinline__ bool key_less(long long da, int ia, long long db, int ib) {
     return da < db || (da == db && ia < ib);
-}
-
-__device__ __forceinline__ int warp_sum_int(int v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 __device__ __forceinline__ long long warp_max_ll(long long v) {
@@ -71,61 +62,90 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
-// Cholesky of the packed upper Gram matrix G into R (row-major 9x9, upper),
-// run by one lane.  Returns false on a non-positive pivot.
+// Packed upper storage of the symmetric 9x9 Gram matrix: entry (a, b), a <= b,
+// sits at a * 9 - a (a - 1) / 2 + (b - a), 45 entries in all.  Lane l owns
+// entries l and l + 32 (the second only for l < 13).
+__device__ __forceinline__ int pk_idx(int a, int b) { return a * NCOL - a * (a - 1) / 2 + (b - a); }
+
+struct GramOwn {
+    int a1, b1, a2, b2;
+    bool two;
+};
+
+__device__ __forceinline__ void pk_rowcol(int e, int &a, int &b) {
+    int e0 = 0;
+    a = 0;
+    while (e - e0 >= NCOL - a) { e0 += NCOL - a; ++a; }
+    b = a + (e - e0);
+}
+
+__device__ __forceinline__ GramOwn gram_own(int lane) {
+    GramOwn o;
+    o.two = lane + 32 < NCOL * (NCOL + 1) / 2;
+    pk_rowcol(lane, o.a1, o.b1);
+    pk_rowcol(o.two ? lane + 32 : 0, o.a2, o.b2);
+    return o;
+}
+
+// Cholesky G = R^T R of the packed Gram matrix by the whole warp: right-looking,
+// each lane updating the trailing entries it owns after the pivot row k is
+// scaled.  R is row-major upper (the strict lower part is not written), Ri the
+// reciprocals of its diagonal.  G is overwritten.  Returns false on a
+// non-positive pivot, the same decision in every lane.
 template <class T>
-__device__ bool cholesky9(const T *G, T *R) {
-    for (int i = 0; i < NCOL; ++i) {
-        for (int j = i; j < NCOL; ++j) {
-            int a = i, b = j;
-            int e = a * NCOL - a * (a - 1) / 2 + (b - a);  // packed upper index
-            T s = G[e];
-            for (int k = 0; k < i; ++k) s -= R[k * NCOL + i] * R[k * NCOL + j];
-            if (j == i) {
-                if (!(s > (T)0)) return false;
-                R[i * NCOL + i] = sqrt(s);
-            } else {
-                R[i * NCOL + j] = s / R[i * NCOL + i];
-            }
+__device__ bool cholesky_warp(T *G, T *R, T *Ri, const GramOwn &o, int lane) {
+    for (int k = 0; k < NCOL; ++k) {
+        const T gkk = G[pk_idx(k, k)];
+        if (!(gkk > (T)0)) return false;
+        const T d = sqrt(gkk), rd = (T)1 / d;
+        if (o.a1 == k) R[k * NCOL + o.b1] = (o.b1 == k) ? d : G[lane] * rd;
+        else if (o.a1 > k) G[lane] -= (G[pk_idx(k, o.a1)] * rd) * (G[pk_idx(k, o.b1)] * rd);
+        if (o.two) {
+            if (o.a2 == k) R[k * NCOL + o.b2] = (o.b2 == k) ? d : G[lane + 32] * rd;
+            else if (o.a2 > k) G[lane + 32] -= (G[pk_idx(k, o.a2)] * rd) * (G[pk_idx(k, o.b2)] * rd);
         }
-        for (int j = 0; j < i; ++j) R[i * NCOL + j] = (T)0;
+        if (lane == 0) Ri[k] = rd;
+        __syncwarp();
     }
     return true;
 }
 
 // solve q R = a for the row vector q (R upper), in place on v
 template <class T>
-__device__ __forceinline__ void row_solve_upper(const T *R, T *v) {
+__device__ __forceinline__ void row_solve_upper(const T *R, const T *Ri, T *v) {
 #pragma unroll
     for (int c = 0; c < NCOL; ++c) {
         T s = v[c];
 #pragma unroll
         for (int k = 0; k < c; ++k) s -= v[k] * R[k * NCOL + c];
-        v[c] = s / R[c * NCOL + c];
+        v[c] = s * Ri[c];
     }
 }
 
 // solve R z = v for the column vector z (R upper), in place
 template <class T>
-__device__ __forceinline__ void col_solve_upper(const T *R, T *v) {
+__device__ __forceinline__ void col_solve_upper(const T *R, const T *Ri, T *v) {
 #pragma unroll
     for (int c = NCOL - 1; c >= 0; --c) {
         T s = v[c];
 #pragma unroll
         for (int k = c + 1; k < NCOL; ++k) s -= R[c * NCOL + k] * v[k];
-        v[c] = s / R[c * NCOL + c];
+        v[c] = s * Ri[c];
     }
 }
 
-// Gram matrix of the staged rows: lane e < 45 owns entry (pa[e], pb[e])
+// Gram matrix of the m staged rows, the lane's two owned entries accumulated
+// side by side
 template <class T>
-__device__ __forceinline__ void gram(const T *A, int m, T *G, int lane) {
-    for (int e = lane; e < 45; e += 32) {
-        int a = c_pa[e], b = c_pb[e];
-        T s = (T)0;
-        for (int j = 0; j < m; ++j) s = fma(A[j * ASTR + a], A[j * ASTR + b], s);
-        G[e] = s;
+__device__ __forceinline__ void gram(const T *A, int m, T *G, const GramOwn &o, int lane) {
+    T s1 = (T)0, s2 = (T)0;
+    for (int j = 0; j < m; ++j) {
+        const T *r = A + j * ASTR;
+        s1 = fma(r[o.a1], r[o.b1], s1);
+        s2 = fma(r[o.a2], r[o.b2], s2);
     }
+    G[lane] = s1;
+    if (o.two) G[lane + 32] = s2;
 }
 
 __device__ __forceinline__ double exp_t(double v) { return exp(v); }
@@ -137,12 +157,15 @@ __device__ __forceinline__ float exp_t(float v) { return expf(v); }
 // P = (W V0)^+ W unscaled by h and h^2, returned in FP64.  Returns false when
 // a Cholesky pivot fails; rratio = min |R_ii| / max |R_ii|.
 template <class T>
-__device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__restrict__ ic, double unit,
-                           double ec, double inv_1mec, double (&qout)[NCOL], double &lapj, double &rratio) {
+__device__ bool wls_column(WarpSmem &W, int m, int lane, const GramOwn &own, int4 c0, const int4 *__restrict__ ic,
+                           double unit, double ec, double inv_1mec, double (&qout)[NCOL], double &lapj,
+                           double &rratio) {
     T *A = reinterpret_cast<T *>(W.A);
     T *G = reinterpret_cast<T *>(W.G);
     T *R1 = reinterpret_cast<T *>(W.R1);
     T *R2 = reinterpret_cast<T *>(W.R2);
+    T *Ri1 = reinterpret_cast<T *>(W.Ri1);
+    T *Ri2 = reinterpret_cast<T *>(W.Ri2);
     long long off[3] = {0, 0, 0};
     long long mydist = 0, amax = 0;
     if (lane < m) {
@@ -178,26 +201,22 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__
         for (int e = 0; e < NCOL; ++e) A[lane * ASTR + e] = row[e];
     }
     __syncwarp();
-    gram<T>(A, m, G, lane);
+    gram<T>(A, m, G, own, lane);
     __syncwarp();
-    if (lane == 0) W.flag = cholesky9<T>(G, R1) ? 1 : 0;
-    __syncwarp();
-    bool ok = W.flag != 0;
+    bool ok = cholesky_warp<T>(G, R1, Ri1, own, lane);
     T q[NCOL];
     if (ok) {
         if (lane < m) {
 #pragma unroll
             for (int e = 0; e < NCOL; ++e) q[e] = A[lane * ASTR + e];
-            row_solve_upper<T>(R1, q);
+            row_solve_upper<T>(R1, Ri1, q);
 #pragma unroll
             for (int e = 0; e < NCOL; ++e) A[lane * ASTR + e] = q[e];
         }
         __syncwarp();
-        gram<T>(A, m, G, lane);
+        gram<T>(A, m, G, own, lane);
         __syncwarp();
-        if (lane == 0) W.flag = cholesky9<T>(G, R2) ? 1 : 0;
-        __syncwarp();
-        ok = W.flag != 0;
+        ok = cholesky_warp<T>(G, R2, Ri2, own, lane);
     }
     rratio = 0.0;
     lapj = 0.0;
@@ -216,9 +235,9 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, int4 c0, const int4 *__
     if (lane < m) {
 #pragma unroll
         for (int e = 0; e < NCOL; ++e) q[e] = A[lane * ASTR + e];
-        row_solve_upper<T>(R2, q);
-        col_solve_upper<T>(R2, q);
-        col_solve_upper<T>(R1, q);
+        row_solve_upper<T>(R2, Ri2, q);
+        col_solve_upper<T>(R2, Ri2, q);
+        col_solve_upper<T>(R1, Ri1, q);
         T lj = (T)0;
 #pragma unroll
         for (int e = 0; e < NCOL; ++e) {
@@ -259,33 +278,51 @@ __global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stenci
     int m = 0, ring = 0;
     double rmin_over_rmax = 0.0;
 
+    const GramOwn own = gram_own(lane);
+
     for (int k = 1; k <= ring_max && !done; ++k) {
         // ---- grow the ring by one layer (Section 4.3: (k+1)-ring = k-ring
-        // plus the face neighbours of its nodes)
+        // plus the face neighbours of its nodes).  The frontier [head, tail)
+        // does not change while the layer grows, so the adjacency of up to
+        // eight 32-slot batches is loaded before any of them is merged.
         const int nslots = (tail - head) * 24;
-        for (int base = 0; base < nslots; base += 32) {
-            int s = base + lane;
-            int v = -1;
-            if (s < nslots) {
-                int u = W.cand[head + s / 24];
-                int slot = s % 24;
-                if (u < n_int) v = adj[(int64_t)u * 24 + slot];
-                else if (slot == 0) v = bowner[u - n_int];
+        for (int g0 = 0; g0 < nslots; g0 += 8 * 32) {
+            int vb[8];
+#pragma unroll
+            for (int bt = 0; bt < 8; ++bt) {
+                const int s = g0 + bt * 32 + lane;
+                int v = -1;
+                if (s < nslots) {
+                    const int u = W.cand[head + s / 24];
+                    const int slot = s % 24;
+                    if (u < n_int) v = adj[(int64_t)u * 24 + slot];
+                    else if (slot == 0) v = bowner[u - n_int];
+                }
+                vb[bt] = v;
             }
-            bool fresh = v >= 0;
-            for (int t = 0; fresh && t < nc; ++t)
-                if (W.cand[t] == v) fresh = false;
-            unsigned peers = __match_any_sync(FULL, fresh ? v : -2 - lane);
-            if (fresh && lane != __ffs(peers) - 1) fresh = false;
-            unsigned bal = __ballot_sync(FULL, fresh);
-            int p = nc + __popc(bal & lt);
-            if (fresh) {
-                if (p < MAXC) W.cand[p] = v;
-                else overflow = true;
+#pragma unroll
+            for (int bt = 0; bt < 8; ++bt) {
+                if (g0 + bt * 32 >= nslots) break;
+                const int v = vb[bt];
+                bool fresh = v >= 0;
+                for (int t = 0; fresh && t < nc; t += 4) {
+                    const int4 c4 = *reinterpret_cast<const int4 *>(&W.cand[t]);
+                    if (c4.x == v || (c4.y == v && t + 1 < nc) || (c4.z == v && t + 2 < nc) ||
+                        (c4.w == v && t + 3 < nc))
+                        fresh = false;
+                }
+                unsigned peers = __match_any_sync(FULL, fresh ? v : -2 - lane);
+                if (fresh && lane != __ffs(peers) - 1) fresh = false;
+                unsigned bal = __ballot_sync(FULL, fresh);
+                int p = nc + __popc(bal & lt);
+                if (fresh) {
+                    if (p < MAXC) W.cand[p] = v;
+                    else overflow = true;
+                }
+                nc += __popc(bal);
+                if (nc > MAXC) nc = MAXC;
+                __syncwarp();
             }
-            nc += __popc(bal);
-            if (nc > MAXC) nc = MAXC;
-            __syncwarp();
         }
         if (__any_sync(FULL, overflow)) break;
         head = tail;
@@ -295,7 +332,8 @@ __global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stenci
         if (ncand < m_target && k < ring_max) continue;
         if (ncand < NCOL) continue;
 
-        // ---- rank candidates (Section 3.1 quadrant criterion, octants in 3-D)
+        // ---- order the candidates by (exact integer squared distance, node
+        // index): every later choice is a prefix of this order
         for (int t = 1 + lane; t < nc; t += 32) {
             int4 q = ic[W.cand[t]];
             long long dx = (long long)q.x - c0.x, dy = (long long)q.y - c0.y, dz = (long long)q.z - c0.z;
@@ -303,67 +341,83 @@ __global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stenci
             W.oct[t] = (uint8_t)(((dx >= 0) << 2) | ((dy >= 0) << 1) | (dz >= 0));
         }
         __syncwarp();
-        int nA = 0;
         for (int t = 1 + lane; t < nc; t += 32) {
-            long long dt = W.d2[t];
-            int it = W.cand[t], ot = W.oct[t], r = 0;
-            for (int u = 1; u < nc; ++u)
-                if (W.oct[u] == ot && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
-            W.pick[t] = (r < 2) ? 1 : 0;
-            nA += (r < 2);
+            const long long dt = W.d2[t];
+            const int it = W.cand[t];
+            int r = 0;
+            for (int u = 1; u < nc; ++u) r += key_less(W.d2[u], W.cand[u], dt, it) ? 1 : 0;
+            W.srt[r] = (uint16_t)t;
         }
-        nA = warp_sum_int(nA);
+        __syncwarp();
+        // ---- Section 3.1 quadrant criterion, octants in 3-D: the two nearest
+        // in each octant, counted along the order 32 positions at a time
+        int nA = 0;
+        {
+            int cnt[8];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) cnt[o] = 0;
+            for (int p0 = 0; p0 < ncand; p0 += 32) {
+                const int pos = p0 + lane;
+                const int o = (pos < ncand) ? (int)W.oct[W.srt[pos]] : -1;
+                int before = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const unsigned bq = __ballot_sync(FULL, o == q);
+                    if (o == q) before = cnt[q] + __popc(bq & lt);
+                    cnt[q] += __popc(bq);
+                }
+                const bool pk = o >= 0 && before < 2;
+                if (pos < ncand) W.pick[pos] = pk ? 1 : 0;
+                nA += __popc(__ballot_sync(FULL, pk));
+            }
+        }
         __syncwarp();
         // target sizes m_target, m_target + 2, ... (a rank-deficient stencil or
-        // one whose Laplacian diagonal is not negative is not used)
+        // one whose Laplacian diagonal is not negative is not used).  One pass
+        // along the order: the picks, then the nearest non-picked up to the
+        // target (the last of them sets the cut distance), then every further
+        // candidate tied at the cut while the stencil has room, in index order;
+        // the stencil is written in (d2, index) order.
         for (int mt = m_target; mt <= MMAX && !done; mt += 2) {
         const int need = mt - nA;
-        int nfill = 0;
-        if (lane == 0) W.cut_set = 0;
-        for (int t = 1 + lane; t < nc; t += 32) { W.fill[t] = 0; W.tie[t] = 0; }
-        __syncwarp();
-        if (need > 0) {
-            for (int t = 1 + lane; t < nc; t += 32) {
-                if (W.pick[t]) continue;
-                long long dt = W.d2[t];
-                int it = W.cand[t], r = 0;
-                for (int u = 1; u < nc; ++u)
-                    if (!W.pick[u] && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
-                if (r < need) {
-                    W.fill[t] = 1;
-                    ++nfill;
-                    if (r == need - 1) { W.cut = dt; W.cut_set = 1; }
+        const int room = MMAX - nA - (need > 0 ? need : 0);
+        int nsel = 0, nnp = 0, ntie = 0;
+        bool cut_found = false;
+        long long cut = 0;
+        for (int p0 = 0; p0 < ncand; p0 += 32) {
+            const int pos = p0 + lane;
+            const bool valid = pos < ncand;
+            int t = 0;
+            long long d = 0;
+            bool pk = false;
+            if (valid) { t = W.srt[pos]; d = W.d2[t]; pk = W.pick[pos] != 0; }
+            const bool np = valid && !pk;
+            const unsigned bnp = __ballot_sync(FULL, np);
+            const int npr = nnp + __popc(bnp & lt);
+            const bool fill = np && npr < need;
+            if (!cut_found) {
+                const unsigned bc = __ballot_sync(FULL, np && npr == need - 1);
+                if (bc) {
+                    cut = __shfl_sync(FULL, d, __ffs(bc) - 1);
+                    cut_found = true;
                 }
             }
-            nfill = warp_sum_int(nfill);
-        }
-        __syncwarp();
-        int ntie = 0;
-        if (W.cut_set) {
-            const long long cut = W.cut;
-            const int room = MMAX - nA - nfill;
-            for (int t = 1 + lane; t < nc; t += 32) {
-                if (W.pick[t] || W.fill[t] || W.d2[t] != cut) continue;
-                int it = W.cand[t], r = 0;
-                for (int u = 1; u < nc; ++u)
-                    if (!W.pick[u] && !W.fill[u] && W.d2[u] == cut && W.cand[u] < it) ++r;
-                if (r < room) { W.tie[t] = 1; ++ntie; }
+            const bool te = np && !fill && cut_found && d == cut;
+            const unsigned bte = __ballot_sync(FULL, te);
+            const bool tie = te && ntie + __popc(bte & lt) < room;
+            ntie += __popc(__ballot_sync(FULL, tie));
+            const bool sl = pk || fill || tie;
+            const unsigned bs = __ballot_sync(FULL, sl);
+            if (sl) {
+                const int r = nsel + __popc(bs & lt);
+                W.sel[r] = W.cand[t];
+                W.seld2[r] = d;
             }
-            ntie = warp_sum_int(ntie);
+            nsel += __popc(bs);
+            nnp += __popc(bnp);
         }
         __syncwarp();
-        m = nA + nfill + ntie;
-        // final order by (d2, index)
-        for (int t = 1 + lane; t < nc; t += 32) {
-            if (!(W.pick[t] | W.fill[t] | W.tie[t])) continue;
-            long long dt = W.d2[t];
-            int it = W.cand[t], r = 0;
-            for (int u = 1; u < nc; ++u)
-                if ((W.pick[u] | W.fill[u] | W.tie[u]) && key_less(W.d2[u], W.cand[u], dt, it)) ++r;
-            if (r < MMAX) { W.sel[r] = it; W.seld2[r] = dt; }
-        }
-        __syncwarp();
-        if (m > MMAX) m = MMAX;
+        m = nsel;
 
         // ---- weighted least squares: FP32 first when asked, FP64 for blocks the
         // FP32 factorisation cannot certify (Cholesky failure or condition
@@ -371,11 +425,11 @@ __global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stenci
         double q[NCOL], lapj = 0.0;
         bool ok = false;
         if (fp32_first) {
-            ok = wls_column<float>(W, m, lane, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
+            ok = wls_column<float>(W, m, lane, own, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
             if (ok && rmin_over_rmax < FP32_RATIO_MIN) ok = false;
             if (!ok && lane == 0) atomicAdd(fp64_count, 1);
         }
-        if (!ok) ok = wls_column<double>(W, m, lane, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
+        if (!ok) ok = wls_column<double>(W, m, lane, own, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
         if (ok) ok = rmin_over_rmax >= RANK_TOL;
         if (!ok) lapj = 0.0;
         const double lsum = warp_sum_d(lapj);
@@ -522,20 +576,8 @@ apcloud_status launch_stencil(apcloud_ctx *c, int n, double unit, double ec, dou
 
 }  // namespace
 
-static bool g_pairs_set = false;
-
 apcloud_status build_stencils(apcloud_ctx *c) {
     const int n = c->n_int, nt = c->n_tot;
-    if (!g_pairs_set) {
-        unsigned char pa[45], pb[45];
-        int e = 0;
-        for (int a = 0; a < NCOL; ++a)
-            for (int b = a; b < NCOL; ++b) { pa[e] = (unsigned char)a; pb[e] = (unsigned char)b; ++e; }
-        APC_CUDA(c, cudaMemcpyToSymbolAsync(c_pa, pa, sizeof pa, 0, cudaMemcpyHostToDevice, c->s));
-        APC_CUDA(c, cudaMemcpyToSymbolAsync(c_pb, pb, sizeof pb, 0, cudaMemcpyHostToDevice, c->s));
-        APC_CUDA(c, cudaStreamSynchronize(c->s));
-        g_pairs_set = true;
-    }
     const int64_t dstride = ((int64_t)n + 31) / 32 * 32;
     int32_t *nbr = ensure<int32_t>(c, c->nbr, (int64_t)n * MMAX);
     int32_t *msz = ensure<int32_t>(c, c->msz, n + 1);
