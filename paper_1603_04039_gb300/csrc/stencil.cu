@@ -110,6 +110,52 @@ __device__ bool cholesky_warp(T *G, T *R, T *Ri, const GramOwn &o, int lane) {
     return true;
 }
 
+// FP32 Cholesky of the packed Gram matrix computed by every lane at once in
+// registers (the 45 entries are broadcast from shared memory, the nine pivot
+// steps run without any exchange between lanes); lane 0 stores R and the
+// reciprocal pivots for the triangular solves.  The reciprocal square root of
+// each pivot gives both R_kk = g * rsqrt(g) and 1 / R_kk.  Returns false on a
+// non-positive pivot, the same decision in every lane.
+__device__ bool cholesky_regs(const float *G, float *R, float *Ri, int lane) {
+    float g[45];
+#pragma unroll
+    for (int e = 0; e < 45; ++e) g[e] = G[e];
+    float rd[NCOL];
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < NCOL; ++k) {
+        const float gkk = g[pk_idx(k, k)];
+        ok = ok && gkk > 0.f;
+        const float r = rsqrtf(ok ? gkk : 1.f);
+        rd[k] = r;
+        g[pk_idx(k, k)] = gkk * r;
+#pragma unroll
+        for (int j = k + 1; j < NCOL; ++j) g[pk_idx(k, j)] *= r;
+#pragma unroll
+        for (int i = k + 1; i < NCOL; ++i)
+#pragma unroll
+            for (int j = i; j < NCOL; ++j) g[pk_idx(i, j)] = fmaf(-g[pk_idx(k, i)], g[pk_idx(k, j)], g[pk_idx(i, j)]);
+    }
+    if (!ok) return false;
+    if (lane == 0) {
+#pragma unroll
+        for (int a = 0; a < NCOL; ++a) {
+            Ri[a] = rd[a];
+#pragma unroll
+            for (int b = a; b < NCOL; ++b) R[a * NCOL + b] = g[pk_idx(a, b)];
+        }
+    }
+    __syncwarp();
+    return true;
+}
+
+// the FP32 path factors in registers, the FP64 path with the warp
+template <class T>
+__device__ __forceinline__ bool cholesky(T *G, T *R, T *Ri, const GramOwn &o, int lane) {
+    if constexpr (sizeof(T) == 4) return cholesky_regs(G, R, Ri, lane);
+    else return cholesky_warp<T>(G, R, Ri, o, lane);
+}
+
 // solve q R = a for the row vector q (R upper), in place on v
 template <class T>
 __device__ __forceinline__ void row_solve_upper(const T *R, const T *Ri, T *v) {
@@ -203,7 +249,7 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, const GramOwn &own, int
     __syncwarp();
     gram<T>(A, m, G, own, lane);
     __syncwarp();
-    bool ok = cholesky_warp<T>(G, R1, Ri1, own, lane);
+    bool ok = cholesky<T>(G, R1, Ri1, own, lane);
     T q[NCOL];
     if (ok) {
         if (lane < m) {
@@ -216,7 +262,7 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, const GramOwn &own, int
         __syncwarp();
         gram<T>(A, m, G, own, lane);
         __syncwarp();
-        ok = cholesky_warp<T>(G, R2, Ri2, own, lane);
+        ok = cholesky<T>(G, R2, Ri2, own, lane);
     }
     rratio = 0.0;
     lapj = 0.0;
@@ -255,7 +301,7 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, const GramOwn &own, int
 
 // SW warps (nodes) per block, one WarpSmem each; the autotuner picks SW
 template <int SW>
-__global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stencil(
+__global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
     const int4 *__restrict__ ic, const int32_t *__restrict__ adj, const int32_t *__restrict__ bowner, int n_int,
     int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
     int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,
@@ -284,7 +330,11 @@ __global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stenci
         // ---- grow the ring by one layer (Section 4.3: (k+1)-ring = k-ring
         // plus the face neighbours of its nodes).  The frontier [head, tail)
         // does not change while the layer grows, so the adjacency of up to
-        // eight 32-slot batches is loaded before any of them is merged.
+        // eight 32-slot batches is loaded before any of them is merged; the
+        // valid slots (about a quarter: a face with a same-size or coarser
+        // neighbour fills one of its four) are packed densely in the d2 area,
+        // which is free until the candidates are ranked.
+        int32_t *stg = reinterpret_cast<int32_t *>(W.d2);
         const int nslots = (tail - head) * 24;
         for (int g0 = 0; g0 < nslots; g0 += 8 * 32) {
             int vb[8];
@@ -300,10 +350,16 @@ __global__ void __launch_bounds__(SW * 32, (12 / SW > 0 ? 12 / SW : 1)) k_stenci
                 }
                 vb[bt] = v;
             }
+            int nv = 0;
 #pragma unroll
             for (int bt = 0; bt < 8; ++bt) {
-                if (g0 + bt * 32 >= nslots) break;
-                const int v = vb[bt];
+                const unsigned bv = __ballot_sync(FULL, vb[bt] >= 0);
+                if (vb[bt] >= 0) stg[nv + __popc(bv & lt)] = vb[bt];
+                nv += __popc(bv);
+            }
+            __syncwarp();
+            for (int b0 = 0; b0 < nv; b0 += 32) {
+                const int v = (b0 + lane < nv) ? stg[b0 + lane] : -1;
                 bool fresh = v >= 0;
                 for (int t = 0; fresh && t < nc; t += 4) {
                     const int4 c4 = *reinterpret_cast<const int4 *>(&W.cand[t]);
