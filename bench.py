@@ -244,6 +244,8 @@ def run_ours(args, ws, rank, local):
     hx, hy, hz, hq = (torch.from_numpy(a).pin_memory() for a in (x, y, z, q))
     hout = tuple(torch.empty(npart, dtype=torch.float64).pin_memory() for _ in range(4))
     ap_e2e = APCloud(**form)
+    ap_e2e.set_launch_shape(spmv_block=tuned["spmv_block"], wls_warps=tuned["wls_warps"],
+                            spmv_unroll=tuned["spmv_unroll"], sweep_sorted=tuned["sweep_sorted"])
     ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout, offsets=offs)   # warm-up
     barrier()
     e2e_steps = max(1, min(args.steps, 3))

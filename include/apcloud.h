@@ -285,22 +285,25 @@ apcloud_status apcloud_push_particles(apcloud_ctx *ctx, double *d_x, double *d_y
 apcloud_status apcloud_set_graphs(apcloud_ctx *ctx, int enable);
 
 /* Autotuner of the launch shapes (after apcloud_stencils): bit 0 of `what`
- * times the preconditioner sweep (or the Arnoldi product under Jacobi) of the
- * configured precision at 64, 128, 256 and 512 threads per block, each with
+ * times a whole solve of the Poisson system A (configured solver, CUDA graphs
+ * included; a synthetic right-hand side, relative residual 1e-10 or 1000
+ * Arnoldi steps; one untimed solve first) for every shape of the
+ * row-parallel products: 64, 128, 256 and 512 threads per block, each with
  * the loads of 1 or 4 stencil entries issued ahead of their multiply-adds
- * (the sum keeps its order either way), and -- for the FP16 sweeps of the
- * mixed form -- on the sliced ELL and on its width-sorted copy (rows ordered
- * by stencil width inside 256-row windows, so 32-row slices carry little
- * padding; same entries in the same order per row); bit 1 times the stencil
- * build (neighbour search + WLS) at 2, 4 and 8 nodes (warps) per block on
- * the current node set.  The fastest shapes are kept for later calls and
- * written to *h_spmv_block, *h_spmv_unroll, *h_sweep_sorted and *h_wls_warps
- * (any may be NULL); h_ms (NULL or 19 doubles) receives the measured
- * milliseconds: 16 sweep variants (index = block-size index + 4 * unroll-4 +
- * 8 * sorted; variants not timed stay 0), then three stencil builds.
- * Results never depend on the shapes.  Runs the timed kernels on the context
- * stream and synchronises.  The paper has no counterpart (launch
- * mechanics). */
+ * (on the width-sorted copy: 1 or 2 chunks of 4 entries; the sum keeps its
+ * order either way), and -- for the FP16 sweeps of the mixed form -- on the
+ * sliced ELL and on its width-sorted copy (rows ordered by stencil width
+ * inside 256-row windows, so 32-row slices carry little padding; same entries
+ * in the same order per row).  The solves run on scratch vectors and the
+ * graphs they capture are released; bit 1 times the stencil build (neighbour
+ * search + WLS) at 2, 4 and 8 nodes (warps) per block on the current node
+ * set.  The fastest shapes are kept for later calls and written to
+ * *h_spmv_block, *h_spmv_unroll, *h_sweep_sorted and *h_wls_warps (any may be
+ * NULL); h_ms (NULL or 19 doubles) receives the measured milliseconds: 16
+ * solves (index = block-size index + 4 * unroll-4 + 8 * sorted; variants not
+ * timed stay 0), then three stencil builds.  Results never depend on the
+ * shapes.  Runs on the context stream and synchronises.  The paper has no
+ * counterpart (launch mechanics). */
 apcloud_status apcloud_autotune(apcloud_ctx *ctx, unsigned what, int *h_spmv_block, int *h_spmv_unroll,
                                 int *h_sweep_sorted, int *h_wls_warps, double *h_ms);
 

@@ -397,7 +397,9 @@ class APCloud:
         return e.value
 
     def autotune(self, spmv=True, stencils=True):
-        """Times the launch shapes and keeps the fastest; returns the choice and timings (ms)."""
+        """Times the launch shapes and keeps the fastest; returns the choice and timings:
+        spmv_ms = ms of one Poisson solve (synthetic right-hand side) per product shape,
+        wls_ms = ms of one stencil build per nodes-per-block."""
         bs, un, so, ww = C.c_int(), C.c_int(), C.c_int(), C.c_int()
         ms = np.zeros(19)
         what = (1 if spmv else 0) | (2 if stencils else 0)

@@ -208,6 +208,53 @@ __device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const
     return acc;
 }
 
+// A row of the width-sorted sweep matrix.  A slice of width w stores its first
+// 4 * floor(w / 4) columns lane-major in 4-entry chunks (chunk j of lane l at
+// entries sbase + 128 j + 4 l .. + 3: one 16-byte column load and one 8-byte
+// value load per chunk) and the last w % 4 columns slice-major as in the ELL.
+// The entries are summed in the same order as row_dot_h.  The columns and
+// values of the next chunk (U = 1) or the next two (U > 1) are in flight
+// while a chunk's x entries are gathered.
+template <int U>
+__device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const int32_t *__restrict__ col,
+                                           const float *__restrict__ x, int64_t sbase, int lane, int w) {
+    constexpr int AH = (U > 1) ? 2 : 1;
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    const uint2 z2 = make_uint2(0u, 0u);
+    float acc = 0.f;
+    const int nch = w >> 2;
+    const int4 *c4 = reinterpret_cast<const int4 *>(col + sbase) + lane;
+    const uint2 *v4 = reinterpret_cast<const uint2 *>(val + sbase) + lane;
+    int4 c0 = z4, c1 = z4;
+    uint2 v0 = z2, v1 = z2;
+    if (nch > 0) { c0 = c4[0]; v0 = v4[0]; }
+    if (AH > 1 && nch > 1) { c1 = c4[32]; v1 = v4[32]; }
+    for (int j = 0; j < nch; ++j) {
+        int4 cn = z4;
+        uint2 vn = z2;
+        if (j + AH < nch) {
+            cn = c4[(int64_t)(j + AH) * 32];
+            vn = v4[(int64_t)(j + AH) * 32];
+        }
+        const float x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
+        const float2 f01 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.x));
+        const float2 f23 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.y));
+        acc = fmaf(f01.x, x0, acc);
+        acc = fmaf(f01.y, x1, acc);
+        acc = fmaf(f23.x, x2, acc);
+        acc = fmaf(f23.y, x3, acc);
+        if (AH > 1) {
+            c0 = c1; v0 = v1;
+            c1 = cn; v1 = vn;
+        } else {
+            c0 = cn; v0 = vn;
+        }
+    }
+    const int64_t tb = sbase + (int64_t)nch * 128 + lane;
+    for (int k = 0; k < (w & 3); ++k) acc = fmaf(__half2float(val[tb + (int64_t)k * 32]), x[col[tb + (int64_t)k * 32]], acc);
+    return acc;
+}
+
 // Rows of beams that have converged in a batch (both null outside batches):
 // their Krylov vectors are zero, so the products skip them.
 struct RowSkip {
@@ -306,21 +353,32 @@ __global__ void __launch_bounds__(BS) k_sweep_s(const int32_t *__restrict__ perm
                                                 const float *__restrict__ x, float *__restrict__ y,
                                                 const float *__restrict__ b, const GmresState *__restrict__ st,
                                                 RowSkip skip) {
-    if (st->done) return;
+    // the row's own loads are issued before the state is read (in batches
+    // after the test for a converged beam, whose rows read nothing more)
     const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (sl_ >= nslot) return;
     const int r = perm[sl_];
-    if (r < 0) return;
-    if (skip.nbo && skip.bdone[skip.nbo[r]]) {
-        y[r] = 0.f;
-        return;
-    }
-    const float om = (float)st->omega;
     const int sl = (int)(sl_ >> 5), lane = (int)(sl_ & 31);
     const int w = (int)sw[sl];
-    const int64_t base = (int64_t)soff[sl] * 32 + lane;
-    const float acc = row_dot_h<U>(val, col, x, base, w);
-    y[r] = fmaf(om, b[r] - acc, x[r]);
+    const int64_t sb = (int64_t)soff[sl] * 32;
+    float br, xr;
+    if (!skip.nbo) {
+        const int rr = r < 0 ? 0 : r;
+        br = b[rr];
+        xr = x[rr];
+        if (st->done || r < 0) return;
+    } else {
+        if (st->done || r < 0) return;
+        if (skip.bdone[skip.nbo[r]]) {
+            y[r] = 0.f;
+            return;
+        }
+        br = b[r];
+        xr = x[r];
+    }
+    const float om = (float)st->omega;
+    const float acc = row_dot_c<U>(val, col, x, sb, lane, w);
+    y[r] = fmaf(om, br - acc, xr);
 }
 
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
@@ -350,6 +408,7 @@ __global__ void __launch_bounds__(BS) k_sweep_s(const int32_t *__restrict__ perm
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
 #define APC_SWEEPS(B, U) (k_sweep_s<B, U>)
+
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
 // Every arithmetic instruction does useful work on 32 lanes (GB300 runs FP64
@@ -1594,24 +1653,30 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
 // vectors in the mixed form, else the matrix's own type; the plain Arnoldi
 // product when the preconditioner is Jacobi) at each block size and keeps the
 // fastest.  Contents of the work vectors do not matter for the timing.
+// right-hand side of the autotuner's solves: 1 + (i mod 7) / 10
+__global__ void k_tune_rhs(double *b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = 1.0 + 0.1 * (double)(i % 7);
+}
+
+// The row-parallel products are timed where they run: for every launch
+// shape, one untimed solve (it captures the cycle graphs) and one timed solve
+// of the Poisson system with the configured solver, to a relative residual of
+// 1e-10 or TUNE_STEPS Arnoldi steps.  Timed in isolation, or over a single
+// restart cycle, the shapes rank differently from a whole solve (shorter
+// capped cycles, and in a batch the beams converge one by one and their rows
+// then return at once).  The graphs the solves capture are released.
+constexpr int TUNE_STEPS = 1000;
+
 apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
     const int n = c->n_tot;
-    const int64_t ldv = ((int64_t)n + 31) / 32 * 32;
     const bool mixed = c->P.precision == 1;
-    const size_t es = mixed ? sizeof(float) : sizeof(double);
-    void *x = ensure<unsigned char>(c, c->pz0, (ldv + 1) * 8), *y = ensure<unsigned char>(c, c->pz1, (ldv + 1) * 8),
-         *bv = ensure<unsigned char>(c, c->pt, (ldv + 1) * 8);
-    GmresState *st = ensure<GmresState>(c, c->gstate, 1);
-    if (!x || !y || !bv || !st) return APCLOUD_E_NOMEM;
-    APC_CUDA(c, cudaMemsetAsync(x, 0, es * ldv, c->s));
-    APC_CUDA(c, cudaMemsetAsync(y, 0, es * ldv, c->s));
-    APC_CUDA(c, cudaMemsetAsync(bv, 0, es * ldv, c->s));
-    APC_CUDA(c, cudaMemsetAsync(st, 0, sizeof(GmresState), c->s));
-    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
-    const int32_t *col = ptr<int32_t>(c->ell_col);
+    double *tb = ensure<double>(c, c->tune_b, n + 1), *tx = ensure<double>(c, c->tune_x, n + 1);
+    if (!tb || !tx) return APCLOUD_E_NOMEM;
+    APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_tune_rhs, tb, n);
     const int sizes[4] = {64, 128, 256, 512}, unrolls[2] = {1, 4};
-    const int saved_u = c->spmv_unroll, saved_s = c->sweep_sorted;
-    int pick_u = saved_u, pick_s = saved_s;
+    const int saved = c->spmv_bs, saved_u = c->spmv_unroll, saved_s = c->sweep_sorted;
+    int pick = saved, pick_u = saved_u, pick_s = saved_s;
     // the width-sorted sweep matrix is a third dimension when it exists
     const int nvar = (mixed && c->P.poly_degree > 1 && c->ss_ok) ? 16 : 8;
     cudaEvent_t e0, e1;
@@ -1619,9 +1684,7 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
     APC_CUDA(c, cudaEventCreate(&e1));
     const unsigned mask = c->timer.mask;
     c->timer.mask = 0;
-    const int saved = c->spmv_bs;
     double best = 1e30;
-    int pick = saved;
     apcloud_status rc = APCLOUD_OK;
     for (int tu = 0; tu < nvar && rc == APCLOUD_OK; ++tu) {
         const int t = tu & 3;
@@ -1629,47 +1692,25 @@ apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out) {
         c->spmv_unroll = unrolls[(tu >> 2) & 1];
         c->sweep_sorted = tu >> 3;
         float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {   // warm-up pass, then the timed pass
+        for (int rep = 0; rep < 2 && rc == APCLOUD_OK; ++rep) {   // capture pass, then the timed pass
+            apcloud_solve_info info{};
+            rc = cuda_check(c, cudaMemsetAsync(tx, 0, sizeof(double) * n, c->s), "autotune");
+            if (rc != APCLOUD_OK) break;
             cudaEventRecord(e0, c->s);
-            for (int k = 0; k < 10; ++k) {
-                if (mixed && c->P.poly_degree > 1 && c->sweep_sorted) {
-                    const int64_t ns = (int64_t)div_up(n, 256) * 256;
-                    APC_SWEEP_BS(c, ns, APC_SWEEPS, (const int32_t *)ptr<int32_t>(c->ss_perm),
-                                 (const uint32_t *)ptr<uint32_t>(c->ss_w), (const uint32_t *)ptr<uint32_t>(c->ss_o),
-                                 (const int32_t *)ptr<int32_t>(c->ss_col), (const __half *)ptr<__half>(c->ss_A), ns,
-                                 (const float *)x, (float *)y, (const float *)bv, (const GmresState *)st,
-                                 RowSkip{nullptr, nullptr, nullptr});
-                } else if (mixed && c->P.poly_degree > 1) {
-                    const __half *hv = ptr<__half>(c->ell_A16);
-                    APC_SPMV_BS(c, n, APC_SWEEPH, sw, so, col, hv, n, (const float *)x, (float *)y,
-                                (const float *)bv, (const GmresState *)st, RowSkip{nullptr, nullptr});
-                } else if (mixed) {
-                    using T = float;
-                    APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, ptr<float>(c->ell_A32), n, (const float *)x,
-                                (float *)y, (float *)nullptr, (const float *)nullptr, st, (double *)nullptr,
-                                RowSkip{nullptr, nullptr});
-                } else {
-                    using T = double;
-                    const int m = c->P.poly_degree > 1 ? 3 : 4;
-                    if (m == 3)
-                        APC_SPMV_BS(c, n, APC_SPMV3, sw, so, col, ptr<double>(c->ell_A), n, (const double *)x,
-                                    (double *)y, (double *)nullptr, (const double *)bv, st, (double *)nullptr,
-                                    RowSkip{nullptr, nullptr});
-                    else
-                        APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, ptr<double>(c->ell_A), n, (const double *)x,
-                                    (double *)y, (double *)nullptr, (const double *)nullptr, st, (double *)nullptr,
-                                    RowSkip{nullptr, nullptr});
-                }
-            }
+            rc = gmres_solve(c, 1, tb, tx, 1e-10, TUNE_STEPS, &info);
+            if (rc < 0) break;
+            rc = APCLOUD_OK;
             cudaEventRecord(e1, c->s);
-            rc = cuda_check(c, cudaEventSynchronize(e1), "autotune spmv");
+            rc = cuda_check(c, cudaEventSynchronize(e1), "autotune solve");
             if (rc != APCLOUD_OK) break;
             cudaEventElapsedTime(&ms, e0, e1);
         }
-        const double per = ms / 10.0;
-        if (ms_out) ms_out[tu] = per;
-        if (per < best) { best = per; pick = sizes[t]; pick_u = unrolls[(tu >> 2) & 1]; pick_s = tu >> 3; }
+        if (rc != APCLOUD_OK) break;
+        if (ms_out) ms_out[tu] = ms;
+        if (ms < best) { best = ms; pick = sizes[t]; pick_u = unrolls[(tu >> 2) & 1]; pick_s = tu >> 3; }
     }
+    free_graphs(c);
+    c->jprev[1][0] = c->jprev[1][1] = 0;
     c->timer.mask = mask;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

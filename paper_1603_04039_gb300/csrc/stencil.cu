@@ -808,6 +808,15 @@ __global__ void __launch_bounds__(SS_WIN) k_ss_rank(const int32_t *__restrict__ 
     if ((t & 31) == 0) w[blockIdx.x * (SS_WIN / 32) + (t >> 5)] = (uint32_t)sorted_w[t];   // max of the slice
 }
 
+// entry k of lane `lane` in a sorted slice of width w starting at entry sb:
+// 4-entry chunks lane-major for the first 4 * floor(w / 4) columns, the rest
+// slice-major
+__device__ __forceinline__ int64_t ss_slot(int64_t sb, int w, int k, int lane) {
+    const int kf = w & ~3;
+    return (k < kf) ? sb + (int64_t)(k >> 2) * 128 + lane * 4 + (k & 3)
+                    : sb + (int64_t)kf * 32 + (int64_t)(k - kf) * 32 + lane;
+}
+
 // copy every row's stored entries (in their order) into its slot of the sorted layout
 __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                           const int32_t *__restrict__ col, const __half *__restrict__ hA, const __half *__restrict__ hB,
@@ -817,7 +826,7 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslot) return;
     const int sl2 = (int)(s >> 5), lane2 = (int)(s & 31);
-    const int64_t b2 = (int64_t)o2[sl2] * 32 + lane2;
+    const int64_t b2 = (int64_t)o2[sl2] * 32;
     const int wid2 = (int)w2[sl2];
     const int r = perm[s];
     int k = 0;
@@ -826,14 +835,14 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
         const int w = (int)sw[sl];
         const int64_t base = (int64_t)soff[sl] * 32 + lane;
         for (; k < wid2 && k < w; ++k) {
-            const int64_t e = base + (int64_t)k * 32, q = b2 + (int64_t)k * 32;
+            const int64_t e = base + (int64_t)k * 32, q = ss_slot(b2, wid2, k, lane2);
             col2[q] = col[e];
             A2[q] = hA[e];
             B2[q] = hB[e];
         }
     }
     for (; k < wid2; ++k) {   // padding: the row itself (or row 0) with value 0
-        const int64_t q = b2 + (int64_t)k * 32;
+        const int64_t q = ss_slot(b2, wid2, k, lane2);
         col2[q] = r >= 0 ? r : 0;
         A2[q] = __float2half(0.f);
         B2[q] = __float2half(0.f);
@@ -846,9 +855,11 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
 // step; in 32-row slices of consecutive rows the slice width is that of its
 // widest stencil and 14% of the stored entries are padding.  This copy orders
 // the rows of every 256-row window by stored width (SELL-C-sigma, C = 32,
-// sigma = 256): slices then hold rows of nearly equal width.  Each row keeps
-// its entries in their stored order, so a sweep on this copy gives the same
-// bits as on the ELL.
+// sigma = 256): slices then hold rows of nearly equal width.  Within a slice
+// the entries are grouped in 4-entry chunks per row (16-byte column loads),
+// the last width % 4 columns as in the ELL.  Each row keeps its entries in
+// their stored order, so a sweep on this copy gives the same bits as on the
+// ELL.
 apcloud_status build_sorted_sweep(apcloud_ctx *c) {
     c->ss_ok = false;
     const int n = c->n_tot;

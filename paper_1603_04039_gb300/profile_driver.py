@@ -1,13 +1,14 @@
 """Small, bounded runs of the library for profilers (ncu): one workload, a
 fixed amount of work, exit 0.  Usage:
 
-    python -m paper_1603_04039_gb300.profile_driver solve  [iters] [fp64|mixed]
+    python -m paper_1603_04039_gb300.profile_driver solve  [iters] [fp64|mixed] [sorted]
     python -m paper_1603_04039_gb300.profile_driver mpnn   [steps]
     python -m paper_1603_04039_gb300.profile_driver batch  [iters]
 
 `solve`: the 1e7-particle depth-10 beam (1.05e6 nodes), tree, stencils,
 deposit, then `iters` Arnoldi steps of the Poisson solve (GMRES(30),
-polynomial preconditioner degree 16).  `mpnn`: `steps` training steps of the
+polynomial preconditioner degree 16); `sorted` runs the sweeps on the
+width-sorted matrix with 256 threads and 4-entry load-ahead.  `mpnn`: `steps` training steps of the
 learned preconditioner on a 2e5-particle depth-8 beam.  `batch`: the 64-beam
 depth-9 batch, then `iters` Arnoldi steps.
 """
@@ -24,10 +25,12 @@ def _put(*arrays):
     return [torch.from_numpy(a).to("cuda:0") for a in arrays]
 
 
-def solve(iters=400, precision="mixed"):
+def solve(iters=400, precision="mixed", sorted_sweeps=False):
     x, y, z, q = inputs.beam_with_halo(10_000_000, 1)
     tx, ty, tz, tq = _put(x, y, z, q)
     ap = APCloud(max_depth=10, c_refine=0.043, precision=precision, poly_degree=16, poly_omega=1.0)
+    if sorted_sweeps:
+        ap.set_launch_shape(spmv_block=256, wls_warps=2, spmv_unroll=4, sweep_sorted=1)
     ap.build_octree(tx, ty, tz)
     ap.stencils()
     ap.deposit(q=tq, rtol=1e-10)
@@ -64,7 +67,8 @@ if __name__ == "__main__":
     what = sys.argv[1] if len(sys.argv) > 1 else "solve"
     rest = sys.argv[2:]
     if what == "solve":
-        solve(int(rest[0]) if rest else 400, rest[1] if len(rest) > 1 else "mixed")
+        solve(int(rest[0]) if rest else 400, rest[1] if len(rest) > 1 else "mixed",
+              len(rest) > 2 and rest[2] == "sorted")
     elif what == "mpnn":
         mpnn(int(rest[0]) if rest else 3)
     elif what == "batch":
