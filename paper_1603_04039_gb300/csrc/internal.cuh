@@ -145,6 +145,7 @@ struct apcloud_ctx {
     // width-sorted copy of the FP16 sweep matrix: rows ordered by stencil width
     // inside windows of 256 rows, so 32-row slices pad little (see build_sorted_sweep)
     apc::DBuf ss_perm, ss_w, ss_o, ss_col, ss_A, ss_B;
+    apc::DBuf beam_part;        // per-beam norms: partial sums, BSQ_CH per beam
     apc::DBuf tune_b, tune_x;   // autotuner: right-hand side and iterate of its timed restart cycles
     bool ss_ok = false;
     int64_t ss_entries = 0;

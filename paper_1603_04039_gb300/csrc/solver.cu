@@ -780,15 +780,22 @@ struct BeamMask {
     double rtol;
 };
 
-// squared norm of r over the nodes of each beam (one block per beam, fixed order)
+// squared norm of r over the nodes of each beam, in fixed order: BSQ_CH
+// blocks per beam each sum one part of every row segment of the beam, then
+// the parts are added in order (one block per beam left the largest beam's
+// ~4e5 rows to a single SM)
+constexpr int BSQ_CH = 16;
+
 template <class T>
-__global__ void k_beam_sq(const T *__restrict__ r, const int64_t *__restrict__ rng, int nb, double *__restrict__ out) {
+__global__ void __launch_bounds__(256) k_beam_sq_part(const T *__restrict__ r, const int64_t *__restrict__ rng, int nb,
+                                                      double *__restrict__ part) {
     __shared__ double sh[256];
-    const int beam = blockIdx.x;
+    const int beam = blockIdx.x / BSQ_CH, ch = blockIdx.x % BSQ_CH;
     double s = 0.0;
     for (int seg = 0; seg < 7; ++seg) {
         const int64_t lo = rng[(int64_t)seg * (nb + 1) + beam], hi = rng[(int64_t)seg * (nb + 1) + beam + 1];
-        for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma((double)r[i], (double)r[i], s);
+        const int64_t a = lo + (hi - lo) * ch / BSQ_CH, e = lo + (hi - lo) * (ch + 1) / BSQ_CH;
+        for (int64_t i = a + threadIdx.x; i < e; i += blockDim.x) s = fma((double)r[i], (double)r[i], s);
     }
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -796,7 +803,23 @@ __global__ void k_beam_sq(const T *__restrict__ r, const int64_t *__restrict__ r
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[beam] = sh[0];
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_beam_sq_sum(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    const int beam = blockIdx.x * blockDim.x + threadIdx.x;
+    if (beam >= nb) return;
+    double s = 0.0;
+    for (int ch = 0; ch < BSQ_CH; ++ch) s += part[(int64_t)beam * BSQ_CH + ch];
+    out[beam] = s;
+}
+
+// out[b] = sum of r^2 over the rows of beam b (its 7 row segments)
+template <class T>
+void beam_sq(apcloud_ctx *c, const T *r, const int64_t *rng, int nb, double *out) {
+    double *part = ptr<double>(c->beam_part);
+    APC_LAUNCH(c, K_VEC, nb * BSQ_CH, 256, 0, k_beam_sq_part<T>, r, rng, nb, part);
+    APC_LAUNCH(c, K_VEC, div_up(nb, 64), 64, 0, k_beam_sq_sum, (const double *)part, nb, out);
 }
 
 // one block: mark converged beams, then restart the cycle on the others:
@@ -860,7 +883,7 @@ __global__ void k_tile_active(const int32_t *__restrict__ nbo, const int *__rest
 template <class T>
 apcloud_status mask_residual(apcloud_ctx *c, const BeamMask &bm, T *r, GmresState *st) {
     const int n = c->n_tot;
-    APC_LAUNCH(c, K_VEC, bm.nb, 256, 0, k_beam_sq<T>, (const T *)r, bm.rng, bm.nb, bm.r2);
+    beam_sq<T>(c, (const T *)r, bm.rng, bm.nb, bm.r2);
     APC_LAUNCH(c, K_VEC, 1, 256, 0, k_beam_mask, (const double *)bm.r2, bm.b2, bm.nb, bm.rtol, bm.bdone, st);
     APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_mask_rows<T>, r, n, bm.nbo, (const int *)bm.bdone);
     APC_LAUNCH(c, K_VEC, (int)bm.ntile, 256, 0, k_tile_active, bm.nbo, (const int *)bm.bdone, n, bm.tact);
@@ -1203,8 +1226,7 @@ __global__ void k_save_jend(GmresState *st) {
 template <class T>
 apcloud_status bstart_launches(apcloud_ctx *c, const Krylov<T> &K) {
     const BKry &bk = *K.bk;
-    APC_LAUNCH(c, K_VEC, bk.nb, 256, 0, k_beam_sq<T>, (const T *)K.wraw, (const int64_t *)ptr<int64_t>(c->beam_rng),
-               bk.nb, bk.r2);
+    beam_sq<T>(c, (const T *)K.wraw, (const int64_t *)ptr<int64_t>(c->beam_rng), bk.nb, bk.r2);
     APC_LAUNCH(c, K_VEC, 1, 256, 0, k_bstart, bk, K.st);
     return cuda_check(c, cudaGetLastError(), "batched restart");
 }
@@ -1372,8 +1394,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
     if (K.mask) APC_TRY(mask_residual<T>(c, *K.mask, K.wraw, st));
     if (K.bk) {
         // per-beam ||b_b|| once, then every beam's first cycle
-        APC_LAUNCH(c, K_VEC, K.bk->nb, 256, 0, k_beam_sq<T>, b, (const int64_t *)ptr<int64_t>(c->beam_rng),
-                   K.bk->nb, K.bk->r2);
+        beam_sq<T>(c, b, (const int64_t *)ptr<int64_t>(c->beam_rng), K.bk->nb, K.bk->r2);
         APC_LAUNCH(c, K_VEC, div_up(K.bk->nb, 64), 64, 0, k_bnorm_init, *K.bk);
         APC_TRY(bstart_launches<T>(c, K));
     }
@@ -1491,12 +1512,13 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         int *bdone = ensure<int>(c, c->beam_done, nb);
         int32_t *nbo = ensure<int32_t>(c, c->node_beam, n);
         uint8_t *tact = ensure<uint8_t>(c, c->tile_act, ntile);
-        if (!b2 || !r2 || !bdone || !nbo || !tact) return APCLOUD_E_NOMEM;
+        double *bpart = ensure<double>(c, c->beam_part, (int64_t)nb * BSQ_CH);
+        if (!b2 || !r2 || !bdone || !nbo || !tact || !bpart) return APCLOUD_E_NOMEM;
         APC_TRY(node_beams(c, nbo));
         APC_CUDA(c, cudaMemsetAsync(bdone, 0, sizeof(int) * nb, c->s));
         APC_CUDA(c, cudaMemsetAsync(tact, 1, ntile, c->s));
         const int64_t *rng = ptr<int64_t>(c->beam_rng);
-        APC_LAUNCH(c, K_VEC, nb, 256, 0, k_beam_sq<double>, b, rng, nb, b2);
+        beam_sq<double>(c, b, rng, nb, b2);
         bmv = BeamMask{nb, rng, b2, r2, bdone, nbo, tact, ntile, rtol};
         bm = &bmv;
         // work items of the per-beam Krylov spaces: chunks of at most BITEM rows
