@@ -636,8 +636,61 @@ def run_learned(args):
                        "train_law": "beam with halo, alternating 2e4 particles depth 6 c 0.3 and 1e5 "
                                     "particles depth 8 c 0.15, seeds 10000..",
                        "eval_seeds": args.eval_seeds, "net": "3 x 64 message passing, BF16 tcgen05 layers",
-                       "ilu0": "not built"},
+                       "ilu0": "bench.py --ilu (same seeds)"},
             "train_seconds": round(t_train, 1), "loss_curve": curve, "eval": rows}
+
+
+def run_ilu(args):
+    """ILU(0) against Jacobi on the held-out seeds of the learned-preconditioner
+    comparison (1e7-particle depth-10 workload, FP64 GMRES(30), rtol 1e-10).
+    The Jacobi solve of the deposited system gives phi; both preconditioners
+    then solve A x = A phi (the same operator and, up to the solve tolerance,
+    the same right-hand side) from zero."""
+    import torch
+    from paper_1603_04039_gb300 import APCloud, inputs
+    dev = torch.device("cuda", 0)
+    npart, depth, c = WORKLOADS["beam_halo_1e7_depth10"]
+    rows = []
+
+    def timed(f):
+        best, out = None, None
+        for rep in range(2):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(ap.stream)
+            out = f()
+            e1.record(ap.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        return out, best
+
+    for seed in args.eval_seeds:
+        x, y, z, q = inputs.beam_with_halo(npart, seed)
+        tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
+        ap = APCloud(max_depth=depth, c_refine=c, device=dev, precision="fp64", poly_degree=1)
+        ap.build_octree(tx, ty, tz)
+        ap.stencils()
+        ap.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
+        phi, _ = ap.solve(rtol=RTOL, max_iter=MAX_ITER)
+        b = ap.matvec("A", phi)
+        (xj, ij), msj = timed(lambda: ap.solve_system("A", b, rtol=RTOL, max_iter=MAX_ITER))
+        (xi, ii), msi = timed(lambda: ap.solve_system_ilu0("A", b, rtol=RTOL, max_iter=args.ilu_max_iter))
+        rows.append({"seed": seed, "n_nodes": ap.n_nodes,
+                     "jacobi": {"iters": ij["iters"], "ms": round(msj, 2), "relres": ij["relres"],
+                                "status": ij["status"]},
+                     "ilu0": {"iters": ii["iters"], "ms": round(msi, 2), "relres": ii["relres"], "status": ii["status"],
+                              "host_setup_ms": round(ii["setup_ms"], 1), "levels_lower": ii["levels_lower"],
+                              "levels_upper": ii["levels_upper"], "nnz": ii["nnz"],
+                              "rel_l2_x_vs_jacobi": float(torch.linalg.norm(xi - xj) / torch.linalg.norm(xj))}})
+        ap.close()
+    speed = float(np.mean([r["jacobi"]["ms"] / r["ilu0"]["ms"] for r in rows]))
+    return {"metric": "Poisson solve time to rtol 1e-10 on held-out seeds, ILU(0) against Jacobi (FP64 GMRES(30))",
+            "value": round(speed, 3), "unit": "x", "n_gpus": 1, "steps": len(args.eval_seeds), "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "ilu0_beam_halo_1e7_depth10", "eval_seeds": args.eval_seeds,
+                       "ilu0": "factorised on the host, level-scheduled triangular sweeps on the GPU"},
+            "eval": rows}
 
 
 def main():
@@ -658,12 +711,17 @@ def main():
     ap.add_argument("--train-systems", type=int, default=10000)
     ap.add_argument("--eval-seeds", type=int, nargs="+", default=[90001, 90002])
     ap.add_argument("--learned-max-iter", type=int, default=100000)
+    ap.add_argument("--ilu", action="store_true", help="ILU(0) against Jacobi on the learned comparison's seeds")
+    ap.add_argument("--ilu-max-iter", type=int, default=3000)
     args = ap.parse_args()
     if args.vp:
         print(json.dumps(run_vp(args)))
         return
     if args.learned:
         print(json.dumps(run_learned(args)))
+        return
+    if args.ilu:
+        print(json.dumps(run_ilu(args)))
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -51,7 +51,8 @@ typedef enum {
     APCLOUD_E_CUDA = -4,         /* a CUDA call failed */
     APCLOUD_E_NOMEM = -5,        /* device allocation failed */
     APCLOUD_E_TIMEOUT = -6,      /* a bounded device wait gave up */
-    APCLOUD_E_STATE = -7         /* call out of order */
+    APCLOUD_E_STATE = -7,        /* call out of order */
+    APCLOUD_E_NUMERIC = -8       /* a factorisation met a zero pivot */
 } apcloud_status;
 
 /* Method parameters (defaults from apcloud_default_params). */
@@ -233,6 +234,32 @@ apcloud_status apcloud_solve_system(apcloud_ctx *ctx, int which, const double *d
  * race and give undefined results.  Synchronises the context stream. */
 apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *ctx, int which, const double *d_b, double *d_x,
                                             double rtol, int max_iter, apcloud_solve_info *info);
+
+/* ILU(0)-preconditioned GMRES(restart) on the density (which = 0) or Poisson
+ * (which = 1) system: the comparison baseline for the learned preconditioner
+ * (besides Jacobi).  The paper has no counterpart.  ILU(0) is the incomplete
+ * LU factorisation with no fill outside the pattern of the stored matrix
+ * (Saad, Iterative Methods for Sparse Linear Systems, Algorithm 10.4, IKJ
+ * order), taken of the stored column-scaled FP64 values; it is computed on
+ * the host at every call, and every application (LU)^-1 v runs on the GPU as
+ * a forward and a backward sweep, one launch per dependency level (no CUDA
+ * graphs).  d_b, d_x and the result are as in apcloud_solve_system (x is the
+ * start and the answer, n = interior + boundary nodes, device memory).  FP64
+ * form (precision 0) and single-beam contexts only, else APCLOUD_E_INVALID;
+ * APCLOUD_E_NUMERIC on a zero pivot.  h_stats (NULL or 4 doubles) receives the
+ * host setup milliseconds (copy, factorisation, level schedule, upload), the
+ * numbers of forward and backward levels, and the stored nonzeros.
+ * Synchronises the context stream. */
+apcloud_status apcloud_solve_system_ilu0(apcloud_ctx *ctx, int which, const double *d_b, double *d_x, double rtol,
+                                         int max_iter, apcloud_solve_info *info, double *h_stats);
+
+/* The ILU(0) factorisation of the comparison solve on a host CSR matrix, in
+ * place: n rows, h_rowptr[n + 1], column indices h_col sorted and distinct in
+ * every row, each row holding its diagonal; h_val is overwritten with the
+ * strict lower part of L (unit diagonal implied) and U.  Host memory only; no
+ * GPU is used.  APCLOUD_E_INVALID on a malformed pattern, APCLOUD_E_NUMERIC
+ * on a zero pivot. */
+apcloud_status apcloud_ilu0_factor_host(int64_t n, const int64_t *h_rowptr, const int32_t *h_col, double *h_val);
 
 /* The whole solve on host arrays: copies positions and charges (h_q NULL =
  * q_uniform) to the device, runs the five steps with g = 0, and copies phi

@@ -10,7 +10,7 @@ from . import inputs  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("APCloud", "APCloudError", "MPNN", "kernel_names", "load"):
+    if name in ("APCloud", "APCloudError", "MPNN", "kernel_names", "load", "ilu0_factor_host"):
         from . import _binding
         return getattr(_binding, name)
     if name == "VlasovPoisson":

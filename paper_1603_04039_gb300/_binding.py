@@ -23,7 +23,7 @@ MMAX = 32
 NCOL = 9
 
 STATUS = {0: "OK", 1: "W_NOT_CONVERGED", -1: "E_INVALID", -2: "E_DOMAIN", -3: "E_STENCIL", -4: "E_CUDA",
-          -5: "E_NOMEM", -6: "E_TIMEOUT", -7: "E_STATE"}
+          -5: "E_NOMEM", -6: "E_TIMEOUT", -7: "E_STATE", -8: "E_NUMERIC"}
 
 _lock = threading.Lock()
 _lib = None
@@ -80,6 +80,8 @@ def load():
             "apcloud_matvec": (I, [P, I, P, P]),
             "apcloud_solve_system": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo)]),
             "apcloud_solve_system_noalloc": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo)]),
+            "apcloud_solve_system_ilu0": (I, [P, I, P, P, D, I, C.POINTER(SolveInfo), P]),
+            "apcloud_ilu0_factor_host": (I, [L, P, P, P]),
             "apcloud_field_host": (I, [P, P, P, P, P, D, L, D, I, P, P, P, P, C.POINTER(SolveInfo),
                                        C.POINTER(SolveInfo)]),
             "apcloud_field_host_batched": (I, [P, P, P, P, P, D, C.POINTER(L), I, D, I, P, P, P, P,
@@ -133,6 +135,21 @@ def _f64(t, n=None):
     if n is not None and t.numel() != n:
         raise ValueError("expected %d entries, got %d" % (n, t.numel()))
     return t
+
+
+def ilu0_factor_host(rowptr, col, val):
+    """ILU(0) of a host CSR matrix (columns sorted, diagonal present) through the
+    library's host routine; returns the factored values (L strictly below the
+    diagonal with a unit diagonal implied, U on and above it)."""
+    lib = load()
+    rp = np.ascontiguousarray(rowptr, dtype=np.int64)
+    cj = np.ascontiguousarray(col, dtype=np.int32)
+    a = np.array(val, dtype=np.float64, copy=True)
+    st = lib.apcloud_ilu0_factor_host(len(rp) - 1, rp.ctypes.data_as(C.c_void_p), cj.ctypes.data_as(C.c_void_p),
+                                      a.ctypes.data_as(C.c_void_p))
+    if st < 0:
+        raise APCloudError(st, "ILU(0) factorisation")
+    return a
 
 
 def measure_fma_peak():
@@ -327,6 +344,20 @@ class APCloud:
             st = self._check(self._lib.apcloud_solve_system(self._ctx, 1 if which == "A" else 0, _dptr(b), _dptr(x),
                                                             rtol, int(max_iter), C.byref(info)))
         return x, dict(info.as_dict(), status=st)
+
+    def solve_system_ilu0(self, which, b, x0=None, rtol=1e-10, max_iter=100000):
+        """GMRES with the ILU(0) right preconditioner (FP64 form, single beam): the
+        comparison baseline of the learned preconditioner."""
+        _f64(b, self.n_nodes)
+        x = torch.zeros(self.n_nodes, dtype=torch.float64, device=self.device) if x0 is None else x0.clone()
+        info = SolveInfo()
+        stats = np.zeros(4)
+        with torch.cuda.device(self.device):
+            st = self._check(self._lib.apcloud_solve_system_ilu0(self._ctx, 1 if which == "A" else 0, _dptr(b),
+                                                                 _dptr(x), rtol, int(max_iter), C.byref(info),
+                                                                 stats.ctypes.data_as(C.c_void_p)))
+        return x, dict(info.as_dict(), status=st, setup_ms=float(stats[0]), levels_lower=int(stats[1]),
+                       levels_upper=int(stats[2]), nnz=int(stats[3]))
 
     def solve_system_noalloc(self, which, b, x, rtol=1e-10, max_iter=100000):
         """apcloud_solve_system_noalloc on caller-owned tensors: x holds the

@@ -83,6 +83,16 @@ struct Timer {
     double flops[NKIND] = {0};   // algorithmic floating-point operations
 };
 
+// ILU(0) factors on the device for the comparison solve: rows listed level by
+// level (forward and backward), the strict lower / upper entries of each listed
+// row, 1 / U_rr per backward position; level offsets on the host
+struct IluDev {
+    const int32_t *lrows = nullptr, *urows = nullptr, *lcol = nullptr, *ucol = nullptr;
+    const int64_t *lrp = nullptr, *urp = nullptr;
+    const double *lval = nullptr, *uval = nullptr, *udinv = nullptr;
+    std::vector<int> loff, uoff;
+};
+
 }  // namespace apc
 
 struct apcloud_ctx {
@@ -146,7 +156,11 @@ struct apcloud_ctx {
     // inside windows of 256 rows, so 32-row slices pad little (see build_sorted_sweep)
     apc::DBuf ss_perm, ss_w, ss_o, ss_col, ss_A, ss_B;
     apc::DBuf beam_part;        // per-beam norms: partial sums, BSQ_CH per beam
-    apc::DBuf tune_b, tune_x;   // autotuner: right-hand side and iterate of its timed restart cycles
+    apc::DBuf tune_b, tune_x;
+    // ILU(0) comparison solve: factors of system ilu_which while it runs (-1: none)
+    apc::IluDev ilu;
+    int ilu_which = -1;
+    apc::DBuf ilu_lrows, ilu_urows, ilu_lrp, ilu_urp, ilu_lcol, ilu_ucol, ilu_lval, ilu_uval, ilu_dinv;   // autotuner: right-hand side and iterate of its timed restart cycles
     bool ss_ok = false;
     int64_t ss_entries = 0;
     // solver
@@ -216,6 +230,8 @@ apcloud_status build_stencils(apcloud_ctx *c);
 apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform);
 apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x_inout_scaled, double rtol,
                            int max_iter, apcloud_solve_info *info);
+bool ilu0_factor(int64_t n, const int64_t *rp, const int32_t *cj, const int64_t *dg, double *a);
+double *ilu_apply(apcloud_ctx *c, const IluDev &I, const double *v, double *z, const GmresState *st);
 apcloud_status spmv(apcloud_ctx *c, int which, const double *x, double *y, double scale, double *copy_out);
 apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *ey, double *ez);
 apcloud_status interpolate_phi(apcloud_ctx *c, const double *x, const double *y, const double *z, int64_t n,

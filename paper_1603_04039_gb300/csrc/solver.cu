@@ -1171,6 +1171,7 @@ struct Krylov {
     const uint8_t *tact = nullptr;          // batches: tiles holding a row of an unconverged beam
     const BeamMask *mask = nullptr;         // batches: per-beam convergence at every restart
     const BKry *bk = nullptr;               // batches: an independent Krylov space per beam
+    const IluDev *ilu = nullptr;            // FP64 comparison solve: (LU)^-1 of ILU(0) instead of the polynomial
 };
 
 
@@ -1183,6 +1184,9 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     const int n = c->n_tot;
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
+    if constexpr (sizeof(T) == 8) {
+        if (K.ilu) return ilu_apply(c, *K.ilu, (const double *)v, (double *)z_first, (const GmresState *)st);
+    }
     T *cur = z_first, *nxt = (z_first == K.z0) ? K.z1 : K.z0;
     for (int i = 1; i < K.pdeg; ++i) {
         if constexpr (sizeof(T) == 4) {
@@ -1421,7 +1425,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         {
             // per Arnoldi step: one product with the full matrix, pdeg - 1 sweeps (FP16
             // values when available); the cycle end adds pdeg - 1 sweeps, the restart one product
-            const double sweeps = (K.pdeg <= 1) ? 0.0 : (double)(K.pdeg - 1) * (je + 1);
+            const double sweeps = (K.pdeg <= 1 || K.ilu) ? 0.0 : (double)(K.pdeg - 1) * (je + 1);
             const double prods = je + 1.0;
             const double sb = K.hval ? 2.0 : vb;
             account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
@@ -1576,13 +1580,19 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         Krylov<double> K{ensure<double>(c, c->V, (int64_t)(m + 1) * ldv), ldv, ensure<double>(c, c->w0, ldv + 1),
                          ensure<double>(c, c->w1, ldv + 1), ptr<GmresState>(c->gstate), partial, nblk};
         if (!K.V || !K.w || !K.wraw) return APCLOUD_E_NOMEM;
-        if (c->P.poly_degree > 1) {
-            K.pdeg = c->P.poly_degree;
+        const bool ilu = c->ilu_which == which && !bm;
+        if (c->P.poly_degree > 1 || ilu) {
+            // the ILU(0) comparison takes the polynomial's place: one application per step
+            K.pdeg = ilu ? 2 : c->P.poly_degree;
             K.omega = c->P.poly_omega;
             K.z0 = ensure<double>(c, c->pz0, ldv + 1);
             K.z1 = ensure<double>(c, c->pz1, ldv + 1);
             K.t = ensure<double>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
+            if (ilu) {
+                K.ilu = &c->ilu;
+                K.graphs = false;   // thousands of level launches per step
+            }
         }
         if (bk && K.pdeg > 1) {
             K.bk = bk;
