@@ -62,6 +62,7 @@ def _load():
             "or_get_adjacency": (None, [P, P, P]),
             "or_criterion_opens": (I, [L, I, I, D, D, D]),
             "or_wls": (I, [I, P, D, D, P, P, P, P]),
+            "or_select": (I, [I, P, P, I, P]),
             "or_stencils": (I, [P]),
             "or_get_stencils": (None, [P, P, P, P, P, P, P]),
             "or_matrix_nnz": (L, [P]),
@@ -114,6 +115,20 @@ def wls(dint, unit: float, weight_c: float = 4.0):
     if bad:
         return None
     return P, lap, ld.value, rr.value
+
+
+def select_neighbours(dint, idx, m_target: int):
+    """Stencil of one node from its ring candidates (Section 3.1, two nearest per
+    octant, then the nearest up to m_target, then the ties at the cut; at most
+    MMAX): integer offsets dint (nc x 3) and node indices idx in, the chosen
+    indices in rank order out."""
+    dint = np.ascontiguousarray(dint, dtype=np.int64).reshape(-1, 3)
+    idx = np.ascontiguousarray(idx, dtype=np.int32)
+    sel = np.zeros(MMAX, dtype=np.int32)
+    m = _load().or_select(len(idx), _p(dint), _p(idx), int(m_target), _p(sel))
+    if m < 0:
+        raise OracleError("or_select: out of memory")
+    return sel[:m].copy()
 
 
 def gmres(rowptr, col, val, b, x0=None, rtol=1e-10, max_iter=10000, restart=30):

@@ -631,6 +631,40 @@ static int cmp_cand(const void *a, const void *b) {
     return (x->idx > y->idx) - (x->idx < y->idx);
 }
 
+/* Section 3.1, "two nearest nodes from each quadrant", in 3-D (reading R4):
+ * the stencil of one node chosen from nc ring candidates, given by their
+ * integer offsets dint (nc x 3, from the node to the candidate) and node
+ * indices idx.  Candidates are ranked by (squared distance, index).  The
+ * octant of a candidate is the sign pattern of its offset, a zero component
+ * counting as +.  Taken are: the two nearest candidates of every octant;
+ * then the nearest remaining ones until mt are taken; then every remaining
+ * candidate at the squared distance of the last one taken in that fill; at
+ * most OR_MMAX in all.  Writes the chosen indices, in rank order, to sel
+ * (room for OR_MMAX) and returns their number (-1 when out of memory). */
+int or_select(int nc, const int64_t *dint, const int32_t *idx, int mt, int32_t *sel) {
+    cand_t *cand = (cand_t *)xcalloc((size_t)nc, sizeof(cand_t));
+    int8_t *pk = (int8_t *)xcalloc((size_t)nc, 1);
+    if (!cand || !pk) { free(cand); free(pk); return -1; }
+    for (int t = 0; t < nc; ++t) {
+        const int64_t *d = dint + 3 * (size_t)t;
+        cand[t].d2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+        cand[t].idx = idx[t];
+        cand[t].oct = (int)((d[0] >= 0) << 2 | (d[1] >= 0) << 1 | (d[2] >= 0));
+    }
+    qsort(cand, (size_t)nc, sizeof(cand_t), cmp_cand);
+    int taken[8] = {0}, m = 0;
+    for (int t = 0; t < nc && m < OR_MMAX; ++t)
+        if (taken[cand[t].oct] < 2) { taken[cand[t].oct]++; pk[t] = 1; m++; }
+    int64_t cut = -1;
+    for (int t = 0; t < nc && m < mt && m < OR_MMAX; ++t) if (!pk[t]) { pk[t] = 1; m++; cut = cand[t].d2; }
+    for (int t = 0; t < nc && m < OR_MMAX; ++t) if (!pk[t] && cand[t].d2 == cut) { pk[t] = 1; m++; }
+    int s = 0;
+    for (int t = 0; t < nc && s < m; ++t) if (pk[t]) sel[s++] = cand[t].idx;
+    free(cand);
+    free(pk);
+    return m;
+}
+
 int or_stencils(or_ctx *c) {
     int n = c->n_int, nt = c->n_int + c->n_bnd, M = c->m_target, W = OR_MMAX;
     if (M < OR_NCOL || M > OR_MMAX || c->ring_max < 2) return OR_E_INVALID;
@@ -643,8 +677,9 @@ int or_stencils(or_ctx *c) {
     c->lapd = (double *)xcalloc((size_t)n, sizeof(double));
     int32_t *mark = (int32_t *)xcalloc((size_t)nt, sizeof(int32_t));
     int32_t *list = (int32_t *)xcalloc((size_t)nt, sizeof(int32_t));
-    cand_t *cand = (cand_t *)xcalloc((size_t)nt, sizeof(cand_t));
-    if (!c->nbr || !mark || !list || !cand) return OR_E_NOMEM;
+    int64_t *coff = (int64_t *)xcalloc((size_t)nt * 3, sizeof(int64_t));
+    int32_t *cidx = (int32_t *)xcalloc((size_t)nt, sizeof(int32_t));
+    if (!c->nbr || !mark || !list || !coff || !cidx) return OR_E_NOMEM;
     for (int i = 0; i < nt; ++i) mark[i] = -1;
     double unit = unit_len(c);
     int status = OR_OK;
@@ -671,43 +706,20 @@ int or_stencils(or_ctx *c) {
             if (nc < OR_NCOL) continue;
             for (int t = 1; t < nl; ++t) {
                 int v = list[t];
-                int64_t dd[3], d2 = 0;
-                for (int d = 0; d < 3; ++d) {
-                    dd[d] = (int64_t)c->icoord[3 * v + d] - (int64_t)c->icoord[3 * y0 + d];
-                    d2 += dd[d] * dd[d];
-                }
-                cand[t - 1].d2 = d2;
-                cand[t - 1].idx = v;
-                cand[t - 1].oct = (int)((dd[0] >= 0) << 2 | (dd[1] >= 0) << 1 | (dd[2] >= 0));
+                for (int d = 0; d < 3; ++d)
+                    coff[3 * (size_t)(t - 1) + d] = (int64_t)c->icoord[3 * v + d] - (int64_t)c->icoord[3 * y0 + d];
+                cidx[t - 1] = v;
             }
-            qsort(cand, (size_t)nc, sizeof(cand_t), cmp_cand);
             /* target sizes m_target, m_target + 2, ... up to OR_MMAX (reading R9) */
             int last_k = (k == c->ring_max);
             for (int mt = M; mt <= OR_MMAX && !done; mt += 2) {
-                /* octant criterion (reading R4): two nearest per octant first, then
-                 * the nearest remaining up to mt, then every candidate tied with
-                 * the last one filled (at most OR_MMAX in all) */
-                int taken[8] = {0}, m = 0;
-                int8_t pick[4096];
-                int8_t *pk = nc <= 4096 ? pick : (int8_t *)xcalloc((size_t)nc, 1);
-                for (int t = 0; t < nc; ++t) {
-                    pk[t] = 0;
-                    if (taken[cand[t].oct] < 2) { taken[cand[t].oct]++; pk[t] = 1; m++; }
-                }
-                int64_t cut = -1;
-                for (int t = 0; t < nc && m < mt; ++t) if (!pk[t]) { pk[t] = 1; m++; cut = cand[t].d2; }
-                for (int t = 0; t < nc && m < OR_MMAX; ++t) if (!pk[t] && cand[t].d2 == cut) { pk[t] = 1; m++; }
-                int64_t dint[OR_MMAX * 3];
                 int32_t ids[OR_MMAX];
-                int s = 0;
-                for (int t = 0; t < nc && s < m; ++t) {
-                    if (!pk[t]) continue;
-                    ids[s] = cand[t].idx;
+                int m = or_select(nc, coff, cidx, mt, ids);
+                if (m < 0) { status = OR_E_NOMEM; break; }
+                int64_t dint[OR_MMAX * 3];
+                for (int s = 0; s < m; ++s)
                     for (int d = 0; d < 3; ++d)
                         dint[3 * s + d] = (int64_t)c->icoord[3 * ids[s] + d] - (int64_t)c->icoord[3 * y0 + d];
-                    ++s;
-                }
-                if (pk != pick) free(pk);
                 double P[OR_NCOL * OR_MMAX], lp[OR_MMAX], ld, rr;
                 int bad = or_wls(m, dint, unit, c->weight_c, P, lp, &ld, &rr);
                 /* R8: rank deficient, R9: Laplacian diagonal not negative */
@@ -736,7 +748,7 @@ int or_stencils(or_ctx *c) {
             status = OR_E_STENCIL;
         }
     }
-    free(mark); free(list); free(cand);
+    free(mark); free(list); free(coff); free(cidx);
     return status;
 }
 

@@ -91,3 +91,37 @@ def test_backward_matches_finite_differences(system):
             tm = theta.copy(); tm[i] -= eps
             fd = (mpnn.loss_and_grad(tp, Ah, F, P, b)[0][0] - mpnn.loss_and_grad(tm, Ah, F, P, b)[0][0]) / (2 * eps)
             assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (name, i, fd, g[i])
+
+
+def _frac_table():
+    import os
+    from fractions import Fraction
+    rows = {"a": [], "node": [], "p": [], "f": []}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "mpnn_features_4node.txt")):
+        t = line.split("#")[0].split()
+        if t:
+            rows[t[0]].append([float(Fraction(v)) for v in t[1:]])
+    return {k: np.array(v) for k, v in rows.items()}
+
+
+def test_features_of_hand_made_system():
+    """Every feature column (fixture tests/golden/mpnn_features_4node.txt):
+    a 4-node system whose aggregation weights, offsets, level jumps and
+    right-hand side were worked out by hand.  Row and column sums, the
+    symmetrised graph, the row-normalised aggregation, offsets scaled by the
+    receiving node's own cell edge, and the level offset's direction all
+    differ between right and wrong readings here."""
+    import scipy.sparse as sp
+    g = _frac_table()
+    n = 4
+    r, c, v = g["a"][:, 0].astype(int), g["a"][:, 1].astype(int), g["a"][:, 2]
+    Ah = (sp.csr_matrix((v, (r, c)), shape=(n, n)) + sp.identity(n)).tocsr()
+    nd = g["node"]
+    F, P = mpnn.features(Ah, nd[:, 1:4], nd[:, 4].astype(np.int8), nd[:, 5], nd[:, 6], 2.0)
+    want_P = np.zeros((n, n))
+    want_P[g["p"][:, 0].astype(int), g["p"][:, 1].astype(int)] = g["p"][:, 2]
+    assert np.allclose(P.toarray(), want_P, rtol=0, atol=1e-15)
+    want = g["f"][:, 1:].copy()
+    want[:, 2:7] = np.sign(want[:, 2:7]) * np.log1p(np.abs(want[:, 2:7]))
+    assert F.shape == (n, mpnn.NF)
+    assert np.allclose(F, want, rtol=1e-14, atol=1e-15), np.abs(F - want).max(axis=0)

@@ -51,7 +51,6 @@ def _gaussian_errors(depth, sig):
     return e_phi, e_e
 
 
-@pytest.mark.slow
 def _paper_orders():
     """Orders of Table convergence_order (fixture tests/golden/convergence_order_table.txt)."""
     rows = []
@@ -62,6 +61,7 @@ def _paper_orders():
     return np.array(rows)
 
 
+@pytest.mark.slow
 def test_second_order_convergence_without_mc_noise():
     """Sections 3.3 and 5: with exact cell integrals the second-order method
     converges at order ~2 in both phi and grad phi; every observed order must
