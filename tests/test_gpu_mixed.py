@@ -1,7 +1,8 @@
 """The mixed-precision form against the FP64 oracle.
 
-FP32 stencils (with FP64 refactorisation of blocks whose condition estimate
-exceeds 1e3) and FP32 GMRES iterations inside an FP64 iterative-refinement
+FP32 stencils (with FP64 refactorisation of blocks whose FP32 condition
+estimate min|R_ii|/max|R_ii| is below fp32_rcond_min, 1e-3 by default) and
+FP32 GMRES iterations inside an FP64 iterative-refinement
 loop.  Integer results stay bit-exact (the selection is integer arithmetic
 and the accept/reject tests agree unless a value sits on a threshold); the
 fields must match the FP64 oracle within a relative L2 of 1e-6 (FP32
@@ -94,3 +95,42 @@ def test_polynomial_preconditioner_matches_oracle(precision, tol):
     ap1.deposit(q=_t(q), rtol=rtol)
     _, ip1 = ap1.solve(rtol=rtol)
     assert ip["iters"] * 4 < ip1["iters"]
+
+
+@pytest.mark.parametrize("rcond_min", [0.05, 2.0])
+def test_fp64_refactorisation_of_uncertified_blocks(rcond_min):
+    """Mixed form: a block whose FP32 condition estimate falls below
+    fp32_rcond_min is refactorised in FP64.  Raising the limit from 1e-3 sends
+    some (0.05) or every (2, above any ratio) block down that branch; each such
+    row then carries FP64 accuracy (1e-11 of the row's largest weight, like
+    the FP64 form) where FP32 rows agree only to ~1e-6, and the fields still
+    match the FP64 oracle within 1e-6."""
+    from paper_1603_04039_gb300 import APCloud
+    n, depth, c = 100000, 6, 0.5
+    x, y, z, q = inputs.beam_with_halo(n, 2)
+    ap = APCloud(max_depth=depth, c_refine=c, precision="mixed", fp32_rcond_min=rcond_min)
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    nfp64 = ap.sizes()["fp64_stencils"]
+    o = oracle.Oracle(max_depth=depth, c_refine=c)
+    o.build(x, y, z)
+    w = o.stencils()
+    g = {k: v.cpu().numpy() for k, v in ap.get_stencils().items()}
+    assert np.array_equal(g["nbr"], w["nbr"]) and np.array_equal(g["m"], w["m"])
+    dscale = np.abs(w["D"]).max(axis=(1, 2))
+    derr = np.abs(g["D"] - w["D"]).max(axis=(1, 2)) / dscale
+    exact = int(np.sum(derr <= 1e-11))
+    if rcond_min >= 1.0:
+        assert nfp64 == ap.n_int and exact == ap.n_int
+    else:
+        assert 0 < nfp64 < ap.n_int
+        assert exact >= nfp64
+        assert np.all(derr <= 1e-5)
+    rho, ir = ap.deposit(q=_t(q), rtol=1e-10)
+    phi, ip = ap.solve(rtol=1e-10)
+    php, ex, ey, ez = ap.gather_field()
+    ref = o.run(x, y, z, q=q, rtol=1e-12)
+    assert rel(phi.cpu().numpy(), ref["phi"]) < 1e-6
+    assert rel(php.cpu().numpy(), ref["phi_p"]) < 1e-6
+    for a, b in ((ex, ref["ex"]), (ey, ref["ey"]), (ez, ref["ez"])):
+        assert rel(a.cpu().numpy(), b) < 1e-6
