@@ -67,13 +67,19 @@ typedef struct {
     double poisson_c;    /* c in Lap phi = c rho (Eq. Poisson), 1 in Section 5 */
     int restart;         /* GMRES restart length, 1..64 */
     int precision;       /* 0 = FP64 throughout; 1 = mixed: FP32 WLS stencils with FP64
-                            refactorisation of blocks whose condition estimate exceeds 1e3,
+                            refactorisation of blocks the FP32 factorisation cannot certify
+                            (fp32_rcond_min below),
                             FP32 GMRES iterations inside an FP64 iterative-refinement loop
                             (FP64 residual and solution), FP64 charge sums and gather */
     int poly_degree;     /* right preconditioner of GMRES: 1 = Jacobi; d > 1 = Jacobi-Neumann
                             polynomial omega sum_{i<d} (I - omega D^-1 A)^i, i.e. d damped
                             Jacobi sweeps per Arnoldi step (1..32) */
     double poly_omega;   /* damping omega of those sweeps, 0 < omega < 2 */
+    double fp32_rcond_min; /* mixed form: a stencil block whose FP32 factorisation gives a
+                              condition estimate min|R_ii| / max|R_ii| below this value (or
+                              fails) is refactorised in FP64; 0..2, default 1e-3 (FP32
+                              Cholesky QR squares the condition number).  apcloud_get_sizes
+                              counts those blocks. */
 } apcloud_params;
 
 /* Optional device allocator; NULL selects cudaMallocAsync/cudaFreeAsync on
@@ -94,7 +100,7 @@ typedef struct apcloud_ctx apcloud_ctx;
 
 /* Fills *p with the defaults: domain [-1,1]^3, max_depth 6, c_refine 1,
  * m_target 20, ring_max 5, weight_c 4, poisson_c 1, restart 30, FP64,
- * Jacobi preconditioning (poly_degree 1, poly_omega 0.7). */
+ * Jacobi preconditioning (poly_degree 1, poly_omega 0.7), fp32_rcond_min 1e-3. */
 void apcloud_default_params(apcloud_params *p);
 
 /* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy
@@ -217,21 +223,32 @@ apcloud_status apcloud_matvec(apcloud_ctx *ctx, int which, const double *d_x, do
 apcloud_status apcloud_solve_system(apcloud_ctx *ctx, int which, const double *d_b, double *d_x, double rtol,
                                     int max_iter, apcloud_solve_info *info);
 
-/* Allocation-free variant of apcloud_solve_system, for callers that may not
- * allocate memory once their setup is done: code running inside CUDA stream
- * capture or under a memory manager that forbids cudaMalloc, real-time loops
- * with a fixed memory budget, or hosts that own every allocation themselves.
- * The paper has no counterpart; this is a deployment convenience.
- * Same arguments and results as apcloud_solve_system, but the Krylov basis,
- * work vectors, reduction partials and device state live in one file-scope
- * device array of 20 MiB that every GPU loading the library holds until the
- * process exits, so the call allocates nothing (timers are ignored during it).
+/* Allocation-free GMRES solve, for callers that cannot allocate device
+ * memory once their setup is done: a host whose device memory is all handed
+ * out up front (a fixed budget, or a memory manager that owns every byte of
+ * the device and rejects cudaMalloc), or a real-time loop where a pool
+ * growing or a cudaMalloc stalling the device is not acceptable.  The paper
+ * has no counterpart; this is a deployment convenience.
+ * It solves B x = b (which = 0) or A x = b (which = 1) by FP64 GMRES(restart)
+ * with Jacobi preconditioning, one Krylov space and one stopping test
+ * ||b - A x|| <= rtol ||b||: the algorithm apcloud_solve_system runs in an
+ * FP64 single-beam context with poly_degree 1, giving the same iterations and
+ * results there.  Other contexts (precision 1, poly_degree > 1, or a batch of
+ * beams) return APCLOUD_E_INVALID.  The Krylov basis, work vectors,
+ * reduction partials and device state live in one file-scope device array
+ * of 20 MiB, which every GPU that loads the library holds until the process
+ * exits; the call allocates nothing and kernel timers are ignored during it.
  * Limits: at most 65536 nodes (interior + boundary) and restart <= 30;
- * larger problems return APCLOUD_E_INVALID.  The first call on a device
- * resolves the array's device address (cudaGetSymbolAddress) and must not be
- * made during stream capture.  All calls share the array: two calls whose
- * work overlaps on the GPU (other streams, other contexts, other threads)
- * race and give undefined results.  Synchronises the context stream. */
+ * larger problems return APCLOUD_E_INVALID.  The context's device must be
+ * the current device (APCLOUD_E_INVALID otherwise).  The first call on a
+ * device also looks up the array's device address (cudaGetSymbolAddress).
+ * The call reads the residual back to the host once per restart cycle, so it
+ * synchronises the context stream every cycle and must not be called while
+ * that stream is being captured into a CUDA graph.  All calls share the one
+ * array: two calls whose work overlaps on the GPU (other streams, other
+ * contexts, other host threads) race and give undefined results; each call
+ * clears the state it needs, since the array keeps the previous call's
+ * contents. */
 apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *ctx, int which, const double *d_b, double *d_x,
                                             double rtol, int max_iter, apcloud_solve_info *info);
 

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import sys
 import threading
 
 import numpy as np
@@ -39,7 +40,7 @@ class Params(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("max_depth", C.c_int), ("c_refine", C.c_double),
                 ("m_target", C.c_int), ("ring_max", C.c_int), ("weight_c", C.c_double),
                 ("poisson_c", C.c_double), ("restart", C.c_int), ("precision", C.c_int),
-                ("poly_degree", C.c_int), ("poly_omega", C.c_double)]
+                ("poly_degree", C.c_int), ("poly_omega", C.c_double), ("fp32_rcond_min", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -47,6 +48,58 @@ class SolveInfo(C.Structure):
 
     def as_dict(self):
         return {"iters": self.iters, "restarts": self.restarts, "relres": self.relres}
+
+
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class Allocator(C.Structure):
+    """apcloud_allocator: alloc(bytes, stream, user) / free(ptr, stream, user)."""
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", C.c_void_p)]
+
+
+class TorchAllocator:
+    """The context's device allocator backed by PyTorch's caching allocator, so
+    the library's buffers come from (and return to) the same pool as the
+    caller's tensors, on the context's stream.  Counts its calls; `fail_at`
+    (1-based) makes that allocation call report failure instead (tests of the
+    out-of-memory path)."""
+
+    def __init__(self, device, fail_at=None):
+        self.device = torch.device(device).index or 0
+        self.fail_at = fail_at
+        self.allocs = 0
+        self.frees = 0
+        self.live = {}
+        self._cb_alloc = _ALLOC_FN(self._alloc)
+        self._cb_free = _FREE_FN(self._free)
+        self.struct = Allocator(self._cb_alloc, self._cb_free, None)
+
+    @property
+    def live_bytes(self):
+        return sum(self.live.values())
+
+    def _alloc(self, nbytes, stream, user):
+        self.allocs += 1
+        if self.fail_at is not None and self.allocs == self.fail_at:
+            return None
+        try:
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), device=self.device, stream=int(stream or 0))
+        except Exception:   # out of memory: the library reports APCLOUD_E_NOMEM
+            return None
+        self.live[p] = int(nbytes)
+        return p
+
+    def _free(self, ptr, stream, user):
+        if not ptr:
+            return
+        self.frees += 1
+        self.live.pop(ptr, None)
+        try:
+            torch.cuda.caching_allocator_delete(ptr)
+        except Exception:
+            pass
 
 
 def load():
@@ -172,7 +225,10 @@ class APCloud:
 
     def __init__(self, lo=-1.0, hi=1.0, max_depth=6, c_refine=1.0, m_target=20, ring_max=5, weight_c=4.0,
                  poisson_c=1.0, restart=30, precision="fp64", poly_degree=1, poly_omega=0.7, device="cuda:0",
-                 stream=None):
+                 stream=None, allocator="torch", fp32_rcond_min=1e-3):
+        """allocator: "torch" (default) gives the context PyTorch's caching
+        allocator; None selects the library's own cudaMallocAsync pool; a
+        TorchAllocator instance is used as given."""
         lib = load()
         self._lib = lib
         self.device = torch.device(device)
@@ -185,12 +241,17 @@ class APCloud:
         p.weight_c, p.poisson_c, p.restart = float(weight_c), float(poisson_c), int(restart)
         p.precision = {"fp64": 0, "mixed": 1}[precision]
         p.poly_degree, p.poly_omega = int(poly_degree), float(poly_omega)
+        p.fp32_rcond_min = float(fp32_rcond_min)
         self.params = p
         with torch.cuda.device(self.device):
             s = stream if stream is not None else torch.cuda.current_stream(self.device)
             self.stream = s
             ctx = C.c_void_p()
-            st = lib.apcloud_create(C.byref(p), None, C.c_void_p(s.cuda_stream), C.byref(ctx))
+            if allocator == "torch":
+                allocator = TorchAllocator(self.device)
+            self.allocator = allocator   # keeps the callbacks alive as long as the context
+            a = C.byref(allocator.struct) if allocator is not None else None
+            st = lib.apcloud_create(C.byref(p), a, C.c_void_p(s.cuda_stream), C.byref(ctx))
         if st != 0:
             raise APCloudError(st, "apcloud_create failed")
         self._ctx = ctx
@@ -204,6 +265,10 @@ class APCloud:
             self._ctx = None
 
     def __del__(self):
+        # at interpreter exit the allocator's Python callbacks may be gone: leave
+        # the buffers to the process teardown
+        if sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:

@@ -121,6 +121,7 @@ void free_graphs(apcloud_ctx *c) {
     for (GraphEntry *g : c->graphs) destroy_entry(g);
     c->graphs.clear();
     c->last_replayed = nullptr;
+    c->last_stepped = nullptr;
 }
 
 GraphEntry *find_graph(apcloud_ctx *c, const GraphKey &key) {
@@ -130,10 +131,12 @@ GraphEntry *find_graph(apcloud_ctx *c, const GraphKey &key) {
 }
 
 GraphEntry *begin_capture(apcloud_ctx *c, const GraphKey &key) {
-    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        c->cap_stream = nullptr;
-        cudaGetLastError();
-        return nullptr;
+    for (cudaStream_t *ps : {&c->cap_stream, &c->body_stream}) {
+        if (!*ps && cudaStreamCreateWithFlags(ps, cudaStreamNonBlocking) != cudaSuccess) {
+            *ps = nullptr;
+            cudaGetLastError();
+            return nullptr;
+        }
     }
     GraphEntry *g = new GraphEntry;
     g->key = key;
@@ -146,15 +149,86 @@ GraphEntry *begin_capture(apcloud_ctx *c, const GraphKey &key) {
         delete g;
         return nullptr;
     }
+    // one condition per Arnoldi step, created on the graph being captured and
+    // reset to 0 (skip) at every replay
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const int nstep = key.jmax > 0 ? key.jmax : 0;
+    g->cond.assign(nstep, cudaGraphConditionalHandle{});
+    g->step_kernels.assign(nstep, 0);
+    if (cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &graph) != cudaSuccess || !graph) g->broken = true;
+    for (int j = 1; j < nstep && !g->broken; ++j)
+        if (cudaGraphConditionalHandleCreate(&g->cond[j], graph, 0, cudaGraphCondAssignDefault) != cudaSuccess)
+            g->broken = true;
     c->capturing = g;
     return g;
 }
 
+void count_captured(apcloud_ctx *c) {
+    GraphEntry *g = c->capturing;
+    if (g->cur_step > 0) g->step_kernels[g->cur_step]++;
+    else g->kernels++;
+}
+
+// IF node on cond[j] after everything captured so far; the launches that
+// follow go to its body (captured on the body stream) until end_step
+void begin_step(apcloud_ctx *c, int j) {
+    GraphEntry *g = c->capturing;
+    if (!g || j < 1 || j >= (int)g->cond.size() || g->broken) return;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(c->s, &cs, nullptr, &graph, &deps, nullptr, &nd) != cudaSuccess || !graph) {
+        g->broken = true;
+        return;
+    }
+    cudaGraphNodeParams p = {cudaGraphNodeTypeConditional};
+    p.conditional.handle = g->cond[j];
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, deps, nullptr, nd, &p) != cudaSuccess ||
+        cudaStreamUpdateCaptureDependencies(c->s, &node, nullptr, 1, cudaStreamSetCaptureDependencies) !=
+            cudaSuccess ||
+        cudaStreamBeginCaptureToGraph(c->body_stream, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        g->broken = true;
+        return;
+    }
+    std::swap(c->s, c->body_stream);
+    g->cur_step = j;
+}
+
+void end_step(apcloud_ctx *c) {
+    GraphEntry *g = c->capturing;
+    if (!g || g->cur_step < 1) return;
+    cudaGraph_t body = nullptr;
+    if (cudaStreamEndCapture(c->s, &body) != cudaSuccess) g->broken = true;
+    std::swap(c->s, c->body_stream);
+    g->cur_step = -1;
+}
+
+cudaGraphConditionalHandle next_step_cond(const apcloud_ctx *c, int j) {
+    const GraphEntry *g = c->capturing;
+    if (!g || j + 1 >= (int)g->cond.size()) return cudaGraphConditionalHandle{};
+    return g->cond[j + 1];
+}
+
+void count_replayed_steps(apcloud_ctx *c, int je) {
+    GraphEntry *g = c->last_stepped;
+    c->last_stepped = nullptr;
+    if (!g) return;
+    for (int j = 1; j < je && j < (int)g->step_kernels.size(); ++j) c->launches += g->step_kernels[j];
+}
+
 GraphEntry *end_capture(apcloud_ctx *c, GraphEntry *g, apcloud_status st) {
+    if (g->cur_step > 0) end_step(c);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(c->s, &graph);
     std::swap(c->s, c->cap_stream);
     c->capturing = nullptr;
+    if (g->broken) e = cudaErrorStreamCaptureInvalidated;
     if (st >= 0 && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g->exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (st < 0 || e != cudaSuccess || !g->exec) {
@@ -168,6 +242,8 @@ GraphEntry *end_capture(apcloud_ctx *c, GraphEntry *g, apcloud_status st) {
         size_t old = 0;
         for (size_t i = 1; i < c->graphs.size(); ++i)
             if (c->graphs[i]->last_use < c->graphs[old]->last_use) old = i;
+        if (c->last_stepped == c->graphs[old]) c->last_stepped = nullptr;
+        if (c->last_replayed == c->graphs[old]) c->last_replayed = nullptr;
         destroy_entry(c->graphs[old]);
         c->graphs.erase(c->graphs.begin() + old);
     }
@@ -179,6 +255,7 @@ apcloud_status launch_graph(apcloud_ctx *c, GraphEntry *g) {
     g->last_use = ++c->graph_clock;
     APC_CUDA(c, cudaGraphLaunch(g->exec, c->s));
     c->launches += g->kernels;
+    c->last_stepped = g;
     c->graph_replays++;
     c->last_replayed = g->ev.empty() ? nullptr : g;
     return APCLOUD_OK;
@@ -248,6 +325,10 @@ static apcloud_status validate(const apcloud_params *p, char *msg, size_t len) {
     if (p->restart < 1 || p->restart > MAX_RESTART) { snprintf(msg, len, "restart must be 1..64"); return APCLOUD_E_INVALID; }
     if (p->poly_degree < 1 || p->poly_degree > 32) { snprintf(msg, len, "poly_degree must be 1..32"); return APCLOUD_E_INVALID; }
     if (!(p->poly_omega > 0 && p->poly_omega < 2)) { snprintf(msg, len, "poly_omega must be in (0, 2)"); return APCLOUD_E_INVALID; }
+    if (!(p->fp32_rcond_min >= 0 && p->fp32_rcond_min <= 2)) {
+        snprintf(msg, len, "fp32_rcond_min must be in [0, 2]");
+        return APCLOUD_E_INVALID;
+    }
     if (p->precision != 0 && p->precision != 1) {
         snprintf(msg, len, "precision must be 0 (FP64) or 1 (mixed)");
         return APCLOUD_E_INVALID;
@@ -274,6 +355,7 @@ void apcloud_default_params(apcloud_params *p) {
     p->precision = 0;
     p->poly_degree = 1;
     p->poly_omega = 0.7;
+    p->fp32_rcond_min = 1e-3;
 }
 
 apcloud_status apcloud_create(const apcloud_params *params, const apcloud_allocator *alloc, void *stream,
@@ -290,6 +372,11 @@ apcloud_status apcloud_create(const apcloud_params *params, const apcloud_alloca
     c->P = *params;
     if (alloc) { c->A = *alloc; c->default_alloc = false; }
     c->s = (cudaStream_t)stream;
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return APCLOUD_E_CUDA;
+    }
     if (cudaMallocHost(&c->h_pinned, 4096) != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -311,7 +398,7 @@ void apcloud_destroy(apcloud_ctx *c) {
     DBuf *bufs[] = {&c->key[0], &c->key[1], &c->val[0], &c->val[1], &c->ucell[0], &c->ucell[1], &c->ustart[0],
                     &c->ustart[1], &c->opened, &c->cand[0], &c->cand[1], &c->cval[0], &c->cval[1], &c->flags,
                     &c->scan, &c->scan_blk, &c->lkey, &c->lval, &c->leaf_anchor, &c->leaf_level, &c->leaf_first,
-                    &c->leaf_count, &c->node_ic, &c->bowner, &c->bface, &c->bidx, &c->adj, &c->nbr, &c->msz,
+                    &c->leaf_count, &c->pleaf, &c->spos, &c->qsort, &c->node_ic, &c->bowner, &c->bface, &c->bidx, &c->adj, &c->nbr, &c->msz,
                     &c->ring, &c->lap, &c->lapd, &c->D, &c->rcond, &c->slice_w, &c->slice_off, &c->ell_col,
                     &c->ell_A, &c->ell_B, &c->dA, &c->dB, &c->V, &c->w0, &c->w1, &c->u, &c->b, &c->partial,
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->tmp, &c->derr, &c->dsmall,
@@ -327,6 +414,7 @@ void apcloud_destroy(apcloud_ctx *c) {
     cudaStreamSynchronize(c->s);
     free_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->body_stream) cudaStreamDestroy(c->body_stream);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;

@@ -5,9 +5,13 @@
 // Node pass: one thread per node walks its ELL row (the stencil neighbours in
 // order) and the derivative operator stored with nodes fastest, so the loads
 // of a warp are contiguous.  Particle pass: one thread per particle in the
-// caller's order recomputes the particle's Morton key, finds its leaf by
-// binary search over the Morton-ordered leaf anchors (the leaves partition
-// the key space), and writes phi and E coalesced -- no permutation is read.
+// caller's order reads the particle's leaf (recorded when the tree was
+// built), its position, the leaf's centre and its record (potential and
+// derivatives), and writes phi and E coalesced; the particle streams bypass L2
+// retention so the node records stay cached.  Interpolation at arbitrary
+// points (no recorded leaf) recomputes the point's Morton key and finds its
+// leaf by binary search over the Morton-ordered leaf anchors (the leaves
+// partition the key space).
 #include <cmath>
 
 #include "internal.cuh"
@@ -53,6 +57,67 @@ __device__ __forceinline__ int leaf_of(const uint64_t *anchor, int n, uint64_t v
     return lo - 1;
 }
 
+// Second-order Taylor expansion about the leaf centre (Section 3.2 step 3):
+// phi_p = phi + g.r + r.H.r / 2, E_p = g + H r (E = grad phi, Section 2).
+__device__ __forceinline__ void taylor(const double *__restrict__ nf, int j, double r0, double r1, double r2,
+                                       double &php, double &ex, double &ey, double &ez) {
+    const double2 *f2 = reinterpret_cast<const double2 *>(nf + (int64_t)j * NF);
+    const double2 a = f2[0], b = f2[1], c = f2[2], d = f2[3], e = f2[4];
+    // a = (phi, fx), b = (fy, fz), c = (fxx, fxy), d = (fxz, fyy), e = (fyz, fzz)
+    const double hr0 = c.x * r0 + c.y * r1 + d.x * r2;
+    const double hr1 = c.y * r0 + d.y * r1 + e.x * r2;
+    const double hr2 = d.x * r0 + e.x * r1 + e.y * r2;
+    const double g0 = a.y, g1 = b.x, g2 = b.y;
+    php = a.x + (g0 * r0 + g1 * r1 + g2 * r2) + 0.5 * (r0 * hr0 + r1 * hr1 + r2 * hr2);
+    ex = g0 + hr0;
+    ey = g1 + hr1;
+    ez = g2 + hr2;
+}
+
+// The same expansion with the corrections (g.r, H r, r.H.r) in FP32 around the
+// FP64 node potential: the mixed form, whose node derivatives carry FP32
+// accuracy already (FP32 stencils), so FP32 terms cost no accuracy there and
+// keep the particle pass off the slow FP64 pipe.
+__device__ __forceinline__ void taylor_f32(const double *__restrict__ nf, int j, float r0, float r1, float r2,
+                                           double &php, double &ex, double &ey, double &ez) {
+    const double2 *f2 = reinterpret_cast<const double2 *>(nf + (int64_t)j * NF);
+    const double2 a = f2[0], b = f2[1], c = f2[2], d = f2[3], e = f2[4];
+    const float fxx = (float)c.x, fxy = (float)c.y, fxz = (float)d.x, fyy = (float)d.y, fyz = (float)e.x,
+                fzz = (float)e.y;
+    const float g0 = (float)a.y, g1 = (float)b.x, g2 = (float)b.y;
+    const float hr0 = fmaf(fxz, r2, fmaf(fxy, r1, fxx * r0));
+    const float hr1 = fmaf(fyz, r2, fmaf(fyy, r1, fxy * r0));
+    const float hr2 = fmaf(fzz, r2, fmaf(fyz, r1, fxz * r0));
+    const float corr = fmaf(g2, r2, fmaf(g1, r1, g0 * r0)) + 0.5f * fmaf(r2, hr2, fmaf(r1, hr1, r0 * hr0));
+    php = a.x + (double)corr;
+    ex = (double)(g0 + hr0);
+    ey = (double)(g1 + hr1);
+    ez = (double)(g2 + hr2);
+}
+
+template <bool F32>
+__global__ void __launch_bounds__(256) k_gather_leaf(
+    const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z, int64_t n,
+    double lo0, double lo1, double lo2, double unit, const int32_t *__restrict__ pleaf, const int4 *__restrict__ ic,
+    const double *__restrict__ nf, double *__restrict__ php, double *__restrict__ ex, double *__restrict__ ey,
+    double *__restrict__ ez) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = __ldcs(pleaf + i);
+    const double p0 = __ldcs(x + i), p1 = __ldcs(y + i), p2 = __ldcs(z + i);
+    const int4 q = ic[j];
+    const double r0 = p0 - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
+    const double r1 = p1 - __dadd_rn(lo1, __dmul_rn((double)q.y, unit));
+    const double r2 = p2 - __dadd_rn(lo2, __dmul_rn((double)q.z, unit));
+    double v, gx, gy, gz;
+    if (F32) taylor_f32(nf, j, (float)r0, (float)r1, (float)r2, v, gx, gy, gz);
+    else taylor(nf, j, r0, r1, r2, v, gx, gy, gz);
+    if (php) __stcs(php + i, v);
+    if (ex) __stcs(ex + i, gx);
+    if (ey) __stcs(ey + i, gy);
+    if (ez) __stcs(ez + i, gz);
+}
+
 __global__ void k_gather(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
                          int64_t n, double lo0, double lo1, double lo2, double s, int shift, double unit,
                          const int64_t *__restrict__ offs, int nb, int L, const uint64_t *__restrict__ anchor, int n_int, const int4 *__restrict__ ic,
@@ -83,17 +148,12 @@ __global__ void k_gather(const double *__restrict__ x, const double *__restrict_
     const double r0 = p[0] - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
     const double r1 = p[1] - __dadd_rn(lo1, __dmul_rn((double)q.y, unit));
     const double r2 = p[2] - __dadd_rn(lo2, __dmul_rn((double)q.z, unit));
-    const double2 *f2 = reinterpret_cast<const double2 *>(nf + (int64_t)j * NF);
-    const double2 a = f2[0], b = f2[1], c = f2[2], d = f2[3], e = f2[4];
-    // a = (phi, fx), b = (fy, fz), c = (fxx, fxy), d = (fxz, fyy), e = (fyz, fzz)
-    const double hr0 = c.x * r0 + c.y * r1 + d.x * r2;
-    const double hr1 = c.y * r0 + d.y * r1 + e.x * r2;
-    const double hr2 = d.x * r0 + e.x * r1 + e.y * r2;
-    const double g0 = a.y, g1 = b.x, g2 = b.y;
-    if (php) php[i] = a.x + (g0 * r0 + g1 * r1 + g2 * r2) + 0.5 * (r0 * hr0 + r1 * hr1 + r2 * hr2);
-    if (ex) ex[i] = g0 + hr0;
-    if (ey) ey[i] = g1 + hr1;
-    if (ez) ez[i] = g2 + hr2;
+    double v, gx, gy, gz;
+    taylor(nf, j, r0, r1, r2, v, gx, gy, gz);
+    if (php) php[i] = v;
+    if (ex) ex[i] = gx;
+    if (ey) ey[i] = gy;
+    if (ez) ez[i] = gz;
 }
 
 }  // namespace
@@ -106,15 +166,21 @@ apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *e
     APC_LAUNCH(c, K_DERIV, div_up(n, 128), 128, 0, k_derivs, ptr<uint32_t>(c->slice_w), ptr<uint32_t>(c->slice_off),
                ptr<int32_t>(c->ell_col), ptr<double>(c->D), dstride, ptr<double>(c->phi), n, nf);
     const double ext = c->P.hi[0] - c->P.lo[0];
-    const double s = ldexp(1.0, KEY_DEPTH) / ext;
     const double unit = ldexp(ext, -(KEY_DEPTH + 1));
-    APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather, c->px, c->py, c->pz, c->N, c->P.lo[0], c->P.lo[1],
-               c->P.lo[2], s, KEY_DEPTH - c->L, unit, ptr<int64_t>(c->beam_off), c->nbeams, c->L,
-               ptr<uint64_t>(c->leaf_anchor), n, ptr<int4>(c->node_ic), nf, phi_p, ex, ey, ez);
+    if (c->P.precision == 1)
+        APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather_leaf<true>, c->px, c->py, c->pz, c->N,
+                   c->P.lo[0], c->P.lo[1], c->P.lo[2], unit, (const int32_t *)ptr<int32_t>(c->pleaf),
+                   ptr<int4>(c->node_ic), nf, phi_p, ex, ey, ez);
+    else
+        APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather_leaf<false>, c->px, c->py, c->pz, c->N,
+                   c->P.lo[0], c->P.lo[1], c->P.lo[2], unit, (const int32_t *)ptr<int32_t>(c->pleaf),
+                   ptr<int4>(c->node_ic), nf, phi_p, ex, ey, ez);
     // node pass: operator (72 B), column (4 B) and neighbour value (8 B) per
-    // stencil entry plus the 96 B record; particle pass: 24 B in, 32 B out
+    // stencil entry plus the 96 B record; particle pass: leaf index and
+    // position in (28 B), phi and E out (32 B), and each leaf's 96 B record
+    // and 16 B centre once
     account(c, K_DERIV, 84.0 * c->sum_m + 104.0 * n, 19.0 * c->sum_m);
-    account(c, K_GATHER, 56.0 * c->N, 38.0 * c->N);
+    account(c, K_GATHER, 60.0 * c->N + 112.0 * n, 38.0 * c->N);
     return cuda_check(c, cudaGetLastError(), "gather");
 }
 

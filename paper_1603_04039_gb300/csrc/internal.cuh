@@ -34,6 +34,23 @@ struct DBuf {
     size_t bytes = 0;
 };
 
+// Leaves are in Morton order and so are the particles, so the particle ranges
+// [first_j, first_j + count_j) of consecutive leaves tile the key-sorted
+// particles in order.  A warp can own 32 consecutive leaves (lane l holding
+// leaf j0 + l's first particle, INT_MAX past the last leaf) and stream their
+// particles coalesced.  The leaf of sorted particle i within such a group is
+// the last lane whose first is <= i; an empty leaf shares its first with the
+// next leaf and is never chosen.  All 32 lanes must call it.
+__device__ __forceinline__ int group_leaf(int my_first, int i) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int f = __shfl_sync(0xffffffffu, my_first, lo + step);
+        if (f <= i) lo += step;
+    }
+    return lo;
+}
+
 // GMRES bookkeeping kept on the device so that a whole restart cycle runs
 // without host round trips.
 struct GmresState {
@@ -63,10 +80,18 @@ struct GraphKey {
     const void *p[32];
 };
 
+// Arnoldi step j >= 1 of a captured cycle sits in an IF node whose condition
+// (cond[j], reset to 0 at every replay) the last kernel of step j - 1 sets
+// while the cycle's stopping test has not passed, so the steps after it are
+// skipped on the device instead of launched.
 struct GraphEntry {
     GraphKey key;
     cudaGraphExec_t exec = nullptr;
-    int64_t kernels = 0;             // kernel nodes per replay
+    int64_t kernels = 0;             // kernel nodes outside the step bodies (run at every replay)
+    std::vector<int64_t> step_kernels;             // kernel nodes of the body of step j
+    std::vector<cudaGraphConditionalHandle> cond;  // condition of step j's body (j >= 1)
+    int cur_step = -1;               // body being captured (-1: none)
+    bool broken = false;             // a capture step failed: the graph is discarded
     std::vector<cudaEvent_t> ev;     // timing pairs recorded by event nodes
     std::vector<int> kind;
     uint64_t last_use = 0;
@@ -100,6 +125,7 @@ struct apcloud_ctx {
     apcloud_allocator A;
     bool default_alloc = true;
     cudaStream_t s = nullptr;
+    int device = 0;  // device current at apcloud_create; the context's buffers live there
     int stage = 0;  // 0 created, 1 octree, 2 stencils, 3 deposit, 4 solved, 5 gathered
     char err[512] = {0};
     int64_t launches = 0;
@@ -114,11 +140,14 @@ struct apcloud_ctx {
     bool graphs_on = true;
     bool graph_timing_ok = true;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t body_stream = nullptr;   // capture of conditional step bodies
     apc::GraphEntry *capturing = nullptr;
     apc::GraphEntry *last_replayed = nullptr;
+    apc::GraphEntry *last_stepped = nullptr;   // last replayed graph whose step kernels are not counted yet
     std::vector<apc::GraphEntry *> graphs;
     uint64_t graph_clock = 0;
     int64_t graph_replays = 0;
+    bool stopped = false;   // timed direct launches: the cycle's stopping test passed
 
     // particles (caller's device arrays, kept until the next build)
     const double *px = nullptr, *py = nullptr, *pz = nullptr;
@@ -142,6 +171,9 @@ struct apcloud_ctx {
     apc::DBuf ucell[2], ustart[2], opened, cand[2], cval[2], flags, scan, scan_blk, lkey, lval;
     // nodes
     apc::DBuf leaf_anchor, leaf_level, leaf_first, leaf_count, node_ic, bowner, bface, bidx, adj;
+    apc::DBuf pleaf;   // leaf of every particle, in the caller's particle order
+    apc::DBuf spos;    // key-sorted position of every particle, in the caller's order
+    apc::DBuf qsort;   // charges in key-sorted order (deposit)
     apc::DBuf beam_off, leaf_beam, beam_rng, beam_norm, beam_r2, beam_done, node_beam, tile_act;
     apc::DBuf bk_items, bk_ioff, bk_d, bk_i;   // per-beam Krylov spaces of a batch
     apc::DBuf mp[48];   // learned preconditioner: graph, activations, gradients (indices in mpnn.cu)
@@ -180,6 +212,16 @@ namespace apc {
 apcloud_status fail(apcloud_ctx *c, apcloud_status st, const char *fmt, ...);
 apcloud_status cuda_check(apcloud_ctx *c, cudaError_t e, const char *what);
 void *raw_alloc(apcloud_ctx *c, size_t bytes);
+void count_captured(apcloud_ctx *c);
+// inside a capture: the launches up to end_step form the body of an IF node on
+// cond[j]; the condition of step j + 1 (0 when there is none) for the step's
+// last kernel
+void begin_step(apcloud_ctx *c, int j);
+void end_step(apcloud_ctx *c);
+cudaGraphConditionalHandle next_step_cond(const apcloud_ctx *c, int j);
+// kernels of the first je steps' bodies of the last replayed graph, added to
+// the launch count once the host knows je
+void count_replayed_steps(apcloud_ctx *c, int je);
 void raw_free(apcloud_ctx *c, void *p);
 bool ensure_bytes(apcloud_ctx *c, DBuf &b, size_t bytes, bool keep = false);
 template <class T>
@@ -277,7 +319,7 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
             ::apc::timer_begin(c, kind);                                        \
             kern<<<(grid), (block), (smem), (c)->s>>>(__VA_ARGS__);             \
             ::apc::timer_end(c, kind);                                          \
-            if ((c)->capturing) (c)->capturing->kernels++;                      \
+            if ((c)->capturing) ::apc::count_captured(c);                        \
             else (c)->launches++;                                               \
         }                                                                       \
     } while (0)

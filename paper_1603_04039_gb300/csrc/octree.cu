@@ -22,6 +22,8 @@
 // relation crosses from one beam to another.
 #include <cmath>
 
+#include <climits>
+
 #include "internal.cuh"
 
 namespace apc {
@@ -203,6 +205,35 @@ __global__ void k_leaf_geom(const uint64_t *__restrict__ anchor, const uint32_t 
     uint32_t edge = (1u << lev) - 1u;
 #pragma unroll
     for (int f = 0; f < 6; ++f) bflag[f * n + j] = (c[f >> 1] == ((f & 1) ? edge : 0u)) ? 1u : 0u;
+}
+
+// Leaf and key-sorted position of every particle in the caller's order (read
+// by the gather and the deposit, so that neither needs a search or a gather
+// through the permutation): each warp owns 32 consecutive leaves and walks
+// their key-sorted particle range, writing through the permutation.
+__global__ void k_particle_leaf(const int32_t *__restrict__ first, const int32_t *__restrict__ count, int n_leaf,
+                                const uint32_t *__restrict__ perm, int32_t *__restrict__ pleaf,
+                                int32_t *__restrict__ spos) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+    if (j0 >= n_leaf) return;   // the whole warp
+    const int64_t j = j0 + lane;
+    const bool valid = j < n_leaf;
+    const int f = valid ? first[j] : INT_MAX;
+    int e = valid ? f + count[j] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(0xffffffffu, e, o));
+    const int s = __shfl_sync(0xffffffffu, f, 0);
+#pragma unroll 4
+    for (int base = s; base < e; base += 32) {
+        const int i = base + lane;
+        const int k = group_leaf(f, i);
+        if (i < e) {
+            const uint32_t p = __ldcs(perm + i);
+            pleaf[p] = (int32_t)(j0 + k);
+            spos[p] = i;
+        }
+    }
 }
 
 __global__ void k_boundary(const uint32_t *__restrict__ bflag, const uint32_t *__restrict__ bpos, int64_t n,
@@ -459,6 +490,11 @@ apcloud_status build_octree(apcloud_ctx *c, const double *x, const double *y, co
     int4 *ic = ensure<int4>(c, c->node_ic, 7 * nleaf);
     if (!ic) return APCLOUD_E_NOMEM;
     APC_LAUNCH(c, K_TREE, div_up(nleaf, T), T, 0, k_leaf_geom, la, alv, nleaf, L, skeys, n, ll, lf, lc, ic, bfl, lb);
+    int32_t *pl = ensure<int32_t>(c, c->pleaf, nn), *sp = ensure<int32_t>(c, c->spos, nn);
+    if (!pl || !sp) return APCLOUD_E_NOMEM;
+    if (n > 0)
+        APC_LAUNCH(c, K_TREE, div_up(nleaf, 32 * (T / 32)), T, 0, k_particle_leaf, (const int32_t *)lf,
+                   (const int32_t *)lc, (int)nleaf, (const uint32_t *)ptr<uint32_t>(c->val[c->kbuf]), pl, sp);
     APC_TRY(scan_u32(c, bfl, bpos, 6 * nleaf, small + 4));
     uint32_t hb;
     APC_TRY(read_back(c, &hb, small + 4, sizeof hb));

@@ -19,6 +19,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <climits>
+
 #include "internal.cuh"
 
 namespace apc {
@@ -110,25 +112,81 @@ __device__ void final_sums(const double *partial, int nblk, int nk, double *sm, 
 // ---------------------------------------------------------------- deposit
 // Cell-indicator charge assignment (Section 5): Q_j = sum of the charges of
 // the particles in leaf j, rho_M = Q_j / h_j^3; boundary rows copy the owner.
-__global__ void k_deposit(const double *__restrict__ q, double qu, const uint32_t *__restrict__ perm,
-                          const int32_t *__restrict__ first, const int32_t *__restrict__ count,
-                          const int4 *__restrict__ ic, int n_int, double ext, double *__restrict__ rho_m) {
-    int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
-    if (j >= n_int) return;
-    int f = first[j], c = count[j];
+// Two passes, both coalesced on the particle side:
+//  * k_charge_sort, one thread per particle in the caller's order: the
+//    charge goes to its key-sorted position (recorded by the tree build);
+//    the scattered stores land in an array that L2 keeps (evict-last hint)
+//    while the caller's charges stream through (evict-first);
+//  * k_deposit: each warp owns 32 consecutive leaves and streams their
+//    sorted charges in chunks of 32; a segmented scan over the lanes sums
+//    each leaf's charges within a chunk, and the lane ending a leaf's run
+//    adds that partial to the leaf's accumulator in shared memory.
+// The summation order is fixed, so the result does not depend on timing.
+constexpr int DEP_WARPS = 8;
+constexpr int DEP_U = 4;
+
+__global__ void __launch_bounds__(256) k_charge_sort(const double *__restrict__ q, const int32_t *__restrict__ spos,
+                                                     int64_t n, double *__restrict__ qs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint64_t keep;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
+    const double v = __ldcs(q + i);
+    double *dst = qs + __ldcs(spos + i);
+    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(dst), "d"(v), "l"(keep) : "memory");
+}
+
+__global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(
+    const double *__restrict__ qs, double qu, const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+    const int4 *__restrict__ ic, int n_int, double ext, double *__restrict__ rho_m) {
+    __shared__ double acc[DEP_WARPS][32];
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t j0 = ((int64_t)blockIdx.x * DEP_WARPS + wid) * 32;
+    if (j0 >= n_int) return;   // the whole warp
+    const int64_t j = j0 + lane;
+    const bool valid = j < n_int;
+    const int f = valid ? first[j] : INT_MAX;
+    const int cnt = valid ? count[j] : 0;
     double Q;
-    if (q) {
-        double s = 0.0;
-        for (int i = f + lane; i < f + c; i += 32) s += q[perm[i]];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        Q = s;
+    if (!qs) {
+        Q = (double)cnt * qu;
     } else {
-        Q = (double)c * qu;
+        acc[wid][lane] = 0.0;
+        int e = valid ? f + cnt : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(FULL, e, o));
+        const int s = __shfl_sync(FULL, f, 0);
+        __syncwarp();
+        for (int base = s; base < e; base += 32 * DEP_U) {
+            double v[DEP_U];
+#pragma unroll
+            for (int u = 0; u < DEP_U; ++u) {
+                const int i = base + 32 * u + lane;
+                v[u] = i < e ? __ldcs(qs + i) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < DEP_U; ++u) {
+                const int i = base + 32 * u + lane;
+                const bool in = i < e;
+                int k = group_leaf(f, i);
+                if (!in) k = 32;
+                double x = v[u];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const double up = __shfl_up_sync(FULL, x, d);
+                    const int ku = __shfl_up_sync(FULL, k, d);
+                    if (lane >= d && ku == k) x += up;
+                }
+                const int kn = __shfl_down_sync(FULL, k, 1);
+                if (in && (lane == 31 || kn != k)) acc[wid][k] += x;
+                __syncwarp();
+            }
+        }
+        Q = acc[wid][lane];
     }
-    if (lane == 0) {
-        double h = ldexp(ext, -ic[j].w);
+    if (valid) {
+        const double h = ldexp(ext, -ic[j].w);
         rho_m[j] = Q / (h * h * h);
     }
 }
@@ -546,10 +604,13 @@ __global__ void __launch_bounds__(DT) k_gs_dots(const T *__restrict__ V, int64_t
 
 // wraw = w - V h2 ; ||wraw||^2 ; Hessenberg column, Givens rotation and
 // convergence test in the last block (Saad, Algorithms 6.9 / 6.10)
+// In a captured cycle it also sets the condition of the next step's body
+// (set_next): 1 while the stopping test has not passed.
 template <class T>
 __global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t ldv, int nrow, int j,
                                                 const T *__restrict__ w, T *__restrict__ wraw, GmresState *st,
-                                                double *__restrict__ partial, const uint8_t *__restrict__ tact) {
+                                                double *__restrict__ partial, const uint8_t *__restrict__ tact,
+                                                cudaGraphConditionalHandle next, int set_next) {
     typedef typename Vec<T>::type VT;
     constexpr int VN = Vec<T>::n;
     __shared__ T hs[MAX_RESTART];
@@ -600,6 +661,7 @@ __global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t
         if (fabs(st->g[j + 1]) <= st->rtol * st->bnorm || hn == 0.0) st->done = 1;
         st->inv_norm = hn > 0.0 ? 1.0 / hn : 0.0;
         st->ticket = 0;
+        if (set_next) cudaGraphSetConditional(next, st->done ? 0u : 1u);
     }
 }
 
@@ -743,7 +805,7 @@ int stream_blocks(int64_t nrow) {
 
 template <class T>
 void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, int j, T *w, T *wraw, GmresState *st,
-                 double *partial, const uint8_t *tact) {
+                 double *partial, const uint8_t *tact, cudaGraphConditionalHandle next = {}, int set_next = 0) {
     (void)nblk;
     const int nrow = (int)ldv;
     if (pass == 0)
@@ -752,7 +814,7 @@ void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, in
         APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial, tact);
     else
         APC_LAUNCH(c, K_UPDNORM, stream_blocks(ldv), GT, 0, k_gs_norm<T>, V, ldv, nrow, j, (const T *)w, wraw, st,
-                   partial, tact);
+                   partial, tact, next, set_next);
 }
 
 // grid of the streaming reductions (norms, cycle end); the partial buffer
@@ -1009,7 +1071,8 @@ __global__ void __launch_bounds__(BGT) k_bgs_norm(const T *__restrict__ V, int64
 // estimate, stopping test; then (block 0 of a single-block launch) the
 // number of beams still in their cycle decides st->done
 __global__ void __launch_bounds__(256) k_bfinal_norm(int j, BKry bk, GmresState *st,
-                                                     const double *__restrict__ partial) {
+                                                     const double *__restrict__ partial,
+                                                     cudaGraphConditionalHandle next, int set_next) {
     __shared__ int act[256];
     int a = 0;
     if (!st->done) {
@@ -1051,6 +1114,7 @@ __global__ void __launch_bounds__(256) k_bfinal_norm(int j, BKry bk, GmresState 
         __syncthreads();
     }
     if (threadIdx.x == 0 && !st->done && act[0] == 0) st->done = 1;
+    if (threadIdx.x == 0 && set_next) cudaGraphSetConditional(next, st->done ? 0u : 1u);
 }
 
 // per beam: y = H^-1 g (jend x jend, upper triangular after the rotations)
@@ -1225,6 +1289,19 @@ __global__ void k_save_jend(GmresState *st) {
     if (threadIdx.x == 0) st->jlast = st->jend;
 }
 
+// Direct launches with kernel timers on (the roofline pass): the host reads
+// the stopping flag after every Arnoldi step and ends the cycle there, so no
+// launch after the test is timed.  Captured cycles skip those steps on the
+// device instead (IF nodes); untimed direct launches run every step.
+apcloud_status stop_when_done(apcloud_ctx *c, GmresState *st) {
+    c->stopped = false;
+    if (c->capturing || c->timer.mask == 0) return APCLOUD_OK;
+    int done = 0;
+    APC_TRY(read_back(c, &done, &st->done, sizeof done));
+    c->stopped = done != 0;
+    return APCLOUD_OK;
+}
+
 // Per-beam Krylov spaces: the residual that opens a cycle gives every beam its
 // own beta and stopping test (k_bstart).
 template <class T>
@@ -1246,6 +1323,7 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
     const BKry &bk = *K.bk;
     const RowSkip active{bk.nbo, bk.done, bk.binv};
     for (int j = 0; j < jmax; ++j) {
+        begin_step(c, j);
         if (K.pdeg <= 1) {
             APC_SPMV_BS(c, n, APC_SPMV1, sw, so, col, val, n, (const T *)K.wraw, K.w, K.V + (int64_t)j * K.ldv,
                         (const T *)nullptr, st, (double *)nullptr, active);
@@ -1266,7 +1344,11 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
                    (const double *)K.partial);
         APC_LAUNCH(c, K_UPDNORM, bk.nitems, BGT, 0, k_bgs_norm<T>, (const T *)K.V, K.ldv, j, (const T *)K.w, K.wraw,
                    bk, (const GmresState *)st, K.partial);
-        APC_LAUNCH(c, K_UPDNORM, 1, 256, 0, k_bfinal_norm, j, bk, st, (const double *)K.partial);
+        APC_LAUNCH(c, K_UPDNORM, 1, 256, 0, k_bfinal_norm, j, bk, st, (const double *)K.partial,
+                   next_step_cond(c, j), (c->capturing && j + 1 < jmax) ? 1 : 0);
+        end_step(c);
+        APC_TRY(stop_when_done(c, st));
+        if (c->stopped) break;
     }
     APC_LAUNCH(c, K_CYCLE, div_up(bk.nb, 64), 64, 0, k_bsolve_y, bk);
     if (K.pdeg <= 1) {
@@ -1298,6 +1380,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     GmresState *st = K.st;
     if (K.bk) return bcycle_launches<T>(c, val, b, u, K, jmax);
     for (int j = 0; j < jmax; ++j) {
+        begin_step(c, j);
         if (K.pdeg <= 1) {
             APC_SPMV_BS(c, n, APC_SPMV1, sw, so, col, val, n, (const T *)K.wraw, K.w, K.V + (int64_t)j * K.ldv,
                         (const T *)nullptr, st, (double *)nullptr, K.skip);
@@ -1312,7 +1395,11 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
         }
         gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
         gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
-        gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
+        gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact, next_step_cond(c, j),
+                       (c->capturing && j + 1 < jmax) ? 1 : 0);
+        end_step(c);
+        APC_TRY(stop_when_done(c, st));
+        if (c->stopped) break;
     }
     if (K.pdeg <= 1) {
         APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv, u,
@@ -1339,7 +1426,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
 
 template <class T>
 apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const Krylov<T> &K, int jmax, bool graph) {
-    if (graph && c->graphs_on && (c->timer.mask == 0 || c->graph_timing_ok)) {
+    if (graph && c->graphs_on && c->timer.mask == 0) {
         GraphKey key;
         memset(&key, 0, sizeof key);
         key.tsize = (int)sizeof(T);
@@ -1421,6 +1508,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
         harvest_graph_timing(c);
         const int je = tail.jlast;
+        count_replayed_steps(c, je);
         // algorithmic traffic of the launches that did work (values + column index per entry)
         {
             // per Arnoldi step: one product with the full matrix, pdeg - 1 sweeps (FP16
@@ -1463,12 +1551,18 @@ apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform) {
     const int n = c->n_int, nt = c->n_tot;
     double *rm = ensure<double>(c, c->rho_m, nt + 1);
     if (!rm) return APCLOUD_E_NOMEM;
-    const uint32_t *perm = ptr<uint32_t>(c->val[c->kbuf]);
     const double ext = c->P.hi[0] - c->P.lo[0];
-    APC_LAUNCH(c, K_DEPOSIT, div_up(n, 8), 256, 0, k_deposit, q, q_uniform, perm, ptr<int32_t>(c->leaf_first),
-               ptr<int32_t>(c->leaf_count), ptr<int4>(c->node_ic), n, ext, rm);
+    double *qs = nullptr;
+    if (q && c->N > 0) {
+        qs = ensure<double>(c, c->qsort, c->N);
+        if (!qs) return APCLOUD_E_NOMEM;
+        APC_LAUNCH(c, K_DEPOSIT, div_up(c->N, 256), 256, 0, k_charge_sort, q,
+                   (const int32_t *)ptr<int32_t>(c->spos), c->N, qs);
+    }
+    APC_LAUNCH(c, K_DEPOSIT, div_up(n, 32 * DEP_WARPS), 32 * DEP_WARPS, 0, k_deposit, (const double *)qs, q_uniform,
+               ptr<int32_t>(c->leaf_first), ptr<int32_t>(c->leaf_count), ptr<int4>(c->node_ic), n, ext, rm);
     APC_LAUNCH(c, K_DEPOSIT, div_up(c->n_bnd, 256), 256, 0, k_bcopy, ptr<int32_t>(c->bowner), n, c->n_bnd, rm);
-    // permutation and charge per particle, rho_M per node
+    // sorted position and charge per particle, rho_M per node
     account(c, K_DEPOSIT, (q ? 12.0 * c->N : 0.0) + 8.0 * nt, q ? (double)c->N : (double)n);
     return cuda_check(c, cudaGetLastError(), "deposit");
 }
@@ -1777,11 +1871,16 @@ unsigned char *g_noalloc_base[NOALLOC_MAX_DEVICES] = {};
 
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// Device address of the scratch array for the current device (the host-side
-// name of the array is only a stand-in); resolved once per device.
+// Device address of the scratch array on the context's device (the host-side
+// name of the array is only a stand-in); resolved once per device.  The
+// context's device must be current: cudaGetSymbolAddress answers for the
+// current device, and the scratch must sit on the device of the context's
+// matrices and stream.
 apcloud_status noalloc_base(apcloud_ctx *c, unsigned char **out) {
     int dev = 0;
     APC_CUDA(c, cudaGetDevice(&dev));
+    if (dev != c->device)
+        return fail(c, APCLOUD_E_INVALID, "current device %d is not the context's device %d", dev, c->device);
     if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(c, APCLOUD_E_INVALID, "device index %d too large", dev);
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
     if (!g_noalloc_base[dev]) {
@@ -1811,6 +1910,12 @@ extern "C" apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *c, int which
     if (m > NOALLOC_MAX_RESTART)
         return fail(c, APCLOUD_E_INVALID, "restart %d exceeds the limit %d of the allocation-free solve", m,
                     NOALLOC_MAX_RESTART);
+    // it runs one algorithm only: FP64 GMRES with Jacobi on one Krylov space
+    // and one global stopping test; other forms would silently change results
+    if (c->P.precision != 0 || c->P.poly_degree > 1 || c->nbeams > 1)
+        return fail(c, APCLOUD_E_INVALID,
+                    "the allocation-free solve runs FP64 Jacobi GMRES on a single-beam context only "
+                    "(precision %d, poly_degree %d, beams %d)", c->P.precision, c->P.poly_degree, c->nbeams);
     unsigned char *base = nullptr;
     APC_TRY(noalloc_base(c, &base));
     // carve: state | basis | w | wraw | u | partials

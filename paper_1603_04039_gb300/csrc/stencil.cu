@@ -24,7 +24,6 @@ namespace apc {
 
 namespace {
 
-constexpr double FP32_RATIO_MIN = 1e-3;  // condition estimate limit of the FP32 factorisation
 constexpr int ASTR = NCOL;      // row stride of the staged Vandermonde
 
 struct __align__(16) WarpSmem {
@@ -306,7 +305,7 @@ __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
     int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
     int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,
     double *__restrict__ lapd_out, double *__restrict__ D_out, int64_t dstride, double *__restrict__ rcond_out,
-    int fp32_first, int *__restrict__ fp64_count, unsigned *err) {
+    int fp32_first, double fp32_rcond_min, int *__restrict__ fp64_count, unsigned *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem &W = reinterpret_cast<WarpSmem *>(smem_raw)[wid];
@@ -477,12 +476,13 @@ __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
 
         // ---- weighted least squares: FP32 first when asked, FP64 for blocks the
         // FP32 factorisation cannot certify (Cholesky failure or condition
-        // estimate above 1e3, where FP32 Cholesky QR loses its accuracy)
+        // estimate min|R_ii|/max|R_ii| below fp32_rcond_min, by default 1e-3,
+        // where FP32 Cholesky QR loses its accuracy)
         double q[NCOL], lapj = 0.0;
         bool ok = false;
         if (fp32_first) {
             ok = wls_column<float>(W, m, lane, own, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
-            if (ok && rmin_over_rmax < FP32_RATIO_MIN) ok = false;
+            if (ok && rmin_over_rmax < fp32_rcond_min) ok = false;
             if (!ok && lane == 0) atomicAdd(fp64_count, 1);
         }
         if (!ok) ok = wls_column<double>(W, m, lane, own, c0, ic, unit, ec, inv_1mec, q, lapj, rmin_over_rmax);
@@ -625,7 +625,7 @@ apcloud_status launch_stencil(apcloud_ctx *c, int n, double unit, double ec, dou
     }
     APC_LAUNCH(c, K_STENCIL, div_up(n, SW), SW * 32, smem, k_stencil<SW>, ptr<int4>(c->node_ic),
                ptr<int32_t>(c->adj), ptr<int32_t>(c->bowner), n, c->P.m_target, c->P.ring_max, unit, ec, inv_1mec,
-               nbr, msz, ring, lap, lapd, D, dstride, rc, c->P.precision == 1 ? 1 : 0,
+               nbr, msz, ring, lap, lapd, D, dstride, rc, c->P.precision == 1 ? 1 : 0, c->P.fp32_rcond_min,
                reinterpret_cast<int *>(derr + 1), derr);
     return APCLOUD_OK;
 }
