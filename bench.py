@@ -42,8 +42,20 @@ BATCH_WORKLOADS = {
 }
 
 
+_PROBLEMS = {}
+
+
 def make_problem(workload, seed):
-    """(x, y, z, q, offsets or None, max_depth, c_refine, solves per step)"""
+    """(x, y, z, q, offsets or None, max_depth, c_refine, solves per step);
+    the arrays of the last workload drawn are kept for the next call."""
+    key = (workload, seed)
+    if key not in _PROBLEMS:
+        _PROBLEMS.clear()
+        _PROBLEMS[key] = _make_problem(workload, seed)
+    return _PROBLEMS[key]
+
+
+def _make_problem(workload, seed):
     from paper_1603_04039_gb300 import inputs
     if workload in BATCH_WORKLOADS:
         nb, depth, c = BATCH_WORKLOADS[workload]
@@ -63,24 +75,27 @@ def _dist():
     return ws, rank, local
 
 
-def _ncu_traffic(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from a committed ncu summary
-    (a line 'traffic: kernel=... workload=... bytes_per_launch=...'), else None."""
-    d = os.path.join(ROOT, "profiles")
+def _dram_traffic(kind, workload):
+    """DRAM bytes per working launch of kernel kind `kind` on `workload` from
+    the committed record of an ncu capture (profiles/dram_traffic.json), or
+    None.  A record holds the SHA-256 of the source file the kernel was built
+    from; once that file has changed the counters no longer describe the
+    kernel and None is returned."""
+    import hashlib
     try:
-        names = sorted(os.listdir(d))
-    except OSError:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
+            records = json.load(f)
+    except (OSError, ValueError):
         return None
-    for fn in names:
-        if not fn.endswith(".md"):
+    for r in records:
+        if r.get("kind") != kind or r.get("workload") != workload:
             continue
-        for line in open(os.path.join(d, fn)):
-            if not line.startswith("traffic:"):
-                continue
-            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
-            if kv.get("kernel") == kernel and kv.get("workload") == workload:
-                return {"file": "profiles/" + fn, "bytes_per_launch": float(kv["bytes_per_launch"]),
-                        "algorithmic_bytes_per_working_launch": float(kv["algorithmic_bytes_per_working_launch"])}
+        try:
+            with open(os.path.join(ROOT, r["source"]), "rb") as f:
+                sha = hashlib.sha256(f.read()).hexdigest()
+        except OSError:
+            return None
+        return r if sha == r.get("source_sha256") else None
     return None
 
 
@@ -174,10 +189,10 @@ def run_ours(args, ws, rank, local):
         ni, nb = build(ap)
         ap.stencils()
         _, ir = ap.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
-        _, ip = ap.solve(rtol=RTOL, max_iter=MAX_ITER)
+        phi_nodes, ip = ap.solve(rtol=RTOL, max_iter=MAX_ITER)
         ap.gather_field(out)
         info.update(n_int=ni, n_bnd=nb, iters_rho=ir["iters"], iters_phi=ip["iters"], relres_phi=ip["relres"],
-                    status=max(ir["status"], ip["status"]))
+                    status=max(ir["status"], ip["status"]), phi=phi_nodes)
 
     def barrier():
         if ws > 1:
@@ -272,7 +287,7 @@ def run_ours(args, ws, rank, local):
         build(ap64)
         ap64.stencils()
         _, pr = ap64.deposit(q=tq, rtol=RTOL, max_iter=MAX_ITER)
-        _, pp = ap64.solve(rtol=RTOL, max_iter=MAX_ITER)
+        phi64, pp = ap64.solve(rtol=RTOL, max_iter=MAX_ITER)
         ap64.gather_field(ref)
         f1.record(ap64.stream)
         torch.cuda.synchronize()
@@ -325,7 +340,7 @@ def run_ours(args, ws, rank, local):
     # the kernel's arithmetic type sets its ALU peak: in the mixed form the Krylov
     # iterations and the stencil factorisations run in FP32, everything else FP64
     fp32_kinds = {"spmv", "precond_sweep", "gmres_dots", "gmres_update_dots", "gmres_update_norm",
-                  "gmres_cycle_end", "ring_select_wls"}
+                  "gmres_cycle_end", "ring_select_wls", "gather"}
     alu_peak = fp32_peak if (args.precision == "mixed" and dominant in fp32_kinds) else fp64_peak
     alu_name = "FP32" if alu_peak == fp32_peak else "FP64"
     # work per byte decides the bound: above ALU peak / HBM peak the ALU limits
@@ -345,13 +360,15 @@ def run_ours(args, ws, rank, local):
                  "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64/FP32 FMA chains on all SMs "
                                 "(apcloud_measure_fma_peak) in this run",
                  "fp64_peak_tflops": round(fp64_peak, 4), "fp32_peak_tflops": round(fp32_peak, 3)})
-    tr = _ncu_traffic(dominant, args.workload)
+    tr = _dram_traffic(dominant, args.workload)
     if tr:
         roof["traffic"] = tr["bytes_per_launch"]
-        roof["traffic_note"] = ("DRAM read + write of one working launch from an ncu capture (%s); "
-                                "algorithmic bytes of a working launch %.4g; the per-launch average above also "
-                                "counts launches that exit at once after convergence" %
-                                (tr["file"], tr["algorithmic_bytes_per_working_launch"]))
+        roof["traffic_note"] = ("DRAM read + write of one working launch from an ncu capture of this kernel "
+                                "source (%s, %s); algorithmic bytes of that launch %.4g; the per-launch "
+                                "average above also counts launches that exit at once after convergence" %
+                                (tr["summary"], tr["kernel"], tr["algorithmic_bytes_per_launch"]))
+    else:
+        roof["traffic_note"] = "no ncu capture of the current source of this kernel is recorded"
     solves = ws * nsolve * 1000.0 / ms_step
     line = {
         "metric": METRIC, "value": round(solves, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
@@ -380,40 +397,85 @@ def run_ours(args, ws, rank, local):
         "unbatched_same_form": unbatched,
         "stage_ms_by_kernel": {k: round(v[0] / 1, 3) for k, v in solve_kinds.items()},
     }
+    if offs is None:   # node potentials of both forms, judged in the oracle's own system (CPU leg)
+        line["_phi_nodes"] = {args.precision + "_poly%d" % args.poly_degree: info["phi"].cpu().numpy(),
+                              "fp64_jacobi": phi64.cpu().numpy()}
     return line
 
 
 # ---------------------------------------------------------------- oracle
-def oracle_sample(workload, seed=1, gmres_sample=10, gmres_iters_hint=None):
-    """Times the CPU oracle on the workload: the tree, stencils, deposit and
-    gather in full, and `gmres_sample` GMRES iterations of each system, scaled
-    to the iteration counts of a converged solve.  Returns (seconds per solve,
-    description)."""
+def _oracle_counts(workload, seed):
+    """Iterations of the oracle's own converged solve of this workload
+    (oracle/solve_counts.json, written by `python -m oracle.solve_counts`)."""
+    try:
+        with open(os.path.join(ROOT, "oracle", "solve_counts.json")) as f:
+            rec = json.load(f).get("%s/seed%d" % (workload, seed))
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("status_phi") != 0 or rec.get("status_rho") != 0:
+        return None
+    return rec
+
+
+def oracle_sample(workload, seed=1, gpu_phi=None, warm=None):
+    """Times a bounded sample of the CPU oracle's solve of the workload (one
+    core): tree, stencils, deposit, the density solve to convergence, one
+    full GMRES(30) restart cycle of the Poisson solve, and the gather -- all
+    measured.  The Poisson solve is extrapolated from the sampled cycle to the
+    iteration count of the oracle's own converged solve of this workload
+    (oracle/solve_counts.json): every cycle but the last is a full cycle of
+    the same cost, so (cycle time / 30) x iterations slightly overestimates
+    only the last, partial cycle.  gpu_phi (optional): node potentials of the
+    GPU path, whose residual in the oracle's own Poisson system is returned
+    (the systems are judged only when the node sets agree).
+    Returns a dict: seconds per solve (extrapolated, or None without a
+    recorded count), seconds measured, stage seconds, description,
+    relres of gpu_phi."""
     import oracle
     x, y, z, q, offs, depth, c, nsolve = make_problem(workload, seed)
     if offs is not None:
         return oracle_batch_sample(workload, x, y, z, q, offs, depth, c)
+    t0s = time.perf_counter()
     o = oracle.Oracle(max_depth=depth, c_refine=c)
     t = {}
     t0 = time.perf_counter(); o.build(x, y, z); t["build"] = time.perf_counter() - t0
     t0 = time.perf_counter(); o.stencils(); t["stencils"] = time.perf_counter() - t0
     t0 = time.perf_counter(); rhs, _, _ = o.density_rhs(q); t["deposit"] = time.perf_counter() - t0
-    # without a GPU measurement: GMRES(30) + Jacobi needed 3176-3393 iterations on this
-    # workload in FP64 on GB300 (8 for the density system)
-    it_r, it_p = gmres_iters_hint or (8, 3300)
     t0 = time.perf_counter()
-    rho, k_r, _, _ = o.solve_density(rhs, rtol=RTOL, max_iter=min(gmres_sample, it_r))
-    t_r = time.perf_counter() - t0
+    rho, k_r, rr_r, _ = o.solve_density(rhs, rtol=RTOL, max_iter=MAX_ITER)
+    t["solve_rho"] = time.perf_counter() - t0
     t0 = time.perf_counter()
-    phi, k_p, _, _ = o.solve_poisson(rho, rtol=RTOL, max_iter=gmres_sample)
-    t_p = time.perf_counter() - t0
-    t["solve_rho"] = t_r / max(k_r, 1) * it_r
-    t["solve_phi"] = t_p / max(k_p, 1) * it_p
+    phi, k_p, _, _ = o.solve_poisson(rho, rtol=RTOL, max_iter=30)
+    t_cycle = time.perf_counter() - t0
+    t["solve_phi_one_cycle"] = t_cycle
     t0 = time.perf_counter(); o.gather(phi); t["gather"] = time.perf_counter() - t0
-    total = sum(t.values())
-    desc = ("oracle on %s seed %d: tree, stencils, deposit and gather in full; %d+%d GMRES iterations timed and "
-            "scaled to %d+%d (a converged solve)" % (workload, seed, k_r, k_p, it_r, it_p))
-    return total, desc, {k: round(v, 3) for k, v in t.items()}
+    measured = time.perf_counter() - t0s
+    counts = _oracle_counts(workload, seed)
+    out = {"measured_s": measured, "stage_s": {k: round(v, 3) for k, v in t.items()}, "relres_gpu_phi": None}
+    if counts:
+        it_p = counts["iters_phi"]
+        t_phi = t_cycle / max(k_p, 1) * it_p
+        out["s_per_solve"] = sum(v for k, v in t.items() if k != "solve_phi_one_cycle") + t_phi
+        out["sample"] = ("oracle on %s seed %d, one core: tree, stencils, deposit, density solve (%d GMRES "
+                         "iterations, converged), one Poisson GMRES(30) restart cycle (%d iterations) and gather "
+                         "measured (%.1f s); the Poisson solve extrapolated from that cycle to the %d iterations "
+                         "of the oracle's own converged solve of this system (oracle/solve_counts.json): %.1f s"
+                         % (workload, seed, k_r, k_p, measured, it_p, t_phi))
+    else:
+        out["s_per_solve"] = None
+        out["sample"] = ("oracle on %s seed %d, one core: %.1f s measured; no converged oracle solve of this "
+                         "workload is recorded, so no solve time" % (workload, seed, measured))
+    if gpu_phi is not None:
+        sizes = {len(v) for v in gpu_phi.values()}
+        if sizes == {o.n_nodes}:
+            rp, col, val = o.matrix("A")
+            rho_c, _, _, _ = o.solve_density(rhs, rtol=1e-13, max_iter=MAX_ITER, x0=rho)
+            b = o.poisson_rhs(rho_c)
+            out["relres_gpu_phi"] = {k: float(np.linalg.norm(b - np.add.reduceat(val * v[col], rp[:-1])) /
+                                              np.linalg.norm(b)) for k, v in gpu_phi.items()}
+        else:
+            out["relres_gpu_phi"] = "node sets differ: %s GPU, %d oracle" % (sorted(sizes), o.n_nodes)
+    return out
 
 
 def oracle_batch_sample(workload, x, y, z, q, offs, depth, c, n_sample=3):
@@ -436,29 +498,40 @@ def oracle_batch_sample(workload, x, y, z, q, offs, depth, c, n_sample=3):
         t0 = time.perf_counter(); phi, _, _, _ = o.solve_poisson(rho, rtol=RTOL); t["solve_phi"] += time.perf_counter() - t0
         t0 = time.perf_counter(); o.gather(phi); t["gather"] += time.perf_counter() - t0
     scale = float(sizes.sum()) / float(sizes[pick].sum())
-    total = sum(t.values()) * scale
-    desc = ("oracle on %s: full solves of the %d smallest beams (%d particles), scaled by particle count to the "
-            "batch's %d particles (%d beams)" % (workload, n_sample, int(sizes[pick].sum()), int(sizes.sum()),
-                                                 len(sizes)))
-    return total / len(sizes), desc, {k: round(v * scale, 3) for k, v in t.items()}
+    measured = sum(t.values())
+    desc = ("oracle on %s, one core: full solves (GMRES(30) + Jacobi to 1e-10) of the %d smallest beams (%d "
+            "particles) measured (%.1f s), scaled by particle count to the batch's %d particles (%d beams); the "
+            "oracle's cost grows faster than the particle count, so this underestimates it"
+            % (workload, n_sample, int(sizes[pick].sum()), measured, int(sizes.sum()), len(sizes)))
+    return {"s_per_solve": measured * scale / len(sizes), "measured_s": measured,
+            "stage_s": {k: round(v * scale, 3) for k, v in t.items()}, "sample": desc, "relres_gpu_phi": None}
 
 
 def run_reference(args, ws, rank):
+    """The reference arm: the CPU oracle, one core.  Warm-up steps run the
+    oracle's whole solve on the small 1e5-particle workload (loads the
+    library, touches every code path); every timed step is the bounded sample
+    of oracle_sample on the benchmark workload.  value = 1 / (seconds per
+    solve, extrapolated as oracle_sample states); ms_per_step = the wall time
+    a timed step actually took."""
     if rank != 0:
         return None
-    times = []
-    for w in range(args.warmup + args.steps):
-        tot, desc, stages = oracle_sample(args.workload, gmres_sample=5)
-        if w >= args.warmup:
-            times.append(tot)
-    sec = float(np.mean(times))
+    for _ in range(args.warmup):
+        oracle_sample("beam_halo_1e5_depth6")
+    runs = [oracle_sample(args.workload) for _ in range(args.steps)]
+    measured = float(np.mean([r["measured_s"] for r in runs]))
+    sps = [r["s_per_solve"] for r in runs]
+    if any(v is None for v in sps):
+        return {"impl": "reference", "unavailable": runs[0]["sample"]}
+    sec = float(np.mean(sps))
     val = 1.0 / sec
     return {"metric": METRIC, "value": round(val, 6), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": round(measured * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": args.workload}, "stage_s": stages,
+            "config": {"workload": args.workload}, "stage_s": runs[-1]["stage_s"],
+            "seconds_per_solve_extrapolated": round(sec, 2),
             "cpu_baseline": {"value": round(val, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": desc},
+                             "sample": runs[-1]["sample"]},
             "e2e": {"value": round(val, 6), "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -693,6 +766,83 @@ def run_ilu(args):
             "eval": rows}
 
 
+PROFILE_RUNS = ("solve", "batch", "mpnn", "small", "medium")
+
+
+def run_profile(args):
+    """Bounded runs for profilers (ncu): one workload, a fixed amount of work,
+    no timing, exit 0.
+      solve: the 1e7-particle depth-10 beam (1.05e6 nodes): tree, stencils,
+             deposit, then --profile-iters Arnoldi steps of the Poisson solve
+             (GMRES(30), polynomial degree 16) in --precision; --profile-sorted
+             sweeps on the width-sorted matrix at the shape the autotuner
+             picks for it (128 threads, two 4-entry chunks in flight).
+      batch: the 64-beam depth-9 batch, then --profile-iters Arnoldi steps
+             (--profile-sorted: 512 threads, one chunk in flight).
+      mpnn:  --profile-iters training steps of the learned preconditioner on
+             a 2e5-particle depth-8 beam.
+      small: one whole solve (tree, stencils, deposit, Poisson solve, gather)
+             on 2e6 beam-with-halo particles at depth 9 (c = 0.1), a device
+             footprint of about 1 GB: the case for multi-pass captures of
+             single kernels.
+      medium: the same on 2e7 particles at depth 9 (c = 0.15), about 3 GB on
+             the device: particle arrays (charges and permutation 240 MB,
+             positions 480 MB) larger than L2, for captures of the particle
+             kernels (deposit, gather)."""
+    import torch
+    from paper_1603_04039_gb300 import APCloud, MPNN, inputs
+    dev = torch.device("cuda", 0)
+
+    def put(*arrays):
+        return [torch.from_numpy(a).to(dev) for a in arrays]
+
+    form = dict(precision=args.precision, poly_degree=args.poly_degree, poly_omega=args.poly_omega, device=dev)
+    it = args.profile_iters
+    if args.profile_run == "solve":
+        x, y, z, q = inputs.beam_with_halo(10_000_000, 1)
+        tx, ty, tz, tq = put(x, y, z, q)
+        ap = APCloud(max_depth=10, c_refine=0.043, **form)
+        if args.profile_sorted:
+            ap.set_launch_shape(spmv_block=128, wls_warps=2, spmv_unroll=4, sweep_sorted=1)
+        ap.build_octree(tx, ty, tz)
+        ap.stencils()
+        ap.deposit(q=tq, rtol=RTOL)
+        ap.solve(rtol=1e-30, max_iter=it)
+    elif args.profile_run == "batch":
+        x, y, z, q, offs, _ = inputs.beam_batch(64, 1)
+        tx, ty, tz, tq = put(x, y, z, q)
+        ap = APCloud(max_depth=9, c_refine=0.05, **form)
+        if args.profile_sorted:
+            ap.set_launch_shape(spmv_block=512, wls_warps=8, spmv_unroll=1, sweep_sorted=1)
+        ap.build_octree_batched(tx, ty, tz, offs)
+        ap.stencils()
+        ap.deposit(q=tq, rtol=RTOL)
+        ap.solve(rtol=1e-30, max_iter=it)
+    elif args.profile_run == "mpnn":
+        x, y, z, q = inputs.beam_with_halo(200_000, 3)
+        tx, ty, tz, tq = put(x, y, z, q)
+        ap = APCloud(max_depth=8, c_refine=0.1, device=dev)
+        ap.build_octree(tx, ty, tz)
+        ap.stencils()
+        ap.deposit(q=tq, rtol=RTOL)
+        net = MPNN(seed=1)
+        for _ in range(it):
+            net.loss(ap, backward=True)
+            net.adam(ap, 1e-3)
+    else:
+        npart, cc = (2_000_000, 0.1) if args.profile_run == "small" else (20_000_000, 0.15)
+        x, y, z, q = inputs.beam_with_halo(npart, 1)
+        tx, ty, tz, tq = put(x, y, z, q)
+        ap = APCloud(max_depth=9, c_refine=cc, **form)
+        ap.build_octree(tx, ty, tz)
+        ap.stencils()
+        ap.deposit(q=tq, rtol=RTOL)
+        ap.solve(rtol=RTOL, max_iter=MAX_ITER)
+        ap.gather_field()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_run": args.profile_run, "n_nodes": ap.n_nodes, "launches": ap.launch_count()}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -713,7 +863,14 @@ def main():
     ap.add_argument("--learned-max-iter", type=int, default=100000)
     ap.add_argument("--ilu", action="store_true", help="ILU(0) against Jacobi on the learned comparison's seeds")
     ap.add_argument("--ilu-max-iter", type=int, default=3000)
+    ap.add_argument("--profile-run", choices=PROFILE_RUNS,
+                    help="a bounded run for a profiler instead of the benchmark (see run_profile)")
+    ap.add_argument("--profile-iters", type=int, default=400)
+    ap.add_argument("--profile-sorted", action="store_true")
     args = ap.parse_args()
+    if args.profile_run:
+        run_profile(args)
+        return
     if args.vp:
         print(json.dumps(run_vp(args)))
         return
@@ -739,15 +896,14 @@ def main():
     line = run_ours(args, ws, rank, local)
     if rank == 0:
         if ws == 1 and not args.no_cpu_baseline:
-            # the oracle runs GMRES(30) + Jacobi: scale its sampled iterations to the
-            # count that algorithm needs on this workload (measured above in FP64 on the GPU)
-            pl = line["plain_fp64_form"]
-            tot, desc, stages = oracle_sample(args.workload, gmres_sample=10,
-                                              gmres_iters_hint=(pl["iters_rho"], pl["iters_phi"]))
-            line["cpu_baseline"] = {"value": round(1.0 / tot, 6), "unit": "solves/s", "cores": 1, "kind": "oracle",
-                                    "sample": desc, "stage_s": stages}
+            r = oracle_sample(args.workload, gpu_phi=line.pop("_phi_nodes", None))
+            line["cpu_baseline"] = {"value": None if r["s_per_solve"] is None else round(1.0 / r["s_per_solve"], 6),
+                                    "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": r["sample"],
+                                    "stage_s": r["stage_s"]}
+            line["relres_vs_oracle_matrix"] = r["relres_gpu_phi"]
         else:
             line["cpu_baseline"] = None
+        line.pop("_phi_nodes", None)
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
