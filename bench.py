@@ -181,6 +181,8 @@ def run_ours(args, ws, rank, local):
     form = dict(max_depth=depth, c_refine=c, restart=30, precision=args.precision, poly_degree=args.poly_degree,
                 poly_omega=args.poly_omega, device=dev)
     ap = APCloud(**form)
+    if args.no_graphs:
+        ap.set_graphs(False)
     out = tuple(torch.empty(npart, dtype=torch.float64, device=dev) for _ in range(4))
     stream = ap.stream
     info = {}
@@ -771,7 +773,7 @@ PROFILE_RUNS = ("solve", "batch", "mpnn", "small", "medium")
 
 def run_profile(args):
     """Bounded runs for profilers (ncu): one workload, a fixed amount of work,
-    no timing, exit 0.
+    no timing, every kernel launched directly (no CUDA graphs), exit 0.
       solve: the 1e7-particle depth-10 beam (1.05e6 nodes): tree, stencils,
              deposit, then --profile-iters Arnoldi steps of the Poisson solve
              (GMRES(30), polynomial degree 16) in --precision; --profile-sorted
@@ -798,6 +800,13 @@ def run_profile(args):
 
     form = dict(precision=args.precision, poly_degree=args.poly_degree, poly_omega=args.poly_omega, device=dev)
     it = args.profile_iters
+    # direct launches: ncu cannot profile the kernel nodes of graphs with conditional nodes
+    _APCloud = APCloud
+
+    def APCloud(**kw):
+        a = _APCloud(**kw)
+        a.set_graphs(False)
+        return a
     if args.profile_run == "solve":
         x, y, z, q = inputs.beam_with_halo(10_000_000, 1)
         tx, ty, tz, tq = put(x, y, z, q)
@@ -863,6 +872,9 @@ def main():
     ap.add_argument("--learned-max-iter", type=int, default=100000)
     ap.add_argument("--ilu", action="store_true", help="ILU(0) against Jacobi on the learned comparison's seeds")
     ap.add_argument("--ilu-max-iter", type=int, default=3000)
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch every kernel of the timed steps directly (for a profiler's launch list: ncu cannot "
+                         "profile the kernel nodes of graphs with conditional nodes)")
     ap.add_argument("--profile-run", choices=PROFILE_RUNS,
                     help="a bounded run for a profiler instead of the benchmark (see run_profile)")
     ap.add_argument("--profile-iters", type=int, default=400)

@@ -322,9 +322,14 @@ apcloud_status apcloud_push_particles(apcloud_ctx *ctx, double *d_x, double *d_y
  * Gram-Schmidt reductions, preconditioner sweeps, the update of the iterate
  * and the residual that opens the next cycle) is captured once per set of
  * buffers and sizes and replayed with one cudaGraphLaunch on the context
- * stream; the host synchronises once per cycle for the convergence test.  On
- * by default; enable = 0 launches every kernel directly (same results, the
- * same kernels in the same order).  Synchronises the context stream.  The
+ * stream; the host synchronises once per cycle for the convergence test.
+ * Arnoldi step j >= 1 of a captured cycle is the body of a conditional (IF)
+ * node that the previous step sets while the cycle's stopping test has not
+ * passed, so the steps after it are skipped on the device.  On by default;
+ * enable = 0 launches every kernel directly and reads the stopping flag back
+ * after every Arnoldi step (the same kernels in the same order, the same
+ * results).  Kernel timers (apcloud_set_timing) also run cycles as direct
+ * launches, stopped the same way.  Synchronises the context stream.  The
  * paper has no counterpart (launch mechanics). */
 apcloud_status apcloud_set_graphs(apcloud_ctx *ctx, int enable);
 

@@ -301,6 +301,7 @@ apcloud_status check_device_errors(apcloud_ctx *c) {
     if (e[0] & ERR_STENCIL)
         return fail(c, APCLOUD_E_STENCIL, "a node has no full-rank stencil within ring %d", c->P.ring_max);
     if (e[0] & ERR_BALANCE) return fail(c, APCLOUD_E_INVALID, "internal: 2:1 balance violated");
+    if (e[0] & ERR_TIMEOUT) return fail(c, APCLOUD_E_TIMEOUT, "a kernel gave up waiting for its bulk copy");
     return APCLOUD_OK;
 }
 
@@ -401,7 +402,7 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->leaf_count, &c->pleaf, &c->spos, &c->qsort, &c->node_ic, &c->bowner, &c->bface, &c->bidx, &c->adj, &c->nbr, &c->msz,
                     &c->ring, &c->lap, &c->lapd, &c->D, &c->rcond, &c->slice_w, &c->slice_off, &c->ell_col,
                     &c->ell_A, &c->ell_B, &c->dA, &c->dB, &c->V, &c->w0, &c->w1, &c->u, &c->b, &c->partial,
-                    &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->tmp, &c->derr, &c->dsmall,
+                    &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->nodefield32, &c->tmp, &c->derr, &c->dsmall,
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
                     &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,

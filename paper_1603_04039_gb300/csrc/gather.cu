@@ -21,10 +21,16 @@ namespace apc {
 namespace {
 
 constexpr int NF = 12;  // per-node record: phi, 9 derivatives, 2 pad
+// compact per-node record of the mixed form's particle pass, 80 bytes in 4-byte
+// words: phi and the node centre (FP64, words 0-7), gradient and Hessian
+// fx fy fz fxx fxy fxz fyy fyz fzz (FP32, words 8-16), pad
+constexpr int NF32 = 20;
 
 __global__ void k_derivs(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                          const int32_t *__restrict__ col, const double *__restrict__ D, int64_t dstride,
-                         const double *__restrict__ phi, int n_int, double *__restrict__ nf) {
+                         const double *__restrict__ phi, int n_int, double *__restrict__ nf,
+                         const int4 *__restrict__ ic, double lo0, double lo1, double lo2, double unit,
+                         float *__restrict__ nf32) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n_int) return;
     const int sl = j >> 5, lane = j & 31;
@@ -46,6 +52,16 @@ __global__ void k_derivs(const uint32_t *__restrict__ sw, const uint32_t *__rest
     for (int r = 0; r < NCOL; ++r) o[1 + r] = acc[r];
     o[10] = 0.0;
     o[11] = 0.0;
+    if (nf32) {
+        const int4 q = ic[j];
+        double2 *c2 = reinterpret_cast<double2 *>(nf32 + (int64_t)j * NF32);
+        c2[0] = make_double2(p0, __dadd_rn(lo0, __dmul_rn((double)q.x, unit)));
+        c2[1] = make_double2(__dadd_rn(lo1, __dmul_rn((double)q.y, unit)), __dadd_rn(lo2, __dmul_rn((double)q.z, unit)));
+        float4 *f4 = reinterpret_cast<float4 *>(nf32 + (int64_t)j * NF32 + 8);
+        f4[0] = make_float4((float)acc[0], (float)acc[1], (float)acc[2], (float)acc[3]);
+        f4[1] = make_float4((float)acc[4], (float)acc[5], (float)acc[6], (float)acc[7]);
+        f4[2] = make_float4((float)acc[8], 0.f, 0.f, 0.f);
+    }
 }
 
 __device__ __forceinline__ int leaf_of(const uint64_t *anchor, int n, uint64_t v) {
@@ -74,44 +90,43 @@ __device__ __forceinline__ void taylor(const double *__restrict__ nf, int j, dou
     ez = g2 + hr2;
 }
 
-// The same expansion with the corrections (g.r, H r, r.H.r) in FP32 around the
-// FP64 node potential: the mixed form, whose node derivatives carry FP32
-// accuracy already (FP32 stencils), so FP32 terms cost no accuracy there and
-// keep the particle pass off the slow FP64 pipe.
-__device__ __forceinline__ void taylor_f32(const double *__restrict__ nf, int j, float r0, float r1, float r2,
-                                           double &php, double &ex, double &ey, double &ez) {
-    const double2 *f2 = reinterpret_cast<const double2 *>(nf + (int64_t)j * NF);
-    const double2 a = f2[0], b = f2[1], c = f2[2], d = f2[3], e = f2[4];
-    const float fxx = (float)c.x, fxy = (float)c.y, fxz = (float)d.x, fyy = (float)d.y, fyz = (float)e.x,
-                fzz = (float)e.y;
-    const float g0 = (float)a.y, g1 = (float)b.x, g2 = (float)b.y;
-    const float hr0 = fmaf(fxz, r2, fmaf(fxy, r1, fxx * r0));
-    const float hr1 = fmaf(fyz, r2, fmaf(fyy, r1, fxy * r0));
-    const float hr2 = fmaf(fzz, r2, fmaf(fyz, r1, fxz * r0));
-    const float corr = fmaf(g2, r2, fmaf(g1, r1, g0 * r0)) + 0.5f * fmaf(r2, hr2, fmaf(r1, hr1, r0 * hr0));
-    php = a.x + (double)corr;
-    ex = (double)(g0 + hr0);
-    ey = (double)(g1 + hr1);
-    ez = (double)(g2 + hr2);
-}
-
 template <bool F32>
 __global__ void __launch_bounds__(256) k_gather_leaf(
     const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z, int64_t n,
     double lo0, double lo1, double lo2, double unit, const int32_t *__restrict__ pleaf, const int4 *__restrict__ ic,
-    const double *__restrict__ nf, double *__restrict__ php, double *__restrict__ ex, double *__restrict__ ey,
-    double *__restrict__ ez) {
+    const double *__restrict__ nf, const float *__restrict__ nf32, double *__restrict__ php, double *__restrict__ ex,
+    double *__restrict__ ey, double *__restrict__ ez) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int j = __ldcs(pleaf + i);
     const double p0 = __ldcs(x + i), p1 = __ldcs(y + i), p2 = __ldcs(z + i);
-    const int4 q = ic[j];
-    const double r0 = p0 - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
-    const double r1 = p1 - __dadd_rn(lo1, __dmul_rn((double)q.y, unit));
-    const double r2 = p2 - __dadd_rn(lo2, __dmul_rn((double)q.z, unit));
     double v, gx, gy, gz;
-    if (F32) taylor_f32(nf, j, (float)r0, (float)r1, (float)r2, v, gx, gy, gz);
-    else taylor(nf, j, r0, r1, r2, v, gx, gy, gz);
+    if (F32) {
+        // the mixed form: corrections (g.r, H r, r.H.r) in FP32 around the FP64
+        // node potential, from the compact record; its node derivatives carry
+        // FP32 accuracy already (FP32 stencils), and the pass stays off the slow
+        // FP64 pipe
+        const double2 *c2 = reinterpret_cast<const double2 *>(nf32 + (int64_t)j * NF32);
+        const float4 *f4 = reinterpret_cast<const float4 *>(nf32 + (int64_t)j * NF32 + 8);
+        const double2 pc = c2[0], cc = c2[1];
+        const float4 u = f4[0], w = f4[1], t = f4[2];
+        const float r0 = (float)(p0 - pc.y), r1 = (float)(p1 - cc.x), r2 = (float)(p2 - cc.y);
+        // u = (fx, fy, fz, fxx), w = (fxy, fxz, fyy, fyz), t.x = fzz
+        const float hr0 = fmaf(w.y, r2, fmaf(w.x, r1, u.w * r0));
+        const float hr1 = fmaf(w.w, r2, fmaf(w.z, r1, w.x * r0));
+        const float hr2 = fmaf(t.x, r2, fmaf(w.w, r1, w.y * r0));
+        const float corr = fmaf(u.z, r2, fmaf(u.y, r1, u.x * r0)) + 0.5f * fmaf(r2, hr2, fmaf(r1, hr1, r0 * hr0));
+        v = pc.x + (double)corr;
+        gx = (double)(u.x + hr0);
+        gy = (double)(u.y + hr1);
+        gz = (double)(u.z + hr2);
+    } else {
+        const int4 q = ic[j];
+        const double r0 = p0 - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
+        const double r1 = p1 - __dadd_rn(lo1, __dmul_rn((double)q.y, unit));
+        const double r2 = p2 - __dadd_rn(lo2, __dmul_rn((double)q.z, unit));
+        taylor(nf, j, r0, r1, r2, v, gx, gy, gz);
+    }
     if (php) __stcs(php + i, v);
     if (ex) __stcs(ex + i, gx);
     if (ey) __stcs(ey + i, gy);
@@ -160,27 +175,31 @@ __global__ void k_gather(const double *__restrict__ x, const double *__restrict_
 
 apcloud_status gather_field(apcloud_ctx *c, double *phi_p, double *ex, double *ey, double *ez) {
     const int n = c->n_int;
+    const bool mixed = c->P.precision == 1;
     double *nf = ensure<double>(c, c->nodefield, (int64_t)n * NF);
-    if (!nf) return APCLOUD_E_NOMEM;
+    float *nf32 = mixed ? ensure<float>(c, c->nodefield32, (int64_t)n * NF32 + 4) : nullptr;
+    if (!nf || (mixed && !nf32)) return APCLOUD_E_NOMEM;
     const int64_t dstride = ((int64_t)n + 31) / 32 * 32;
-    APC_LAUNCH(c, K_DERIV, div_up(n, 128), 128, 0, k_derivs, ptr<uint32_t>(c->slice_w), ptr<uint32_t>(c->slice_off),
-               ptr<int32_t>(c->ell_col), ptr<double>(c->D), dstride, ptr<double>(c->phi), n, nf);
     const double ext = c->P.hi[0] - c->P.lo[0];
     const double unit = ldexp(ext, -(KEY_DEPTH + 1));
-    if (c->P.precision == 1)
+    APC_LAUNCH(c, K_DERIV, div_up(n, 128), 128, 0, k_derivs, ptr<uint32_t>(c->slice_w), ptr<uint32_t>(c->slice_off),
+               ptr<int32_t>(c->ell_col), ptr<double>(c->D), dstride, ptr<double>(c->phi), n, nf,
+               ptr<int4>(c->node_ic), c->P.lo[0], c->P.lo[1], c->P.lo[2], unit, nf32);
+    if (mixed)
         APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather_leaf<true>, c->px, c->py, c->pz, c->N,
                    c->P.lo[0], c->P.lo[1], c->P.lo[2], unit, (const int32_t *)ptr<int32_t>(c->pleaf),
-                   ptr<int4>(c->node_ic), nf, phi_p, ex, ey, ez);
+                   ptr<int4>(c->node_ic), (const double *)nf, (const float *)nf32, phi_p, ex, ey, ez);
     else
         APC_LAUNCH(c, K_GATHER, div_up(c->N, 256), 256, 0, k_gather_leaf<false>, c->px, c->py, c->pz, c->N,
                    c->P.lo[0], c->P.lo[1], c->P.lo[2], unit, (const int32_t *)ptr<int32_t>(c->pleaf),
-                   ptr<int4>(c->node_ic), nf, phi_p, ex, ey, ez);
+                   ptr<int4>(c->node_ic), (const double *)nf, (const float *)nullptr, phi_p, ex, ey, ez);
     // node pass: operator (72 B), column (4 B) and neighbour value (8 B) per
-    // stencil entry plus the 96 B record; particle pass: leaf index and
-    // position in (28 B), phi and E out (32 B), and each leaf's 96 B record
-    // and 16 B centre once
-    account(c, K_DERIV, 84.0 * c->sum_m + 104.0 * n, 19.0 * c->sum_m);
-    account(c, K_GATHER, 60.0 * c->N + 112.0 * n, 38.0 * c->N);
+    // stencil entry plus the 96 B record (and the 80 B compact record of the
+    // mixed form); particle pass: leaf index and position in (28 B), phi and E
+    // out (32 B), and each leaf's record once (FP64: 96 B and the 16 B centre;
+    // mixed: the 80 B compact record)
+    account(c, K_DERIV, 84.0 * c->sum_m + (mixed ? 200.0 : 104.0) * n, 19.0 * c->sum_m);
+    account(c, K_GATHER, 60.0 * c->N + (mixed ? 80.0 : 112.0) * n, 38.0 * c->N);
     return cuda_check(c, cudaGetLastError(), "gather");
 }
 

@@ -27,7 +27,7 @@ enum Kind {
 static_assert(NKIND == APCLOUD_NUM_KINDS, "kind count");
 
 // device error word bits
-enum : unsigned { ERR_DOMAIN = 1u, ERR_STENCIL = 2u, ERR_BALANCE = 4u, ERR_OVERFLOW = 8u };
+enum : unsigned { ERR_DOMAIN = 1u, ERR_STENCIL = 2u, ERR_BALANCE = 4u, ERR_OVERFLOW = 8u, ERR_TIMEOUT = 16u };
 
 struct DBuf {
     void *p = nullptr;
@@ -197,6 +197,7 @@ struct apcloud_ctx {
     int64_t ss_entries = 0;
     // solver
     apc::DBuf V, w0, w1, u, b, partial, gstate, rho_m, rho, phi, nodefield, tmp;
+    apc::DBuf nodefield32;   // mixed form: compact node records of the particle pass
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
     apc::DBuf pz0, pz1, pt;                         // polynomial preconditioner sweeps
     // device staging for apcloud_field_host

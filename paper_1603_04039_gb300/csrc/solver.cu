@@ -113,82 +113,70 @@ __device__ void final_sums(const double *partial, int nblk, int nk, double *sm, 
 // Cell-indicator charge assignment (Section 5): Q_j = sum of the charges of
 // the particles in leaf j, rho_M = Q_j / h_j^3; boundary rows copy the owner.
 // Two passes, both coalesced on the particle side:
-//  * k_charge_sort, one thread per particle in the caller's order: the
-//    charge goes to its key-sorted position (recorded by the tree build);
-//    the scattered stores land in an array that L2 keeps (evict-last hint)
-//    while the caller's charges stream through (evict-first);
-//  * k_deposit: each warp owns 32 consecutive leaves and streams their
-//    sorted charges in chunks of 32; a segmented scan over the lanes sums
-//    each leaf's charges within a chunk, and the lane ending a leaf's run
-//    adds that partial to the leaf's accumulator in shared memory.
+//  * k_charge_sort, four particles per thread in the caller's order: each
+//    charge goes to its key-sorted position (recorded by the tree build); the
+//    scattered stores land in an array that L2 keeps (evict-last hint) while
+//    the caller's charges stream through (evict-first);
+//  * k_deposit, one thread per leaf: the leaf's sorted charges (a contiguous
+//    range) summed in order, one FP64 add per particle -- a warp-wide tree
+//    reduction per leaf would cost 32 lanes of FP64 adds at every step on
+//    this GPU's narrow FP64 pipe.
 // The summation order is fixed, so the result does not depend on timing.
-constexpr int DEP_WARPS = 8;
-constexpr int DEP_U = 4;
+constexpr int CS_PER = 4;
 
 __global__ void __launch_bounds__(256) k_charge_sort(const double *__restrict__ q, const int32_t *__restrict__ spos,
                                                      int64_t n, double *__restrict__ qs) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int64_t i0 = ((int64_t)blockIdx.x * blockDim.x) * CS_PER + threadIdx.x;
     uint64_t keep;
     asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
-    const double v = __ldcs(q + i);
-    double *dst = qs + __ldcs(spos + i);
-    asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(dst), "d"(v), "l"(keep) : "memory");
+    double v[CS_PER];
+    int32_t p[CS_PER];
+#pragma unroll
+    for (int u = 0; u < CS_PER; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        if (i < n) {
+            v[u] = __ldcs(q + i);
+            p[u] = __ldcs(spos + i);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < CS_PER; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        if (i < n)
+            asm volatile("st.global.L2::cache_hint.f64 [%0], %1, %2;" ::"l"(qs + p[u]), "d"(v[u]), "l"(keep)
+                         : "memory");
+    }
 }
 
-__global__ void __launch_bounds__(DEP_WARPS * 32) k_deposit(
-    const double *__restrict__ qs, double qu, const int32_t *__restrict__ first, const int32_t *__restrict__ count,
-    const int4 *__restrict__ ic, int n_int, double ext, double *__restrict__ rho_m) {
-    __shared__ double acc[DEP_WARPS][32];
-    const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t j0 = ((int64_t)blockIdx.x * DEP_WARPS + wid) * 32;
-    if (j0 >= n_int) return;   // the whole warp
-    const int64_t j = j0 + lane;
-    const bool valid = j < n_int;
-    const int f = valid ? first[j] : INT_MAX;
-    const int cnt = valid ? count[j] : 0;
+// rho_M = Q / h^3 with h = ext 2^-level: Q (1 / ext^3) 2^(3 level), the power
+// of two built from its exponent bits (no FP64 division)
+__global__ void __launch_bounds__(256) k_deposit(const double *__restrict__ qs, double qu,
+                                                 const int32_t *__restrict__ first, const int32_t *__restrict__ count,
+                                                 const int4 *__restrict__ ic, int n_int, double inv_ext3,
+                                                 double *__restrict__ rho_m) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n_int) return;
+    const int f = first[j], c = count[j];
     double Q;
-    if (!qs) {
-        Q = (double)cnt * qu;
-    } else {
-        acc[wid][lane] = 0.0;
-        int e = valid ? f + cnt : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) e = max(e, __shfl_xor_sync(FULL, e, o));
-        const int s = __shfl_sync(FULL, f, 0);
-        __syncwarp();
-        for (int base = s; base < e; base += 32 * DEP_U) {
-            double v[DEP_U];
-#pragma unroll
-            for (int u = 0; u < DEP_U; ++u) {
-                const int i = base + 32 * u + lane;
-                v[u] = i < e ? __ldcs(qs + i) : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < DEP_U; ++u) {
-                const int i = base + 32 * u + lane;
-                const bool in = i < e;
-                int k = group_leaf(f, i);
-                if (!in) k = 32;
-                double x = v[u];
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const double up = __shfl_up_sync(FULL, x, d);
-                    const int ku = __shfl_up_sync(FULL, k, d);
-                    if (lane >= d && ku == k) x += up;
-                }
-                const int kn = __shfl_down_sync(FULL, k, 1);
-                if (in && (lane == 31 || kn != k)) acc[wid][k] += x;
-                __syncwarp();
-            }
+    if (qs) {
+        double s = 0.0;
+        int i = f;
+        const int e = f + c;
+        for (; i + 4 <= e; i += 4) {
+            const double a0 = __ldcs(qs + i), a1 = __ldcs(qs + i + 1), a2 = __ldcs(qs + i + 2),
+                         a3 = __ldcs(qs + i + 3);
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
         }
-        Q = acc[wid][lane];
+        for (; i < e; ++i) s += __ldcs(qs + i);
+        Q = s;
+    } else {
+        Q = (double)c * qu;
     }
-    if (valid) {
-        const double h = ldexp(ext, -ic[j].w);
-        rho_m[j] = Q / (h * h * h);
-    }
+    const double p3 = __longlong_as_double((long long)(1023 + 3 * ic[j].w) << 52);
+    rho_m[j] = (Q * inv_ext3) * p3;
 }
 
 __global__ void k_bcopy(const int32_t *__restrict__ owner, int n_int, int n_bnd, double *__restrict__ v) {
@@ -639,30 +627,44 @@ __global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t
     if (tid == 0) partial[(int64_t)blockIdx.x * 64] = tot;
     if (!last_block(&st->ticket)) return;
     final_sums(partial, gridDim.x, 1, sm, fs);
+    // Hessenberg column j, its rotations and the stopping test: the inputs are
+    // loaded in parallel into shared memory, the serial part runs there, and the
+    // results are written back in parallel (dependent global round trips in one
+    // thread would dominate the kernel)
+    __shared__ double col[MAX_RESTART + 1], csj[MAX_RESTART], snj[MAX_RESTART];
+    if (tid <= j) col[tid] = __ldcg(&st->h1[tid]) + __ldcg(&st->h2[tid]);
+    if (tid < j) {
+        csj[tid] = __ldcg(&st->cs[tid]);
+        snj[tid] = __ldcg(&st->sn[tid]);
+    }
+    __syncthreads();
     if (tid == 0) {
         const int M = MAX_RESTART;
-        double hn = sqrt(fs[0]);
-        for (int i = 0; i <= j; ++i) st->H[i * M + j] = st->h1[i] + st->h2[i];
-        st->H[(j + 1) * M + j] = hn;
+        const double hn = sqrt(fs[0]);
+        col[j + 1] = hn;
         for (int i = 0; i < j; ++i) {
-            double a = st->H[i * M + j], bb = st->H[(i + 1) * M + j];
-            st->H[i * M + j] = st->cs[i] * a + st->sn[i] * bb;
-            st->H[(i + 1) * M + j] = -st->sn[i] * a + st->cs[i] * bb;
+            const double a = col[i], bb = col[i + 1];
+            col[i] = csj[i] * a + snj[i] * bb;
+            col[i + 1] = -snj[i] * a + csj[i] * bb;
         }
-        double a = st->H[j * M + j], bb = st->H[(j + 1) * M + j];
-        double den = sqrt(a * a + bb * bb);
-        st->cs[j] = den != 0.0 ? a / den : 1.0;
-        st->sn[j] = den != 0.0 ? bb / den : 0.0;
-        st->H[j * M + j] = den;
-        st->H[(j + 1) * M + j] = 0.0;
-        st->g[j + 1] = -st->sn[j] * st->g[j];
-        st->g[j] = st->cs[j] * st->g[j];
+        const double a = col[j], bb = col[j + 1];
+        const double den = sqrt(a * a + bb * bb);
+        const double cj = den != 0.0 ? a / den : 1.0, sj = den != 0.0 ? bb / den : 0.0;
+        st->cs[j] = cj;
+        st->sn[j] = sj;
+        col[j] = den;
+        col[j + 1] = 0.0;
+        const double gj = __ldcg(&st->g[j]);
+        st->g[j + 1] = -sj * gj;
+        st->g[j] = cj * gj;
         st->jend = j + 1;
-        if (fabs(st->g[j + 1]) <= st->rtol * st->bnorm || hn == 0.0) st->done = 1;
+        if (fabs(sj * gj) <= st->rtol * st->bnorm || hn == 0.0) st->done = 1;
         st->inv_norm = hn > 0.0 ? 1.0 / hn : 0.0;
         st->ticket = 0;
         if (set_next) cudaGraphSetConditional(next, st->done ? 0u : 1u);
     }
+    __syncthreads();
+    if (tid <= j + 1) st->H[tid * MAX_RESTART + j] = col[tid];
 }
 
 // u += V y with H y = g solved (upper triangular, jend x jend) in every block
@@ -825,6 +827,7 @@ int reduction_blocks(apcloud_ctx *c, int n) {
     int a = stream_blocks(ldv), b = dot_blocks(ldv);
     return a > b ? a : b;
 }
+
 
 // Per-beam convergence of a batch: at every restart the residual of each beam
 // is compared with rtol ||b_b||; converged beams are frozen (their residual
@@ -1085,14 +1088,16 @@ __global__ void __launch_bounds__(256) k_bfinal_norm(int j, BKry bk, GmresState 
             double *H = bk.H + (int64_t)beam * (M + 1) * M, *cs = bk.cs + (int64_t)beam * M,
                    *sn = bk.sn + (int64_t)beam * M, *g = bk.g + (int64_t)beam * (M + 1);
             const double *h1 = bk.h1 + (int64_t)beam * (M + 1), *h2 = bk.h2 + (int64_t)beam * (M + 1);
-            for (int i = 0; i <= j; ++i) H[i * M + j] = h1[i] + h2[i];
-            H[(j + 1) * M + j] = hn;
+            // rotation i acts on entries i and i + 1 of column j: the entry it
+            // carries to the next rotation stays in a register, the others are
+            // the unrotated h1 + h2 (no store-then-load chain through memory)
+            double carried = h1[0] + h2[0];
             for (int i = 0; i < j; ++i) {
-                const double x0 = H[i * M + j], x1 = H[(i + 1) * M + j];
+                const double x0 = carried, x1 = h1[i + 1] + h2[i + 1];
                 H[i * M + j] = cs[i] * x0 + sn[i] * x1;
-                H[(i + 1) * M + j] = -sn[i] * x0 + cs[i] * x1;
+                carried = -sn[i] * x0 + cs[i] * x1;
             }
-            const double x0 = H[j * M + j], x1 = H[(j + 1) * M + j];
+            const double x0 = carried, x1 = hn;
             const double den = sqrt(x0 * x0 + x1 * x1);
             cs[j] = den != 0.0 ? x0 / den : 1.0;
             sn[j] = den != 0.0 ? x1 / den : 0.0;
@@ -1289,13 +1294,15 @@ __global__ void k_save_jend(GmresState *st) {
     if (threadIdx.x == 0) st->jlast = st->jend;
 }
 
-// Direct launches with kernel timers on (the roofline pass): the host reads
-// the stopping flag after every Arnoldi step and ends the cycle there, so no
-// launch after the test is timed.  Captured cycles skip those steps on the
-// device instead (IF nodes); untimed direct launches run every step.
+// Direct launches with kernel timers on (the roofline pass) or with graphs
+// turned off by the caller (apcloud_set_graphs): the host reads the stopping
+// flag after every Arnoldi step and ends the cycle there, so no launch after
+// the test is issued or timed.  Captured cycles skip those steps on the
+// device instead (IF nodes).  Solves that never use graphs (the ILU(0)
+// comparison, the allocation-free solve) launch every step of a cycle.
 apcloud_status stop_when_done(apcloud_ctx *c, GmresState *st) {
     c->stopped = false;
-    if (c->capturing || c->timer.mask == 0) return APCLOUD_OK;
+    if (c->capturing || (c->timer.mask == 0 && c->graphs_on)) return APCLOUD_OK;
     int done = 0;
     APC_TRY(read_back(c, &done, &st->done, sizeof done));
     c->stopped = done != 0;
@@ -1556,11 +1563,12 @@ apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform) {
     if (q && c->N > 0) {
         qs = ensure<double>(c, c->qsort, c->N);
         if (!qs) return APCLOUD_E_NOMEM;
-        APC_LAUNCH(c, K_DEPOSIT, div_up(c->N, 256), 256, 0, k_charge_sort, q,
+        APC_LAUNCH(c, K_DEPOSIT, div_up(c->N, 256 * CS_PER), 256, 0, k_charge_sort, q,
                    (const int32_t *)ptr<int32_t>(c->spos), c->N, qs);
     }
-    APC_LAUNCH(c, K_DEPOSIT, div_up(n, 32 * DEP_WARPS), 32 * DEP_WARPS, 0, k_deposit, (const double *)qs, q_uniform,
-               ptr<int32_t>(c->leaf_first), ptr<int32_t>(c->leaf_count), ptr<int4>(c->node_ic), n, ext, rm);
+    APC_LAUNCH(c, K_DEPOSIT, div_up(n, 256), 256, 0, k_deposit, (const double *)qs, q_uniform,
+               ptr<int32_t>(c->leaf_first), ptr<int32_t>(c->leaf_count), ptr<int4>(c->node_ic), n,
+               1.0 / (ext * ext * ext), rm);
     APC_LAUNCH(c, K_DEPOSIT, div_up(c->n_bnd, 256), 256, 0, k_bcopy, ptr<int32_t>(c->bowner), n, c->n_bnd, rm);
     // sorted position and charge per particle, rho_M per node
     account(c, K_DEPOSIT, (q ? 12.0 * c->N : 0.0) + 8.0 * nt, q ? (double)c->N : (double)n);
