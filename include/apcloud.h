@@ -340,10 +340,10 @@ apcloud_status apcloud_set_graphs(apcloud_ctx *ctx, int enable);
  * row-parallel products: 64, 128, 256 and 512 threads per block, each with
  * the loads of 1 or 4 stencil entries issued ahead of their multiply-adds
  * (on the width-sorted copy: 1 or 2 chunks of 4 entries; the sum keeps its
- * order either way), and -- for the FP16 sweeps of the mixed form -- on the
- * sliced ELL and on its width-sorted copy (rows ordered by stencil width
- * inside 256-row windows, so 32-row slices carry little padding; same entries
- * in the same order per row).  The solves run on scratch vectors and the
+ * order either way), and -- for the FP16 sweeps and FP32 Arnoldi products of
+ * the mixed form -- on the sliced ELL and on its width-sorted copy (rows
+ * ordered by stencil width inside 256-row windows, so 32-row slices carry
+ * little padding; same entries in the same order per row).  The solves run on scratch vectors and the
  * graphs they capture are released; bit 1 times the stencil build (neighbour
  * search + WLS) at 2, 4 and 8 nodes (warps) per block on the current node
  * set.  The fastest shapes are kept for later calls and written to

@@ -73,38 +73,56 @@ static void capture_event(apcloud_ctx *c, int kind, bool begin) {
     cudaEventRecordWithFlags(e, c->s, cudaEventRecordExternal);
 }
 
+void timer_close(apcloud_ctx *c) {
+    Timer &t = c->timer;
+    if (t.open < 0) return;
+    cudaEventRecord(t.ev[t.open * 2 + 1], c->s);
+    t.used++;
+    t.open = -1;
+}
+
 void timer_begin(apcloud_ctx *c, int kind) {
     Timer &t = c->timer;
+    if (c->capturing) {
+        if (t.mask >> kind & 1u) capture_event(c, kind, true);
+        return;
+    }
+    if (t.open >= 0 && (t.kind[t.open] != kind || !(t.mask >> kind & 1u))) timer_close(c);
     if (!(t.mask >> kind & 1u)) return;
-    if (c->capturing) { capture_event(c, kind, true); return; }
+    if (t.open >= 0) {   // the same kind again: the open pair covers this launch too
+        t.nl[t.open]++;
+        return;
+    }
     if (t.used * 2 + 2 > t.ev.size()) {
         size_t old = t.ev.size();
         size_t nn = old ? old * 2 : 512;
         t.ev.resize(nn);
         for (size_t i = old; i < nn; ++i) cudaEventCreate(&t.ev[i]);
         t.kind.resize(nn / 2);
+        t.nl.resize(nn / 2);
     }
     cudaEventRecord(t.ev[t.used * 2], c->s);
     t.kind[t.used] = kind;
+    t.nl[t.used] = 1;
+    t.open = (long)t.used;
 }
 
 void timer_end(apcloud_ctx *c, int kind) {
     Timer &t = c->timer;
     if (!(t.mask >> kind & 1u)) return;
-    if (c->capturing) { capture_event(c, kind, false); return; }
-    cudaEventRecord(t.ev[t.used * 2 + 1], c->s);
-    t.used++;
+    if (c->capturing) capture_event(c, kind, false);
 }
 
 static void timer_collect(apcloud_ctx *c) {
     Timer &t = c->timer;
+    timer_close(c);
     if (!t.used) return;
     cudaStreamSynchronize(c->s);
     for (size_t i = 0; i < t.used; ++i) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]) == cudaSuccess) {
             t.ms[t.kind[i]] += ms;
-            t.launches[t.kind[i]]++;
+            t.launches[t.kind[i]] += t.nl[i];
         }
     }
     t.used = 0;
@@ -282,6 +300,7 @@ void harvest_graph_timing(apcloud_ctx *c) {
 }
 
 apcloud_status read_back(apcloud_ctx *c, void *host, const void *dev, size_t bytes) {
+    timer_close(c);   // a timed pair must not span the host's wait
     if (bytes > 256) {
         APC_CUDA(c, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->s));
         return cuda_check(c, cudaStreamSynchronize(c->s), "synchronise");
@@ -405,10 +424,10 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->nodefield32, &c->tmp, &c->derr, &c->dsmall,
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
-                    &c->pz0, &c->pz1, &c->pt, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
+                    &c->pz0, &c->pz1, &c->pt, &c->zbasis, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
                     &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act,
                     &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col,
-                    &c->ss_A, &c->ss_B, &c->tune_b, &c->tune_x, &c->beam_part, &c->ilu_lrows, &c->ilu_urows, &c->ilu_lrp, &c->ilu_urp,
+                    &c->ss_A, &c->ss_B, &c->ss_A32, &c->ss_B32, &c->tune_b, &c->tune_x, &c->beam_part, &c->ilu_lrows, &c->ilu_urows, &c->ilu_lrp, &c->ilu_urp,
                     &c->ilu_lcol, &c->ilu_ucol, &c->ilu_lval, &c->ilu_uval, &c->ilu_dinv};
     for (DBuf *b : bufs) free_buf(c, *b);
     for (DBuf &b : c->mp) free_buf(c, b);

@@ -97,11 +97,16 @@ struct GraphEntry {
     uint64_t last_use = 0;
 };
 
+// Per-kind kernel timers.  Consecutive launches of one timed kind share one
+// event pair (one start before the first, one end after the last): any
+// launch of another kind, timed or not, and any host read-back close it.
 struct Timer {
     unsigned mask = 0;
     std::vector<cudaEvent_t> ev;   // pairs
     std::vector<int> kind;          // per pair
+    std::vector<int> nl;            // launches per pair
     size_t used = 0;
+    long open = -1;                 // pair still open (its end not recorded), or -1
     double ms[NKIND] = {0};
     int64_t launches[NKIND] = {0};
     double bytes[NKIND] = {0};   // algorithmic bytes of the timed launches
@@ -187,6 +192,7 @@ struct apcloud_ctx {
     // width-sorted copy of the FP16 sweep matrix: rows ordered by stencil width
     // inside windows of 256 rows, so 32-row slices pad little (see build_sorted_sweep)
     apc::DBuf ss_perm, ss_w, ss_o, ss_col, ss_A, ss_B;
+    apc::DBuf ss_A32, ss_B32;   // FP32 values in the same layout (Arnoldi products of the mixed form)
     apc::DBuf beam_part;        // per-beam norms: partial sums, BSQ_CH per beam
     apc::DBuf tune_b, tune_x;
     // ILU(0) comparison solve: factors of system ilu_which while it runs (-1: none)
@@ -200,6 +206,7 @@ struct apcloud_ctx {
     apc::DBuf nodefield32;   // mixed form: compact node records of the particle pass
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
     apc::DBuf pz0, pz1, pt;                         // polynomial preconditioner sweeps
+    apc::DBuf zbasis;                               // preconditioned basis Z (flexible cycle end)
     // device staging for apcloud_field_host
     apc::DBuf hx, hy, hz, hq, hphi, hex, hey, hez;
     // error word, small host-visible values
@@ -236,6 +243,7 @@ inline T *ptr(DBuf &b) { return static_cast<T *>(b.p); }
 // event timers around launches of one kind
 void timer_begin(apcloud_ctx *c, int kind);
 void timer_end(apcloud_ctx *c, int kind);
+void timer_close(apcloud_ctx *c);
 // add algorithmic traffic of launches of `kind` (only while that kind is timed)
 inline void account(apcloud_ctx *c, int kind, double bytes, double flops) {
     if (c->timer.mask >> kind & 1u) { c->timer.bytes[kind] += bytes; c->timer.flops[kind] += flops; }

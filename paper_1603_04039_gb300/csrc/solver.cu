@@ -72,8 +72,10 @@ __device__ __forceinline__ bool last_block(unsigned *ticket) {
 }
 
 // Last block: deterministic sums over blocks of partial[b * 64 + k], k < nk.
-// nk == 1 uses every thread on one value; otherwise thread t takes value
-// t % 64 and every fourth block starting at t / 64.  Result in out[k] (shared).
+// nk == 1 uses every thread on one value; otherwise each value gets a group
+// of G = min(32, 2^floor(log2(blockDim / nk))) lanes of one warp, lane l of
+// the group summing blocks l, l + G, ... (four chains in flight) before a
+// shuffle tree over the group.  Result in out[k] (shared).
 __device__ void final_sums(const double *partial, int nblk, int nk, double *sm, double *out) {
     const int t = threadIdx.x;
     if (nk == 1) {
@@ -84,27 +86,23 @@ __device__ void final_sums(const double *partial, int nblk, int nk, double *sm, 
         block_reduce_many<1>(a, 1, sm, &tot);
         if (t == 0) out[0] = tot;
     } else {
-        // thread t: value k = t % 64 over blocks part, part + P, ... (P = blockDim / 64),
-        // four independent partial sums so several loads are in flight
-        const int k = t & 63, part = t >> 6, P = blockDim.x >> 6;
+        int G = 32;
+        while (G > 1 && G * nk > (int)blockDim.x) G >>= 1;
+        const int k = t / G, l = t & (G - 1);
         double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
         if (k < nk) {
-            int b = part;
-            for (; b + 3 * P < nblk; b += 4 * P) {
+            int b = l;
+            for (; b + 3 * G < nblk; b += 4 * G) {
                 v0 += __ldcg(&partial[(int64_t)b * 64 + k]);
-                v1 += __ldcg(&partial[(int64_t)(b + P) * 64 + k]);
-                v2 += __ldcg(&partial[(int64_t)(b + 2 * P) * 64 + k]);
-                v3 += __ldcg(&partial[(int64_t)(b + 3 * P) * 64 + k]);
+                v1 += __ldcg(&partial[(int64_t)(b + G) * 64 + k]);
+                v2 += __ldcg(&partial[(int64_t)(b + 2 * G) * 64 + k]);
+                v3 += __ldcg(&partial[(int64_t)(b + 3 * G) * 64 + k]);
             }
-            for (; b < nblk; b += P) v0 += __ldcg(&partial[(int64_t)b * 64 + k]);
+            for (; b < nblk; b += G) v0 += __ldcg(&partial[(int64_t)b * 64 + k]);
         }
-        sm[t] = (v0 + v1) + (v2 + v3);
-        __syncthreads();
-        if (t < nk) {
-            double s = 0.0;
-            for (int q = 0; q < P; ++q) s += sm[t + 64 * q];
-            out[t] = s;
-        }
+        double v = (v0 + v1) + (v2 + v3);
+        for (int o = G >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o, G);
+        if (k < nk && l == 0) out[k] = v;
     }
     __syncthreads();
 }
@@ -264,24 +262,30 @@ __device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const
 template <int U>
 __device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const int32_t *__restrict__ col,
                                            const float *__restrict__ x, int64_t sbase, int lane, int w) {
-    constexpr int AH = (U > 1) ? 2 : 1;
+    constexpr int AH = (U > 1) ? 2 : 1;   // chunks whose loads are in flight
     const int4 z4 = make_int4(0, 0, 0, 0);
     const uint2 z2 = make_uint2(0u, 0u);
     float acc = 0.f;
     const int nch = w >> 2;
     const int4 *c4 = reinterpret_cast<const int4 *>(col + sbase) + lane;
     const uint2 *v4 = reinterpret_cast<const uint2 *>(val + sbase) + lane;
-    int4 c0 = z4, c1 = z4;
-    uint2 v0 = z2, v1 = z2;
-    if (nch > 0) { c0 = c4[0]; v0 = v4[0]; }
-    if (AH > 1 && nch > 1) { c1 = c4[32]; v1 = v4[32]; }
+    int4 cq[AH];
+    uint2 vq[AH];
+#pragma unroll
+    for (int a = 0; a < AH; ++a) {
+        cq[a] = a < nch ? c4[(int64_t)a * 32] : z4;
+        vq[a] = a < nch ? v4[(int64_t)a * 32] : z2;
+    }
     for (int j = 0; j < nch; ++j) {
-        int4 cn = z4;
-        uint2 vn = z2;
-        if (j + AH < nch) {
-            cn = c4[(int64_t)(j + AH) * 32];
-            vn = v4[(int64_t)(j + AH) * 32];
+        const int4 c0 = cq[0];
+        const uint2 v0 = vq[0];
+#pragma unroll
+        for (int a = 0; a + 1 < AH; ++a) {
+            cq[a] = cq[a + 1];
+            vq[a] = vq[a + 1];
         }
+        cq[AH - 1] = (j + AH < nch) ? c4[(int64_t)(j + AH) * 32] : z4;
+        vq[AH - 1] = (j + AH < nch) ? v4[(int64_t)(j + AH) * 32] : z2;
         const float x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
         const float2 f01 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.x));
         const float2 f23 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.y));
@@ -289,12 +293,6 @@ __device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const
         acc = fmaf(f01.y, x1, acc);
         acc = fmaf(f23.x, x2, acc);
         acc = fmaf(f23.y, x3, acc);
-        if (AH > 1) {
-            c0 = c1; v0 = v1;
-            c1 = cn; v1 = vn;
-        } else {
-            c0 = cn; v0 = vn;
-        }
     }
     const int64_t tb = sbase + (int64_t)nch * 128 + lane;
     for (int k = 0; k < (w & 3); ++k) acc = fmaf(__half2float(val[tb + (int64_t)k * 32]), x[col[tb + (int64_t)k * 32]], acc);
@@ -427,6 +425,69 @@ __global__ void __launch_bounds__(BS) k_sweep_s(const int32_t *__restrict__ perm
     y[r] = fmaf(om, br - acc, xr);
 }
 
+// A row of the width-sorted copy with FP32 values: the same chunked layout as
+// row_dot_c (one 16-byte column load and one 16-byte value load per 4-entry
+// chunk, one or two chunks in flight), the entries in their stored order.
+template <int U>
+__device__ __forceinline__ float row_dot_cf(const float *__restrict__ val, const int32_t *__restrict__ col,
+                                            const float *__restrict__ x, int64_t sbase, int lane, int w) {
+    constexpr int AH = (U > 1) ? 2 : 1;
+    const int4 z4 = make_int4(0, 0, 0, 0);
+    const float4 zf = make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc = 0.f;
+    const int nch = w >> 2;
+    const int4 *c4 = reinterpret_cast<const int4 *>(col + sbase) + lane;
+    const float4 *v4 = reinterpret_cast<const float4 *>(val + sbase) + lane;
+    int4 cq[AH];
+    float4 vq[AH];
+#pragma unroll
+    for (int a = 0; a < AH; ++a) {
+        cq[a] = a < nch ? c4[(int64_t)a * 32] : z4;
+        vq[a] = a < nch ? v4[(int64_t)a * 32] : zf;
+    }
+    for (int j = 0; j < nch; ++j) {
+        const int4 c0 = cq[0];
+        const float4 v0 = vq[0];
+#pragma unroll
+        for (int a = 0; a + 1 < AH; ++a) {
+            cq[a] = cq[a + 1];
+            vq[a] = vq[a + 1];
+        }
+        cq[AH - 1] = (j + AH < nch) ? c4[(int64_t)(j + AH) * 32] : z4;
+        vq[AH - 1] = (j + AH < nch) ? v4[(int64_t)(j + AH) * 32] : zf;
+        const float x0 = x[c0.x], x1 = x[c0.y], x2 = x[c0.z], x3 = x[c0.w];
+        acc = fmaf(v0.x, x0, acc);
+        acc = fmaf(v0.y, x1, acc);
+        acc = fmaf(v0.z, x2, acc);
+        acc = fmaf(v0.w, x3, acc);
+    }
+    const int64_t tb = sbase + (int64_t)nch * 128 + lane;
+    for (int k = 0; k < (w & 3); ++k) acc = fmaf(val[tb + (int64_t)k * 32], x[col[tb + (int64_t)k * 32]], acc);
+    return acc;
+}
+
+// y = Ahat x on the width-sorted FP32 copy, skipped once the cycle is done
+// (the Arnoldi product of k_spmv<4, float> with the same bits)
+template <int BS, int U = 1>
+__global__ void __launch_bounds__(BS) k_spmv_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
+                                               const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
+                                               const float *__restrict__ val, int64_t nslot,
+                                               const float *__restrict__ x, float *__restrict__ y,
+                                               const GmresState *__restrict__ st, RowSkip skip) {
+    const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
+    if (sl_ >= nslot) return;
+    const int r = perm[sl_];
+    const int sl = (int)(sl_ >> 5), lane = (int)(sl_ & 31);
+    const int w = (int)sw[sl];
+    const int64_t sb = (int64_t)soff[sl] * 32;
+    if (st->done || r < 0) return;
+    if (skip.nbo && skip.bdone[skip.nbo[r]]) {
+        y[r] = 0.f;
+        return;
+    }
+    y[r] = row_dot_cf<U>(val, col, x, sb, lane, w);
+}
+
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
 // autotuner chose (64, 128, 256 or 512 threads).
 #define APC_ROWS_BS(c, kind, n, KERNEL_OF, ...)                                                                 \
@@ -454,6 +515,7 @@ __global__ void __launch_bounds__(BS) k_sweep_s(const int32_t *__restrict__ perm
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
 #define APC_SWEEPS(B, U) (k_sweep_s<B, U>)
+#define APC_SPMVS(B, U) (k_spmv_s<B, U>)
 
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
@@ -504,6 +566,10 @@ template <class VT> __device__ __forceinline__ VT zerov();
 template <> __device__ __forceinline__ double2 zerov<double2>() { return make_double2(0.0, 0.0); }
 template <> __device__ __forceinline__ float4 zerov<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
 
+// Dots of the staged tile ws with the basis vectors.  A basis of j1 <= GW / 2
+// vectors splits the tile's chunks into GW / j1 parts, warp wid taking vector
+// wid % j1 over part wid / j1 (every warp streams even for the first steps of
+// a cycle); larger bases give warp wid the vectors wid, wid + GW, ...
 template <class T>
 __device__ __forceinline__ void tile_dots(const T *__restrict__ V, int64_t ldv, int64_t base, int lim, int j1,
                                           const T *ws, T (&acc)[KPW]) {
@@ -511,13 +577,25 @@ __device__ __forceinline__ void tile_dots(const T *__restrict__ V, int64_t ldv, 
     constexpr int VN = Vec<T>::n;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const VT *wv = reinterpret_cast<const VT *>(ws);
+    const int parts = GW / j1;
+    if (parts >= 2) {
+        const int k = wid % j1, part = wid / j1;
+        if (part < parts) {
+            const VT *vk = reinterpret_cast<const VT *>(V + (int64_t)k * ldv + base);
+            T a = acc[0];
+#pragma unroll 8
+            for (int c = lane + 32 * part; c < lim / VN; c += 32 * parts) a = dotv(__ldg(vk + c), wv[c], a);
+            acc[0] = a;
+        }
+        return;
+    }
 #pragma unroll
     for (int kk = 0; kk < KPW; ++kk) {
         const int k = wid + GW * kk;
         if (k < j1) {   // uniform across the warp
             const VT *vk = reinterpret_cast<const VT *>(V + (int64_t)k * ldv + base);
             T a = acc[kk];
-#pragma unroll 4
+#pragma unroll 8
             for (int c = lane; c < lim / VN; c += 32) a = dotv(__ldg(vk + c), wv[c], a);
             acc[kk] = a;
         }
@@ -530,117 +608,26 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.   (nrow = ldv)
-template <int PASS, class T>
-__global__ void __launch_bounds__(DT) k_gs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
-                                                T *__restrict__ w, GmresState *st, double *__restrict__ partial,
-                                                const uint8_t *__restrict__ tact) {
-    typedef typename Vec<T>::type VT;
-    constexpr int VN = Vec<T>::n;
-    __shared__ __align__(16) T ws[TILE];
-    __shared__ T hs[MAX_RESTART];
-    __shared__ double red[MAX_RESTART];
-    __shared__ double sm[DT + DT / 32 + 8];
-    __shared__ double fs[64];
-    if (st->done) return;
-    const int j1 = j + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (PASS == 1 && tid < j1) hs[tid] = (T)st->h1[tid];
-    __syncthreads();
-    T acc[KPW];
-#pragma unroll
-    for (int kk = 0; kk < KPW; ++kk) acc[kk] = (T)0;
-    VT *wsv = reinterpret_cast<VT *>(ws);
-    for (int64_t base = (int64_t)blockIdx.x * TILE; base < nrow; base += (int64_t)gridDim.x * TILE) {
-        if (tact && !tact[base / TILE]) continue;   // every row of the tile is zero (converged beams)
-        const int lim = (int)((nrow - base) < TILE ? (nrow - base) : TILE);
-        VT *wg = reinterpret_cast<VT *>(w + base);
-        if (PASS == 0) {
-            for (int cix = tid; cix < lim / VN; cix += DT) wsv[cix] = wg[cix];
-        } else {
-            for (int cix = tid; cix < lim / VN; cix += DT) {
-                VT wi = wg[cix];
-                const T *vb = V + base;
-#pragma unroll 4
-                for (int k = 0; k < j1; ++k)
-                    wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(vb + (int64_t)k * ldv) + cix), hs[k]);
-                wg[cix] = wi;
-                wsv[cix] = wi;
-            }
-        }
-        __syncthreads();
-        tile_dots<T>(V, ldv, base, lim, j1, ws, acc);
-        __syncthreads();
-    }
-#pragma unroll
-    for (int kk = 0; kk < KPW; ++kk) {
-        const int k = wid + GW * kk;
-        if (k < j1) {
-            double v = warp_sum((double)acc[kk]);
-            if (lane == 0) red[k] = v;
-        }
-    }
-    __syncthreads();
-    if (tid < j1) partial[(int64_t)blockIdx.x * 64 + tid] = red[tid];
-    if (!last_block(&st->ticket)) return;
-    final_sums(partial, gridDim.x, j1, sm, fs);
-    if (tid < j1) {
-        if (PASS == 0) st->h1[tid] = fs[tid];
-        else st->h2[tid] = fs[tid];
-    }
-    if (tid == 0) st->ticket = 0;
-}
-
-// wraw = w - V h2 ; ||wraw||^2 ; Hessenberg column, Givens rotation and
-// convergence test in the last block (Saad, Algorithms 6.9 / 6.10)
-// In a captured cycle it also sets the condition of the next step's body
-// (set_next): 1 while the stopping test has not passed.
-template <class T>
-__global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t ldv, int nrow, int j,
-                                                const T *__restrict__ w, T *__restrict__ wraw, GmresState *st,
-                                                double *__restrict__ partial, const uint8_t *__restrict__ tact,
-                                                cudaGraphConditionalHandle next, int set_next) {
-    typedef typename Vec<T>::type VT;
-    constexpr int VN = Vec<T>::n;
-    __shared__ T hs[MAX_RESTART];
-    __shared__ double sm[RT + RT / 32 + 8];
-    __shared__ double fs[1];
-    if (st->done) return;
-    const int j1 = j + 1, tid = threadIdx.x;
-    if (tid < j1) hs[tid] = (T)st->h2[tid];
-    __syncthreads();
-    T sq = (T)0;
-    const int nch = nrow / VN;
-    const VT *wv = reinterpret_cast<const VT *>(w);
-    VT *ov = reinterpret_cast<VT *>(wraw);
-    for (int cix = blockIdx.x * GT + tid; cix < nch; cix += gridDim.x * GT) {
-        if (tact && !tact[(int64_t)cix * VN / TILE]) continue;
-        VT wi = wv[cix];
-#pragma unroll 4
-        for (int k = 0; k < j1; ++k)
-            wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix), hs[k]);
-        ov[cix] = wi;
-        sq = sumsq(wi, sq);
-    }
-    double a1[1] = {(double)sq};
-    double tot = 0.0;
-    block_reduce_many<1>(a1, 1, sm, &tot);
-    if (tid == 0) partial[(int64_t)blockIdx.x * 64] = tot;
-    if (!last_block(&st->ticket)) return;
-    final_sums(partial, gridDim.x, 1, sm, fs);
-    // Hessenberg column j, its rotations and the stopping test: the inputs are
-    // loaded in parallel into shared memory, the serial part runs there, and the
-    // results are written back in parallel (dependent global round trips in one
-    // thread would dominate the kernel)
+// Hessenberg column j (h1 + h2 over its first j + 1 rows, h_{j+1,j} =
+// sqrt(hn2)), its Givens rotations and the stopping test (Saad, Algorithms
+// 6.9 / 6.10), run by the whole last block of a reduction: the inputs are
+// loaded in parallel into shared memory, the serial part runs in thread 0
+// (the only thread whose hn2 is read), the column is written back in
+// parallel (dependent global round trips in one thread would dominate the
+// kernel).  In a captured cycle it also sets the condition of the next
+// step's body (set_next): 1 while the stopping test has not passed.
+__device__ void arnoldi_tail(GmresState *st, int j, const double *h2s, double hn2, cudaGraphConditionalHandle next,
+                             int set_next) {
     __shared__ double col[MAX_RESTART + 1], csj[MAX_RESTART], snj[MAX_RESTART];
-    if (tid <= j) col[tid] = __ldcg(&st->h1[tid]) + __ldcg(&st->h2[tid]);
+    const int tid = threadIdx.x;
+    if (tid <= j) col[tid] = __ldcg(&st->h1[tid]) + h2s[tid];
     if (tid < j) {
         csj[tid] = __ldcg(&st->cs[tid]);
         snj[tid] = __ldcg(&st->sn[tid]);
     }
     __syncthreads();
     if (tid == 0) {
-        const int M = MAX_RESTART;
-        const double hn = sqrt(fs[0]);
+        const double hn = sqrt(hn2 > 0.0 ? hn2 : 0.0);
         col[j + 1] = hn;
         for (int i = 0; i < j; ++i) {
             const double a = col[i], bb = col[i + 1];
@@ -667,6 +654,151 @@ __global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t
     if (tid <= j + 1) st->H[tid * MAX_RESTART + j] = col[tid];
 }
 
+// PASS 0: h1 = V^T w.   PASS 1: w -= V h1, then h2 = V^T w.   (nrow = ldv)
+// PASS 2: PASS 1 and ||w||^2 in the same sweep (j + 1 < 64); the last block
+// closes the Arnoldi step with ||w - V h2||^2 = ||w||^2 - ||h2||^2 (V has
+// orthonormal columns and h2 = V^T w), so that the second update and the
+// normalisation can run as one pass at the start of the next step
+// (k_gs_update_normalize).
+template <int PASS, class T>
+__global__ void __launch_bounds__(DT, 2) k_gs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                T *__restrict__ w, GmresState *st, double *__restrict__ partial,
+                                                const uint8_t *__restrict__ tact, cudaGraphConditionalHandle next,
+                                                int set_next) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ __align__(16) T ws[TILE];
+    __shared__ T hs[MAX_RESTART];
+    __shared__ double red[MAX_RESTART + 1];
+    __shared__ double wsum[GW];
+    __shared__ double sm[DT + DT / 32 + 8];
+    __shared__ double fs[MAX_RESTART + 1];
+    if (st->done) return;
+    const int j1 = j + 1, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nk = j1 + (PASS == 2 ? 1 : 0);
+    if (PASS >= 1 && tid < j1) hs[tid] = (T)st->h1[tid];
+    __syncthreads();
+    T acc[KPW];
+#pragma unroll
+    for (int kk = 0; kk < KPW; ++kk) acc[kk] = (T)0;
+    T sq = (T)0;
+    VT *wsv = reinterpret_cast<VT *>(ws);
+    for (int64_t base = (int64_t)blockIdx.x * TILE; base < nrow; base += (int64_t)gridDim.x * TILE) {
+        if (tact && !tact[base / TILE]) continue;   // every row of the tile is zero (converged beams)
+        const int lim = (int)((nrow - base) < TILE ? (nrow - base) : TILE);
+        VT *wg = reinterpret_cast<VT *>(w + base);
+        if (PASS == 0) {
+            for (int cix = tid; cix < lim / VN; cix += DT) wsv[cix] = wg[cix];
+        } else {
+            for (int cix = tid; cix < lim / VN; cix += DT) {
+                VT wi = wg[cix];
+                const T *vb = V + base;
+#pragma unroll 8
+                for (int k = 0; k < j1; ++k)
+                    wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(vb + (int64_t)k * ldv) + cix), hs[k]);
+                wg[cix] = wi;
+                wsv[cix] = wi;
+                if (PASS == 2) sq = sumsq(wi, sq);
+            }
+        }
+        __syncthreads();
+        tile_dots<T>(V, ldv, base, lim, j1, ws, acc);
+        __syncthreads();
+    }
+    if (GW / j1 >= 2) {
+        // one partial per warp; the parts of each vector summed in a fixed order
+        const double v = warp_sum((double)acc[0]);
+        if (lane == 0) wsum[wid] = v;
+        __syncthreads();
+        if (tid < j1) {
+            double s = 0.0;
+            for (int part = 0; part < GW / j1; ++part) s += wsum[tid + j1 * part];
+            red[tid] = s;
+        }
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < KPW; ++kk) {
+            const int k = wid + GW * kk;
+            if (k < j1) {
+                double v = warp_sum((double)acc[kk]);
+                if (lane == 0) red[k] = v;
+            }
+        }
+    }
+    if (PASS == 2) {
+        __syncthreads();
+        const double v = warp_sum((double)sq);
+        if (lane == 0) wsum[wid] = v;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int q = 0; q < GW; ++q) s += wsum[q];
+            red[j1] = s;
+        }
+    }
+    __syncthreads();
+    if (tid < nk) partial[(int64_t)blockIdx.x * 64 + tid] = red[tid];
+    if (!last_block(&st->ticket)) return;
+    final_sums(partial, gridDim.x, nk, sm, fs);
+    if (PASS == 2) {
+        if (tid < j1) st->h2[tid] = fs[tid];
+        double hn2 = 0.0;
+        if (tid == 0) {
+            double h2sq = 0.0;
+            for (int k = 0; k < j1; ++k) h2sq = fma(fs[k], fs[k], h2sq);
+            hn2 = fs[j1] - h2sq;
+        }
+        arnoldi_tail(st, j, fs, hn2, next, set_next);
+        return;
+    }
+    if (tid < j1) {
+        if (PASS == 0) st->h1[tid] = fs[tid];
+        else st->h2[tid] = fs[tid];
+    }
+    if (tid == 0) st->ticket = 0;
+}
+
+// wraw = w - V h2 ; ||wraw||^2 ; Hessenberg column, Givens rotation and
+// convergence test in the last block (arnoldi_tail)
+template <class T>
+__global__ void __launch_bounds__(GT) k_gs_norm(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                const T *__restrict__ w, T *__restrict__ wraw, GmresState *st,
+                                                double *__restrict__ partial, const uint8_t *__restrict__ tact,
+                                                cudaGraphConditionalHandle next, int set_next) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ T hs[MAX_RESTART];
+    __shared__ double sm[RT + RT / 32 + 8];
+    __shared__ double fs[1];
+    if (st->done) return;
+    const int j1 = j + 1, tid = threadIdx.x;
+    if (tid < j1) hs[tid] = (T)st->h2[tid];
+    __syncthreads();
+    T sq = (T)0;
+    const int nch = nrow / VN;
+    const VT *wv = reinterpret_cast<const VT *>(w);
+    VT *ov = reinterpret_cast<VT *>(wraw);
+    for (int cix = blockIdx.x * GT + tid; cix < nch; cix += gridDim.x * GT) {
+        if (tact && !tact[(int64_t)cix * VN / TILE]) continue;
+        VT wi = wv[cix];
+#pragma unroll 8
+        for (int k = 0; k < j1; ++k)
+            wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix), hs[k]);
+        ov[cix] = wi;
+        sq = sumsq(wi, sq);
+    }
+    double a1[1] = {(double)sq};
+    double tot = 0.0;
+    block_reduce_many<1>(a1, 1, sm, &tot);
+    if (tid == 0) partial[(int64_t)blockIdx.x * 64] = tot;
+    if (!last_block(&st->ticket)) return;
+    final_sums(partial, gridDim.x, 1, sm, fs);
+    __shared__ double h2s[MAX_RESTART];
+    if (tid <= j) h2s[tid] = __ldcg(&st->h2[tid]);
+    __syncthreads();
+    arnoldi_tail(st, j, h2s, fs[0], next, set_next);
+}
+
 // u += V y with H y = g solved (upper triangular, jend x jend) in every block
 template <class T>
 __global__ void __launch_bounds__(GT) k_cycle_end(const T *__restrict__ V, int64_t ldv, int nrow, T *__restrict__ u,
@@ -690,7 +822,7 @@ __global__ void __launch_bounds__(GT) k_cycle_end(const T *__restrict__ V, int64
     VT *uv = reinterpret_cast<VT *>(u);
     for (int cix = blockIdx.x * GT + threadIdx.x; cix < nrow / VN; cix += gridDim.x * GT) {
         VT s = zerov<VT>();
-#pragma unroll 4
+#pragma unroll 8
         for (int k = 0; k < je; ++k) s = fmav(__ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix), ys[k], s);
         uv[cix] = addv(uv[cix], s);
     }
@@ -736,6 +868,33 @@ __global__ void k_normalize_first(const T *__restrict__ wraw, T *__restrict__ vj
         T v = wraw[i] * (T)st->inv_norm;
         vj[i] = v;
         z[i] = (T)st->omega * v;
+    }
+}
+
+// Start of Arnoldi step j >= 1 after a PASS 2 step: V_j = (w - V h2) / h_{j,j-1}
+// over the j previous basis vectors, z = omega V_j (first sweep of the
+// polynomial from z = 0)
+template <class T>
+__global__ void __launch_bounds__(GT) k_gs_update_normalize(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                            const T *__restrict__ w, T *__restrict__ vj,
+                                                            T *__restrict__ z, const GmresState *__restrict__ st) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ T hs[MAX_RESTART];
+    if (st->done) return;
+    if (threadIdx.x < j) hs[threadIdx.x] = (T)st->h2[threadIdx.x];
+    __syncthreads();
+    const T inv = (T)st->inv_norm, om = (T)st->omega;
+    const VT *wv = reinterpret_cast<const VT *>(w);
+    VT *vv = reinterpret_cast<VT *>(vj), *zv = reinterpret_cast<VT *>(z);
+    for (int cix = blockIdx.x * GT + threadIdx.x; cix < nrow / VN; cix += gridDim.x * GT) {
+        VT wi = wv[cix];
+#pragma unroll 8
+        for (int k = 0; k < j; ++k)
+            wi = axpyv(wi, __ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix), hs[k]);
+        const VT v = fmav(wi, inv, zerov<VT>());
+        vv[cix] = v;
+        zv[cix] = fmav(v, om, zerov<VT>());
     }
 }
 
@@ -811,9 +970,14 @@ void gs_dispatch(apcloud_ctx *c, int pass, int nblk, const T *V, int64_t ldv, in
     (void)nblk;
     const int nrow = (int)ldv;
     if (pass == 0)
-        APC_LAUNCH(c, K_DOT, dot_blocks(ldv), DT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial, tact);
+        APC_LAUNCH(c, K_DOT, dot_blocks(ldv), DT, 0, (k_gs_dots<0, T>), V, ldv, nrow, j, w, st, partial, tact,
+                   next, 0);
     else if (pass == 1)
-        APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial, tact);
+        APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<1, T>), V, ldv, nrow, j, w, st, partial, tact,
+                   next, 0);
+    else if (pass == 3)   // PASS 2 of k_gs_dots: the step's last kernel
+        APC_LAUNCH(c, K_UPDDOT, dot_blocks(ldv), DT, 0, (k_gs_dots<2, T>), V, ldv, nrow, j, w, st, partial, tact,
+                   next, set_next);
     else
         APC_LAUNCH(c, K_UPDNORM, stream_blocks(ldv), GT, 0, k_gs_norm<T>, V, ldv, nrow, j, (const T *)w, wraw, st,
                    partial, tact, next, set_next);
@@ -1232,8 +1396,12 @@ struct Krylov {
     const int32_t *sperm = nullptr, *scol = nullptr;
     const uint32_t *ssw = nullptr, *sso = nullptr;
     const __half *sval = nullptr;
+    const float *sval32 = nullptr;  // FP32 values of the same copy (Arnoldi products)
     int64_t nslot = 0;
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
+    // flexible basis: Z_j = p(Ahat) v_j kept from step j, so that the cycle ends
+    // with u += Z y instead of applying the polynomial to V y once more
+    T *Z = nullptr;
     bool graphs = true;             // replay full restart cycles as CUDA graphs
     int *jhint = nullptr;           // Arnoldi steps the last cycle of this system used (cycle cap)
     RowSkip skip{nullptr, nullptr};         // batches: rows of converged beams
@@ -1246,10 +1414,11 @@ struct Krylov {
 
 // z = p(Ahat) v with p(A) = omega sum_{i<d} (I - omega A)^i: d damped Jacobi
 // sweeps from z = 0 (the first one is z = omega v).  Returns the buffer
-// holding z.  v is read with a full row and the sweeps ping-pong z0/z1.
+// holding z.  v is read with a full row and the sweeps ping-pong z0/z1; the
+// last sweep writes to `last` when it is given.
 template <class T>
 T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov<T> &K, GmresState *st,
-              RowSkip skip) {
+              RowSkip skip, T *last = nullptr) {
     const int n = c->n_tot;
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
@@ -1258,6 +1427,7 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     }
     T *cur = z_first, *nxt = (z_first == K.z0) ? K.z1 : K.z0;
     for (int i = 1; i < K.pdeg; ++i) {
+        if (last && i + 1 == K.pdeg) nxt = last;   // the last sweep writes where the caller keeps z
         if constexpr (sizeof(T) == 4) {
             if (K.hval && K.sperm) {
                 APC_SWEEP_BS(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
@@ -1277,6 +1447,25 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
         T *tmp = cur; cur = nxt; nxt = tmp;
     }
     return cur;
+}
+
+// w = Ahat z of a polynomial-preconditioned Arnoldi step (skipped once the
+// cycle is done): on the width-sorted FP32 copy when the sweeps use it, else
+// on the ELL
+template <class T>
+void arnoldi_product(apcloud_ctx *c, const T *val, const Krylov<T> &K, const T *z, GmresState *st, RowSkip skip) {
+    const int n = c->n_tot;
+    if constexpr (sizeof(T) == 4) {
+        if (K.sval32 && K.sperm) {
+            APC_SPMV_BS(c, K.nslot, APC_SPMVS, K.sperm, K.ssw, K.sso, K.scol, K.sval32, K.nslot, (const float *)z,
+                        (float *)K.w, (const GmresState *)st, skip);
+            return;
+        }
+    }
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, z, K.w, (T *)nullptr, (const T *)nullptr, st,
+                (double *)nullptr, skip);
 }
 
 // bnorm .. jlast of GmresState, read back once per restart cycle; jlast is the
@@ -1338,9 +1527,9 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
             T *vj = K.V + (int64_t)j * K.ldv;
             APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_bnormalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
                        bk.nbo, (const int *)bk.done, (const double *)bk.binv, (const GmresState *)st);
-            T *z = poly_apply<T>(c, val, vj, K.z0, K, st, RowSkip{bk.nbo, bk.done, nullptr});
-            APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, (const T *)z, K.w, (T *)nullptr,
-                        (const T *)nullptr, st, (double *)nullptr, RowSkip{bk.nbo, bk.done, nullptr});
+            T *z = poly_apply<T>(c, val, vj, K.z0, K, st, RowSkip{bk.nbo, bk.done, nullptr},
+                                 K.Z ? K.Z + (int64_t)j * K.ldv : nullptr);
+            arnoldi_product<T>(c, val, K, (const T *)z, st, RowSkip{bk.nbo, bk.done, nullptr});
         }
         APC_LAUNCH(c, K_DOT, bk.nitems, BGT, 0, (k_bgs_dots<0, T>), (const T *)K.V, K.ldv, j, K.w, bk,
                    (const GmresState *)st, K.partial);
@@ -1358,8 +1547,9 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
         if (c->stopped) break;
     }
     APC_LAUNCH(c, K_CYCLE, div_up(bk.nb, 64), 64, 0, k_bsolve_y, bk);
-    if (K.pdeg <= 1) {
-        APC_LAUNCH(c, K_CYCLE, bk.nitems, BGT, 0, (k_bcombine<true, T>), (const T *)K.V, K.ldv, u, bk);
+    if (K.pdeg <= 1 || K.Z) {
+        APC_LAUNCH(c, K_CYCLE, bk.nitems, BGT, 0, (k_bcombine<true, T>), (const T *)(K.Z ? K.Z : K.V), K.ldv, u,
+                   bk);
     } else {
         // u += p(Ahat) (V y), beam by beam; beams converged before this cycle are skipped
         APC_LAUNCH(c, K_CYCLE, bk.nitems, BGT, 0, (k_bcombine<false, T>), (const T *)K.V, K.ldv, K.t, bk);
@@ -1377,6 +1567,17 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
     return cuda_check(c, cudaGetLastError(), "batched gmres cycle");
 }
 
+// A single-beam polynomial (or ILU) cycle closes each Arnoldi step with the
+// second Gram-Schmidt pass and the norm in one sweep (k_gs_dots PASS 2) and
+// opens the next with the second update and the normalisation in one
+// (k_gs_update_normalize): two reductions and three passes over the basis
+// per step.  Jacobi cycles normalise inside their product and batches skip
+// converged tiles, so they keep the separate norm pass.
+template <class T>
+bool gs_fused(const Krylov<T> &K, int jmax) {
+    return K.pdeg > 1 && !K.bk && !K.tact && !K.skip.nbo && jmax < MAX_RESTART;
+}
+
 // One restart cycle of jmax Arnoldi steps, the update of u, and the residual
 // b - Ahat u that opens the next cycle (beta, g, done for it).
 template <class T>
@@ -1386,6 +1587,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     const int32_t *col = ptr<int32_t>(c->ell_col);
     GmresState *st = K.st;
     if (K.bk) return bcycle_launches<T>(c, val, b, u, K, jmax);
+    const bool fused = gs_fused(K, jmax);
     for (int j = 0; j < jmax; ++j) {
         begin_step(c, j);
         if (K.pdeg <= 1) {
@@ -1394,23 +1596,33 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
         } else {
             // w = Ahat p(Ahat) v_j (right preconditioning)
             T *vj = K.V + (int64_t)j * K.ldv;
-            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_normalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
-                       (const GmresState *)st);
-            T *z = poly_apply<T>(c, val, vj, K.z0, K, st, K.skip);
-            APC_SPMV_BS(c, n, APC_SPMV4, sw, so, col, val, n, (const T *)z, K.w, (T *)nullptr,
-                        (const T *)nullptr, st, (double *)nullptr, K.skip);
+            if (fused && j > 0)
+                APC_LAUNCH(c, K_UPDNORM, stream_blocks(K.ldv), GT, 0, k_gs_update_normalize<T>, (const T *)K.V,
+                           K.ldv, (int)K.ldv, j, (const T *)K.w, vj, K.z0, (const GmresState *)st);
+            else
+                APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_normalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
+                           (const GmresState *)st);
+            T *z = poly_apply<T>(c, val, vj, K.z0, K, st, K.skip, K.Z ? K.Z + (int64_t)j * K.ldv : nullptr);
+            arnoldi_product<T>(c, val, K, (const T *)z, st, K.skip);
         }
+        const int set_next = (c->capturing && j + 1 < jmax) ? 1 : 0;
         gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
-        gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
-        gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact, next_step_cond(c, j),
-                       (c->capturing && j + 1 < jmax) ? 1 : 0);
+        if (fused) {
+            gs_dispatch<T>(c, 3, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact, next_step_cond(c, j),
+                           set_next);
+        } else {
+            gs_dispatch<T>(c, 1, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
+            gs_dispatch<T>(c, 2, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact, next_step_cond(c, j),
+                           set_next);
+        }
         end_step(c);
         APC_TRY(stop_when_done(c, st));
         if (c->stopped) break;
     }
-    if (K.pdeg <= 1) {
-        APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)K.V, K.ldv, (int)K.ldv, u,
-                   (const GmresState *)st);
+    if (K.pdeg <= 1 || K.Z) {
+        // u += V y (Jacobi: the preconditioner is in the stored matrix) or u += Z y
+        APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), GT, 0, k_cycle_end<T>, (const T *)(K.Z ? K.Z : K.V), K.ldv,
+                   (int)K.ldv, u, (const GmresState *)st);
     } else {
         // u += p(Ahat) (V y)
         APC_LAUNCH(c, K_CYCLE, stream_blocks(K.ldv), 256, 0, k_combine<T>, (const T *)K.V, K.ldv, n, K.t,
@@ -1449,7 +1661,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
                            K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,
                            K.bk ? K.bk->H : nullptr, K.bk ? K.bk->done : nullptr,
                            K.bk ? (const void *)(intptr_t)K.bk->nitems : nullptr, K.sperm, K.sval, K.scol, K.ssw,
-                           K.sso};
+                           K.sso, K.Z, K.sval32};
         static_assert(sizeof p <= sizeof key.p, "graph key holds every buffer address");
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
@@ -1520,16 +1732,24 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         {
             // per Arnoldi step: one product with the full matrix, pdeg - 1 sweeps (FP16
             // values when available); the cycle end adds pdeg - 1 sweeps, the restart one product
-            const double sweeps = (K.pdeg <= 1 || K.ilu) ? 0.0 : (double)(K.pdeg - 1) * (je + 1);
+            const double sweeps = (K.pdeg <= 1 || K.ilu) ? 0.0 : (double)(K.pdeg - 1) * (je + (K.Z ? 0 : 1));
             const double prods = je + 1.0;
             const double sb = K.hval ? 2.0 : vb;
             account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
             account(c, K_SWEEP, ((sb + 4.0) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
         }
+        const bool fused = gs_fused(K, jmax);
         for (int j = 0; j < je; ++j) {
             account(c, K_DOT, vb * dn * (j + 2), 2.0 * dn * (j + 1));
-            account(c, K_UPDDOT, vb * dn * (j + 3), 4.0 * dn * (j + 1));
-            account(c, K_UPDNORM, vb * dn * (j + 3), 2.0 * dn * (j + 2));
+            if (fused) {
+                // PASS 2 with its sum of squares; step j >= 1 opened with w - V h2 over
+                // its j predecessors, written to V_j and z
+                account(c, K_UPDDOT, vb * dn * (j + 3), 4.0 * dn * (j + 1) + 2.0 * dn);
+                if (j > 0) account(c, K_UPDNORM, vb * dn * (j + 3), 2.0 * dn * (j + 1));
+            } else {
+                account(c, K_UPDDOT, vb * dn * (j + 3), 4.0 * dn * (j + 1));
+                account(c, K_UPDNORM, vb * dn * (j + 3), 2.0 * dn * (j + 2));
+            }
         }
         account(c, K_CYCLE, vb * dn * (je + 2), 2.0 * dn * je);
         iters += je;
@@ -1691,6 +1911,10 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
             K.z1 = ensure<double>(c, c->pz1, ldv + 1);
             K.t = ensure<double>(c, c->pt, ldv + 1);
             if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
+            if (!ilu) {
+                K.Z = ensure<double>(c, c->zbasis, (int64_t)m * ldv);
+                if (!K.Z) return APCLOUD_E_NOMEM;
+            }
             if (ilu) {
                 K.ilu = &c->ilu;
                 K.graphs = false;   // thousands of level launches per step
@@ -1726,12 +1950,14 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
                 K.sso = ptr<uint32_t>(c->ss_o);
                 K.scol = ptr<int32_t>(c->ss_col);
                 K.sval = ptr<__half>(which ? c->ss_A : c->ss_B);
+                K.sval32 = ptr<float>(which ? c->ss_A32 : c->ss_B32);
                 K.nslot = (int64_t)div_up(c->n_tot, 256) * 256;
             }
             K.z0 = ensure<float>(c, c->pz0, ldv + 1);
             K.z1 = ensure<float>(c, c->pz1, ldv + 1);
             K.t = ensure<float>(c, c->pt, ldv + 1);
-            if (!K.z0 || !K.z1 || !K.t) return APCLOUD_E_NOMEM;
+            K.Z = ensure<float>(c, c->zbasis, (int64_t)m * ldv);
+            if (!K.z0 || !K.z1 || !K.t || !K.Z) return APCLOUD_E_NOMEM;
         }
         if (bk && K.pdeg > 1) {
             K.bk = bk;   // beams frozen by the outer loop have zero residual: their inner spaces stop at once

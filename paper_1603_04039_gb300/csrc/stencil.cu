@@ -820,9 +820,11 @@ __device__ __forceinline__ int64_t ss_slot(int64_t sb, int w, int k, int lane) {
 // copy every row's stored entries (in their order) into its slot of the sorted layout
 __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                           const int32_t *__restrict__ col, const __half *__restrict__ hA, const __half *__restrict__ hB,
+                          const float *__restrict__ fA, const float *__restrict__ fB,
                           const int32_t *__restrict__ perm, const uint32_t *__restrict__ w2,
                           const uint32_t *__restrict__ o2, int64_t nslot, int32_t *__restrict__ col2,
-                          __half *__restrict__ A2, __half *__restrict__ B2) {
+                          __half *__restrict__ A2, __half *__restrict__ B2, float *__restrict__ A4,
+                          float *__restrict__ B4) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslot) return;
     const int sl2 = (int)(s >> 5), lane2 = (int)(s & 31);
@@ -839,6 +841,8 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
             col2[q] = col[e];
             A2[q] = hA[e];
             B2[q] = hB[e];
+            A4[q] = fA[e];
+            B4[q] = fB[e];
         }
     }
     for (; k < wid2; ++k) {   // padding: the row itself (or row 0) with value 0
@@ -846,6 +850,8 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
         col2[q] = r >= 0 ? r : 0;
         A2[q] = __float2half(0.f);
         B2[q] = __float2half(0.f);
+        A4[q] = 0.f;
+        B4[q] = 0.f;
     }
 }
 
@@ -859,7 +865,8 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
 // the entries are grouped in 4-entry chunks per row (16-byte column loads),
 // the last width % 4 columns as in the ELL.  Each row keeps its entries in
 // their stored order, so a sweep on this copy gives the same bits as on the
-// ELL.
+// ELL.  The copy carries the FP16 values of the sweeps and the FP32 values of
+// the Arnoldi products (also the same bits as the FP32 ELL product).
 apcloud_status build_sorted_sweep(apcloud_ctx *c) {
     c->ss_ok = false;
     const int n = c->n_tot;
@@ -878,11 +885,13 @@ apcloud_status build_sorted_sweep(apcloud_ctx *c) {
     c->ss_entries = (int64_t)tot * 32;
     int32_t *col2 = ensure<int32_t>(c, c->ss_col, c->ss_entries + 1);
     __half *A2 = ensure<__half>(c, c->ss_A, c->ss_entries + 1), *B2 = ensure<__half>(c, c->ss_B, c->ss_entries + 1);
-    if (!col2 || !A2 || !B2) return APCLOUD_E_NOMEM;
+    float *A4 = ensure<float>(c, c->ss_A32, c->ss_entries + 1), *B4 = ensure<float>(c, c->ss_B32, c->ss_entries + 1);
+    if (!col2 || !A2 || !B2 || !A4 || !B4) return APCLOUD_E_NOMEM;
     APC_LAUNCH(c, K_ELL, div_up(nslot, 256), 256, 0, k_ss_fill, (const uint32_t *)ptr<uint32_t>(c->slice_w),
                (const uint32_t *)ptr<uint32_t>(c->slice_off), (const int32_t *)ptr<int32_t>(c->ell_col),
                (const __half *)ptr<__half>(c->ell_A16), (const __half *)ptr<__half>(c->ell_B16),
-               (const int32_t *)perm, (const uint32_t *)w2, (const uint32_t *)o2, nslot, col2, A2, B2);
+               (const float *)ptr<float>(c->ell_A32), (const float *)ptr<float>(c->ell_B32), (const int32_t *)perm,
+               (const uint32_t *)w2, (const uint32_t *)o2, nslot, col2, A2, B2, A4, B4);
     c->ss_ok = true;
     return cuda_check(c, cudaGetLastError(), "sorted sweep matrix");
 }
