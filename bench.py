@@ -555,7 +555,7 @@ def run_vp(args):
                 poly_omega=args.poly_omega)
     net, t_train = None, 0.0
     if args.learned:
-        net, t_train, _ = train_mpnn(args.train_systems)
+        net, t_train, _ = train_mpnn(args.train_systems, args.train_full)
     vp = VlasovPoisson(*t, qm=1.0, rtol=RTOL, net=net, **form)
     dt = 1e-3
     for _ in range(args.warmup):
@@ -615,7 +615,8 @@ def run_vp(args):
             "config": {"workload": "vp_beam_halo_1e7_depth10", "particles": npart, "dt": dt, "sigma_v": 0.01,
                        "precision": args.precision, "poly_degree": args.poly_degree,
                        "learned_preconditioner": (None if net is None else
-                                                  {"train_systems": args.train_systems, "use": "column scaling",
+                                                  {"train_systems": args.train_systems,
+                                                   "train_full_law_systems": args.train_full, "use": "column scaling",
                                                    "train_seconds": round(t_train, 1)}),
                        "mean_gmres_iters": iters / args.steps},
             "energy": {"field_start": w0, "kinetic_start": k0, "field_end": w1, "kinetic_end": k1,
@@ -627,30 +628,50 @@ def run_vp(args):
 TRAIN_SIZES = ((20000, 6, 0.3), (100000, 8, 0.15))
 
 
-def train_mpnn(n_systems, seed0=10000, lr=2e-3, net_seed=7):
-    """Trains the learned preconditioner on the GPU: one Adam step on each of
-    n_systems fresh systems from the beam-with-halo law (seeds seed0, seed0 +
-    1, ...), alternating 2e4 particles at depth 6 and 1e5 at depth 8.
-    Returns the network, seconds spent and the loss curve."""
+def train_mpnn(n_systems, n_full=0, seed0=10000, lr=2e-3, net_seed=7, full_seed0=50000):
+    """Trains the learned preconditioner on the GPU, one Adam step per fresh
+    system: first n_systems beam-with-halo systems at reduced N (alternating
+    2e4 particles at depth 6 and 1e5 at depth 8, host sampler, seeds seed0,
+    seed0 + 1, ...), then n_full systems of the full law of the 1e7-particle
+    depth-10 workload (1.05e6 nodes each), drawn on the device (seeds
+    full_seed0, ...; the held-out evaluation seeds come from the host
+    sampler).  Returns the network, seconds spent and the loss curve."""
     import torch
     from paper_1603_04039_gb300 import APCloud, MPNN, inputs
     dev = torch.device("cuda", 0)
     net = MPNN(seed=net_seed)
-    aps = [APCloud(max_depth=d, c_refine=cc, device=dev) for _, d, cc in TRAIN_SIZES]
     curve = []
     t0 = time.perf_counter()
-    for k in range(n_systems):
-        npart = TRAIN_SIZES[k % len(TRAIN_SIZES)][0]
-        ap = aps[k % len(TRAIN_SIZES)]
-        x, y, z, q = inputs.beam_with_halo(npart, seed0 + k)
-        tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
-        ap.build_octree(tx, ty, tz)
-        ap.stencils()
-        ap.deposit(q=tq, rtol=1e-10)
-        lo = net.loss(ap, backward=True)
-        net.adam(ap, lr=lr)
-        if k % max(1, n_systems // 20) == 0 or k == n_systems - 1:
-            curve.append((k, round(lo["L"], 5), round(lo["Lp"], 5), round(lo["Lg"], 5)))
+    if n_systems:
+        aps = [APCloud(max_depth=d, c_refine=cc, device=dev) for _, d, cc in TRAIN_SIZES]
+        for k in range(n_systems):
+            npart = TRAIN_SIZES[k % len(TRAIN_SIZES)][0]
+            ap = aps[k % len(TRAIN_SIZES)]
+            x, y, z, q = inputs.beam_with_halo(npart, seed0 + k)
+            tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
+            ap.build_octree(tx, ty, tz)
+            ap.stencils()
+            ap.deposit(q=tq, rtol=1e-10)
+            lo = net.loss(ap, backward=True)
+            net.adam(ap, lr=lr)
+            if k % max(1, n_systems // 20) == 0 or k == n_systems - 1:
+                curve.append(("reduced", k, round(lo["L"], 5), round(lo["Lp"], 5), round(lo["Lg"], 5)))
+        for ap in aps:
+            ap.close()
+    if n_full:
+        npart, depth, c = WORKLOADS["beam_halo_1e7_depth10"]
+        apf = APCloud(max_depth=depth, c_refine=c, device=dev)
+        for k in range(n_full):
+            tx, ty, tz, tq = inputs.beam_with_halo_device(npart, full_seed0 + k, dev)
+            apf.build_octree(tx, ty, tz)
+            apf.stencils()
+            apf.deposit(q=tq, rtol=1e-10)
+            lo = net.loss(apf, backward=True)
+            net.adam(apf, lr=lr)
+            if k % max(1, n_full // 20) == 0 or k == n_full - 1:
+                curve.append(("full", k, round(lo["L"], 5), round(lo["Lp"], 5), round(lo["Lg"], 5)))
+        apf.close()
+    torch.cuda.synchronize()
     return net, time.perf_counter() - t0, curve
 
 
@@ -664,7 +685,7 @@ def run_learned(args):
     import torch
     from paper_1603_04039_gb300 import APCloud, inputs
     dev = torch.device("cuda", 0)
-    net, t_train, curve = train_mpnn(args.train_systems)
+    net, t_train, curve = train_mpnn(args.train_systems, args.train_full)
     npart, depth, c = WORKLOADS["beam_halo_1e7_depth10"]
     forms = {"fp64_jacobi": (dict(precision="fp64", poly_degree=1), (1, 3, 4)),
              "mixed_poly16": (dict(precision="mixed", poly_degree=16, poly_omega=1.0), (1, 2, 4))}
@@ -702,14 +723,19 @@ def run_learned(args):
             ap.close()
     mx = [r for r in rows if r["form"] == "mixed_poly16"]
     speed = float(np.mean([r["learned_scaling"]["speedup"] for r in mx]))
+    # what the network adds over the formula it learns: closed-form time / learned time
+    vs_cf = float(np.mean([r["closed_form_scaling"]["ms"] / r["learned_scaling"]["ms"] for r in mx]))
     return {"metric": "Poisson solve time to rtol 1e-10 on held-out seeds, without / with the learned column "
                       "scaling (mixed form, polynomial degree 16)",
             "value": round(speed, 3), "unit": "x", "n_gpus": 1, "steps": len(args.eval_seeds), "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16+f64",
             "data": "synthetic",
+            "learned_vs_closed_form": round(vs_cf, 3),
             "config": {"workload": "learned_preconditioner_beam_halo_1e7_depth10", "train_systems": args.train_systems,
-                       "train_law": "beam with halo, alternating 2e4 particles depth 6 c 0.3 and 1e5 "
-                                    "particles depth 8 c 0.15, seeds 10000..",
+                       "train_full_law_systems": args.train_full,
+                       "train_law": "beam with halo: first alternating 2e4 particles depth 6 c 0.3 and 1e5 "
+                                    "particles depth 8 c 0.15 (host sampler, seeds 10000..), then the full "
+                                    "1e7-particle depth-10 c 0.043 law (device sampler, seeds 50000..)",
                        "eval_seeds": args.eval_seeds, "net": "3 x 64 message passing, BF16 tcgen05 layers",
                        "ilu0": "bench.py --ilu (same seeds)"},
             "train_seconds": round(t_train, 1), "loss_curve": curve, "eval": rows}
@@ -777,10 +803,11 @@ def run_profile(args):
       solve: the 1e7-particle depth-10 beam (1.05e6 nodes): tree, stencils,
              deposit, then --profile-iters Arnoldi steps of the Poisson solve
              (GMRES(30), polynomial degree 16) in --precision; --profile-sorted
-             sweeps on the width-sorted matrix at the shape the autotuner
-             picks for it (128 threads, two 4-entry chunks in flight).
+             sweeps and Arnoldi products on the width-sorted matrix at the
+             shape the autotuner picks for it (128 threads, two 4-entry chunks
+             in flight; 4 nodes per stencil block).
       batch: the 64-beam depth-9 batch, then --profile-iters Arnoldi steps
-             (--profile-sorted: 512 threads, one chunk in flight).
+             (--profile-sorted: 128 threads, two chunks in flight).
       mpnn:  --profile-iters training steps of the learned preconditioner on
              a 2e5-particle depth-8 beam.
       small: one whole solve (tree, stencils, deposit, Poisson solve, gather)
@@ -812,7 +839,7 @@ def run_profile(args):
         tx, ty, tz, tq = put(x, y, z, q)
         ap = APCloud(max_depth=10, c_refine=0.043, **form)
         if args.profile_sorted:
-            ap.set_launch_shape(spmv_block=128, wls_warps=2, spmv_unroll=4, sweep_sorted=1)
+            ap.set_launch_shape(spmv_block=128, wls_warps=4, spmv_unroll=4, sweep_sorted=1)
         ap.build_octree(tx, ty, tz)
         ap.stencils()
         ap.deposit(q=tq, rtol=RTOL)
@@ -822,7 +849,7 @@ def run_profile(args):
         tx, ty, tz, tq = put(x, y, z, q)
         ap = APCloud(max_depth=9, c_refine=0.05, **form)
         if args.profile_sorted:
-            ap.set_launch_shape(spmv_block=512, wls_warps=8, spmv_unroll=1, sweep_sorted=1)
+            ap.set_launch_shape(spmv_block=128, wls_warps=8, spmv_unroll=4, sweep_sorted=1)
         ap.build_octree_batched(tx, ty, tz, offs)
         ap.stencils()
         ap.deposit(q=tq, rtol=RTOL)
@@ -867,7 +894,10 @@ def main():
     ap.add_argument("--learned", action="store_true",
                     help="train the learned preconditioner and compare it with Jacobi on held-out seeds "
                          "(with --vp: use its column scaling in the leapfrog solves)")
-    ap.add_argument("--train-systems", type=int, default=10000)
+    ap.add_argument("--train-systems", type=int, default=10000,
+                    help="reduced-N training systems (2e4 / 1e5 particles)")
+    ap.add_argument("--train-full", type=int, default=0,
+                    help="training systems of the full 1e7-particle depth-10 law after the reduced ones")
     ap.add_argument("--eval-seeds", type=int, nargs="+", default=[90001, 90002])
     ap.add_argument("--learned-max-iter", type=int, default=100000)
     ap.add_argument("--ilu", action="store_true", help="ILU(0) against Jacobi on the learned comparison's seeds")

@@ -125,6 +125,24 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int rows) {
     return (uint32_t)((k >> 4) * rows * 32 + (row >> 3) * 256 + ((k >> 3) & 1) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// the 8 elements of v (row chunk cc of sample k) into column k of a K-major
+// tile with `rows` rows, element i to row 8 cc + ((i + 2 q) & 7)
+__device__ __forceinline__ void scatter_col(unsigned char *tile, uint4 v, int cc, int k, int rows, int q) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+    uint32_t rw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const uint32_t a0 = w[j], a1 = w[(j + 1) & 3], a2 = w[(j + 2) & 3], a3 = w[(j + 3) & 3];
+        rw[j] = q == 0 ? a0 : q == 1 ? a1 : q == 2 ? a2 : a3;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int e = (i + 2 * q) & 7;   // element index; rw[i >> 1] holds elements 2((i>>1)+q), +1
+        const uint16_t h = (uint16_t)((i & 1) ? (rw[i >> 1] >> 16) : (rw[i >> 1] & 0xFFFFu));
+        *reinterpret_cast<uint16_t *>(tile + tile_off(cc * 8 + e, k, rows)) = h;
+    }
+}
+
 constexpr int TC_THREADS = 128;
 constexpr int TC_COLS = 128;        // TMEM columns allocated (N <= 128)
 constexpr int TC_SMEM = 64 * 1024;  // A (<= 32 KB) + B (<= 32 KB)
@@ -170,26 +188,53 @@ __global__ void __launch_bounds__(TC_THREADS) k_dense_tc(TcArgs a) {
     if (MODE == 0 || MODE == 1) {
         const int K = a.K;
         const int row0 = blockIdx.x * 128;
-        const int cpr = K / 8;   // 16-byte chunks per row
-        for (int idx = tid; idx < 128 * cpr; idx += TC_THREADS) {
-            const int r = idx / cpr, cc = idx - r * cpr, row = row0 + r;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (row < a.n) {
-                const __nv_bfloat16 *src;
-                if (a.x1) {
-                    const int ch = a.c / 8;
-                    src = (cc < ch) ? a.x0 + (int64_t)row * a.c + cc * 8 : a.x1 + (int64_t)row * a.c + (cc - ch) * 8;
-                } else {
-                    src = a.x0 + (int64_t)row * K + cc * 8;
+        const int cpr = K / 8;   // 16-byte chunks per row (4, 8 or 16)
+        const int cq = cpr >> 2;
+        // each warp store covers 8 rows x 4 chunks: four whole core matrices,
+        // one 128-byte wavefront each, and 64 contiguous bytes of every row
+        // read; four chunks per thread are loaded before any is stored
+        constexpr int NB = 4;
+        for (int base = tid; base < 128 * cpr; base += NB * TC_THREADS) {
+            uint4 v[NB];
+            uint32_t off[NB];
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int idx = base + u * TC_THREADS;
+                const int g = idx >> 5, l = idx & 31;
+                const int r = (g / cq) * 8 + (l & 7), cc = (g % cq) * 4 + (l >> 3), row = row0 + r;
+                v[u] = make_uint4(0u, 0u, 0u, 0u);
+                off[u] = tile_off(r, cc * 8, 128);
+                if (idx < 128 * cpr && row < a.n) {
+                    const __nv_bfloat16 *src;
+                    if (a.x1) {
+                        const int ch = a.c / 8;
+                        src = (cc < ch) ? a.x0 + (int64_t)row * a.c + cc * 8
+                                        : a.x1 + (int64_t)row * a.c + (cc - ch) * 8;
+                    } else {
+                        src = a.x0 + (int64_t)row * K + cc * 8;
+                    }
+                    v[u] = *reinterpret_cast<const uint4 *>(src);
                 }
-                v = *reinterpret_cast<const uint4 *>(src);
             }
-            *reinterpret_cast<uint4 *>(sA + tile_off(r, cc * 8, 128)) = v;
+#pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (base + u * TC_THREADS < 128 * cpr) *reinterpret_cast<uint4 *>(sA + off[u]) = v[u];
         }
-        for (int idx = tid; idx < N * cpr; idx += TC_THREADS) {
-            const int r = idx / cpr, cc = idx - r * cpr;
-            *reinterpret_cast<uint4 *>(sB + tile_off(r, cc * 8, N)) =
-                *reinterpret_cast<const uint4 *>(a.bmat + (int64_t)r * K + cc * 8);
+        for (int base = tid; base < N * cpr; base += NB * TC_THREADS) {
+            uint4 v[NB];
+            uint32_t off[NB];
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int idx = base + u * TC_THREADS;
+                const int g = idx >> 5, l = idx & 31;
+                const int r = (g / cq) * 8 + (l & 7), cc = (g % cq) * 4 + (l >> 3);
+                off[u] = tile_off(r, cc * 8, N);
+                v[u] = idx < N * cpr ? *reinterpret_cast<const uint4 *>(a.bmat + (int64_t)r * K + cc * 8)
+                                     : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int u = 0; u < NB; ++u)
+                if (base + u * TC_THREADS < N * cpr) *reinterpret_cast<uint4 *>(sB + off[u]) = v[u];
         }
         fence_async_smem();
         __syncthreads();
@@ -240,22 +285,30 @@ __global__ void __launch_bounds__(TC_THREADS) k_dense_tc(TcArgs a) {
                 reinterpret_cast<uint4 *>(smem)[idx] = make_uint4(0u, 0u, 0u, 0u);
             __syncthreads();
             const int k = tid, row = chunk * 128 + k;
+            // thread k scatters its row into column k of the transposed tiles;
+            // the four 8-lane groups of a warp start at rows 2q apart, so one
+            // 2-byte store of the warp lands in 16 distinct banks
+            const int q = (lane >> 3) & 3;
             if (row < a.n) {
-                for (int cc = 0; cc < Kl / 8; ++cc) {
-                    const __nv_bfloat16 *src = (cc < ch) ? a.x0 + (int64_t)row * a.c + cc * 8
-                                                          : a.x1 + (int64_t)row * a.c + (cc - ch) * 8;
-                    uint4 v = *reinterpret_cast<const uint4 *>(src);
-                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+                // Kl / 8 (4 or 16) chunks of X, 8 of dZ: loads of four chunks in flight
+                for (int c0 = 0; c0 < Kl / 8; c0 += 4) {
+                    uint4 v[4];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        *reinterpret_cast<__nv_bfloat16 *>(sA + tile_off(cc * 8 + i, k, 128)) = e[i];
+                    for (int u = 0; u < 4; ++u) {
+                        const int cc = c0 + u;
+                        v[u] = *reinterpret_cast<const uint4 *>(
+                            (cc < ch) ? a.x0 + (int64_t)row * a.c + cc * 8 : a.x1 + (int64_t)row * a.c + (cc - ch) * 8);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) scatter_col(sA, v[u], c0 + u, k, 128, q);
                 }
-                for (int cc = 0; cc < WD / 8; ++cc) {
-                    uint4 v = *reinterpret_cast<const uint4 *>(a.g + (int64_t)row * WD + cc * 8);
-                    const __nv_bfloat16 *e = reinterpret_cast<const __nv_bfloat16 *>(&v);
+                for (int c0 = 0; c0 < WD / 8; c0 += 4) {
+                    uint4 v[4];
 #pragma unroll
-                    for (int i = 0; i < 8; ++i)
-                        *reinterpret_cast<__nv_bfloat16 *>(sB + tile_off(cc * 8 + i, k, WD)) = e[i];
+                    for (int u = 0; u < 4; ++u)
+                        v[u] = *reinterpret_cast<const uint4 *>(a.g + (int64_t)row * WD + (c0 + u) * 8);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) scatter_col(sB, v[u], c0 + u, k, WD, q);
                 }
             }
             fence_async_smem();

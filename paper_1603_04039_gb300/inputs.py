@@ -93,6 +93,32 @@ def beam_with_halo(n: int, seed: int, sigma: float = 0.05, halo_frac: float = 0.
             np.ascontiguousarray(pts[:, 2]), q)
 
 
+def beam_with_halo_device(n: int, seed: int, device, sigma: float = 0.05, halo_frac: float = 0.1,
+                          r0: float = 0.3, r1: float = 0.5, lo: float = -1.0, hi: float = 1.0):
+    """The beam-with-halo law drawn on a CUDA device with torch's generator
+    (a training-set sampler: a million-node system per draw without a host
+    round trip).  Same law as beam_with_halo, another random stream: core
+    draws outside the domain are clamped instead of redrawn (the core's
+    sigma puts the walls 20 sigma away) and the particles come core first,
+    halo second (the tree build orders them itself).  Returns torch float64
+    tensors (x, y, z, q) on the device."""
+    import torch
+    n = int(n)
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    n_halo = int(round(halo_frac * n))
+    core = torch.randn(n - n_halo, 3, generator=g, device=device, dtype=torch.float64) * sigma
+    u = torch.rand(n_halo, 3, generator=g, device=device, dtype=torch.float64)
+    rad = torch.pow(r0 ** 3 + u[:, 0] * (r1 ** 3 - r0 ** 3), 1.0 / 3.0)
+    cz = 2.0 * u[:, 1] - 1.0
+    ph = 2.0 * np.pi * u[:, 2]
+    st = torch.sqrt(torch.clamp(1.0 - cz * cz, min=0.0))
+    halo = torch.stack([rad * st * torch.cos(ph), rad * st * torch.sin(ph), rad * cz], dim=1)
+    pts = torch.clamp(torch.cat([core, halo], dim=0), lo, hi)
+    q = torch.full((n,), 1.0 / n, device=device, dtype=torch.float64)
+    return pts[:, 0].contiguous(), pts[:, 1].contiguous(), pts[:, 2].contiguous(), q
+
+
 def uniform_box(n: int, seed: int, lo: float = -1.0, hi: float = 1.0):
     """n points uniform in the cube [lo, hi]^3 with charge 1/n each."""
     u = uniforms(seed, 4, 3 * n).reshape(-1, 3)
