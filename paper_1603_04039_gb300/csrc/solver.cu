@@ -252,6 +252,13 @@ __device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const
     return acc;
 }
 
+// Resident blocks asked of the width-sorted row kernels: with two chunks in
+// flight (U > 1) they fit 32 registers without spilling, so blocks of up to
+// 256 threads fill the SM's 64 warps (left to itself the compiler takes more
+// registers and fewer warps); the one-chunk form spills at 32 or 40
+// registers and keeps the compiler's choice.
+#define SS_MINB(BS, U) (((U) > 1 && (BS) <= 256) ? 2048 / (BS) : 1)
+
 // A row of the width-sorted sweep matrix.  A slice of width w stores its first
 // 4 * floor(w / 4) columns lane-major in 4-entry chunks (chunk j of lane l at
 // entries sbase + 128 j + 4 l .. + 3: one 16-byte column load and one 8-byte
@@ -391,7 +398,7 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
 // its row from the window's permutation (entries in the same order, so the
 // same bits as k_sweep_h).
 template <int BS, int U = 1>
-__global__ void __launch_bounds__(BS) k_sweep_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
+__global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
                                                 const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
                                                 const __half *__restrict__ val, int64_t nslot,
                                                 const float *__restrict__ x, float *__restrict__ y,
@@ -469,7 +476,7 @@ __device__ __forceinline__ float row_dot_cf(const float *__restrict__ val, const
 // y = Ahat x on the width-sorted FP32 copy, skipped once the cycle is done
 // (the Arnoldi product of k_spmv<4, float> with the same bits)
 template <int BS, int U = 1>
-__global__ void __launch_bounds__(BS) k_spmv_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
+__global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_spmv_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
                                                const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
                                                const float *__restrict__ val, int64_t nslot,
                                                const float *__restrict__ x, float *__restrict__ y,
