@@ -75,12 +75,38 @@ def _dist():
     return ws, rank, local
 
 
+def _source_items(text, items):
+    """The source text of the named items of a CUDA file, joined: for a
+    function, from its declaration line to its matching closing brace; for a
+    `#define`, its line.  An item is a string that occurs once in the file."""
+    out = []
+    for item in items:
+        i = text.find(item)
+        if i < 0:
+            return None
+        start = text.rfind("\n", 0, i) + 1
+        if item.startswith("#define"):
+            out.append(text[start:text.find("\n", i)])
+            continue
+        j = text.find("{", i)
+        depth = 0
+        for k in range(j, len(text)):
+            depth += {"{": 1, "}": -1}.get(text[k], 0)
+            if depth == 0:
+                out.append(text[start:k + 1])
+                break
+        else:
+            return None
+    return "\n".join(out)
+
+
 def _dram_traffic(kind, workload):
     """DRAM bytes per working launch of kernel kind `kind` on `workload` from
     the committed record of an ncu capture (profiles/dram_traffic.json), or
-    None.  A record holds the SHA-256 of the source file the kernel was built
-    from; once that file has changed the counters no longer describe the
-    kernel and None is returned."""
+    None.  A record holds the SHA-256 of the kernel's source (the listed items
+    of its source file: the kernel, the device functions it calls and the
+    macros of its launch bounds); once that source has changed the counters no
+    longer describe the kernel and None is returned."""
     import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.json")) as f:
@@ -91,11 +117,13 @@ def _dram_traffic(kind, workload):
         if r.get("kind") != kind or r.get("workload") != workload:
             continue
         try:
-            with open(os.path.join(ROOT, r["source"]), "rb") as f:
-                sha = hashlib.sha256(f.read()).hexdigest()
-        except OSError:
+            with open(os.path.join(ROOT, r["source"])) as f:
+                src = _source_items(f.read(), r["source_items"])
+        except (OSError, KeyError):
             return None
-        return r if sha == r.get("source_sha256") else None
+        if src is None:
+            return None
+        return r if hashlib.sha256(src.encode()).hexdigest() == r.get("source_sha256") else None
     return None
 
 

@@ -446,7 +446,10 @@ apcloud_status apcloud_solve_learned(apcloud_ctx *ctx, apcloud_mpnn *net, unsign
  * APCLOUD_NUM_KINDS entries, any may be NULL): summed milliseconds, launch
  * count, and the algorithmic bytes and floating-point operations of those
  * launches (what the kernel must move and compute, not what it did), since
- * the last reset (reset = 1 clears). */
+ * the last reset (reset = 1 clears).  Consecutive launches of one timed kind
+ * share one pair of events (before the first, after the last), so their time
+ * includes the gaps between them; a launch of any other kind or a host
+ * read-back closes the pair. */
 #define APCLOUD_NUM_KINDS 19
 apcloud_status apcloud_set_timing(apcloud_ctx *ctx, unsigned mask);
 apcloud_status apcloud_get_timing(apcloud_ctx *ctx, double *h_ms, int64_t *h_launches, double *h_bytes,

@@ -62,17 +62,6 @@ static void free_buf(apcloud_ctx *c, DBuf &b) {
     b.bytes = 0;
 }
 
-// inside a stream capture the timing pair becomes two event nodes of the graph,
-// owned by the graph entry and read after every replay
-static void capture_event(apcloud_ctx *c, int kind, bool begin) {
-    GraphEntry *g = c->capturing;
-    cudaEvent_t e;
-    if (cudaEventCreate(&e) != cudaSuccess) return;
-    g->ev.push_back(e);
-    if (begin) g->kind.push_back(kind);
-    cudaEventRecordWithFlags(e, c->s, cudaEventRecordExternal);
-}
-
 void timer_close(apcloud_ctx *c) {
     Timer &t = c->timer;
     if (t.open < 0) return;
@@ -83,10 +72,9 @@ void timer_close(apcloud_ctx *c) {
 
 void timer_begin(apcloud_ctx *c, int kind) {
     Timer &t = c->timer;
-    if (c->capturing) {
-        if (t.mask >> kind & 1u) capture_event(c, kind, true);
-        return;
-    }
+    // cycles are captured only with every timer off (event records cannot
+    // sit in the conditional step bodies); timed cycles run as direct launches
+    if (c->capturing) return;
     if (t.open >= 0 && (t.kind[t.open] != kind || !(t.mask >> kind & 1u))) timer_close(c);
     if (!(t.mask >> kind & 1u)) return;
     if (t.open >= 0) {   // the same kind again: the open pair covers this launch too
@@ -107,12 +95,6 @@ void timer_begin(apcloud_ctx *c, int kind) {
     t.open = (long)t.used;
 }
 
-void timer_end(apcloud_ctx *c, int kind) {
-    Timer &t = c->timer;
-    if (!(t.mask >> kind & 1u)) return;
-    if (c->capturing) capture_event(c, kind, false);
-}
-
 static void timer_collect(apcloud_ctx *c) {
     Timer &t = c->timer;
     timer_close(c);
@@ -131,14 +113,12 @@ static void timer_collect(apcloud_ctx *c) {
 // ---------------------------------------------------------------- CUDA graphs
 static void destroy_entry(GraphEntry *g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
-    for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
     delete g;
 }
 
 void free_graphs(apcloud_ctx *c) {
     for (GraphEntry *g : c->graphs) destroy_entry(g);
     c->graphs.clear();
-    c->last_replayed = nullptr;
     c->last_stepped = nullptr;
 }
 
@@ -261,7 +241,6 @@ GraphEntry *end_capture(apcloud_ctx *c, GraphEntry *g, apcloud_status st) {
         for (size_t i = 1; i < c->graphs.size(); ++i)
             if (c->graphs[i]->last_use < c->graphs[old]->last_use) old = i;
         if (c->last_stepped == c->graphs[old]) c->last_stepped = nullptr;
-        if (c->last_replayed == c->graphs[old]) c->last_replayed = nullptr;
         destroy_entry(c->graphs[old]);
         c->graphs.erase(c->graphs.begin() + old);
     }
@@ -275,29 +254,9 @@ apcloud_status launch_graph(apcloud_ctx *c, GraphEntry *g) {
     c->launches += g->kernels;
     c->last_stepped = g;
     c->graph_replays++;
-    c->last_replayed = g->ev.empty() ? nullptr : g;
     return APCLOUD_OK;
 }
 
-// after the stream has synchronised: the replayed graph's timing pairs
-void harvest_graph_timing(apcloud_ctx *c) {
-    GraphEntry *g = c->last_replayed;
-    c->last_replayed = nullptr;
-    if (!g) return;
-    Timer &t = c->timer;
-    for (size_t i = 0; i < g->kind.size() && 2 * i + 1 < g->ev.size(); ++i) {
-        float ms = 0.f;
-        if (cudaEventElapsedTime(&ms, g->ev[2 * i], g->ev[2 * i + 1]) == cudaSuccess) {
-            t.ms[g->kind[i]] += ms;
-            t.launches[g->kind[i]]++;
-        } else {
-            // event nodes that cannot be timed: later timed cycles run without graphs
-            cudaGetLastError();
-            c->graph_timing_ok = false;
-            return;
-        }
-    }
-}
 
 apcloud_status read_back(apcloud_ctx *c, void *host, const void *dev, size_t bytes) {
     timer_close(c);   // a timed pair must not span the host's wait

@@ -92,8 +92,6 @@ struct GraphEntry {
     std::vector<cudaGraphConditionalHandle> cond;  // condition of step j's body (j >= 1)
     int cur_step = -1;               // body being captured (-1: none)
     bool broken = false;             // a capture step failed: the graph is discarded
-    std::vector<cudaEvent_t> ev;     // timing pairs recorded by event nodes
-    std::vector<int> kind;
     uint64_t last_use = 0;
 };
 
@@ -143,11 +141,9 @@ struct apcloud_ctx {
     int wls_warps = 4;     // nodes (warps) per block of the stencil build
     // CUDA graphs of GMRES restart cycles (captured on cap_stream, replayed on s)
     bool graphs_on = true;
-    bool graph_timing_ok = true;
     cudaStream_t cap_stream = nullptr;
     cudaStream_t body_stream = nullptr;   // capture of conditional step bodies
     apc::GraphEntry *capturing = nullptr;
-    apc::GraphEntry *last_replayed = nullptr;
     apc::GraphEntry *last_stepped = nullptr;   // last replayed graph whose step kernels are not counted yet
     std::vector<apc::GraphEntry *> graphs;
     uint64_t graph_clock = 0;
@@ -242,7 +238,6 @@ inline T *ptr(DBuf &b) { return static_cast<T *>(b.p); }
 
 // event timers around launches of one kind
 void timer_begin(apcloud_ctx *c, int kind);
-void timer_end(apcloud_ctx *c, int kind);
 void timer_close(apcloud_ctx *c);
 // add algorithmic traffic of launches of `kind` (only while that kind is timed)
 inline void account(apcloud_ctx *c, int kind, double bytes, double flops) {
@@ -275,7 +270,6 @@ GraphEntry *find_graph(apcloud_ctx *c, const GraphKey &key);
 GraphEntry *begin_capture(apcloud_ctx *c, const GraphKey &key);
 GraphEntry *end_capture(apcloud_ctx *c, GraphEntry *g, apcloud_status st);
 apcloud_status launch_graph(apcloud_ctx *c, GraphEntry *g);
-void harvest_graph_timing(apcloud_ctx *c);
 void free_graphs(apcloud_ctx *c);
 apcloud_status build_stencils(apcloud_ctx *c);
 apcloud_status deposit(apcloud_ctx *c, const double *q, double q_uniform);
@@ -327,7 +321,6 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
         if ((grid) > 0) {                                                       \
             ::apc::timer_begin(c, kind);                                        \
             kern<<<(grid), (block), (smem), (c)->s>>>(__VA_ARGS__);             \
-            ::apc::timer_end(c, kind);                                          \
             if ((c)->capturing) ::apc::count_captured(c);                        \
             else (c)->launches++;                                               \
         }                                                                       \

@@ -1732,7 +1732,6 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
         // when the cycle is a full one, otherwise direct launches
         APC_TRY(run_cycle<T>(c, val, b, u, K, jmax, jmax == cap && K.graphs));
         APC_TRY(read_back(c, &tail, &st->bnorm, sizeof tail));
-        harvest_graph_timing(c);
         const int je = tail.jlast;
         count_replayed_steps(c, je);
         // algorithmic traffic of the launches that did work (values + column index per entry)
