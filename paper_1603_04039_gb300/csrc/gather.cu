@@ -14,6 +14,7 @@
 // partition the key space).
 #include <cmath>
 
+#include "fpconv.cuh"
 #include "internal.cuh"
 
 namespace apc {
@@ -104,22 +105,23 @@ __global__ void __launch_bounds__(256) k_gather_leaf(
     if (F32) {
         // the mixed form: corrections (g.r, H r, r.H.r) in FP32 around the FP64
         // node potential, from the compact record; its node derivatives carry
-        // FP32 accuracy already (FP32 stencils), and the pass stays off the slow
-        // FP64 pipe
+        // FP32 accuracy already (FP32 stencils).  The pass stays off the slow
+        // FP64 pipe but for the offsets from the centre and the potential's
+        // add: the seven double/float conversions run on the integer pipe
         const double2 *c2 = reinterpret_cast<const double2 *>(nf32 + (int64_t)j * NF32);
         const float4 *f4 = reinterpret_cast<const float4 *>(nf32 + (int64_t)j * NF32 + 8);
         const double2 pc = c2[0], cc = c2[1];
         const float4 u = f4[0], w = f4[1], t = f4[2];
-        const float r0 = (float)(p0 - pc.y), r1 = (float)(p1 - cc.x), r2 = (float)(p2 - cc.y);
+        const float r0 = f64_to_f32_int(p0 - pc.y), r1 = f64_to_f32_int(p1 - cc.x), r2 = f64_to_f32_int(p2 - cc.y);
         // u = (fx, fy, fz, fxx), w = (fxy, fxz, fyy, fyz), t.x = fzz
         const float hr0 = fmaf(w.y, r2, fmaf(w.x, r1, u.w * r0));
         const float hr1 = fmaf(w.w, r2, fmaf(w.z, r1, w.x * r0));
         const float hr2 = fmaf(t.x, r2, fmaf(w.w, r1, w.y * r0));
         const float corr = fmaf(u.z, r2, fmaf(u.y, r1, u.x * r0)) + 0.5f * fmaf(r2, hr2, fmaf(r1, hr1, r0 * hr0));
-        v = pc.x + (double)corr;
-        gx = (double)(u.x + hr0);
-        gy = (double)(u.y + hr1);
-        gz = (double)(u.z + hr2);
+        v = pc.x + f32_to_f64_int(corr);
+        gx = f32_to_f64_int(u.x + hr0);
+        gy = f32_to_f64_int(u.y + hr1);
+        gz = f32_to_f64_int(u.z + hr2);
     } else {
         const int4 q = ic[j];
         const double r0 = p0 - __dadd_rn(lo0, __dmul_rn((double)q.x, unit));
