@@ -281,7 +281,9 @@ apcloud_status apcloud_ilu0_factor_host(int64_t n, const int64_t *h_rowptr, cons
 /* The whole solve on host arrays: copies positions and charges (h_q NULL =
  * q_uniform) to the device, runs the five steps with g = 0, and copies phi
  * and E at the particles back.  Host arrays may be pageable or pinned; pinned
- * memory makes the copies asynchronous. */
+ * memory makes the copies asynchronous, and the charges' copy then runs on a
+ * second stream of the context while the tree and the stencils are built.
+ * Returns with no copy from or to the host arrays in flight, on every path. */
 apcloud_status apcloud_field_host(apcloud_ctx *ctx, const double *h_x, const double *h_y, const double *h_z,
                                   const double *h_q, double q_uniform, int64_t n, double rtol, int max_iter,
                                   double *h_phi, double *h_ex, double *h_ey, double *h_ez,

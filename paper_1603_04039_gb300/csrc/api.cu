@@ -394,6 +394,11 @@ void apcloud_destroy(apcloud_ctx *c) {
     free_graphs(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->body_stream) cudaStreamDestroy(c->body_stream);
+    if (c->copy_stream) {
+        cudaStreamSynchronize(c->copy_stream);
+        cudaStreamDestroy(c->copy_stream);
+    }
+    if (c->copy_done) cudaEventDestroy(c->copy_done);
     for (cudaEvent_t e : c->timer.ev) cudaEventDestroy(e);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     delete c;
@@ -633,11 +638,10 @@ apcloud_status apcloud_solve_system(apcloud_ctx *c, int which, const double *b, 
     return gmres_solve(c, which, b, x, rtol, max_iter, info);
 }
 
-static apcloud_status field_host(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
-                                 const double *hq, double q_uniform, int64_t n, const int64_t *offsets, int nbeams,
-                                 double rtol, int max_iter, double *hphi, double *hex, double *hey, double *hez,
-                                 apcloud_solve_info *ir, apcloud_solve_info *ip) {
-    if (!c) return APCLOUD_E_INVALID;
+static apcloud_status field_host_run(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
+                                     const double *hq, double q_uniform, int64_t n, const int64_t *offsets,
+                                     int nbeams, double rtol, int max_iter, double *hphi, double *hex, double *hey,
+                                     double *hez, apcloud_solve_info *ir, apcloud_solve_info *ip) {
     if (n < 0 || (n > 0 && (!hx || !hy || !hz))) return fail(c, APCLOUD_E_INVALID, "bad host particle arrays");
     size_t nb = (size_t)(n > 0 ? n : 1) * sizeof(double);
     double *dx = ensure<double>(c, c->hx, n + 1), *dy = ensure<double>(c, c->hy, n + 1),
@@ -646,16 +650,45 @@ static apcloud_status field_host(apcloud_ctx *c, const double *hx, const double 
     double *dp = ensure<double>(c, c->hphi, n + 1), *de0 = ensure<double>(c, c->hex, n + 1),
            *de1 = ensure<double>(c, c->hey, n + 1), *de2 = ensure<double>(c, c->hez, n + 1);
     if (!dx || !dy || !dz || (hq && !dq) || !dp || !de0 || !de1 || !de2) return APCLOUD_E_NOMEM;
+    // the charges are not needed before the deposit: their copy runs on a
+    // second stream while the tree and the stencils are built
+    bool q_side = false;
     if (n > 0) {
         APC_CUDA(c, cudaMemcpyAsync(dx, hx, nb, cudaMemcpyHostToDevice, c->s));
         APC_CUDA(c, cudaMemcpyAsync(dy, hy, nb, cudaMemcpyHostToDevice, c->s));
         APC_CUDA(c, cudaMemcpyAsync(dz, hz, nb, cudaMemcpyHostToDevice, c->s));
-        if (hq) APC_CUDA(c, cudaMemcpyAsync(dq, hq, nb, cudaMemcpyHostToDevice, c->s));
+        if (hq) {
+            if (!c->copy_stream) {
+                if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&c->copy_done, cudaEventDisableTiming) != cudaSuccess) {
+                    cudaGetLastError();
+                    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+                    c->copy_stream = nullptr;
+                }
+            }
+            if (c->copy_stream) {
+                // the device buffer may still be read by earlier work on the context stream
+                APC_CUDA(c, cudaEventRecord(c->copy_done, c->s));
+                APC_CUDA(c, cudaStreamWaitEvent(c->copy_stream, c->copy_done, 0));
+                APC_CUDA(c, cudaMemcpyAsync(dq, hq, nb, cudaMemcpyHostToDevice, c->copy_stream));
+                APC_CUDA(c, cudaEventRecord(c->copy_done, c->copy_stream));
+                q_side = true;
+            } else {
+                APC_CUDA(c, cudaMemcpyAsync(dq, hq, nb, cudaMemcpyHostToDevice, c->s));
+            }
+        }
     }
     int64_t ni, nbd;
-    if (offsets) APC_TRY(apcloud_build_octree_batched(c, dx, dy, dz, offsets, nbeams, &ni, &nbd));
-    else APC_TRY(apcloud_build_octree(c, dx, dy, dz, n, &ni, &nbd));
-    APC_TRY(apcloud_stencils(c));
+    apcloud_status sb;
+    if (offsets) sb = apcloud_build_octree_batched(c, dx, dy, dz, offsets, nbeams, &ni, &nbd);
+    else sb = apcloud_build_octree(c, dx, dy, dz, n, &ni, &nbd);
+    if (sb == APCLOUD_OK) sb = apcloud_stencils(c);
+    if (q_side) {
+        // joined on every path, so that no copy into dq is left running
+        cudaError_t e = cudaStreamWaitEvent(c->s, c->copy_done, 0);
+        if (sb == APCLOUD_OK && e != cudaSuccess) sb = cuda_check(c, e, "charge copy");
+    }
+    APC_TRY(sb);
     apcloud_status s1 = apcloud_deposit(c, dq, q_uniform, rtol, max_iter, nullptr, ir);
     if (s1 < 0) return s1;
     apcloud_status s2 = apcloud_solve(c, nullptr, nullptr, rtol, max_iter, nullptr, ip);
@@ -669,6 +702,22 @@ static apcloud_status field_host(apcloud_ctx *c, const double *hx, const double 
     }
     APC_CUDA(c, cudaStreamSynchronize(c->s));
     return (s1 > 0 || s2 > 0) ? APCLOUD_W_NOT_CONVERGED : APCLOUD_OK;
+}
+
+// every return leaves no copy from or to the caller's host arrays in flight
+static apcloud_status field_host(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,
+                                 const double *hq, double q_uniform, int64_t n, const int64_t *offsets, int nbeams,
+                                 double rtol, int max_iter, double *hphi, double *hex, double *hey, double *hez,
+                                 apcloud_solve_info *ir, apcloud_solve_info *ip) {
+    if (!c) return APCLOUD_E_INVALID;
+    const apcloud_status st = field_host_run(c, hx, hy, hz, hq, q_uniform, n, offsets, nbeams, rtol, max_iter, hphi,
+                                             hex, hey, hez, ir, ip);
+    if (st < 0) {
+        cudaStreamSynchronize(c->s);
+        if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+        cudaGetLastError();
+    }
+    return st;
 }
 
 apcloud_status apcloud_field_host(apcloud_ctx *c, const double *hx, const double *hy, const double *hz,

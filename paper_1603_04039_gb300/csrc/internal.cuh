@@ -143,6 +143,8 @@ struct apcloud_ctx {
     bool graphs_on = true;
     cudaStream_t cap_stream = nullptr;
     cudaStream_t body_stream = nullptr;   // capture of conditional step bodies
+    cudaStream_t copy_stream = nullptr;   // host copies that overlap the tree build (field_host)
+    cudaEvent_t copy_done = nullptr;
     apc::GraphEntry *capturing = nullptr;
     apc::GraphEntry *last_stepped = nullptr;   // last replayed graph whose step kernels are not counted yet
     std::vector<apc::GraphEntry *> graphs;
