@@ -1,4 +1,5 @@
-// fpconv.cuh -- binary64 <-> binary32 conversions on the integer pipe.
+// fpconv.cuh -- binary64 <-> binary32 conversions, and the floor, clamp and
+// range test of the Morton-key quantisation, on the integer pipe.
 //
 // GB300 runs FP64 arithmetic, and the conversions between double and float,
 // on a pipe 58x narrower than FP32 (1.19 TFLOP/s measured).  A particle pass
@@ -8,11 +9,12 @@
 // exponent bits (bias 127), 23 fraction bits -- with integer instructions
 // only, every case included (zeros, subnormal results and inputs, overflow to
 // infinity, infinities, NaNs), and round to nearest, ties to even, the
-// standard's default rounding.  Nothing here may reach the FP64 pipe: a
+// standard's default rounding; the floor-and-clamp and the range test read
+// the same encodings.  Nothing here may reach the FP64 pipe: a
 // hardware conversion kept for a rare case would be evaluated for every
 // value once the compiler turns the branch into a select.  Checked bit for
-// bit against the hardware conversions by tests/test_gpu_fpconv.py (NaNs
-// compare as NaNs).
+// bit against the hardware conversions and the FP64 floor / fmin / fmax /
+// comparison forms by tests/test_gpu_fpconv.py (NaNs compare as NaNs).
 #pragma once
 
 #include <cstdint>
@@ -64,6 +66,32 @@ __device__ __forceinline__ double f32_to_f64_int(float f) {
         lo = (uint32_t)fr;
     }
     return __hiloint2double((int)hi, (int)lo);
+}
+
+// min(max(floor(t), 0), maxv) as an unsigned integer, for maxv < 2^31; NaN
+// gives 0 (as fmin(fmax(NaN, 0), maxv) does)
+__device__ __forceinline__ uint32_t f64_floor_clamp_u32(double t, uint32_t maxv) {
+    const uint64_t b = (uint64_t)__double_as_longlong(t);
+    const int E = (int)((b >> 52) & 0x7FFu);
+    if ((b >> 63) || E < 1023) return 0u;                 // negative, -0, below 1
+    if (E == 0x7FF) return (b & 0xFFFFFFFFFFFFFull) ? 0u : maxv;   // NaN, +inf
+    const int ex = E - 1023;                               // t in [2^ex, 2^(ex+1))
+    if (ex >= 31) return maxv;
+    const uint64_t ip = ((b & 0xFFFFFFFFFFFFFull) | (1ull << 52)) >> (52 - ex);
+    return ip > maxv ? maxv : (uint32_t)ip;
+}
+
+// lo <= p <= hi for finite lo, hi (false for NaN p), compared on the IEEE
+// encodings mapped to integers of the same order
+__device__ __forceinline__ int64_t f64_order_key(double v) {
+    const int64_t b = __double_as_longlong(v);
+    return b >= 0 ? b : (int64_t)(0x8000000000000000ull - (uint64_t)b);   // -0 maps to 0 like +0
+}
+__device__ __forceinline__ bool f64_in_range(double p, double lo, double hi) {
+    const uint64_t b = (uint64_t)__double_as_longlong(p);
+    if (((b >> 52) & 0x7FFu) == 0x7FFu && (b & 0xFFFFFFFFFFFFFull)) return false;   // NaN
+    const int64_t k = f64_order_key(p);
+    return k >= f64_order_key(lo) && k <= f64_order_key(hi);
 }
 
 }  // namespace apc

@@ -1,9 +1,14 @@
-"""The integer-pipe double <-> float conversions of the particle pass
-(paper_1603_04039_gb300/csrc/fpconv.cuh) against the hardware conversions,
-bit for bit: random encodings over the whole exponent range, every rounding
-case of the 29 dropped fraction bits (below, at and above one half, with an
-even and an odd kept fraction), carries into the exponent, overflow to
-infinity, results in the subnormal range, signed zeros, infinities and NaNs.
+"""The integer-pipe helpers of paper_1603_04039_gb300/csrc/fpconv.cuh against
+the FP64 forms they replace, bit for bit:
+  * double <-> float conversions against the hardware conversions: random
+    encodings over the whole exponent range, every rounding case of the 29
+    dropped fraction bits (below, at and above one half, with an even and an
+    odd kept fraction), carries into the exponent, overflow to infinity,
+    results in the subnormal range, signed zeros, infinities and NaNs;
+  * floor-and-clamp of the Morton-key quantisation against
+    (uint32_t)fmin(fmax(floor(t), 0), maxv): integers, values just below and
+    above them, negatives, -0, huge values, infinities, NaNs;
+  * the domain test against lo <= p && p <= hi.
 A small CUDA program including the header is built with nvcc and run."""
 import os
 import shutil
@@ -18,6 +23,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PROGRAM = r"""
 #include <cstdio>
 #include <cstdint>
+#include <cmath>
 #include <cstring>
 #include <vector>
 #include "fpconv.cuh"
@@ -29,6 +35,16 @@ __global__ void conv(const double *d, float *df, float *dh, const float *f, doub
     dh[i] = __double2float_rn(d[i]);
     fd[i] = apc::f32_to_f64_int(f[i]);
     fh[i] = (double)f[i];
+}
+
+__global__ void quant(const double *t, uint32_t maxv, uint32_t *qi, uint32_t *qh, const double *lo,
+                      const double *hi, int *ri, int *rh, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    qi[i] = apc::f64_floor_clamp_u32(t[i], maxv);
+    qh[i] = (uint32_t)fmin(fmax(floor(t[i]), 0.0), (double)maxv);
+    ri[i] = apc::f64_in_range(t[i], lo[i], hi[i]) ? 1 : 0;
+    rh[i] = (t[i] >= lo[i] && t[i] <= hi[i]) ? 1 : 0;
 }
 
 static uint64_t s = 0x9E3779B97F4A7C15ull;
@@ -97,7 +113,51 @@ int main() {
         int e = (int)((b >> 52) & 0x7FF) - 1023 + 127;
         if (e > 0 && e < 255) ++int_path;
     }
-    printf("n %d int_path %ld bad_d2f %ld bad_f2d %ld\n", n, int_path, bad_d, bad_f);
+    // quantisation: t around every integer up to 2^22, random magnitudes, specials
+    std::vector<double> t, lo, hi;
+    for (int k = -4; k < (1 << 22) + 4; k += 97)
+        for (double off : {-0.5, -1e-9, 0.0, 1e-9, 0.5}) t.push_back(k + off);
+    for (int i = 0; i < 1000000; ++i) t.push_back(dbits(next()));
+    for (int i = 0; i < 1000000; ++i) {
+        uint64_t b = next();
+        t.push_back(dbits((b & 0x800FFFFFFFFFFFFFull) | ((uint64_t)(1023 - 30 + (b >> 58) % 60) << 52)));
+    }
+    for (uint64_t b : special) t.push_back(dbits(b));
+    t.push_back(-0.0); t.push_back(2097151.0); t.push_back(2097152.0); t.push_back(nextafter(2097152.0, 0.0));
+    for (size_t i = 0; i < t.size(); ++i) {
+        // bounds: random finite pairs, a third of them around t itself
+        double a = dbits(next() & 0xBFFFFFFFFFFFFFFFull), b = dbits(next() & 0xBFFFFFFFFFFFFFFFull);
+        if (i % 3 == 0 && t[i] == t[i]) { a = t[i]; b = nextafter(t[i], 1e300); }
+        if (i % 3 == 1 && t[i] == t[i]) { a = nextafter(t[i], -1e300); b = t[i]; }
+        if (!(fabs(a) < 1e300)) a = -1.0;
+        if (!(fabs(b) < 1e300)) b = 1.0;
+        lo.push_back(a < b ? a : b); hi.push_back(a < b ? b : a);
+    }
+    const int nt = (int)t.size();
+    double *gt, *glo, *ghi; uint32_t *gqi, *gqh; int *gri, *grh;
+    cudaMalloc(&gt, nt * 8); cudaMalloc(&glo, nt * 8); cudaMalloc(&ghi, nt * 8);
+    cudaMalloc(&gqi, nt * 4); cudaMalloc(&gqh, nt * 4); cudaMalloc(&gri, nt * 4); cudaMalloc(&grh, nt * 4);
+    cudaMemcpy(gt, t.data(), nt * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(glo, lo.data(), nt * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(ghi, hi.data(), nt * 8, cudaMemcpyHostToDevice);
+    long bad_q = 0, bad_r = 0, in_range = 0;
+    for (uint32_t maxv : {2097151u, 1023u, 0x7FFFFFFFu}) {
+        quant<<<(nt + 255) / 256, 256>>>(gt, maxv, gqi, gqh, glo, ghi, gri, grh, nt);
+        if (cudaDeviceSynchronize() != cudaSuccess) { printf("cuda error\n"); return 2; }
+        std::vector<uint32_t> qi(nt), qh(nt);
+        std::vector<int> ri(nt), rh(nt);
+        cudaMemcpy(qi.data(), gqi, nt * 4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(qh.data(), gqh, nt * 4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(ri.data(), gri, nt * 4, cudaMemcpyDeviceToHost);
+        cudaMemcpy(rh.data(), grh, nt * 4, cudaMemcpyDeviceToHost);
+        for (int i = 0; i < nt; ++i) {
+            bad_q += qi[i] != qh[i];
+            bad_r += ri[i] != rh[i];
+            in_range += rh[i];
+        }
+    }
+    printf("n %d int_path %ld bad_d2f %ld bad_f2d %ld nq %d bad_quant %ld bad_range %ld in_range %ld\n", n,
+           int_path, bad_d, bad_f, nt, bad_q, bad_r, in_range);
     return 0;
 }
 """
@@ -117,3 +177,6 @@ def test_integer_conversions_match_hardware(tmp_path):
     fields = dict(zip(out.split()[0::2], map(int, out.split()[1::2])))
     assert fields["int_path"] > 1_500_000, fields          # most inputs exercise the integer path
     assert fields["bad_d2f"] == 0 and fields["bad_f2d"] == 0, fields
+    assert fields["bad_quant"] == 0 and fields["bad_range"] == 0, fields
+    # both outcomes of the range test occur (three bounds runs over nq values)
+    assert fields["nq"] < fields["in_range"] < 3 * fields["nq"], fields
