@@ -116,16 +116,25 @@ __global__ void k_rs_hist(const uint64_t *__restrict__ keys, int64_t n, int shif
 
 // Stable scatter: warp w of the block owns keys [w*256, w*256+256) of the
 // tile and walks them 32 at a time in index order; equal digits inside a
-// step are ranked by lane with __match_any_sync.
+// step are ranked by lane with __match_any_sync.  The tile is then ordered
+// by digit in shared memory (same order inside a digit: warp, step, lane)
+// and written out with consecutive threads on consecutive destinations, so
+// the writes of a digit's run land together instead of one 8-byte key per
+// lane in 32 places.
 __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict__ kin,
                                                      const uint32_t *__restrict__ vin, uint64_t *__restrict__ kout,
                                                      uint32_t *__restrict__ vout, int64_t n, int shift, uint32_t mask,
                                                      const uint32_t *__restrict__ offs, int nblk) {
+    static_assert(RS_T == RS_BINS, "one digit per thread in the block scan");
     __shared__ uint32_t cnt[RS_T / 32][RS_BINS];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < (RS_T / 32) * RS_BINS; i += blockDim.x) (&cnt[0][0])[i] = 0;
+    __shared__ uint32_t loc[RS_BINS], gof[RS_BINS], wtot[RS_T / 32];
+    __shared__ uint64_t sk[RS_TILE];
+    __shared__ uint32_t sv[RS_TILE];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, tid = threadIdx.x;
+    for (int i = tid; i < (RS_T / 32) * RS_BINS; i += blockDim.x) (&cnt[0][0])[i] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * RS_TILE + (int64_t)w * (32 * RS_I);
+    const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
+    const int64_t base = tile0 + (int64_t)w * (32 * RS_I);
     const unsigned lt = (1u << lane) - 1u;
     uint64_t k[RS_I];
     uint32_t v[RS_I];
@@ -146,24 +155,46 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t *__restrict_
         r[i] = before + __popc(peers & lt);
     }
     __syncthreads();
-    // exclusive prefix over warps for each digit
-    for (int dg = threadIdx.x; dg < RS_BINS; dg += blockDim.x) {
-        uint32_t acc = offs[(int64_t)dg * nblk + blockIdx.x];
+    // digit tid: prefix over warps inside the block, the digit's total, and
+    // the block's first destination for it
+    uint32_t tot = 0;
 #pragma unroll
-        for (int ww = 0; ww < RS_T / 32; ++ww) {
-            uint32_t t = cnt[ww][dg];
-            cnt[ww][dg] = acc;
-            acc += t;
-        }
+    for (int ww = 0; ww < RS_T / 32; ++ww) {
+        const uint32_t t = cnt[ww][tid];
+        cnt[ww][tid] = tot;
+        tot += t;
     }
+    gof[tid] = offs[(int64_t)tid * nblk + blockIdx.x];
+    // exclusive scan of the digit totals over the block: where each digit's
+    // run starts in the staged tile
+    uint32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wtot[w] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int ww = 0; ww < w; ++ww) wbase += wtot[ww];
+    loc[tid] = wbase + incl - tot;
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RS_I; ++i) {
         if (d[i] < RS_BINS) {
-            uint32_t dst = cnt[w][d[i]] + r[i];
-            kout[dst] = k[i];
-            vout[dst] = v[i];
+            const uint32_t lp = loc[d[i]] + cnt[w][d[i]] + r[i];
+            sk[lp] = k[i];
+            sv[lp] = v[i];
         }
+    }
+    __syncthreads();
+    const int m = (int)((n - tile0) < RS_TILE ? (n - tile0) : RS_TILE);
+    for (int j = tid; j < m; j += RS_T) {
+        const uint64_t kk = sk[j];
+        const uint32_t dg = (uint32_t)(kk >> shift) & mask;
+        const uint32_t dst = gof[dg] + (uint32_t)j - loc[dg];
+        kout[dst] = kk;
+        vout[dst] = sv[j];
     }
 }
 
