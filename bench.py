@@ -393,9 +393,8 @@ def run_ours(args, ws, rank, local):
     tr = _dram_traffic(dominant, args.workload)
     if tr:
         roof["traffic"] = tr["bytes_per_launch"]
-        roof["traffic_note"] = ("DRAM read + write of one working launch from an ncu capture of this kernel "
-                                "source (%s, %s); algorithmic bytes of that launch %.4g; the per-launch "
-                                "average above also counts launches that exit at once after convergence" %
+        roof["traffic_note"] = ("DRAM read + write of one launch from an ncu capture of this kernel's current "
+                                "source (%s, %s); algorithmic bytes of that launch %.4g" %
                                 (tr["summary"], tr["kernel"], tr["algorithmic_bytes_per_launch"]))
     else:
         roof["traffic_note"] = "no ncu capture of the current source of this kernel is recorded"

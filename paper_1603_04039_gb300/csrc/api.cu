@@ -383,9 +383,9 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->gstate, &c->rho_m, &c->rho, &c->phi, &c->nodefield, &c->nodefield32, &c->tmp, &c->derr, &c->dsmall,
                     &c->hx, &c->hy, &c->hz, &c->hq, &c->hphi, &c->hex, &c->hey, &c->hez, &c->ell_A32,
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
-                    &c->pz0, &c->pz1, &c->pt, &c->zbasis, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
+                    &c->pz0, &c->pz1, &c->pt, &c->zbasis, &c->ell_rd, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
                     &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act,
-                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col,
+                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col, &c->ss_col24,
                     &c->ss_A, &c->ss_B, &c->ss_A32, &c->ss_B32, &c->tune_b, &c->tune_x, &c->beam_part, &c->ilu_lrows, &c->ilu_urows, &c->ilu_lrp, &c->ilu_urp,
                     &c->ilu_lcol, &c->ilu_ucol, &c->ilu_lval, &c->ilu_uval, &c->ilu_dinv};
     for (DBuf *b : bufs) free_buf(c, *b);

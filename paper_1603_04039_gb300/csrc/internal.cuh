@@ -190,6 +190,8 @@ struct apcloud_ctx {
     // width-sorted copy of the FP16 sweep matrix: rows ordered by stencil width
     // inside windows of 256 rows, so 32-row slices pad little (see build_sorted_sweep)
     apc::DBuf ss_perm, ss_w, ss_o, ss_col, ss_A, ss_B;
+    apc::DBuf ss_col24;                             // chunk columns of the sorted copy, 24 bits each
+    bool ss_col24_ok = false;
     apc::DBuf ss_A32, ss_B32;   // FP32 values in the same layout (Arnoldi products of the mixed form)
     apc::DBuf beam_part;        // per-beam norms: partial sums, BSQ_CH per beam
     apc::DBuf tune_b, tune_x;
@@ -205,6 +207,7 @@ struct apcloud_ctx {
     apc::DBuf V32, w32a, w32b, r32, e32, gstate2;   // mixed form: FP32 Krylov scratch, outer state
     apc::DBuf pz0, pz1, pt;                         // polynomial preconditioner sweeps
     apc::DBuf zbasis;                               // preconditioned basis Z (flexible cycle end)
+    apc::DBuf ell_rd;                               // reciprocal diagonals while the ELL is filled
     // device staging for apcloud_field_host
     apc::DBuf hx, hy, hz, hq, hphi, hex, hey, hez;
     // error word, small host-visible values

@@ -306,6 +306,54 @@ __device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const
     return acc;
 }
 
+// row_dot_c with the chunks' columns packed to 24 bits: chunk j of lane l is
+// three words at pbase + 96 j + 32 p + l (p = 0, 1, 2), read by three
+// coalesced 4-byte loads; the last w % 4 columns stay in the 32-bit array.
+// Same entries in the same order: the same bits as row_dot_c.
+template <int U>
+__device__ __forceinline__ float row_dot_c24(const __half *__restrict__ val, const int32_t *__restrict__ col,
+                                             const uint32_t *__restrict__ col24, const float *__restrict__ x,
+                                             int64_t sbase, int64_t pbase, int lane, int w) {
+    constexpr int AH = (U > 1) ? 2 : 1;   // chunks whose loads are in flight
+    const uint3 z3 = make_uint3(0u, 0u, 0u);
+    const uint2 z2 = make_uint2(0u, 0u);
+    float acc = 0.f;
+    const int nch = w >> 2;
+    const uint32_t *p0 = col24 + pbase + lane;
+    const uint2 *v4 = reinterpret_cast<const uint2 *>(val + sbase) + lane;
+    uint3 cq[AH];
+    uint2 vq[AH];
+#pragma unroll
+    for (int a = 0; a < AH; ++a) {
+        cq[a] = a < nch ? make_uint3(p0[a * 96], p0[a * 96 + 32], p0[a * 96 + 64]) : z3;
+        vq[a] = a < nch ? v4[(int64_t)a * 32] : z2;
+    }
+    for (int j = 0; j < nch; ++j) {
+        const uint3 c0 = cq[0];
+        const uint2 v0 = vq[0];
+#pragma unroll
+        for (int a = 0; a + 1 < AH; ++a) {
+            cq[a] = cq[a + 1];
+            vq[a] = vq[a + 1];
+        }
+        const int64_t jn = (int64_t)(j + AH) * 96;
+        cq[AH - 1] = (j + AH < nch) ? make_uint3(p0[jn], p0[jn + 32], p0[jn + 64]) : z3;
+        vq[AH - 1] = (j + AH < nch) ? v4[(int64_t)(j + AH) * 32] : z2;
+        const uint32_t i0 = c0.x & 0xFFFFFFu, i1 = (c0.x >> 24) | ((c0.y & 0xFFFFu) << 8),
+                       i2 = (c0.y >> 16) | ((c0.z & 0xFFu) << 16), i3 = c0.z >> 8;
+        const float x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
+        const float2 f01 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.x));
+        const float2 f23 = __half22float2(*reinterpret_cast<const __half2 *>(&v0.y));
+        acc = fmaf(f01.x, x0, acc);
+        acc = fmaf(f01.y, x1, acc);
+        acc = fmaf(f23.x, x2, acc);
+        acc = fmaf(f23.y, x3, acc);
+    }
+    const int64_t tb = sbase + (int64_t)nch * 128 + lane;
+    for (int k = 0; k < (w & 3); ++k) acc = fmaf(__half2float(val[tb + (int64_t)k * 32]), x[col[tb + (int64_t)k * 32]], acc);
+    return acc;
+}
+
 // Rows of beams that have converged in a batch (both null outside batches):
 // their Krylov vectors are zero, so the products skip them.
 struct RowSkip {
@@ -397,13 +445,13 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
 // The same sweep on the width-sorted copy: thread = slot of a 32-slot slice,
 // its row from the window's permutation (entries in the same order, so the
 // same bits as k_sweep_h).
-template <int BS, int U = 1>
+template <int BS, int U = 1, bool P24 = false>
 __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
                                                 const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
                                                 const __half *__restrict__ val, int64_t nslot,
                                                 const float *__restrict__ x, float *__restrict__ y,
                                                 const float *__restrict__ b, const GmresState *__restrict__ st,
-                                                RowSkip skip) {
+                                                RowSkip skip, const uint32_t *__restrict__ col24) {
     // the row's own loads are issued before the state is read (in batches
     // after the test for a converged beam, whose rows read nothing more)
     const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
@@ -428,7 +476,8 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *_
         xr = x[r];
     }
     const float om = (float)st->omega;
-    const float acc = row_dot_c<U>(val, col, x, sb, lane, w);
+    const float acc = P24 ? row_dot_c24<U>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w)
+                          : row_dot_c<U>(val, col, x, sb, lane, w);
     y[r] = fmaf(om, br - acc, xr);
 }
 
@@ -521,7 +570,8 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_spmv_s(const int32_t *__
 #define APC_SPMV3(B, U) (k_spmv<3, T, B, U>)
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
-#define APC_SWEEPS(B, U) (k_sweep_s<B, U>)
+#define APC_SWEEPS(B, U) (k_sweep_s<B, U, false>)
+#define APC_SWEEPS24(B, U) (k_sweep_s<B, U, true>)
 #define APC_SPMVS(B, U) (k_spmv_s<B, U>)
 
 
@@ -1404,6 +1454,7 @@ struct Krylov {
     const uint32_t *ssw = nullptr, *sso = nullptr;
     const __half *sval = nullptr;
     const float *sval32 = nullptr;  // FP32 values of the same copy (Arnoldi products)
+    const uint32_t *scol24 = nullptr;   // its chunk columns packed to 24 bits (sweeps), or null
     int64_t nslot = 0;
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
     // flexible basis: Z_j = p(Ahat) v_j kept from step j, so that the cycle ends
@@ -1436,9 +1487,17 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     for (int i = 1; i < K.pdeg; ++i) {
         if (last && i + 1 == K.pdeg) nxt = last;   // the last sweep writes where the caller keeps z
         if constexpr (sizeof(T) == 4) {
+            if (K.hval && K.sperm && K.scol24) {
+                APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                             (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
+                             K.scol24);
+                T *tmp = cur; cur = nxt; nxt = tmp;
+                continue;
+            }
             if (K.hval && K.sperm) {
                 APC_SWEEP_BS(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
-                             (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip);
+                             (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
+                             (const uint32_t *)nullptr);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
@@ -1668,7 +1727,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
                            K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,
                            K.bk ? K.bk->H : nullptr, K.bk ? K.bk->done : nullptr,
                            K.bk ? (const void *)(intptr_t)K.bk->nitems : nullptr, K.sperm, K.sval, K.scol, K.ssw,
-                           K.sso, K.Z, K.sval32};
+                           K.sso, K.Z, K.sval32, K.scol24};
         static_assert(sizeof p <= sizeof key.p, "graph key holds every buffer address");
         for (size_t i = 0; i < sizeof p / sizeof p[0]; ++i) key.p[i] = p[i];
         GraphEntry *g = find_graph(c, key);
@@ -1741,8 +1800,9 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             const double sweeps = (K.pdeg <= 1 || K.ilu) ? 0.0 : (double)(K.pdeg - 1) * (je + (K.Z ? 0 : 1));
             const double prods = je + 1.0;
             const double sb = K.hval ? 2.0 : vb;
+            const double cb = K.scol24 ? 3.0 : 4.0;   // column bytes per entry read by a sweep
             account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
-            account(c, K_SWEEP, ((sb + 4.0) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
+            account(c, K_SWEEP, ((sb + cb) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
         }
         const bool fused = gs_fused(K, jmax);
         for (int j = 0; j < je; ++j) {
@@ -1957,6 +2017,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
                 K.scol = ptr<int32_t>(c->ss_col);
                 K.sval = ptr<__half>(which ? c->ss_A : c->ss_B);
                 K.sval32 = ptr<float>(which ? c->ss_A32 : c->ss_B32);
+                if (c->ss_col24_ok) K.scol24 = ptr<uint32_t>(c->ss_col24);
                 K.nslot = (int64_t)div_up(c->n_tot, 256) * 256;
             }
             K.z0 = ensure<float>(c, c->pz0, ldv + 1);

@@ -18,6 +18,7 @@
 
 #include <cmath>
 
+#include "fpconv.cuh"
 #include "internal.cuh"
 
 namespace apc {
@@ -527,19 +528,23 @@ __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
 }
 
 // ---------------------------------------------------------------- matrices
+// diagonals of A and B (the Jacobi scaling) and their reciprocals
 __global__ void k_diag(const int32_t *__restrict__ msz, const double *__restrict__ lapd, const int4 *__restrict__ ic,
-                       int n_int, int n_tot, double ext, double *__restrict__ dA, double *__restrict__ dB) {
+                       int n_int, int n_tot, double ext, double *__restrict__ dA, double *__restrict__ dB,
+                       double *__restrict__ rA, double *__restrict__ rB) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_tot) return;
+    double a = 1.0, b = 1.0;
     if (r < n_int) {
         double h = ldexp(ext, -ic[r].w);
         double s = h * h / 24.0;
-        dA[r] = lapd[r];
-        dB[r] = 1.0 + s * lapd[r];
-    } else {
-        dA[r] = 1.0;
-        dB[r] = 1.0;
+        a = lapd[r];
+        b = 1.0 + s * lapd[r];
     }
+    dA[r] = a;
+    dB[r] = b;
+    rA[r] = 1.0 / a;
+    rB[r] = 1.0 / b;
 }
 
 __global__ void k_slice_width(const int32_t *__restrict__ msz, int n_int, int n_tot, int nsl, uint32_t *__restrict__ w) {
@@ -561,8 +566,9 @@ __global__ void k_slice_width(const int32_t *__restrict__ msz, int n_int, int n_
 // diagonal of the column (Jacobi preconditioning folded into the matrix).
 __global__ void k_ell_fill(const int32_t *__restrict__ msz, const int32_t *__restrict__ nbr,
                            const double *__restrict__ lap, const double *__restrict__ lapd, const int4 *__restrict__ ic,
-                           const double *__restrict__ dA, const double *__restrict__ dB, int n_int, int n_tot,
-                           double ext, const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
+                           const double *__restrict__ dA, const double *__restrict__ dB, const double *__restrict__ rA,
+                           const double *__restrict__ rB, int n_int, int n_tot, double ext,
+                           const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                            int32_t *__restrict__ col, double *__restrict__ vA, double *__restrict__ vB) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     int s = r >> 5, lane = r & 31;
@@ -589,9 +595,12 @@ __global__ void k_ell_fill(const int32_t *__restrict__ msz, const int32_t *__res
         if (k <= m) {
             int cj = nbr[(int64_t)r * MMAX + k - 1];
             double l = lap[(int64_t)r * MMAX + k - 1];
+            // off-diagonal entries times the column's reciprocal diagonal (an
+            // FP64 division per entry would make this pass FP64-bound; the
+            // diagonal entries above keep their exact division, so they stay 1)
             col[e] = cj;
-            vA[e] = l / dA[cj];
-            vB[e] = (sc * l) / dB[cj];
+            vA[e] = l * rA[cj];
+            vB[e] = (sc * l) * rB[cj];
         } else {
             col[e] = r;
             vA[e] = 0.0;
@@ -606,8 +615,10 @@ __global__ void k_values_f32(const double *__restrict__ vA, const double *__rest
                              __half *__restrict__ hB) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        fA[i] = (float)vA[i];
-        fB[i] = (float)vB[i];
+        // the FP32 copies on the integer pipe (bit-exact); the FP16 ones keep
+        // the hardware conversion (a direct rounding from FP64)
+        fA[i] = f64_to_f32_int(vA[i]);
+        fB[i] = f64_to_f32_int(vB[i]);
         hA[i] = __double2half(vA[i]);
         hB[i] = __double2half(vB[i]);
     }
@@ -688,8 +699,11 @@ apcloud_status build_stencils(apcloud_ctx *c) {
     uint32_t *so = ensure<uint32_t>(c, c->slice_off, nsl + 1);
     double *dA = ensure<double>(c, c->dA, nt + 1);
     double *dB = ensure<double>(c, c->dB, nt + 1);
-    if (!sw || !so || !dA || !dB) return APCLOUD_E_NOMEM;
-    APC_LAUNCH(c, K_ELL, div_up(nt, 256), 256, 0, k_diag, msz, lapd, ptr<int4>(c->node_ic), n, nt, ext, dA, dB);
+    double *rd = ensure<double>(c, c->ell_rd, 2 * ((int64_t)nt + 1));   // reciprocals, for the fill only
+    if (!sw || !so || !dA || !dB || !rd) return APCLOUD_E_NOMEM;
+    double *rA = rd, *rB = rd + nt + 1;
+    APC_LAUNCH(c, K_ELL, div_up(nt, 256), 256, 0, k_diag, msz, lapd, ptr<int4>(c->node_ic), n, nt, ext, dA, dB, rA,
+               rB);
     APC_LAUNCH(c, K_ELL, div_up(nsl, 8), 256, 0, k_slice_width, msz, n, nt, nsl, sw);
     uint32_t *small = ptr<uint32_t>(c->dsmall);
     APC_TRY(scan_u32(c, sw, so, nsl, small + 5));
@@ -701,7 +715,8 @@ apcloud_status build_stencils(apcloud_ctx *c) {
     double *vB = ensure<double>(c, c->ell_B, c->ell_entries);
     if (!col || !vA || !vB) return APCLOUD_E_NOMEM;
     APC_LAUNCH(c, K_ELL, div_up((int64_t)nsl * 32, 256), 256, 0, k_ell_fill, msz, nbr, lap, lapd,
-               ptr<int4>(c->node_ic), dA, dB, n, nt, ext, sw, so, col, vA, vB);
+               ptr<int4>(c->node_ic), dA, dB, (const double *)rA, (const double *)rB, n, nt, ext, sw, so, col, vA,
+               vB);
     if (c->P.precision == 1) {
         float *fA = ensure<float>(c, c->ell_A32, c->ell_entries), *fB = ensure<float>(c, c->ell_B32, c->ell_entries);
         __half *hA = ensure<__half>(c, c->ell_A16, c->ell_entries), *hB = ensure<__half>(c, c->ell_B16, c->ell_entries);
@@ -824,7 +839,7 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
                           const int32_t *__restrict__ perm, const uint32_t *__restrict__ w2,
                           const uint32_t *__restrict__ o2, int64_t nslot, int32_t *__restrict__ col2,
                           __half *__restrict__ A2, __half *__restrict__ B2, float *__restrict__ A4,
-                          float *__restrict__ B4) {
+                          float *__restrict__ B4, uint32_t *__restrict__ col24) {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= nslot) return;
     const int sl2 = (int)(s >> 5), lane2 = (int)(s & 31);
@@ -853,6 +868,19 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
         A4[q] = 0.f;
         B4[q] = 0.f;
     }
+    if (col24) {
+        // the columns of the 4-entry chunks again, 24 bits each: a chunk's four
+        // columns in three words, word p of lane l at 24 o + 96 j + 32 p + l
+        const int64_t pw = (int64_t)o2[sl2] * 24 + lane2;
+        for (int j = 0; j < (wid2 >> 2); ++j) {
+            uint32_t cc[4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) cc[t] = (uint32_t)col2[ss_slot(b2, wid2, 4 * j + t, lane2)];
+            col24[pw + (int64_t)j * 96] = cc[0] | (cc[1] << 24);
+            col24[pw + (int64_t)j * 96 + 32] = (cc[1] >> 8) | (cc[2] << 16);
+            col24[pw + (int64_t)j * 96 + 64] = (cc[2] >> 16) | (cc[3] << 8);
+        }
+    }
 }
 
 }  // namespace
@@ -866,7 +894,9 @@ __global__ void k_ss_fill(const uint32_t *__restrict__ sw, const uint32_t *__res
 // the last width % 4 columns as in the ELL.  Each row keeps its entries in
 // their stored order, so a sweep on this copy gives the same bits as on the
 // ELL.  The copy carries the FP16 values of the sweeps and the FP32 values of
-// the Arnoldi products (also the same bits as the FP32 ELL product).
+// the Arnoldi products (also the same bits as the FP32 ELL product), and for
+// the sweeps the chunks' columns packed to 24 bits (while n < 2^24): 20
+// instead of 24 bytes per 4-entry chunk of a bandwidth-bound stream.
 apcloud_status build_sorted_sweep(apcloud_ctx *c) {
     c->ss_ok = false;
     const int n = c->n_tot;
@@ -887,11 +917,19 @@ apcloud_status build_sorted_sweep(apcloud_ctx *c) {
     __half *A2 = ensure<__half>(c, c->ss_A, c->ss_entries + 1), *B2 = ensure<__half>(c, c->ss_B, c->ss_entries + 1);
     float *A4 = ensure<float>(c, c->ss_A32, c->ss_entries + 1), *B4 = ensure<float>(c, c->ss_B32, c->ss_entries + 1);
     if (!col2 || !A2 || !B2 || !A4 || !B4) return APCLOUD_E_NOMEM;
+    // 24-bit columns for the sweeps while every node index fits
+    uint32_t *col24 = nullptr;
+    c->ss_col24_ok = false;
+    if (n < (1 << 24)) {
+        col24 = ensure<uint32_t>(c, c->ss_col24, c->ss_entries / 4 * 3 + 1);
+        if (!col24) return APCLOUD_E_NOMEM;
+        c->ss_col24_ok = true;
+    }
     APC_LAUNCH(c, K_ELL, div_up(nslot, 256), 256, 0, k_ss_fill, (const uint32_t *)ptr<uint32_t>(c->slice_w),
                (const uint32_t *)ptr<uint32_t>(c->slice_off), (const int32_t *)ptr<int32_t>(c->ell_col),
                (const __half *)ptr<__half>(c->ell_A16), (const __half *)ptr<__half>(c->ell_B16),
                (const float *)ptr<float>(c->ell_A32), (const float *)ptr<float>(c->ell_B32), (const int32_t *)perm,
-               (const uint32_t *)w2, (const uint32_t *)o2, nslot, col2, A2, B2, A4, B4);
+               (const uint32_t *)w2, (const uint32_t *)o2, nslot, col2, A2, B2, A4, B4, col24);
     c->ss_ok = true;
     return cuda_check(c, cudaGetLastError(), "sorted sweep matrix");
 }
