@@ -256,7 +256,8 @@ __device__ __forceinline__ float row_dot_h(const __half *__restrict__ val, const
 // flight (U > 1) they fit 32 registers without spilling, so blocks of up to
 // 256 threads fill the SM's 64 warps (left to itself the compiler takes more
 // registers and fewer warps); the one-chunk form spills at 32 or 40
-// registers and keeps the compiler's choice.
+// registers and keeps the compiler's choice.  The FP32 product with packed
+// columns needs 40 (48 warps).
 #define SS_MINB(BS, U) (((U) > 1 && (BS) <= 256) ? 2048 / (BS) : 1)
 
 // A row of the width-sorted sweep matrix.  A slice of width w stores its first
@@ -522,14 +523,59 @@ __device__ __forceinline__ float row_dot_cf(const float *__restrict__ val, const
     return acc;
 }
 
+// row_dot_cf with the chunks' columns packed to 24 bits (see row_dot_c24):
+// the same entries in the same order, the same bits
+template <int U>
+__device__ __forceinline__ float row_dot_cf24(const float *__restrict__ val, const int32_t *__restrict__ col,
+                                              const uint32_t *__restrict__ col24, const float *__restrict__ x,
+                                              int64_t sbase, int64_t pbase, int lane, int w) {
+    constexpr int AH = (U > 1) ? 2 : 1;
+    const uint3 z3 = make_uint3(0u, 0u, 0u);
+    const float4 zf = make_float4(0.f, 0.f, 0.f, 0.f);
+    float acc = 0.f;
+    const int nch = w >> 2;
+    const uint32_t *p0 = col24 + pbase + lane;
+    const float4 *v4 = reinterpret_cast<const float4 *>(val + sbase) + lane;
+    uint3 cq[AH];
+    float4 vq[AH];
+#pragma unroll
+    for (int a = 0; a < AH; ++a) {
+        cq[a] = a < nch ? make_uint3(p0[a * 96], p0[a * 96 + 32], p0[a * 96 + 64]) : z3;
+        vq[a] = a < nch ? v4[(int64_t)a * 32] : zf;
+    }
+    for (int j = 0; j < nch; ++j) {
+        const uint3 c0 = cq[0];
+        const float4 v0 = vq[0];
+#pragma unroll
+        for (int a = 0; a + 1 < AH; ++a) {
+            cq[a] = cq[a + 1];
+            vq[a] = vq[a + 1];
+        }
+        const int64_t jn = (int64_t)(j + AH) * 96;
+        cq[AH - 1] = (j + AH < nch) ? make_uint3(p0[jn], p0[jn + 32], p0[jn + 64]) : z3;
+        vq[AH - 1] = (j + AH < nch) ? v4[(int64_t)(j + AH) * 32] : zf;
+        const uint32_t i0 = c0.x & 0xFFFFFFu, i1 = (c0.x >> 24) | ((c0.y & 0xFFFFu) << 8),
+                       i2 = (c0.y >> 16) | ((c0.z & 0xFFu) << 16), i3 = c0.z >> 8;
+        const float x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
+        acc = fmaf(v0.x, x0, acc);
+        acc = fmaf(v0.y, x1, acc);
+        acc = fmaf(v0.z, x2, acc);
+        acc = fmaf(v0.w, x3, acc);
+    }
+    const int64_t tb = sbase + (int64_t)nch * 128 + lane;
+    for (int k = 0; k < (w & 3); ++k) acc = fmaf(val[tb + (int64_t)k * 32], x[col[tb + (int64_t)k * 32]], acc);
+    return acc;
+}
+
 // y = Ahat x on the width-sorted FP32 copy, skipped once the cycle is done
 // (the Arnoldi product of k_spmv<4, float> with the same bits)
-template <int BS, int U = 1>
-__global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_spmv_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
+template <int BS, int U = 1, bool P24 = false>
+__global__ void __launch_bounds__(BS, (P24 && SS_MINB(BS, U) > 1) ? 1536 / BS : SS_MINB(BS, U)) k_spmv_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
                                                const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
                                                const float *__restrict__ val, int64_t nslot,
                                                const float *__restrict__ x, float *__restrict__ y,
-                                               const GmresState *__restrict__ st, RowSkip skip) {
+                                               const GmresState *__restrict__ st, RowSkip skip,
+                                               const uint32_t *__restrict__ col24) {
     const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (sl_ >= nslot) return;
     const int r = perm[sl_];
@@ -541,7 +587,53 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_spmv_s(const int32_t *__
         y[r] = 0.f;
         return;
     }
-    y[r] = row_dot_cf<U>(val, col, x, sb, lane, w);
+    y[r] = P24 ? row_dot_cf24<U>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w)
+               : row_dot_cf<U>(val, col, x, sb, lane, w);
+}
+
+// r = b - Ahat u and ||r||^2 (the restart residual, MODE 2 of k_spmv) on the
+// width-sorted FP32 copy with 24-bit chunk columns: every row's entries in the
+// same order as on the ELL (the same r), the norm summed over the sorted slots
+template <int U>
+__global__ void __launch_bounds__(RT) k_resid_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
+                                                const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
+                                                const float *__restrict__ val, const uint32_t *__restrict__ col24,
+                                                int64_t nslot, const float *__restrict__ x, float *__restrict__ y,
+                                                const float *__restrict__ b, GmresState *st,
+                                                double *__restrict__ partial) {
+    __shared__ double sm[RT + RT / 32 + 8];
+    const int64_t sl_ = (int64_t)blockIdx.x * RT + threadIdx.x;
+    double yv = 0.0;
+    if (sl_ < nslot) {
+        const int r = perm[sl_];
+        if (r >= 0) {
+            const int sl = (int)(sl_ >> 5), lane = (int)(sl_ & 31);
+            const int w = (int)sw[sl];
+            const int64_t sb = (int64_t)soff[sl] * 32;
+            const float acc = row_dot_cf24<U>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w);
+            const float t = b[r] - acc;
+            y[r] = t;
+            yv = (double)t;
+        }
+    }
+    double a[1] = {yv * yv};
+    double tot = 0.0;
+    block_reduce_many<1>(a, 1, sm, &tot);
+    if (threadIdx.x == 0) partial[blockIdx.x * 64] = tot;
+    if (last_block(&st->ticket)) {
+        __shared__ double fs[1];
+        final_sums(partial, gridDim.x, 1, sm, fs);
+        if (threadIdx.x == 0) {
+            const double beta = sqrt(fs[0]);
+            st->beta = beta;
+            st->g[0] = beta;
+            for (int i = 1; i <= MAX_RESTART; ++i) st->g[i] = 0.0;
+            st->jend = 0;
+            st->done = (beta <= st->rtol * st->bnorm) ? 1 : 0;
+            st->inv_norm = beta > 0.0 ? 1.0 / beta : 0.0;
+            st->ticket = 0;
+        }
+    }
 }
 
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
@@ -572,7 +664,8 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_spmv_s(const int32_t *__
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
 #define APC_SWEEPS(B, U) (k_sweep_s<B, U, false>)
 #define APC_SWEEPS24(B, U) (k_sweep_s<B, U, true>)
-#define APC_SPMVS(B, U) (k_spmv_s<B, U>)
+#define APC_SPMVS(B, U) (k_spmv_s<B, U, false>)
+#define APC_SPMVS24(B, U) (k_spmv_s<B, U, true>)
 
 
 // ---------------------------------------------------------------- Gram-Schmidt passes
@@ -1515,6 +1608,29 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     return cur;
 }
 
+// the restart residual r = b - Ahat u into K.wraw with beta = ||r||: on the
+// packed sorted FP32 copy when the cycle has it, else on the ELL
+template <class T>
+void residual_launch(apcloud_ctx *c, const T *val, const Krylov<T> &K, const T *u, const T *b, GmresState *st) {
+    const int n = c->n_tot;
+    if constexpr (sizeof(T) == 4) {
+        if (K.pdeg > 1 && K.sval32 && K.sperm && K.scol24) {
+            const int nb = div_up(K.nslot, RT);
+            if (c->spmv_unroll == 4)
+                APC_LAUNCH(c, K_SPMV, nb, RT, 0, k_resid_s<4>, K.sperm, K.ssw, K.sso, K.scol, K.sval32, K.scol24,
+                           K.nslot, (const float *)u, (float *)K.wraw, (const float *)b, st, K.partial);
+            else
+                APC_LAUNCH(c, K_SPMV, nb, RT, 0, k_resid_s<1>, K.sperm, K.ssw, K.sso, K.scol, K.sval32, K.scol24,
+                           K.nslot, (const float *)u, (float *)K.wraw, (const float *)b, st, K.partial);
+            return;
+        }
+    }
+    const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
+    const int32_t *col = ptr<int32_t>(c->ell_col);
+    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, u, K.wraw, (T *)nullptr, b, st,
+               K.partial, RowSkip{nullptr, nullptr});
+}
+
 // w = Ahat z of a polynomial-preconditioned Arnoldi step (skipped once the
 // cycle is done): on the width-sorted FP32 copy when the sweeps use it, else
 // on the ELL
@@ -1522,9 +1638,14 @@ template <class T>
 void arnoldi_product(apcloud_ctx *c, const T *val, const Krylov<T> &K, const T *z, GmresState *st, RowSkip skip) {
     const int n = c->n_tot;
     if constexpr (sizeof(T) == 4) {
+        if (K.sval32 && K.sperm && K.scol24) {
+            APC_SPMV_BS(c, K.nslot, APC_SPMVS24, K.sperm, K.ssw, K.sso, K.scol, K.sval32, K.nslot, (const float *)z,
+                        (float *)K.w, (const GmresState *)st, skip, K.scol24);
+            return;
+        }
         if (K.sval32 && K.sperm) {
             APC_SPMV_BS(c, K.nslot, APC_SPMVS, K.sperm, K.ssw, K.sso, K.scol, K.sval32, K.nslot, (const float *)z,
-                        (float *)K.w, (const GmresState *)st, skip);
+                        (float *)K.w, (const GmresState *)st, skip, (const uint32_t *)nullptr);
             return;
         }
     }
@@ -1627,8 +1748,7 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
         APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_add<T>, u, (const T *)z, n);
     }
     APC_LAUNCH(c, K_VEC, 1, 256, 0, k_bmax_jend, bk, st);
-    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
-               (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
+    residual_launch<T>(c, val, K, (const T *)u, b, st);
     APC_TRY(bstart_launches<T>(c, K));
     return cuda_check(c, cudaGetLastError(), "batched gmres cycle");
 }
@@ -1703,8 +1823,7 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     }
     // the next cycle's residual keeps this cycle's column count: save it first
     APC_LAUNCH(c, K_VEC, 1, 32, 0, k_save_jend, st);
-    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
-               (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
+    residual_launch<T>(c, val, K, (const T *)u, b, st);
     if (K.mask) APC_TRY(mask_residual<T>(c, *K.mask, K.wraw, st));
     return cuda_check(c, cudaGetLastError(), "gmres cycle");
 }
@@ -1765,8 +1884,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
     double relres = 0.0;
     apcloud_status status = APCLOUD_W_NOT_CONVERGED;
     const double vb = (double)sizeof(T), nnz = (double)c->sum_m + (double)c->n_int + (double)c->n_bnd, dn = n;
-    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, (const T *)u, K.wraw,
-               (T *)nullptr, b, st, K.partial, RowSkip{nullptr, nullptr});
+    residual_launch<T>(c, val, K, (const T *)u, b, st);
     if (K.mask) APC_TRY(mask_residual<T>(c, *K.mask, K.wraw, st));
     if (K.bk) {
         // per-beam ||b_b|| once, then every beam's first cycle
@@ -1801,7 +1919,9 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             const double prods = je + 1.0;
             const double sb = K.hval ? 2.0 : vb;
             const double cb = K.scol24 ? 3.0 : 4.0;   // column bytes per entry read by a sweep
-            account(c, K_SPMV, ((vb + 4.0) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
+            // Arnoldi products and the restart residual (24-bit columns on the packed sorted copy)
+            const double pcb = (K.pdeg > 1 && K.sval32 && K.scol24) ? 3.0 : 4.0;
+            account(c, K_SPMV, ((vb + pcb) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
             account(c, K_SWEEP, ((sb + cb) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
         }
         const bool fused = gs_fused(K, jmax);
