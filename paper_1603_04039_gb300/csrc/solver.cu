@@ -363,8 +363,10 @@ struct RowSkip {
     const double *binv;   // per-beam Krylov spaces: 1 / ||w|| of each beam (null: st->inv_norm)
 };
 
-// BS: threads per block (one row each); mode 2 runs with RT only, its block
-// partials are sized for div_up(n, RT) blocks.  U: loads issued ahead (row_dot).
+// BS: threads per block (one row each; mode 2 strides over the rows with a
+// grid of resid_blocks(n) blocks of RT threads: one block per row block put
+// 4118 same-address ticket atomics on the last-block test of a 1.05e6-row
+// product).  U: loads issued ahead (row_dot).
 template <int MODE, class T, int BS = RT, int U = 1>
 __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, const uint32_t *__restrict__ soff,
                                              const int32_t *__restrict__ col, const T *__restrict__ val, int n,
@@ -385,7 +387,7 @@ __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, co
     if (MODE == 3) s = (T)st->omega;
     T acc = (T)0;
     double yv = 0.0;
-    if (r < n) {
+    if (MODE != 2 && r < n) {
         const int sl = r >> 5, lane = r & 31;
         const int w = (int)sw[sl];
         const int64_t base = (int64_t)soff[sl] * 32 + lane;
@@ -393,10 +395,18 @@ __global__ void __launch_bounds__(BS) k_spmv(const uint32_t *__restrict__ sw, co
         if (MODE == 0 || MODE == 4) y[r] = acc;
         if (MODE == 1) { y[r] = acc * s; vout[r] = x[r] * s; }
         if (MODE == 3) y[r] = fma(s, b[r] - acc, x[r]);
-        if (MODE == 2) { T t = b[r] - acc; y[r] = t; yv = (double)t; }
     }
     if (MODE == 2) {
-        double a[1] = {yv * yv};
+        for (int rr = r; rr < n; rr += gridDim.x * BS) {
+            const int sl = rr >> 5, lane = rr & 31;
+            const int w = (int)sw[sl];
+            const int64_t base = (int64_t)soff[sl] * 32 + lane;
+            acc = row_dot<U, T, T>(val, col, x, base, w);
+            const T t = b[rr] - acc;
+            y[rr] = t;
+            yv = fma((double)t, (double)t, yv);
+        }
+        double a[1] = {yv};
         double tot = 0.0;
         block_reduce_many<1>(a, 1, sm, &tot);
         if (threadIdx.x == 0) partial[blockIdx.x * 64] = tot;
@@ -594,6 +604,7 @@ __global__ void __launch_bounds__(BS, (P24 && SS_MINB(BS, U) > 1) ? 1536 / BS : 
 // r = b - Ahat u and ||r||^2 (the restart residual, MODE 2 of k_spmv) on the
 // width-sorted FP32 copy with 24-bit chunk columns: every row's entries in the
 // same order as on the ELL (the same r), the norm summed over the sorted slots
+// by a grid of resid_blocks blocks striding over them
 template <int U>
 __global__ void __launch_bounds__(RT) k_resid_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
                                                 const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
@@ -602,9 +613,8 @@ __global__ void __launch_bounds__(RT) k_resid_s(const int32_t *__restrict__ perm
                                                 const float *__restrict__ b, GmresState *st,
                                                 double *__restrict__ partial) {
     __shared__ double sm[RT + RT / 32 + 8];
-    const int64_t sl_ = (int64_t)blockIdx.x * RT + threadIdx.x;
     double yv = 0.0;
-    if (sl_ < nslot) {
+    for (int64_t sl_ = (int64_t)blockIdx.x * RT + threadIdx.x; sl_ < nslot; sl_ += (int64_t)gridDim.x * RT) {
         const int r = perm[sl_];
         if (r >= 0) {
             const int sl = (int)(sl_ >> 5), lane = (int)(sl_ & 31);
@@ -613,10 +623,10 @@ __global__ void __launch_bounds__(RT) k_resid_s(const int32_t *__restrict__ perm
             const float acc = row_dot_cf24<U>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w);
             const float t = b[r] - acc;
             y[r] = t;
-            yv = (double)t;
+            yv = fma((double)t, (double)t, yv);
         }
     }
-    double a[1] = {yv * yv};
+    double a[1] = {yv};
     double tot = 0.0;
     block_reduce_many<1>(a, 1, sm, &tot);
     if (threadIdx.x == 0) partial[blockIdx.x * 64] = tot;
@@ -1103,6 +1113,13 @@ int sm_count() {
 }
 
 // dot kernels: 2 fat blocks per SM (few partials for the last block to sum)
+// grid of the restart residual: 4 blocks of RT threads per SM striding over
+// the rows (few partials and few ticket atomics for the last block)
+int resid_blocks(int64_t nrow) {
+    const int nb = div_up(nrow, RT), cap = 4 * sm_count();
+    return nb < 1 ? 1 : (nb > cap ? cap : nb);
+}
+
 int dot_blocks(int64_t ldv) {
     int nb = div_up(ldv, TILE), cap = 2 * sm_count();
     return nb < 1 ? 1 : (nb > cap ? cap : nb);
@@ -1615,7 +1632,7 @@ void residual_launch(apcloud_ctx *c, const T *val, const Krylov<T> &K, const T *
     const int n = c->n_tot;
     if constexpr (sizeof(T) == 4) {
         if (K.pdeg > 1 && K.sval32 && K.sperm && K.scol24) {
-            const int nb = div_up(K.nslot, RT);
+            const int nb = resid_blocks(K.nslot);
             if (c->spmv_unroll == 4)
                 APC_LAUNCH(c, K_SPMV, nb, RT, 0, k_resid_s<4>, K.sperm, K.ssw, K.sso, K.scol, K.sval32, K.scol24,
                            K.nslot, (const float *)u, (float *)K.wraw, (const float *)b, st, K.partial);
@@ -1627,7 +1644,7 @@ void residual_launch(apcloud_ctx *c, const T *val, const Krylov<T> &K, const T *
     }
     const uint32_t *sw = ptr<uint32_t>(c->slice_w), *so = ptr<uint32_t>(c->slice_off);
     const int32_t *col = ptr<int32_t>(c->ell_col);
-    APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, u, K.wraw, (T *)nullptr, b, st,
+    APC_LAUNCH(c, K_SPMV, resid_blocks(n), RT, 0, (k_spmv<2, T>), sw, so, col, val, n, u, K.wraw, (T *)nullptr, b, st,
                K.partial, RowSkip{nullptr, nullptr});
 }
 
@@ -2162,7 +2179,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         APC_LAUNCH(c, K_VEC, nblk, RT, 0, k_norm2<double>, b, n, so, partial);
         status = APCLOUD_W_NOT_CONVERGED;
         for (;;) {
-            APC_LAUNCH(c, K_SPMV, div_up(n, RT), RT, 0, (k_spmv<2, double>), sw, sof, col, val, n,
+            APC_LAUNCH(c, K_SPMV, resid_blocks(n), RT, 0, (k_spmv<2, double>), sw, sof, col, val, n,
                        (const double *)u, r64, (double *)nullptr, b, so, partial, RowSkip{nullptr, nullptr});
             if (bm) APC_TRY(mask_residual<double>(c, *bm, r64, so));
             double tmp[2];
