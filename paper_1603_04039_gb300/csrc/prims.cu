@@ -2,7 +2,8 @@
 //
 // The tree construction of Section 4 sorts particles by Morton key; these are
 // the primitives it (and the node ordering) is built from.  Both are written
-// for determinism: the scan is a fixed three-phase tree, the sort is stable.
+// for determinism: the scan is a fixed two-phase tree (integer sums, exact in
+// any order), the sort is stable.
 #include "internal.cuh"
 
 namespace apc {
@@ -56,23 +57,18 @@ __global__ void k_scan_reduce(const uint32_t *__restrict__ in, int64_t n, uint32
     if (threadIdx.x == 0) blk[blockIdx.x] = tot;
 }
 
-__global__ void k_scan_blocks(uint32_t *__restrict__ blk, int nb, uint32_t *__restrict__ d_total) {
-    __shared__ uint32_t sh[33];
-    uint32_t carry = 0;
-    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
-        int i = b0 + threadIdx.x;
-        uint32_t v = (i < nb) ? blk[i] : 0u;
-        uint32_t tot;
-        uint32_t e = block_excl_scan(v, sh, &tot);
-        if (i < nb) blk[i] = e + carry;
-        carry += tot;
-    }
-    if (threadIdx.x == 0 && d_total) *d_total = carry;
-}
-
+// Block b scans its tile and adds the sum of the block totals before it (it
+// sums blk[0 .. b) itself, so no pass scans the block totals); the last
+// block writes the grand total.  blk == null: a single block.
 __global__ void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, int64_t n,
-                            const uint32_t *__restrict__ blk) {
+                            const uint32_t *__restrict__ blk, uint32_t *__restrict__ d_total) {
     __shared__ uint32_t sh[33];
+    uint32_t pre = 0;
+    if (blk) {
+        uint32_t ps = 0;
+        for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) ps += blk[i];
+        block_excl_scan(ps, sh, &pre);
+    }
     int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_I;
     uint32_t v[SCAN_I];
     uint32_t s = 0;
@@ -83,7 +79,8 @@ __global__ void k_scan_down(const uint32_t *__restrict__ in, uint32_t *__restric
         s += v[i];
     }
     uint32_t tot;
-    uint32_t e = block_excl_scan(s, sh, &tot) + blk[blockIdx.x];
+    uint32_t e = block_excl_scan(s, sh, &tot) + pre;
+    if (d_total && threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) *d_total = pre + tot;
 #pragma unroll
     for (int i = 0; i < SCAN_I; ++i) {
         int64_t idx = base + i;
@@ -206,11 +203,14 @@ apcloud_status scan_u32(apcloud_ctx *c, const uint32_t *in, uint32_t *out, int64
         return APCLOUD_OK;
     }
     int nb = div_up(n, SCAN_TILE);
+    if (nb == 1) {
+        APC_LAUNCH(c, K_TREE, 1, SCAN_T, 0, k_scan_down, in, out, n, (const uint32_t *)nullptr, d_total);
+        return cuda_check(c, cudaGetLastError(), "scan");
+    }
     uint32_t *blk = ensure<uint32_t>(c, c->scan_blk, nb);
     if (!blk) return APCLOUD_E_NOMEM;
     APC_LAUNCH(c, K_TREE, nb, SCAN_T, 0, k_scan_reduce, in, n, blk);
-    APC_LAUNCH(c, K_TREE, 1, 1024, 0, k_scan_blocks, blk, nb, d_total);
-    APC_LAUNCH(c, K_TREE, nb, SCAN_T, 0, k_scan_down, in, out, n, blk);
+    APC_LAUNCH(c, K_TREE, nb, SCAN_T, 0, k_scan_down, in, out, n, (const uint32_t *)blk, d_total);
     return cuda_check(c, cudaGetLastError(), "scan");
 }
 
