@@ -251,6 +251,7 @@ def run_ours(args, ws, rank, local):
     barrier()
     torch.cuda.synchronize()
     launches0 = ap.launch_count()
+    syncs0 = ap.host_sync_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -263,6 +264,7 @@ def run_ours(args, ws, rank, local):
     barrier()
     ms_total = e0.elapsed_time(e1)
     launches = ap.launch_count() - launches0
+    syncs = ap.host_sync_count() - syncs0
     # roofline region: the same K steps again with CUDA events around every
     # launch of the dominant kernel kind
     ap.set_timing(1 << dom_bit)
@@ -421,6 +423,7 @@ def run_ours(args, ws, rank, local):
         "e2e": {"value": round(ws * nsolve / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,
                 "d2h_bytes_per_step": 32 * npart},
         "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
+        "host_syncs_per_step": round(syncs / args.steps, 1),
         "plain_fp64_form": dict(plain, solves_per_s=round(nsolve * 1000.0 / plain["ms_per_step"], 4),
                                 speedup_of_this_form=round(plain["ms_per_step"] / ms_step, 2)),
         "unbatched_same_form": unbatched,

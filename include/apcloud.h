@@ -474,6 +474,12 @@ apcloud_status apcloud_get_sizes(const apcloud_ctx *ctx, int64_t *h_sizes);
 /* Total kernel launches issued by this context since creation. */
 int64_t apcloud_launch_count(const apcloud_ctx *ctx);
 
+/* Host read-backs since creation that waited for the context stream (tree
+ * sizes, the convergence test of every restart cycle and refinement step,
+ * introspection); each one idles the GPU between the work before and after
+ * it.  No paper counterpart (launch mechanics). */
+int64_t apcloud_host_sync_count(const apcloud_ctx *ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -147,6 +147,7 @@ def load():
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
             "apcloud_launch_count": (L, [P]),
+            "apcloud_host_sync_count": (L, [P]),
             "apcloud_get_sizes": (I, [P, P]),
             "apcloud_interpolate_potential": (I, [P, P, P, P, L, P]),
             "apcloud_push_particles": (I, [P, P, P, P, P, P, P, L, P, P, P, D, D]),
@@ -557,6 +558,9 @@ class APCloud:
 
     def launch_count(self):
         return int(self._lib.apcloud_launch_count(self._ctx))
+
+    def host_sync_count(self):
+        return int(self._lib.apcloud_host_sync_count(self._ctx))
 
 
 class MPNN:

@@ -260,6 +260,7 @@ apcloud_status launch_graph(apcloud_ctx *c, GraphEntry *g) {
 
 apcloud_status read_back(apcloud_ctx *c, void *host, const void *dev, size_t bytes) {
     timer_close(c);   // a timed pair must not span the host's wait
+    c->host_syncs++;
     if (bytes > 256) {
         APC_CUDA(c, cudaMemcpyAsync(host, dev, bytes, cudaMemcpyDeviceToHost, c->s));
         return cuda_check(c, cudaStreamSynchronize(c->s), "synchronise");
@@ -792,6 +793,8 @@ const char *apcloud_kernel_name(int kind) {
 }
 
 int64_t apcloud_launch_count(const apcloud_ctx *c) { return c ? c->launches : 0; }
+
+int64_t apcloud_host_sync_count(const apcloud_ctx *c) { return c ? c->host_syncs : 0; }
 
 apcloud_status apcloud_autotune(apcloud_ctx *c, unsigned what, int *spmv_block, int *spmv_unroll,
                                 int *sweep_sorted, int *wls_warps, double *ms) {

@@ -132,6 +132,7 @@ struct apcloud_ctx {
     int stage = 0;  // 0 created, 1 octree, 2 stencils, 3 deposit, 4 solved, 5 gathered
     char err[512] = {0};
     int64_t launches = 0;
+    int64_t host_syncs = 0;   // read-backs that waited for the stream
     apc::Timer timer;
     // launch shapes chosen by apcloud_autotune
     int spmv_bs = 256;     // threads per block of the Arnoldi products and sweeps
