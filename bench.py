@@ -75,6 +75,29 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(value, ws, device):
+    """The maximum of `value` over the ranks of the process group (the value
+    itself on one rank): a job's step time is that of its slowest rank."""
+    if ws <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _rank_seed(rank):
+    """Each rank solves its own independent beam (replicas only): seed 1 + rank."""
+    return 1 + rank
+
+
+def _job_rate(ws, solves_per_rank, ms_step):
+    """Whole-job throughput: the solves of every rank per second of the
+    slowest rank's step."""
+    return ws * solves_per_rank * 1000.0 / ms_step
+
+
 def _source_items(text, items):
     """The source text of the named items of a CUDA file, joined: for a
     function, from its declaration line to its matching closing brace; for a
@@ -197,7 +220,7 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     fp64_peak, fp32_peak = measure_fma_peak()
-    seed = 1 + rank
+    seed = _rank_seed(rank)
     x, y, z, q, offs, depth, c, nsolve = make_problem(args.workload, seed)
     npart = len(x)
     tx, ty, tz, tq = (torch.from_numpy(a).to(dev) for a in (x, y, z, q))
@@ -280,10 +303,7 @@ def run_ours(args, ws, rank, local):
     ap.set_timing(0)
     clocks = sampler.stop()
     ms_step = ms_total / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = _max_over_ranks(ms_step, ws, dev)
     n_nodes = info["n_int"] + info["n_bnd"]
     sz = ap.sizes()
 
@@ -300,10 +320,7 @@ def run_ours(args, ws, rank, local):
     for _ in range(e2e_steps):
         ap_e2e.field_host(hx, hy, hz, q=hq, rtol=RTOL, max_iter=MAX_ITER, out=hout, offsets=offs)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if ws > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = _max_over_ranks(e2e_s, ws, dev)
     ap_e2e.close()
 
     # the plain FP64 form (GMRES(30) + Jacobi) on the same particles: its fields are
@@ -400,7 +417,7 @@ def run_ours(args, ws, rank, local):
                                 (tr["summary"], tr["kernel"], tr["algorithmic_bytes_per_launch"]))
     else:
         roof["traffic_note"] = "no ncu capture of the current source of this kernel is recorded"
-    solves = ws * nsolve * 1000.0 / ms_step
+    solves = _job_rate(ws, nsolve, ms_step)
     line = {
         "metric": METRIC, "value": round(solves, 4), "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 3), "higher_is_better": True, "scaling": "weak",
@@ -420,7 +437,7 @@ def run_ours(args, ws, rank, local):
                    "parallelism": "independent beam per GPU" if ws > 1 else "single GPU",
                    "autotuned": tuned, "cuda_graphs": ap.graph_stats()},
         "nodes_iters_per_s": round(ws * n_nodes * (iters_total / args.steps) / (ms_step * 1e-3), 1),
-        "e2e": {"value": round(ws * nsolve / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,
+        "e2e": {"value": round(_job_rate(ws, nsolve, 1000.0 * e2e_s), 4), "unit": "solves/s", "h2d_bytes_per_step": 32 * npart,
                 "d2h_bytes_per_step": 32 * npart},
         "roofline": roof, "gpu_launches": int(launches), "clocks": clocks,
         "host_syncs_per_step": round(syncs / args.steps, 1),
