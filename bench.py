@@ -403,8 +403,8 @@ def run_ours(args, ws, rank, local):
                  "algorithmic_bytes_per_launch": by_k / max(nl_k, 1),
                  "algorithmic_flops_per_launch": fl_k / max(nl_k, 1),
                  "share_of_step": round(ms_k / ms_timed_steps, 4),
-                 "region": "a second pass of the K timed steps with CUDA events around every launch of this "
-                           "kind (%.1f ms/step there, %.1f ms/step without the events)"
+                 "region": "a second pass of the K timed steps with CUDA events around every run of consecutive "
+                           "launches of this kind (%.1f ms/step there, %.1f ms/step without the events)"
                            % (ms_timed_steps / args.steps, ms_step),
                  "peak_source": "measured: hbm_gbs of MEASURED_PEAKS.json; FP64/FP32 FMA chains on all SMs "
                                 "(apcloud_measure_fma_peak) in this run",
@@ -412,9 +412,10 @@ def run_ours(args, ws, rank, local):
     tr = _dram_traffic(dominant, args.workload)
     if tr:
         roof["traffic"] = tr["bytes_per_launch"]
-        roof["traffic_note"] = ("DRAM read + write of one launch from an ncu capture of this kernel's current "
-                                "source (%s, %s); algorithmic bytes of that launch %.4g" %
-                                (tr["summary"], tr["kernel"], tr["algorithmic_bytes_per_launch"]))
+        roof["traffic_note"] = ("DRAM read + write per launch from an ncu capture of this kernel's current "
+                                "source (%s, %s; %s); algorithmic bytes per launch %.4g" %
+                                (tr["summary"], tr["kernel"], tr.get("capture", "one launch"),
+                                 tr["algorithmic_bytes_per_launch"]))
     else:
         roof["traffic_note"] = "no ncu capture of the current source of this kernel is recorded"
     solves = _job_rate(ws, nsolve, ms_step)

@@ -364,6 +364,25 @@ apcloud_status apcloud_autotune(apcloud_ctx *ctx, unsigned what, int *h_spmv_blo
 apcloud_status apcloud_set_launch_shape(apcloud_ctx *ctx, int spmv_block, int spmv_unroll, int sweep_sorted,
                                         int wls_warps);
 
+/* L2 residency of the FP16 sweep matrix (width-sorted copy with packed
+ * columns, the mixed form's polynomial preconditioner).  The sweeps of one
+ * polynomial application read the whole matrix one after another; a sweep
+ * loads its first keep_bytes of matrix bytes (5 per stored entry) as
+ * ordinary loads and the rest as streaming loads (ld.global.cs: lines
+ * allocated evict-first in L2), so that the streamed part replaces itself in
+ * L2 and the kept part is still there for the next sweep.  keep_bytes = -1
+ * (the default): 0.4 of the L2 when the matrix and the sweep's vectors (12
+ * bytes per row) take between 3/4 of the L2 and twice the L2, else all of
+ * the matrix (no streaming loads); 0: every matrix load streaming; larger
+ * than the matrix: none.
+ * Results are bit-identical for every value (the same loads in the same
+ * order).  APCLOUD_E_INVALID for keep_bytes < -1.  The getter writes the
+ * value in effect for the current node set (the automatic choice resolved;
+ * INT64_MAX when no load is streaming).  The paper has no counterpart (cache
+ * mechanics). */
+apcloud_status apcloud_set_sweep_l2_keep(apcloud_ctx *ctx, int64_t keep_bytes);
+apcloud_status apcloud_get_sweep_l2_keep(const apcloud_ctx *ctx, int64_t *h_keep_bytes);
+
 /* Graph replays since the context was created and graphs currently cached. */
 apcloud_status apcloud_graph_stats(const apcloud_ctx *ctx, int64_t *h_replays, int64_t *h_cached);
 

@@ -143,6 +143,8 @@ def load():
             "apcloud_set_graphs": (I, [P, I]),
             "apcloud_autotune": (I, [P, C.c_uint, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), P]),
             "apcloud_set_launch_shape": (I, [P, I, I, I, I]),
+            "apcloud_set_sweep_l2_keep": (I, [P, L]),
+            "apcloud_get_sweep_l2_keep": (I, [P, C.POINTER(L)]),
             "apcloud_graph_stats": (I, [P, C.POINTER(L), C.POINTER(L)]),
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
             "apcloud_kernel_name": (C.c_char_p, [I]),
@@ -512,6 +514,14 @@ class APCloud:
     def set_launch_shape(self, spmv_block=256, wls_warps=4, spmv_unroll=1, sweep_sorted=0):
         self._check(self._lib.apcloud_set_launch_shape(self._ctx, int(spmv_block), int(spmv_unroll),
                                                        int(sweep_sorted), int(wls_warps)))
+
+    def set_sweep_l2_keep(self, keep_bytes=-1):
+        self._check(self._lib.apcloud_set_sweep_l2_keep(self._ctx, int(keep_bytes)))
+
+    def sweep_l2_keep(self):
+        v = C.c_int64()
+        self._check(self._lib.apcloud_get_sweep_l2_keep(self._ctx, C.byref(v)))
+        return v.value
 
     def solve_learned(self, net, use=3, rtol=1e-10, max_iter=100000, phi0=None):
         """Poisson solve with the network's column scaling (use bit 0), guess (bit 1)

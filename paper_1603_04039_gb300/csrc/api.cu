@@ -827,6 +827,19 @@ apcloud_status apcloud_set_launch_shape(apcloud_ctx *c, int spmv_block, int spmv
     return APCLOUD_OK;
 }
 
+apcloud_status apcloud_set_sweep_l2_keep(apcloud_ctx *c, int64_t keep_bytes) {
+    if (!c) return APCLOUD_E_INVALID;
+    if (keep_bytes < -1) return fail(c, APCLOUD_E_INVALID, "keep_bytes must be -1 (automatic) or >= 0");
+    c->sweep_keep = keep_bytes;
+    return APCLOUD_OK;
+}
+
+apcloud_status apcloud_get_sweep_l2_keep(const apcloud_ctx *c, int64_t *h_keep_bytes) {
+    if (!c || !h_keep_bytes) return APCLOUD_E_INVALID;
+    *h_keep_bytes = sweep_keep_bytes(c);
+    return APCLOUD_OK;
+}
+
 apcloud_status apcloud_set_graphs(apcloud_ctx *c, int enable) {
     if (!c) return APCLOUD_E_INVALID;
     cudaStreamSynchronize(c->s);

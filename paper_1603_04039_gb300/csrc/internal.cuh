@@ -76,7 +76,7 @@ struct GmresState {
 struct GraphKey {
     int tsize, n, jmax, pdeg, nblk, spmv_bs;
     unsigned mask;
-    int64_t ldv;
+    int64_t ldv, skeep;
     const void *p[32];
 };
 
@@ -138,6 +138,7 @@ struct apcloud_ctx {
     int spmv_bs = 256;     // threads per block of the Arnoldi products and sweeps
     int spmv_unroll = 1;   // stencil entries whose loads a thread issues ahead (1 or 4)
     int sweep_sorted = 0;  // 1: FP16 sweeps on the width-sorted matrix (autotuner's choice)
+    int64_t sweep_keep = -1;   // bytes of that matrix the sweeps read with ordinary loads, the rest streaming (-1: automatic)
     int jprev[2][2] = {{0, 0}, {0, 0}};   // Arnoldi steps of the last cycle, per system (B, A) and FP64/FP32
     int wls_warps = 4;     // nodes (warps) per block of the stencil build
     // CUDA graphs of GMRES restart cycles (captured on cap_stream, replayed on s)
@@ -270,6 +271,7 @@ apcloud_status refresh_lowp(apcloud_ctx *c);          // FP32/FP16 matrix copies
 apcloud_status build_sorted_sweep(apcloud_ctx *c);    // width-sorted FP16 sweep matrix from the ELL
 double *poisson_rhs(apcloud_ctx *c, const double *g);  // b of the Poisson system into c->b
 apcloud_status tune_spmv(apcloud_ctx *c, double *ms_out);      // ms per sweep at 64/128/256/512 threads
+int64_t sweep_keep_bytes(const apcloud_ctx *c);                 // sweep matrix bytes read with ordinary loads
 apcloud_status tune_stencils(apcloud_ctx *c, double *ms_out);  // ms per build at 2/4/8 warps
 // CUDA graphs of restart cycles
 GraphEntry *find_graph(apcloud_ctx *c, const GraphKey &key);

@@ -307,28 +307,51 @@ __device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const
     return acc;
 }
 
+// L2 eviction priority of the sweep's matrix loads.  The polynomial's sweeps
+// follow one another, each reading the whole width-sorted matrix, so what
+// the L2 still holds of one sweep's matrix the next one reads from there.
+// A matrix larger than the L2 read as a plain cyclic stream leaves nothing
+// to reuse (every line is evicted before its next read); with the slices
+// past a threshold read as streaming data (ld.global.cs, __ldcs: lines
+// allocated evict-first in L1 and L2), those lines replace one another and
+// the slices below it stay resident.  The cache operator only steers the
+// caches: the loads, and the results, are the same.
+
 // row_dot_c with the chunks' columns packed to 24 bits: chunk j of lane l is
 // three words at pbase + 96 j + 32 p + l (p = 0, 1, 2), read by three
 // coalesced 4-byte loads; the last w % 4 columns stay in the 32-bit array.
-// Same entries in the same order: the same bits as row_dot_c.
-template <int U>
+// Same entries in the same order: the same bits as row_dot_c.  With EF the
+// matrix loads are streaming loads; the two forms are separate
+// instantiations, chosen per row, so each keeps the 32-register bound.
+template <int U, bool EF>
 __device__ __forceinline__ float row_dot_c24(const __half *__restrict__ val, const int32_t *__restrict__ col,
                                              const uint32_t *__restrict__ col24, const float *__restrict__ x,
                                              int64_t sbase, int64_t pbase, int lane, int w) {
     constexpr int AH = (U > 1) ? 2 : 1;   // chunks whose loads are in flight
-    const uint3 z3 = make_uint3(0u, 0u, 0u);
-    const uint2 z2 = make_uint2(0u, 0u);
     float acc = 0.f;
     const int nch = w >> 2;
     const uint32_t *p0 = col24 + pbase + lane;
     const uint2 *v4 = reinterpret_cast<const uint2 *>(val + sbase) + lane;
     uint3 cq[AH];
     uint2 vq[AH];
+    auto load = [&](int a, uint3 &c, uint2 &v) {
+        if (a >= nch) {
+            c = make_uint3(0u, 0u, 0u);
+            v = make_uint2(0u, 0u);
+        } else {
+            const uint32_t *q = p0 + (int64_t)a * 96;
+            const uint2 *u = v4 + (int64_t)a * 32;
+            if (EF) {
+                c = make_uint3(__ldcs(q), __ldcs(q + 32), __ldcs(q + 64));
+                v = __ldcs(u);
+            } else {
+                c = make_uint3(q[0], q[32], q[64]);
+                v = *u;
+            }
+        }
+    };
 #pragma unroll
-    for (int a = 0; a < AH; ++a) {
-        cq[a] = a < nch ? make_uint3(p0[a * 96], p0[a * 96 + 32], p0[a * 96 + 64]) : z3;
-        vq[a] = a < nch ? v4[(int64_t)a * 32] : z2;
-    }
+    for (int a = 0; a < AH; ++a) load(a, cq[a], vq[a]);
     for (int j = 0; j < nch; ++j) {
         const uint3 c0 = cq[0];
         const uint2 v0 = vq[0];
@@ -337,9 +360,7 @@ __device__ __forceinline__ float row_dot_c24(const __half *__restrict__ val, con
             cq[a] = cq[a + 1];
             vq[a] = vq[a + 1];
         }
-        const int64_t jn = (int64_t)(j + AH) * 96;
-        cq[AH - 1] = (j + AH < nch) ? make_uint3(p0[jn], p0[jn + 32], p0[jn + 64]) : z3;
-        vq[AH - 1] = (j + AH < nch) ? v4[(int64_t)(j + AH) * 32] : z2;
+        load(j + AH, cq[AH - 1], vq[AH - 1]);
         const uint32_t i0 = c0.x & 0xFFFFFFu, i1 = (c0.x >> 24) | ((c0.y & 0xFFFFu) << 8),
                        i2 = (c0.y >> 16) | ((c0.z & 0xFFu) << 16), i3 = c0.z >> 8;
         const float x0 = x[i0], x1 = x[i1], x2 = x[i2], x3 = x[i3];
@@ -351,7 +372,12 @@ __device__ __forceinline__ float row_dot_c24(const __half *__restrict__ val, con
         acc = fmaf(f23.y, x3, acc);
     }
     const int64_t tb = sbase + (int64_t)nch * 128 + lane;
-    for (int k = 0; k < (w & 3); ++k) acc = fmaf(__half2float(val[tb + (int64_t)k * 32]), x[col[tb + (int64_t)k * 32]], acc);
+    for (int k = 0; k < (w & 3); ++k) {
+        const __half *hv = val + tb + (int64_t)k * 32;
+        const int32_t *hc = col + tb + (int64_t)k * 32;
+        const float fv = __half2float(EF ? __ldcs(hv) : *hv);
+        acc = fmaf(fv, x[EF ? __ldcs(hc) : *hc], acc);
+    }
     return acc;
 }
 
@@ -455,14 +481,18 @@ __global__ void __launch_bounds__(BS) k_sweep_h(const uint32_t *__restrict__ sw,
 
 // The same sweep on the width-sorted copy: thread = slot of a 32-slot slice,
 // its row from the window's permutation (entries in the same order, so the
-// same bits as k_sweep_h).
-template <int BS, int U = 1, bool P24 = false>
+// same bits as k_sweep_h).  With packed columns and KS, slices stored from
+// entry `keep` on are read as streaming (evict-first) loads; without KS
+// (no threshold in effect) the kernel holds the ordinary form alone, whose
+// code the branch slows by 5% (98 against 103 us per sweep of a 64-beam
+// batch).
+template <int BS, int U = 1, bool P24 = false, bool KS = false>
 __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *__restrict__ perm, const uint32_t *__restrict__ sw,
                                                 const uint32_t *__restrict__ soff, const int32_t *__restrict__ col,
                                                 const __half *__restrict__ val, int64_t nslot,
                                                 const float *__restrict__ x, float *__restrict__ y,
                                                 const float *__restrict__ b, const GmresState *__restrict__ st,
-                                                RowSkip skip, const uint32_t *__restrict__ col24) {
+                                                RowSkip skip, const uint32_t *__restrict__ col24, int64_t keep) {
     // the row's own loads are issued before the state is read (in batches
     // after the test for a converged beam, whose rows read nothing more)
     const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
@@ -487,8 +517,10 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *_
         xr = x[r];
     }
     const float om = (float)st->omega;
-    const float acc = P24 ? row_dot_c24<U>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w)
-                          : row_dot_c<U>(val, col, x, sb, lane, w);
+    float acc;
+    if (!P24) acc = row_dot_c<U>(val, col, x, sb, lane, w);
+    else if (KS && sb >= keep) acc = row_dot_c24<U, true>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w);
+    else acc = row_dot_c24<U, false>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w);
     y[r] = fmaf(om, br - acc, xr);
 }
 
@@ -674,6 +706,7 @@ __global__ void __launch_bounds__(RT) k_resid_s(const int32_t *__restrict__ perm
 #define APC_SWEEPH(B, U) (k_sweep_h<B, U>)
 #define APC_SWEEPS(B, U) (k_sweep_s<B, U, false>)
 #define APC_SWEEPS24(B, U) (k_sweep_s<B, U, true>)
+#define APC_SWEEPS24K(B, U) (k_sweep_s<B, U, true, true>)
 #define APC_SPMVS(B, U) (k_spmv_s<B, U, false>)
 #define APC_SPMVS24(B, U) (k_spmv_s<B, U, true>)
 
@@ -1110,6 +1143,44 @@ int sm_count() {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms > 0 ? sms : 152;
+}
+
+int64_t l2_bytes() {
+    int b = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b, cudaDevAttrL2CacheSize, dev);
+    return b > 0 ? b : (int64_t)126 << 20;
+}
+
+// Bytes a sweep reads per stored entry of the packed width-sorted matrix (a
+// 2-byte value and 3 bytes of packed column) and per row (x and b read, y
+// written, FP32).
+constexpr double SWEEP_ENTRY_BYTES = 5.0, SWEEP_ROW_BYTES = 12.0;
+
+}  // namespace
+
+// Matrix bytes the sweeps read with ordinary loads when left to the library:
+// all of them when the matrix and the sweep's vectors fit in 3/4 of the L2;
+// 0.4 of the L2 when they take up to twice the L2 (the rest of the L2 holds
+// the vectors and the streamed lines; on the 1.05e6-row, 145 MB matrix of a
+// 1e7-particle beam at depth 10 kept sizes of 0.2 to 0.5 of the L2 gave
+// 30.5 to 31.2 us per sweep against 35.3 us with no streaming loads and
+// 33.0 us with streaming loads only); all of them again beyond (a 650 MB
+// matrix of a 64-beam batch gained nothing from the 8% that can stay and
+// lost 2% to the streaming loads).
+int64_t sweep_keep_bytes(const apcloud_ctx *c) {
+    if (c->sweep_keep >= 0) return c->sweep_keep;
+    const double l2 = (double)l2_bytes();
+    const double tot = SWEEP_ENTRY_BYTES * (double)c->ss_entries + SWEEP_ROW_BYTES * (double)c->n_tot;
+    return (tot <= 0.75 * l2 || tot > 2.0 * l2) ? INT64_MAX : (int64_t)(0.4 * l2);
+}
+
+namespace {
+
+// the same as the entry of the sorted matrix from which slices are hinted
+int64_t sweep_keep_entries(const apcloud_ctx *c) {
+    const int64_t kb = sweep_keep_bytes(c);
+    return kb == INT64_MAX ? INT64_MAX : (int64_t)((double)kb / SWEEP_ENTRY_BYTES);
 }
 
 // dot kernels: 2 fat blocks per SM (few partials for the last block to sum)
@@ -1565,6 +1636,7 @@ struct Krylov {
     const __half *sval = nullptr;
     const float *sval32 = nullptr;  // FP32 values of the same copy (Arnoldi products)
     const uint32_t *scol24 = nullptr;   // its chunk columns packed to 24 bits (sweeps), or null
+    int64_t skeep = INT64_MAX;          // sweeps: slices from this entry on are read with streaming loads
     int64_t nslot = 0;
     T *z0 = nullptr, *z1 = nullptr, *t = nullptr;   // sweep ping-pong and cycle-end combination
     // flexible basis: Z_j = p(Ahat) v_j kept from step j, so that the cycle ends
@@ -1598,16 +1670,21 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
         if (last && i + 1 == K.pdeg) nxt = last;   // the last sweep writes where the caller keeps z
         if constexpr (sizeof(T) == 4) {
             if (K.hval && K.sperm && K.scol24) {
-                APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
-                             (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
-                             K.scol24);
+                if (K.skeep < c->ss_entries)
+                    APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24K, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                                 (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
+                                 K.scol24, K.skeep);
+                else
+                    APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                                 (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
+                                 K.scol24, K.skeep);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
             if (K.hval && K.sperm) {
                 APC_SWEEP_BS(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
                              (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
-                             (const uint32_t *)nullptr);
+                             (const uint32_t *)nullptr, (int64_t)0);
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
@@ -1858,6 +1935,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
         key.ldv = K.ldv;
         key.mask = c->timer.mask;
         key.spmv_bs = c->spmv_bs * 8 + c->spmv_unroll;
+        key.skeep = K.skeep;
         const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
                            c->slice_w.p, c->slice_off.p, c->ell_col.p, K.skip.nbo, K.skip.bdone, K.tact,
                            K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,
@@ -2155,6 +2233,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
                 K.sval = ptr<__half>(which ? c->ss_A : c->ss_B);
                 K.sval32 = ptr<float>(which ? c->ss_A32 : c->ss_B32);
                 if (c->ss_col24_ok) K.scol24 = ptr<uint32_t>(c->ss_col24);
+                K.skeep = sweep_keep_entries(c);
                 K.nslot = (int64_t)div_up(c->n_tot, 256) * 256;
             }
             K.z0 = ensure<float>(c, c->pz0, ldv + 1);

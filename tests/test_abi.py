@@ -56,5 +56,8 @@ def test_param_validation_without_gpu(lib):
     l.apcloud_default_params(C.byref(q))
     q.hi[2] = 2.0                        # not a cube
     assert l.apcloud_create(C.byref(q), None, None, C.byref(ctx)) == -1
+    keep = C.c_int64()
+    assert l.apcloud_set_sweep_l2_keep(None, 0) == -1          # no context
+    assert l.apcloud_get_sweep_l2_keep(None, C.byref(keep)) == -1
     assert l.apcloud_kernel_name(7) == b"spmv"
     assert l.apcloud_kernel_name(99) == b"unknown"

@@ -93,6 +93,34 @@ def test_launch_shapes_do_not_change_results(precision):
             assert np.array_equal(a, b)
 
 
+def test_sweep_l2_keep_does_not_change_results():
+    """The sweeps' streaming loads (on every matrix load, on the part past a
+    threshold, on none) only steer the caches: the mixed solve gives the same
+    bits, replayed from graphs as well as launched directly."""
+    from paper_1603_04039_gb300 import APCloud, APCloudError
+    x, y, z, q = inputs.beam_with_halo(50000, 25)
+    ap = APCloud(max_depth=6, c_refine=0.3, precision="mixed", poly_degree=16, poly_omega=1.0)
+    ap.set_launch_shape(128, 4, 4, 1)
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    ap.deposit(q_uniform=1.0 / len(x), rtol=1e-11)
+    assert ap.sweep_l2_keep() == 2**63 - 1              # a matrix far below the L2: no streaming loads
+    ap.solve(rtol=1e-11)                                 # sets the cycle cap the later solves start from
+    res = []
+    for graphs in (True, False):
+        ap.set_graphs(graphs)
+        for keep in (-1, 0, 1 << 20, 1 << 40):
+            ap.set_sweep_l2_keep(keep)
+            assert ap.sweep_l2_keep() == (2**63 - 1 if keep == -1 else keep)
+            phi, info = ap.solve(rtol=1e-11)
+            assert info["status"] == 0
+            res.append((phi.cpu().numpy(), info["iters"]))
+    for r in res[1:]:
+        assert np.array_equal(r[0], res[0][0]) and r[1] == res[0][1]
+    with pytest.raises(APCloudError):
+        ap.set_sweep_l2_keep(-2)
+
+
 def test_autotune_choices_and_rejects():
     from paper_1603_04039_gb300 import APCloud, APCloudError
     x, y, z, q = inputs.beam_with_halo(80000, 24)
