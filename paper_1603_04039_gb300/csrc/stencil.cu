@@ -299,7 +299,33 @@ __device__ bool wls_column(WarpSmem &W, int m, int lane, const GramOwn &own, int
     return true;
 }
 
-// SW warps (nodes) per block, one WarpSmem each; the autotuner picks SW
+// The rows of the derivative operator D (row-of-operator major, nodes
+// fastest) of a block's SW nodes.  Each warp stages its node's 9 x MMAX block
+// in its W.A as [e * MMAX + lane] (free once the WLS is done); the last warp
+// of the block to finish writes every row as SW consecutive nodes, one
+// 8 x SW-byte run per row, where each warp writing its own node would store
+// 288 lone 8-byte words, each in a sector of its own.  Warps without a node
+// (past n_int) only arrive.
+template <int SW>
+__device__ __forceinline__ void write_block_d(const unsigned char *smem_raw, unsigned *arrived, int lane, int y_base,
+                                              int n_int, double *__restrict__ D_out, int64_t dstride) {
+    __threadfence_block();
+    __syncwarp();
+    unsigned last = 0u;
+    if (lane == 0) last = (atomicAdd(arrived, 1u) == SW - 1) ? 1u : 0u;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence_block();
+    const WarpSmem *Ws = reinterpret_cast<const WarpSmem *>(smem_raw);
+    for (int t = lane; t < NCOL * MMAX * SW; t += 32) {
+        const int row = t / SW, w = t - row * SW;
+        const int y = y_base + w;
+        if (y < n_int) D_out[(int64_t)row * dstride + y] = Ws[w].A[row];
+    }
+}
+
+// SW warps (nodes) per block, one WarpSmem each (and the block's arrival
+// count after them); the autotuner picks SW
 template <int SW>
 __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
     const int4 *__restrict__ ic, const int32_t *__restrict__ adj, const int32_t *__restrict__ bowner, int n_int,
@@ -313,7 +339,13 @@ __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
     const int y0 = blockIdx.x * SW + wid;
     const unsigned FULL = 0xffffffffu;
     const unsigned lt = (1u << lane) - 1u;
-    if (y0 >= n_int) return;
+    unsigned *arrived = reinterpret_cast<unsigned *>(reinterpret_cast<WarpSmem *>(smem_raw) + SW);
+    if (threadIdx.x == 0) *arrived = 0u;
+    __syncthreads();
+    if (y0 >= n_int) {
+        write_block_d<SW>(smem_raw, arrived, lane, blockIdx.x * SW, n_int, D_out, dstride);
+        return;
+    }
 
     const int4 c0 = ic[y0];
     int nc = 1;
@@ -504,9 +536,10 @@ __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
             rcond_out[y0] = rmin_over_rmax;
         }
         __syncwarp();
-        // derivative operator, row-of-operator major with nodes fastest
+        // derivative operator, staged for write_block_d
+        __syncwarp();
 #pragma unroll
-        for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = (lane < m) ? q[e] : 0.0;
+        for (int e = 0; e < NCOL; ++e) W.A[e * MMAX + lane] = (lane < m) ? q[e] : 0.0;
         ring = k;
         done = true;
         }   // target sizes
@@ -521,10 +554,12 @@ __global__ void __launch_bounds__(SW * 32, 16 / SW) k_stencil(
         }
         nbr_out[(int64_t)y0 * MMAX + lane] = -1;
         lap_out[(int64_t)y0 * MMAX + lane] = 0.0;
+        __syncwarp();
 #pragma unroll
-        for (int e = 0; e < NCOL; ++e) D_out[((int64_t)e * MMAX + lane) * dstride + y0] = 0.0;
+        for (int e = 0; e < NCOL; ++e) W.A[e * MMAX + lane] = 0.0;
     }
     (void)ring;
+    write_block_d<SW>(smem_raw, arrived, lane, blockIdx.x * SW, n_int, D_out, dstride);
 }
 
 // ---------------------------------------------------------------- matrices
@@ -628,7 +663,7 @@ template <int SW>
 apcloud_status launch_stencil(apcloud_ctx *c, int n, double unit, double ec, double inv_1mec, int32_t *nbr,
                               int32_t *msz, int32_t *ring, double *lap, double *lapd, double *D, int64_t dstride,
                               double *rc, unsigned *derr) {
-    const size_t smem = SW * sizeof(WarpSmem);
+    const size_t smem = SW * sizeof(WarpSmem) + 16;   // the warps' areas, then the block's arrival count
     static bool attr = false;
     if (!attr) {
         APC_CUDA(c, cudaFuncSetAttribute(k_stencil<SW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
