@@ -380,6 +380,16 @@ apcloud_status apcloud_set_launch_shape(apcloud_ctx *ctx, int spmv_block, int sp
  * value in effect for the current node set (the automatic choice resolved;
  * INT64_MAX when no load is streaming).  The paper has no counterpart (cache
  * mechanics). */
+/* Programmatic dependent launch of the polynomial's sweeps (on by default):
+ * every sweep after the first of an application is launched so that its
+ * blocks may start while the sweep before it drains; each row reads its
+ * slice, b, the solver state and its first matrix chunks, then waits on the
+ * device (griddepcontrol.wait) for the previous sweep to complete before it
+ * reads x or writes y.  enable = 0 launches every sweep in plain stream
+ * order.  Results are bit-identical either way.  The paper has no
+ * counterpart (launch mechanics). */
+apcloud_status apcloud_set_dependent_launch(apcloud_ctx *ctx, int enable);
+
 apcloud_status apcloud_set_sweep_l2_keep(apcloud_ctx *ctx, int64_t keep_bytes);
 apcloud_status apcloud_get_sweep_l2_keep(const apcloud_ctx *ctx, int64_t *h_keep_bytes);
 

@@ -144,6 +144,7 @@ def load():
             "apcloud_autotune": (I, [P, C.c_uint, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I), P]),
             "apcloud_set_launch_shape": (I, [P, I, I, I, I]),
             "apcloud_set_sweep_l2_keep": (I, [P, L]),
+            "apcloud_set_dependent_launch": (I, [P, I]),
             "apcloud_get_sweep_l2_keep": (I, [P, C.POINTER(L)]),
             "apcloud_graph_stats": (I, [P, C.POINTER(L), C.POINTER(L)]),
             "apcloud_get_timing": (I, [P, P, P, P, P, I]),
@@ -514,6 +515,9 @@ class APCloud:
     def set_launch_shape(self, spmv_block=256, wls_warps=4, spmv_unroll=1, sweep_sorted=0):
         self._check(self._lib.apcloud_set_launch_shape(self._ctx, int(spmv_block), int(spmv_unroll),
                                                        int(sweep_sorted), int(wls_warps)))
+
+    def set_dependent_launch(self, enable):
+        self._check(self._lib.apcloud_set_dependent_launch(self._ctx, 1 if enable else 0))
 
     def set_sweep_l2_keep(self, keep_bytes=-1):
         self._check(self._lib.apcloud_set_sweep_l2_keep(self._ctx, int(keep_bytes)))

@@ -840,6 +840,12 @@ apcloud_status apcloud_get_sweep_l2_keep(const apcloud_ctx *c, int64_t *h_keep_b
     return APCLOUD_OK;
 }
 
+apcloud_status apcloud_set_dependent_launch(apcloud_ctx *c, int enable) {
+    if (!c) return APCLOUD_E_INVALID;
+    c->pdl_on = enable != 0;
+    return APCLOUD_OK;
+}
+
 apcloud_status apcloud_set_graphs(apcloud_ctx *c, int enable) {
     if (!c) return APCLOUD_E_INVALID;
     cudaStreamSynchronize(c->s);

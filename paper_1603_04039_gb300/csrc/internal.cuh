@@ -74,7 +74,7 @@ struct GmresState {
 // A captured restart cycle (CUDA graph), keyed by everything its launches
 // depend on: element size, sizes, timing mask and every buffer address.
 struct GraphKey {
-    int tsize, n, jmax, pdeg, nblk, spmv_bs;
+    int tsize, n, jmax, pdeg, nblk, spmv_bs, pdl;
     unsigned mask;
     int64_t ldv, skeep;
     const void *p[32];
@@ -138,6 +138,7 @@ struct apcloud_ctx {
     int spmv_bs = 256;     // threads per block of the Arnoldi products and sweeps
     int spmv_unroll = 1;   // stencil entries whose loads a thread issues ahead (1 or 4)
     int sweep_sorted = 0;  // 1: FP16 sweeps on the width-sorted matrix (autotuner's choice)
+    bool pdl_on = true;        // sweeps after the first of a polynomial application as programmatic dependents
     int64_t sweep_keep = -1;   // bytes of that matrix the sweeps read with ordinary loads, the rest streaming (-1: automatic)
     int jprev[2][2] = {{0, 0}, {0, 0}};   // Arnoldi steps of the last cycle, per system (B, A) and FP64/FP32
     int wls_warps = 4;     // nodes (warps) per block of the stencil build
@@ -329,6 +330,32 @@ inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
         if ((grid) > 0) {                                                       \
             ::apc::timer_begin(c, kind);                                        \
             kern<<<(grid), (block), (smem), (c)->s>>>(__VA_ARGS__);             \
+            if ((c)->capturing) ::apc::count_captured(c);                        \
+            else (c)->launches++;                                               \
+        }                                                                       \
+    } while (0)
+
+// The same launch as programmatic dependent launch: the kernel's blocks may
+// start once every block of the kernel before it in the stream has executed
+// griddepcontrol.launch_dependents (or exited); the kernel must execute
+// griddepcontrol.wait, which returns once that kernel has completed and its
+// writes are visible, before it reads anything that kernel writes or writes
+// anything that kernel reads.  Captured into graphs as programmatic edges.
+#define APC_LAUNCH_PDL(c, kind, grid, block, smem, kern, ...)                   \
+    do {                                                                        \
+        if ((grid) > 0) {                                                       \
+            ::apc::timer_begin(c, kind);                                        \
+            cudaLaunchAttribute _at[1];                                         \
+            _at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;     \
+            _at[0].val.programmaticStreamSerializationAllowed = 1;              \
+            cudaLaunchConfig_t _cfg = {};                                       \
+            _cfg.gridDim = dim3((unsigned)(grid));                              \
+            _cfg.blockDim = dim3((unsigned)(block));                            \
+            _cfg.dynamicSmemBytes = (smem);                                     \
+            _cfg.stream = (c)->s;                                               \
+            _cfg.attrs = _at;                                                   \
+            _cfg.numAttrs = 1;                                                  \
+            (void)cudaLaunchKernelEx(&_cfg, kern, __VA_ARGS__);                 \
             if ((c)->capturing) ::apc::count_captured(c);                        \
             else (c)->launches++;                                               \
         }                                                                       \

@@ -307,6 +307,21 @@ __device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const
     return acc;
 }
 
+// Programmatic dependent launch (APC_LAUNCH_PDL).  A kernel launched with the
+// attribute may start while the kernel before it in the stream is running,
+// once every block of that kernel has executed griddepcontrol.launch_dependents
+// (or exited); griddepcontrol.wait returns once that kernel has completed and
+// its writes are visible.  Without the attribute the wait returns at once.
+// A sweep lets the next one start only after its own wait: so sweep i + 1
+// never runs beside sweep i - 1, which read the buffer (through the SM's
+// read-only cache) that sweep i rewrites and sweep i + 1 reads.  With the
+// release at block start, small grids ran three sweeps side by side and
+// sweep i + 1 read lines that sweep i - 1 had cached: wrong results.
+__device__ __forceinline__ void grid_dep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // L2 eviction priority of the sweep's matrix loads.  The polynomial's sweeps
 // follow one another, each reading the whole width-sorted matrix, so what
 // the L2 still holds of one sweep's matrix the next one reads from there.
@@ -322,11 +337,13 @@ __device__ __forceinline__ float row_dot_c(const __half *__restrict__ val, const
 // coalesced 4-byte loads; the last w % 4 columns stay in the 32-bit array.
 // Same entries in the same order: the same bits as row_dot_c.  With EF the
 // matrix loads are streaming loads; the two forms are separate
-// instantiations, chosen per row, so each keeps the 32-register bound.
+// instantiations, chosen per row, so each keeps the 32-register bound.  The
+// grid-dependency wait (grid_dep_wait) comes after the first chunks' loads
+// are issued and before any x is read; xr receives x[r].
 template <int U, bool EF>
 __device__ __forceinline__ float row_dot_c24(const __half *__restrict__ val, const int32_t *__restrict__ col,
                                              const uint32_t *__restrict__ col24, const float *__restrict__ x,
-                                             int64_t sbase, int64_t pbase, int lane, int w) {
+                                             int64_t sbase, int64_t pbase, int lane, int w, int r, float &xr) {
     constexpr int AH = (U > 1) ? 2 : 1;   // chunks whose loads are in flight
     float acc = 0.f;
     const int nch = w >> 2;
@@ -352,6 +369,8 @@ __device__ __forceinline__ float row_dot_c24(const __half *__restrict__ val, con
     };
 #pragma unroll
     for (int a = 0; a < AH; ++a) load(a, cq[a], vq[a]);
+    grid_dep_wait();
+    xr = x[r];
     for (int j = 0; j < nch; ++j) {
         const uint3 c0 = cq[0];
         const uint2 v0 = vq[0];
@@ -493,8 +512,13 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *_
                                                 const float *__restrict__ x, float *__restrict__ y,
                                                 const float *__restrict__ b, const GmresState *__restrict__ st,
                                                 RowSkip skip, const uint32_t *__restrict__ col24, int64_t keep) {
-    // the row's own loads are issued before the state is read (in batches
-    // after the test for a converged beam, whose rows read nothing more)
+    // Sweeps after the first of a polynomial application are launched as
+    // programmatic dependents of the sweep before them, whose y is their x:
+    // a row reads its slice, b, the state and its first chunks before the
+    // grid-dependency wait (none of them is written by a sweep), x and y only
+    // after it.  The row's own loads are issued before the state is read (in
+    // batches after the test for a converged beam, whose rows read nothing
+    // more).
     const int64_t sl_ = (int64_t)blockIdx.x * BS + threadIdx.x;
     if (sl_ >= nslot) return;
     const int r = perm[sl_];
@@ -503,24 +527,28 @@ __global__ void __launch_bounds__(BS, SS_MINB(BS, U)) k_sweep_s(const int32_t *_
     const int64_t sb = (int64_t)soff[sl] * 32;
     float br, xr;
     if (!skip.nbo) {
-        const int rr = r < 0 ? 0 : r;
-        br = b[rr];
-        xr = x[rr];
+        br = b[r < 0 ? 0 : r];
         if (st->done || r < 0) return;
     } else {
         if (st->done || r < 0) return;
         if (skip.bdone[skip.nbo[r]]) {
+            grid_dep_wait();
             y[r] = 0.f;
             return;
         }
         br = b[r];
-        xr = x[r];
     }
     const float om = (float)st->omega;
     float acc;
-    if (!P24) acc = row_dot_c<U>(val, col, x, sb, lane, w);
-    else if (KS && sb >= keep) acc = row_dot_c24<U, true>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w);
-    else acc = row_dot_c24<U, false>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w);
+    if (!P24) {
+        grid_dep_wait();
+        xr = x[r];
+        acc = row_dot_c<U>(val, col, x, sb, lane, w);
+    } else if (KS && sb >= keep) {
+        acc = row_dot_c24<U, true>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w, r, xr);
+    } else {
+        acc = row_dot_c24<U, false>(val, col, col24, x, sb, (int64_t)soff[sl] * 24, lane, w, r, xr);
+    }
     y[r] = fmaf(om, br - acc, xr);
 }
 
@@ -680,26 +708,28 @@ __global__ void __launch_bounds__(RT) k_resid_s(const int32_t *__restrict__ perm
 
 // Row-parallel products of the Arnoldi steps and sweeps at the block size the
 // autotuner chose (64, 128, 256 or 512 threads).
-#define APC_ROWS_BS(c, kind, n, KERNEL_OF, ...)                                                                 \
+#define APC_ROWS_BS_WITH(LAUNCH, c, kind, n, KERNEL_OF, ...)                                                \
     do {                                                                                                    \
         if ((c)->spmv_unroll == 4) {                                                                        \
             switch ((c)->spmv_bs) {                                                                         \
-            case 64: APC_LAUNCH(c, kind, div_up(n, 64), 64, 0, KERNEL_OF(64, 4), __VA_ARGS__); break;     \
-            case 128: APC_LAUNCH(c, kind, div_up(n, 128), 128, 0, KERNEL_OF(128, 4), __VA_ARGS__); break; \
-            case 512: APC_LAUNCH(c, kind, div_up(n, 512), 512, 0, KERNEL_OF(512, 4), __VA_ARGS__); break; \
-            default: APC_LAUNCH(c, kind, div_up(n, 256), 256, 0, KERNEL_OF(256, 4), __VA_ARGS__); break;  \
+            case 64: LAUNCH(c, kind, div_up(n, 64), 64, 0, KERNEL_OF(64, 4), __VA_ARGS__); break;         \
+            case 128: LAUNCH(c, kind, div_up(n, 128), 128, 0, KERNEL_OF(128, 4), __VA_ARGS__); break;     \
+            case 512: LAUNCH(c, kind, div_up(n, 512), 512, 0, KERNEL_OF(512, 4), __VA_ARGS__); break;     \
+            default: LAUNCH(c, kind, div_up(n, 256), 256, 0, KERNEL_OF(256, 4), __VA_ARGS__); break;      \
             }                                                                                               \
         } else {                                                                                            \
             switch ((c)->spmv_bs) {                                                                         \
-            case 64: APC_LAUNCH(c, kind, div_up(n, 64), 64, 0, KERNEL_OF(64, 1), __VA_ARGS__); break;     \
-            case 128: APC_LAUNCH(c, kind, div_up(n, 128), 128, 0, KERNEL_OF(128, 1), __VA_ARGS__); break; \
-            case 512: APC_LAUNCH(c, kind, div_up(n, 512), 512, 0, KERNEL_OF(512, 1), __VA_ARGS__); break; \
-            default: APC_LAUNCH(c, kind, div_up(n, 256), 256, 0, KERNEL_OF(256, 1), __VA_ARGS__); break;  \
+            case 64: LAUNCH(c, kind, div_up(n, 64), 64, 0, KERNEL_OF(64, 1), __VA_ARGS__); break;         \
+            case 128: LAUNCH(c, kind, div_up(n, 128), 128, 0, KERNEL_OF(128, 1), __VA_ARGS__); break;     \
+            case 512: LAUNCH(c, kind, div_up(n, 512), 512, 0, KERNEL_OF(512, 1), __VA_ARGS__); break;     \
+            default: LAUNCH(c, kind, div_up(n, 256), 256, 0, KERNEL_OF(256, 1), __VA_ARGS__); break;      \
             }                                                                                               \
         }                                                                                                   \
     } while (0)
+#define APC_ROWS_BS(c, kind, n, KERNEL_OF, ...) APC_ROWS_BS_WITH(APC_LAUNCH, c, kind, n, KERNEL_OF, __VA_ARGS__)
 #define APC_SPMV_BS(c, n, KERNEL_OF, ...) APC_ROWS_BS(c, K_SPMV, n, KERNEL_OF, __VA_ARGS__)
 #define APC_SWEEP_BS(c, n, KERNEL_OF, ...) APC_ROWS_BS(c, K_SWEEP, n, KERNEL_OF, __VA_ARGS__)
+#define APC_SWEEP_BS_PDL(c, n, KERNEL_OF, ...) APC_ROWS_BS_WITH(APC_LAUNCH_PDL, c, K_SWEEP, n, KERNEL_OF, __VA_ARGS__)
 #define APC_SPMV1(B, U) (k_spmv<1, T, B, U>)
 #define APC_SPMV3(B, U) (k_spmv<3, T, B, U>)
 #define APC_SPMV4(B, U) (k_spmv<4, T, B, U>)
@@ -1669,22 +1699,30 @@ T *poly_apply(apcloud_ctx *c, const T *val, const T *v, T *z_first, const Krylov
     for (int i = 1; i < K.pdeg; ++i) {
         if (last && i + 1 == K.pdeg) nxt = last;   // the last sweep writes where the caller keeps z
         if constexpr (sizeof(T) == 4) {
-            if (K.hval && K.sperm && K.scol24) {
-                if (K.skeep < c->ss_entries)
-                    APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24K, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
-                                 (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
-                                 K.scol24, K.skeep);
-                else
-                    APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
-                                 (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
-                                 K.scol24, K.skeep);
-                T *tmp = cur; cur = nxt; nxt = tmp;
-                continue;
-            }
             if (K.hval && K.sperm) {
-                APC_SWEEP_BS(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
-                             (const float *)cur, (float *)nxt, (const float *)v, (const GmresState *)st, skip,
-                             (const uint32_t *)nullptr, (int64_t)0);
+                // the first sweep follows the kernel that wrote v and the
+                // state; each later one follows a sweep (APC_LAUNCH_PDL)
+                const bool pdl = i > 1 && c->pdl_on;
+                const float *xc = (const float *)cur;
+                float *yn = (float *)nxt;
+                const GmresState *sc = (const GmresState *)st;
+                if (K.scol24 && K.skeep < c->ss_entries) {
+                    if (pdl) APC_SWEEP_BS_PDL(c, K.nslot, APC_SWEEPS24K, K.sperm, K.ssw, K.sso, K.scol, K.sval,
+                                              K.nslot, xc, yn, (const float *)v, sc, skip, K.scol24, K.skeep);
+                    else APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24K, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                                      xc, yn, (const float *)v, sc, skip, K.scol24, K.skeep);
+                } else if (K.scol24) {
+                    if (pdl) APC_SWEEP_BS_PDL(c, K.nslot, APC_SWEEPS24, K.sperm, K.ssw, K.sso, K.scol, K.sval,
+                                              K.nslot, xc, yn, (const float *)v, sc, skip, K.scol24, K.skeep);
+                    else APC_SWEEP_BS(c, K.nslot, APC_SWEEPS24, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                                      xc, yn, (const float *)v, sc, skip, K.scol24, K.skeep);
+                } else {
+                    if (pdl) APC_SWEEP_BS_PDL(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval,
+                                              K.nslot, xc, yn, (const float *)v, sc, skip,
+                                              (const uint32_t *)nullptr, (int64_t)0);
+                    else APC_SWEEP_BS(c, K.nslot, APC_SWEEPS, K.sperm, K.ssw, K.sso, K.scol, K.sval, K.nslot,
+                                      xc, yn, (const float *)v, sc, skip, (const uint32_t *)nullptr, (int64_t)0);
+                }
                 T *tmp = cur; cur = nxt; nxt = tmp;
                 continue;
             }
@@ -1936,6 +1974,7 @@ apcloud_status run_cycle(apcloud_ctx *c, const T *val, const T *b, T *u, const K
         key.mask = c->timer.mask;
         key.spmv_bs = c->spmv_bs * 8 + c->spmv_unroll;
         key.skeep = K.skeep;
+        key.pdl = c->pdl_on ? 1 : 0;
         const void *p[] = {val, b, u, K.V, K.w, K.wraw, K.st, K.partial, K.z0, K.z1, K.t, K.hval,
                            c->slice_w.p, c->slice_off.p, c->ell_col.p, K.skip.nbo, K.skip.bdone, K.tact,
                            K.mask ? K.mask->r2 : nullptr, K.bk ? K.bk->items : nullptr,

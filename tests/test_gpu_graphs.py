@@ -121,6 +121,44 @@ def test_sweep_l2_keep_does_not_change_results():
         ap.set_sweep_l2_keep(-2)
 
 
+@pytest.mark.parametrize("graphs", [True, False])
+def test_dependent_launch_does_not_change_results(graphs):
+    """Sweeps launched as programmatic dependents of the sweep before them
+    give the same bits as sweeps in plain stream order, on the single-system
+    and the batched path, replayed from graphs and launched directly."""
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(50000, 26)
+    xb, yb, zb, qb, offs, _ = inputs.beam_batch(3, 27, n_lo=5e3, n_hi=2e4)
+    res = {}
+    for pdl in (False, True):
+        ap = APCloud(max_depth=6, c_refine=0.3, precision="mixed", poly_degree=16, poly_omega=1.0)
+        ap.set_graphs(graphs)
+        ap.set_launch_shape(128, 4, 4, 1)
+        ap.set_dependent_launch(pdl)
+        # small grids (a few blocks per sweep) let consecutive sweeps share the SMs the most;
+        # several solves give an ordering race several chances to show
+        runs = []
+        for xs, ys, zs, o in ((x, y, z, None), (xb, yb, zb, offs)):
+            if o is None:
+                ap.build_octree(_t(xs), _t(ys), _t(zs))
+            else:
+                ap.build_octree_batched(_t(xs), _t(ys), _t(zs), o)
+            ap.stencils()
+            if o is None:
+                ap.deposit(q_uniform=1.0 / len(xs), rtol=1e-11)
+            else:
+                ap.deposit(q=_t(qb), rtol=1e-11)
+            for _ in range(4 if pdl else 1):
+                phi, info = ap.solve(rtol=1e-11)
+                assert info["status"] == 0
+                runs.append((phi.cpu().numpy(), info["iters"]))
+        res[pdl] = runs
+    ref = res[False]
+    for k, (phi, iters) in enumerate(res[True]):
+        r_phi, r_iters = ref[k // 4]
+        assert np.array_equal(phi, r_phi) and iters == r_iters
+
+
 def test_autotune_choices_and_rejects():
     from paper_1603_04039_gb300 import APCloud, APCloudError
     x, y, z, q = inputs.beam_with_halo(80000, 24)
