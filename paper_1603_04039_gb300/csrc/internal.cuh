@@ -60,6 +60,14 @@ struct GmresState {
     double y[MAX_RESTART];
     double h1[MAX_RESTART + 1];   // first Gram-Schmidt projection of the current column
     double h2[MAX_RESTART + 1];   // second projection
+    // delayed reorthogonalisation (k_dcgs_dots): the tentative vector q_j of
+    // slot j is w_{j-1} minus its first projection over an estimate nut of
+    // its norm; its second projection s waits for step j
+    double dq[MAX_RESTART + 1];   // s = V^T q_j
+    double nu;                    // ||q_j - V s||
+    double inu;                   // 1 / nu
+    double nut;                   // the estimate that scaled q_j (then q_{j+1})
+    double gpre;                  // g[j] before the tentative rotation of column j
     double bnorm;                 // ||b||
     double beta;                  // ||r|| at cycle start
     double inv_norm;              // 1 / ||w|| of the vector about to become V_{j+1}

@@ -21,6 +21,7 @@
 
 #include <climits>
 
+#include "fpconv.cuh"
 #include "internal.cuh"
 
 namespace apc {
@@ -1121,6 +1122,374 @@ __global__ void __launch_bounds__(GT) k_gs_update_normalize(const T *__restrict_
     }
 }
 
+// ---------------------------------------------------------------- DCGS2
+// Classical Gram-Schmidt with delayed reorthogonalisation (DCGS2: Bielich,
+// Langou, Thomas, Swirydowicz, Yamazaki and Boman, Parallel Computing 112,
+// 2022), one grid reduction and two passes over the basis per Arnoldi step
+// where CGS2 takes two reductions and three passes.  Slot j of V holds the
+// tentative vector q_j: w_{j-1} minus its first projection, scaled by an
+// estimate nut_j of its norm.  Z_j = p(Ahat) q_j and w = Ahat Z_j, so the
+// flexible relation Ahat Z = V H holds for whatever q_j is; the second
+// projection of q_j (s = V^T q_j) is taken at step j together with the first
+// projection of w, and finishes column j - 1 of H.
+
+// tile_dots for two staged tiles at once: acq against qs, acw against ws
+// (nv basis vectors, same work split as tile_dots)
+template <class T>
+__device__ __forceinline__ void tile_dots2(const T *__restrict__ V, int64_t ldv, int64_t base, int lim, int nv,
+                                           const T *qs, const T *ws, T (&acq)[KPW], T (&acw)[KPW]) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const VT *qv = reinterpret_cast<const VT *>(qs);
+    const VT *wv = reinterpret_cast<const VT *>(ws);
+    const int parts = GW / nv;
+    if (parts >= 2) {
+        const int k = wid % nv, part = wid / nv;
+        if (part < parts) {
+            const VT *vk = reinterpret_cast<const VT *>(V + (int64_t)k * ldv + base);
+            T a = acq[0], b = acw[0];
+#pragma unroll 4
+            for (int c = lane + 32 * part; c < lim / VN; c += 32 * parts) {
+                const VT x = __ldg(vk + c);
+                a = dotv(x, qv[c], a);
+                b = dotv(x, wv[c], b);
+            }
+            acq[0] = a;
+            acw[0] = b;
+        }
+        return;
+    }
+#pragma unroll
+    for (int kk = 0; kk < KPW; ++kk) {
+        const int k = wid + GW * kk;
+        if (k < nv) {   // uniform across the warp
+            const VT *vk = reinterpret_cast<const VT *>(V + (int64_t)k * ldv + base);
+            T a = acq[kk], b = acw[kk];
+#pragma unroll 4
+            for (int c = lane; c < lim / VN; c += 32) {
+                const VT x = __ldg(vk + c);
+                a = dotv(x, qv[c], a);
+                b = dotv(x, wv[c], b);
+            }
+            acq[kk] = a;
+            acw[kk] = b;
+        }
+    }
+}
+
+__device__ __forceinline__ void givens(double a, double b, double &c, double &s, double &r) {
+    r = sqrt(a * a + b * b);
+    c = r != 0.0 ? a / r : 1.0;
+    s = r != 0.0 ? b / r : 0.0;
+}
+
+// Compensated FP32 sums for the reductions of k_dcgs_dots: a value is a pair
+// (s, e) whose sum is the value; adding two pairs keeps the rounding error of
+// s_a + s_b in e (TwoSum, Knuth, TAOCP vol. 2, 4.2.2), so the block and grid
+// sums carry about twice the FP32 precision on the FP32 pipe.  GB300 issues
+// one FP64 lane pair per clock and SM: the FP64 shuffle trees and block sums
+// they replace cost ~15 us of a ~50 us kernel.
+struct F2 {
+    float s, e;
+};
+__device__ __forceinline__ F2 f2add(F2 a, F2 b) {
+    const float s = a.s + b.s;
+    const float bb = s - a.s;
+    const float err = (a.s - (s - bb)) + (b.s - bb);
+    return F2{s, (a.e + b.e) + err};
+}
+__device__ __forceinline__ F2 warp_sum_f2(F2 v, int width = 32) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        if (o < width) v = f2add(v, F2{__shfl_xor_sync(0xffffffffu, v.s, o), __shfl_xor_sync(0xffffffffu, v.e, o)});
+    return v;
+}
+__device__ __forceinline__ double f2_value(F2 v) { return f32_to_f64_int(v.s) + f32_to_f64_int(v.e); }
+
+// final_sums for F2 partials (float2 in the 8-byte slots partial[b * 64 + k]):
+// each value gets a group of G = min(32, 2^floor(log2(blockDim / nk))) lanes,
+// lane l of the group adding blocks l, l + G, ... before a shuffle tree over
+// the group; out[k] (shared) in FP64.
+__device__ void final_sums_f2(const double *partial, int nblk, int nk, double *out) {
+    const int t = threadIdx.x;
+    int G = 32;
+    while (G > 1 && G * nk > (int)blockDim.x) G >>= 1;
+    const int k = t / G, l = t & (G - 1);
+    F2 a{0.f, 0.f}, b{0.f, 0.f};
+    if (k < nk) {
+        const float2 *p2 = reinterpret_cast<const float2 *>(partial);
+        int bl = l;
+        for (; bl + G < nblk; bl += 2 * G) {
+            const float2 x = __ldcg(&p2[(int64_t)bl * 64 + k]), y = __ldcg(&p2[(int64_t)(bl + G) * 64 + k]);
+            a = f2add(a, F2{x.x, x.y});
+            b = f2add(b, F2{y.x, y.y});
+        }
+        for (; bl < nblk; bl += G) {
+            const float2 x = __ldcg(&p2[(int64_t)bl * 64 + k]);
+            a = f2add(a, F2{x.x, x.y});
+        }
+    }
+    F2 v = f2add(a, b);
+    for (int o = G >> 1; o > 0; o >>= 1)
+        v = f2add(v, F2{__shfl_xor_sync(0xffffffffu, v.s, o, G), __shfl_xor_sync(0xffffffffu, v.e, o, G)});
+    if (k < nk && l == 0) out[k] = f2_value(v);
+    __syncthreads();
+}
+
+// Last block of k_dcgs_dots.  fs holds s (j values), t (j values), alpha =
+// q_j.q_j, beta = q_j.w, gamma = w.w.  With v_j = (q_j - V s) / nu:
+//   nu = sqrt(alpha - s.s);
+//   w_{j-1} = V (h_{j-1} + nut_j s) + nut_j nu v_j    (column j - 1, final);
+//   tau = v_j.w = (beta - s.t) / nu, h_j = (t, tau)    (first projection of w);
+//   nut_{j+1}^2 = ||w - V h_j||^2 = gamma - t.t - tau^2 (next estimate).
+// Column j - 1 gets its rotation for good (its g[j - 1] comes back from
+// gpre); column j enters with h_{j+1,j} = nut_{j+1} and a tentative rotation
+// whose |g[j + 1]| is the stopping test (Saad, Algorithms 6.9 / 6.10); step
+// j + 1 replaces both.  A cycle that stops here keeps the tentative column:
+// the cycle end solves with it and the restart computes the true residual.
+__device__ void dcgs_tail(GmresState *st, int j, const double *fs, cudaGraphConditionalHandle next,
+                          int set_next) {
+    __shared__ double colp[MAX_RESTART + 1], colc[MAX_RESTART + 2], csj[MAX_RESTART], snj[MAX_RESTART];
+    __shared__ double hp[MAX_RESTART + 1];
+    __shared__ double sums[3], gjs, taus;
+    const int tid = threadIdx.x;
+    const double *s = fs, *t = fs + j;
+    if (tid < j) {
+        csj[tid] = __ldcg(&st->cs[tid]);
+        snj[tid] = __ldcg(&st->sn[tid]);
+        hp[tid] = __ldcg(&st->h1[tid]);
+    }
+    if (tid < 32) {   // s.s, s.t, t.t over the lanes of warp 0 (j < 32)
+        double a = 0.0, b = 0.0, c = 0.0;
+        if (tid < j) {
+            a = s[tid] * s[tid];
+            b = s[tid] * t[tid];
+            c = t[tid] * t[tid];
+        }
+        a = warp_sum(a);
+        b = warp_sum(b);
+        c = warp_sum(c);
+        if (tid == 0) {
+            sums[0] = a;
+            sums[1] = b;
+            sums[2] = c;
+        }
+    }
+    __syncthreads();
+    const double alpha = fs[2 * j], beta = fs[2 * j + 1], gamma = fs[2 * j + 2];
+    // column j - 1 (thread 0) and the rotations of column j before the last
+    // one (thread 32) side by side
+    if ((tid == 0 && j > 0) || tid == 32) {
+        const double nu = j > 0 ? sqrt(fmax(alpha - sums[0], 0.0)) : 1.0;
+        if (tid == 0) {
+            const double nut = __ldcg(&st->nut);
+            for (int k = 0; k < j; ++k) colp[k] = fma(nut, s[k], hp[k]);
+            colp[j] = nut * nu;
+            for (int i = 0; i + 1 < j; ++i) {
+                const double a = colp[i], b = colp[i + 1];
+                colp[i] = csj[i] * a + snj[i] * b;
+                colp[i + 1] = -snj[i] * a + csj[i] * b;
+            }
+            double c, sv, r;
+            givens(colp[j - 1], colp[j], c, sv, r);
+            csj[j - 1] = c;
+            snj[j - 1] = sv;
+            st->cs[j - 1] = c;
+            st->sn[j - 1] = sv;
+            colp[j - 1] = r;
+            colp[j] = 0.0;
+            const double gp = __ldcg(&st->gpre);
+            st->g[j - 1] = c * gp;
+            gjs = -sv * gp;
+        } else {
+            const double tau = nu > 0.0 ? (beta - sums[1]) / nu : 0.0;
+            taus = tau;
+            for (int k = 0; k < j; ++k) colc[k] = t[k];
+            colc[j] = tau;
+            colc[j + 1] = sqrt(fmax(gamma - sums[2] - tau * tau, 0.0));
+            for (int i = 0; i + 1 < j; ++i) {
+                const double a = colc[i], b = colc[i + 1];
+                colc[i] = csj[i] * a + snj[i] * b;
+                colc[i + 1] = -snj[i] * a + csj[i] * b;
+            }
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const double nu = j > 0 ? sqrt(fmax(alpha - sums[0], 0.0)) : 1.0;
+        const double nut1 = colc[j + 1];
+        if (j > 0) {   // the rotation of column j - 1, final now
+            const double a = colc[j - 1], b = colc[j];
+            colc[j - 1] = csj[j - 1] * a + snj[j - 1] * b;
+            colc[j] = -snj[j - 1] * a + csj[j - 1] * b;
+        }
+        double c, sv, r;
+        givens(colc[j], colc[j + 1], c, sv, r);
+        st->cs[j] = c;
+        st->sn[j] = sv;
+        colc[j] = r;
+        colc[j + 1] = 0.0;
+        const double gj = j > 0 ? gjs : __ldcg(&st->g[0]);
+        st->gpre = gj;
+        st->g[j] = c * gj;
+        st->g[j + 1] = -sv * gj;
+        st->jend = j + 1;
+        st->nu = nu;
+        st->inu = nu > 0.0 ? 1.0 / nu : 0.0;
+        st->nut = nut1;
+        st->inv_norm = nut1 > 0.0 ? 1.0 / nut1 : 0.0;
+        if (fabs(sv * gj) <= st->rtol * st->bnorm || nut1 == 0.0 || nu == 0.0) st->done = 1;
+        st->ticket = 0;
+        if (set_next) cudaGraphSetConditional(next, st->done ? 0u : 1u);
+    }
+    __syncthreads();
+    constexpr int M = MAX_RESTART;
+    if (j > 0 && tid <= j) st->H[tid * M + j - 1] = colp[tid];
+    if (tid <= j + 1) st->H[tid * M + j] = colc[tid];
+    if (tid < j) {
+        st->h1[tid] = t[tid];
+        st->dq[tid] = s[tid];
+    }
+    if (tid == j) st->h1[j] = taus;
+}
+
+// Step j's one reduction: s = V_{<j}^T q_j and t = V_{<j}^T w against the
+// first j basis vectors, alpha, beta, gamma over q_j (slot j) and w; tiles of
+// q_j and w staged in shared memory.  FP32 vectors (the form that keeps a
+// flexible basis); warp, block and grid sums are compensated FP32 pairs (F2),
+// FP64 from the last block on.  partial[b * 64 + i] holds pair i < 2 j + 3.
+template <class T>
+__global__ void __launch_bounds__(DT, 2) k_dcgs_dots(const T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                   const T *__restrict__ w, GmresState *st,
+                                                   double *__restrict__ partial, cudaGraphConditionalHandle next,
+                                                   int set_next) {
+    static_assert(sizeof(T) == 4, "DCGS2 runs on FP32 vectors");
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ __align__(16) T qs[TILE];
+    __shared__ __align__(16) T ws[TILE];
+    __shared__ F2 red[2 * MAX_RESTART + 3];
+    __shared__ F2 wsum[3 * GW];
+    __shared__ double fs[64];
+    if (st->done) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int nk = 2 * j + 3;
+    T aq[KPW], aw[KPW];
+#pragma unroll
+    for (int kk = 0; kk < KPW; ++kk) aq[kk] = aw[kk] = (T)0;
+    T qq = (T)0, qw = (T)0, ww = (T)0;
+    VT *qsv = reinterpret_cast<VT *>(qs), *wsv = reinterpret_cast<VT *>(ws);
+    for (int64_t base = (int64_t)blockIdx.x * TILE; base < nrow; base += (int64_t)gridDim.x * TILE) {
+        const int lim = (int)((nrow - base) < TILE ? (nrow - base) : TILE);
+        const VT *qg = reinterpret_cast<const VT *>(V + (int64_t)j * ldv + base);
+        const VT *wg = reinterpret_cast<const VT *>(w + base);
+        for (int cix = tid; cix < lim / VN; cix += DT) {
+            const VT qi = qg[cix], wi = wg[cix];
+            qsv[cix] = qi;
+            wsv[cix] = wi;
+            qq = sumsq(qi, qq);
+            qw = dotv(qi, wi, qw);
+            ww = sumsq(wi, ww);
+        }
+        __syncthreads();
+        if (j > 0) tile_dots2<T>(V, ldv, base, lim, j, qs, ws, aq, aw);
+        __syncthreads();
+    }
+    // per basis vector, the block's parts summed in a fixed order
+    if (j > 0) {
+        if (GW / j >= 2) {
+            const int parts = GW / j;
+            const F2 vq = warp_sum_f2(F2{aq[0], 0.f}), vw = warp_sum_f2(F2{aw[0], 0.f});
+            if (lane == 0) {
+                wsum[wid] = vq;
+                wsum[GW + wid] = vw;
+            }
+            __syncthreads();
+            if (tid < j) {
+                F2 a{0.f, 0.f}, b{0.f, 0.f};
+                for (int part = 0; part < parts; ++part) {
+                    a = f2add(a, wsum[tid + j * part]);
+                    b = f2add(b, wsum[GW + tid + j * part]);
+                }
+                red[tid] = a;
+                red[j + tid] = b;
+            }
+        } else {
+#pragma unroll
+            for (int kk = 0; kk < KPW; ++kk) {
+                const int k = wid + GW * kk;
+                if (k < j) {
+                    const F2 vq = warp_sum_f2(F2{aq[kk], 0.f}), vw = warp_sum_f2(F2{aw[kk], 0.f});
+                    if (lane == 0) {
+                        red[k] = vq;
+                        red[j + k] = vw;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    {
+        const F2 a = warp_sum_f2(F2{qq, 0.f}), b = warp_sum_f2(F2{qw, 0.f}), c = warp_sum_f2(F2{ww, 0.f});
+        if (lane == 0) {
+            wsum[wid] = a;
+            wsum[GW + wid] = b;
+            wsum[2 * GW + wid] = c;
+        }
+        __syncthreads();
+        if (tid < 3) {
+            F2 v{0.f, 0.f};
+            for (int q = 0; q < GW; ++q) v = f2add(v, wsum[tid * GW + q]);
+            red[2 * j + tid] = v;
+        }
+    }
+    __syncthreads();
+    if (tid < nk)
+        reinterpret_cast<float2 *>(partial)[(int64_t)blockIdx.x * 64 + tid] = make_float2(red[tid].s, red[tid].e);
+    if (!last_block(&st->ticket)) return;
+    final_sums_f2(partial, gridDim.x, nk, fs);
+    dcgs_tail(st, j, fs, next, set_next);
+}
+
+// Start of DCGS2 step j >= 1: slot p = j - 1 finished, v_p = (q_p - V_{<p} s)
+// / nu (slot 0 holds v_0 already), and the tentative q_j = (w - V_{<=p} h_p)
+// / nut_j written to slot j, with z = omega q_j for the polynomial.
+template <class T>
+__global__ void __launch_bounds__(GT) k_dcgs_update(T *__restrict__ V, int64_t ldv, int nrow, int j,
+                                                   const T *__restrict__ w, T *__restrict__ z,
+                                                   const GmresState *__restrict__ st) {
+    typedef typename Vec<T>::type VT;
+    constexpr int VN = Vec<T>::n;
+    __shared__ T sq[MAX_RESTART], th[MAX_RESTART + 1];
+    if (st->done) return;
+    const int p = j - 1;
+    if (threadIdx.x < p) sq[threadIdx.x] = (T)st->dq[threadIdx.x];
+    if (threadIdx.x <= p) th[threadIdx.x] = (T)st->h1[threadIdx.x];
+    __syncthreads();
+    const T inu = (T)st->inu, inut = (T)st->inv_norm, om = (T)st->omega;
+    const VT *wv = reinterpret_cast<const VT *>(w);
+    VT *vp = reinterpret_cast<VT *>(V + (int64_t)p * ldv), *vj = reinterpret_cast<VT *>(V + (int64_t)j * ldv);
+    VT *zv = reinterpret_cast<VT *>(z);
+    for (int cix = blockIdx.x * GT + threadIdx.x; cix < nrow / VN; cix += gridDim.x * GT) {
+        VT a = vp[cix], b = wv[cix];
+#pragma unroll 8
+        for (int k = 0; k < p; ++k) {
+            const VT x = __ldg(reinterpret_cast<const VT *>(V + (int64_t)k * ldv) + cix);
+            a = axpyv(a, x, sq[k]);
+            b = axpyv(b, x, th[k]);
+        }
+        if (p > 0) {
+            a = fmav(a, inu, zerov<VT>());
+            vp[cix] = a;
+        }
+        b = axpyv(b, a, th[p]);
+        const VT q = fmav(b, inut, zerov<VT>());
+        vj[cix] = q;
+        zv[cix] = fmav(q, om, zerov<VT>());
+    }
+}
+
 // t = V y with H y = g (the combination the cycle end adds, before preconditioning)
 template <class T>
 __global__ void __launch_bounds__(256) k_combine(const T *__restrict__ V, int64_t ldv, int nrow, T *__restrict__ t,
@@ -1896,6 +2265,15 @@ bool gs_fused(const Krylov<T> &K, int jmax) {
     return K.pdeg > 1 && !K.bk && !K.tact && !K.skip.nbo && jmax < MAX_RESTART;
 }
 
+// DCGS2 (k_dcgs_dots) on the same cycles when they keep the flexible basis
+// (Z_j = p(Ahat) q_j of the tentative q_j; the cycle end without it applies
+// the polynomial to V y, which needs Z = p(Ahat) V) and while its 2 j + 3
+// sums per block fit the 64 partial slots of a block
+template <class T>
+bool gs_dcgs(const Krylov<T> &K, int jmax) {
+    return sizeof(T) == 4 && gs_fused(K, jmax) && K.Z != nullptr && 2 * jmax + 1 <= 64;
+}
+
 // One restart cycle of jmax Arnoldi steps, the update of u, and the residual
 // b - Ahat u that opens the next cycle (beta, g, done for it).
 template <class T>
@@ -1905,7 +2283,8 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
     const int32_t *col = ptr<int32_t>(c->ell_col);
     GmresState *st = K.st;
     if (K.bk) return bcycle_launches<T>(c, val, b, u, K, jmax);
-    const bool fused = gs_fused(K, jmax);
+    const bool dcgs = gs_dcgs(K, jmax);
+    const bool fused = gs_fused(K, jmax) && !dcgs;
     for (int j = 0; j < jmax; ++j) {
         begin_step(c, j);
         if (K.pdeg <= 1) {
@@ -1914,7 +2293,10 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
         } else {
             // w = Ahat p(Ahat) v_j (right preconditioning)
             T *vj = K.V + (int64_t)j * K.ldv;
-            if (fused && j > 0)
+            if (dcgs && j > 0)
+                APC_LAUNCH(c, K_UPDNORM, stream_blocks(K.ldv), GT, 0, k_dcgs_update<T>, K.V, K.ldv, (int)K.ldv, j,
+                           (const T *)K.w, K.z0, (const GmresState *)st);
+            else if (fused && j > 0)
                 APC_LAUNCH(c, K_UPDNORM, stream_blocks(K.ldv), GT, 0, k_gs_update_normalize<T>, (const T *)K.V,
                            K.ldv, (int)K.ldv, j, (const T *)K.w, vj, K.z0, (const GmresState *)st);
             else
@@ -1924,6 +2306,16 @@ apcloud_status cycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, co
             arnoldi_product<T>(c, val, K, (const T *)z, st, K.skip);
         }
         const int set_next = (c->capturing && j + 1 < jmax) ? 1 : 0;
+        if constexpr (sizeof(T) == 4) {
+            if (dcgs) {
+                APC_LAUNCH(c, K_DOT, dot_blocks(K.ldv), DT, 0, k_dcgs_dots<T>, (const T *)K.V, K.ldv, (int)K.ldv, j,
+                           (const T *)K.w, st, K.partial, next_step_cond(c, j), set_next);
+                end_step(c);
+                APC_TRY(stop_when_done(c, st));
+                if (c->stopped) break;
+                continue;
+            }
+        }
         gs_dispatch<T>(c, 0, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact);
         if (fused) {
             gs_dispatch<T>(c, 3, K.nblk, K.V, K.ldv, j, K.w, K.wraw, st, K.partial, K.tact, next_step_cond(c, j),
@@ -2058,8 +2450,15 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             account(c, K_SPMV, ((vb + pcb) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
             account(c, K_SWEEP, ((sb + cb) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
         }
-        const bool fused = gs_fused(K, jmax);
+        const bool dcgs = gs_dcgs(K, jmax), fused = gs_fused(K, jmax) && !dcgs;
         for (int j = 0; j < je; ++j) {
+            if (dcgs) {
+                // one pass over j basis vectors, q_j and w; step j >= 1 opened by one
+                // pass over j - 1 basis vectors, q_{j-1} and w, writing v_{j-1}, q_j, z
+                account(c, K_DOT, vb * dn * (j + 2), 4.0 * dn * j + 6.0 * dn);
+                if (j > 0) account(c, K_UPDNORM, vb * dn * (j + 1 + 3), 4.0 * dn * (j - 1) + 4.0 * dn);
+                continue;
+            }
             account(c, K_DOT, vb * dn * (j + 2), 2.0 * dn * (j + 1));
             if (fused) {
                 // PASS 2 with its sum of squares; step j >= 1 opened with w - V h2 over
