@@ -1823,8 +1823,13 @@ __global__ void __launch_bounds__(BGT) k_bgs_dots(const T *__restrict__ V, int64
         const T *vk = V + (int64_t)k * ldv + lo;
         T a = (T)0;
         for (int r = lane; r < cnt; r += 32) a = fma(vk[r], ws[r], a);
-        const double sum = warp_sum((double)a);
-        if (lane == 0) partial[(int64_t)blockIdx.x * 64 + k] = sum;
+        if constexpr (sizeof(T) == 4) {   // compensated FP32 tree (F2) instead of FP64 shuffles
+            const F2 sum = warp_sum_f2(F2{a, 0.f});
+            if (lane == 0) partial[(int64_t)blockIdx.x * 64 + k] = f2_value(sum);
+        } else {
+            const double sum = warp_sum((double)a);
+            if (lane == 0) partial[(int64_t)blockIdx.x * 64 + k] = sum;
+        }
     }
 }
 
@@ -1847,6 +1852,7 @@ __global__ void __launch_bounds__(BGT) k_bgs_norm(const T *__restrict__ V, int64
                                                   const GmresState *__restrict__ st, double *__restrict__ partial) {
     __shared__ T hs[MAX_RESTART + 1];
     __shared__ double red[BGT / 32];
+    __shared__ F2 redf[BGT / 32];
     if (st->done) return;
     const int4 it = bk.items[blockIdx.x];
     const int beam = it.x, lo = it.y, cnt = it.z - it.y;
@@ -1854,20 +1860,41 @@ __global__ void __launch_bounds__(BGT) k_bgs_norm(const T *__restrict__ V, int64
     const int j1 = j + 1, tid = threadIdx.x;
     if (tid < j1) hs[tid] = (T)bk.h2[(int64_t)beam * (bk.m + 1) + tid];
     __syncthreads();
-    double sq = 0.0;
-    for (int r = tid; r < cnt; r += BGT) {
-        T wi = w[lo + r];
-        for (int k = 0; k < j1; ++k) wi = fma(-V[(int64_t)k * ldv + lo + r], hs[k], wi);
-        wraw[lo + r] = wi;
-        sq = fma((double)wi, (double)wi, sq);
-    }
-    sq = warp_sum(sq);
-    if ((tid & 31) == 0) red[tid >> 5] = sq;
-    __syncthreads();
-    if (tid == 0) {
-        double t = 0.0;
-        for (int q = 0; q < BGT / 32; ++q) t += red[q];
-        partial[(int64_t)blockIdx.x * 64] = t;
+    if constexpr (sizeof(T) == 4) {
+        // ||wraw||^2 as a compensated FP32 sum: each square enters exactly
+        // (p + fma(w, w, -p)); an FP64 product per row kept the FP64 pipe busy
+        F2 sq{0.f, 0.f};
+        for (int r = tid; r < cnt; r += BGT) {
+            T wi = w[lo + r];
+            for (int k = 0; k < j1; ++k) wi = fma(-V[(int64_t)k * ldv + lo + r], hs[k], wi);
+            wraw[lo + r] = wi;
+            const float p = wi * wi;
+            sq = f2add(sq, F2{p, fmaf(wi, wi, -p)});
+        }
+        sq = warp_sum_f2(sq);
+        if ((tid & 31) == 0) redf[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            F2 t{0.f, 0.f};
+            for (int q = 0; q < BGT / 32; ++q) t = f2add(t, redf[q]);
+            partial[(int64_t)blockIdx.x * 64] = f2_value(t);
+        }
+    } else {
+        double sq = 0.0;
+        for (int r = tid; r < cnt; r += BGT) {
+            T wi = w[lo + r];
+            for (int k = 0; k < j1; ++k) wi = fma(-V[(int64_t)k * ldv + lo + r], hs[k], wi);
+            wraw[lo + r] = wi;
+            sq = fma((double)wi, (double)wi, sq);
+        }
+        sq = warp_sum(sq);
+        if ((tid & 31) == 0) red[tid >> 5] = sq;
+        __syncthreads();
+        if (tid == 0) {
+            double t = 0.0;
+            for (int q = 0; q < BGT / 32; ++q) t += red[q];
+            partial[(int64_t)blockIdx.x * 64] = t;
+        }
     }
 }
 
