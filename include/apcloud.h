@@ -80,6 +80,10 @@ typedef struct {
                               fails) is refactorised in FP64; 0..2, default 1e-3 (FP32
                               Cholesky QR squares the condition number).  apcloud_get_sizes
                               counts those blocks. */
+    int stencil_slots;     /* k-ring candidates a node may gather in the first stencil pass,
+                              16..256 (default 256); a node whose ring outgrows them is
+                              redone in a second pass with 512 slots, with the same result
+                              (launch mechanics, no counterpart in the paper) */
 } apcloud_params;
 
 /* Optional device allocator; NULL selects cudaMallocAsync/cudaFreeAsync on
@@ -100,7 +104,8 @@ typedef struct apcloud_ctx apcloud_ctx;
 
 /* Fills *p with the defaults: domain [-1,1]^3, max_depth 6, c_refine 1,
  * m_target 20, ring_max 5, weight_c 4, poisson_c 1, restart 30, FP64,
- * Jacobi preconditioning (poly_degree 1, poly_omega 0.7), fp32_rcond_min 1e-3. */
+ * Jacobi preconditioning (poly_degree 1, poly_omega 0.7), fp32_rcond_min 1e-3,
+ * stencil_slots 256. */
 void apcloud_default_params(apcloud_params *p);
 
 /* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy
@@ -338,7 +343,8 @@ apcloud_status apcloud_set_graphs(apcloud_ctx *ctx, int enable);
 /* Autotuner of the launch shapes (after apcloud_stencils): bit 0 of `what`
  * times a whole solve of the Poisson system A (configured solver, CUDA graphs
  * included; a synthetic right-hand side, relative residual 1e-10 or 1000
- * Arnoldi steps; one untimed solve first) for every shape of the
+ * Arnoldi steps; one untimed solve first, then the best of two timed
+ * ones) for every shape of the
  * row-parallel products: 64, 128, 256 and 512 threads per block, each with
  * the loads of 1 or 4 stencil entries issued ahead of their multiply-adds
  * (on the width-sorted copy: 1 or 2 chunks of 4 entries; the sum keeps its

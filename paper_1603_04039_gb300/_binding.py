@@ -40,7 +40,8 @@ class Params(C.Structure):
     _fields_ = [("lo", C.c_double * 3), ("hi", C.c_double * 3), ("max_depth", C.c_int), ("c_refine", C.c_double),
                 ("m_target", C.c_int), ("ring_max", C.c_int), ("weight_c", C.c_double),
                 ("poisson_c", C.c_double), ("restart", C.c_int), ("precision", C.c_int),
-                ("poly_degree", C.c_int), ("poly_omega", C.c_double), ("fp32_rcond_min", C.c_double)]
+                ("poly_degree", C.c_int), ("poly_omega", C.c_double), ("fp32_rcond_min", C.c_double),
+                ("stencil_slots", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -229,7 +230,7 @@ class APCloud:
 
     def __init__(self, lo=-1.0, hi=1.0, max_depth=6, c_refine=1.0, m_target=20, ring_max=5, weight_c=4.0,
                  poisson_c=1.0, restart=30, precision="fp64", poly_degree=1, poly_omega=0.7, device="cuda:0",
-                 stream=None, allocator="torch", fp32_rcond_min=1e-3):
+                 stream=None, allocator="torch", fp32_rcond_min=1e-3, stencil_slots=256):
         """allocator: "torch" (default) gives the context PyTorch's caching
         allocator; None selects the library's own cudaMallocAsync pool; a
         TorchAllocator instance is used as given."""
@@ -246,6 +247,7 @@ class APCloud:
         p.precision = {"fp64": 0, "mixed": 1}[precision]
         p.poly_degree, p.poly_omega = int(poly_degree), float(poly_omega)
         p.fp32_rcond_min = float(fp32_rcond_min)
+        p.stencil_slots = int(stencil_slots)
         self.params = p
         with torch.cuda.device(self.device):
             s = stream if stream is not None else torch.cuda.current_stream(self.device)

@@ -305,6 +305,10 @@ static apcloud_status validate(const apcloud_params *p, char *msg, size_t len) {
     if (p->restart < 1 || p->restart > MAX_RESTART) { snprintf(msg, len, "restart must be 1..64"); return APCLOUD_E_INVALID; }
     if (p->poly_degree < 1 || p->poly_degree > 32) { snprintf(msg, len, "poly_degree must be 1..32"); return APCLOUD_E_INVALID; }
     if (!(p->poly_omega > 0 && p->poly_omega < 2)) { snprintf(msg, len, "poly_omega must be in (0, 2)"); return APCLOUD_E_INVALID; }
+    if (p->stencil_slots < 16 || p->stencil_slots > MAXC_FAST) {
+        snprintf(msg, len, "stencil_slots must be in [16, %d]", MAXC_FAST);
+        return APCLOUD_E_INVALID;
+    }
     if (!(p->fp32_rcond_min >= 0 && p->fp32_rcond_min <= 2)) {
         snprintf(msg, len, "fp32_rcond_min must be in [0, 2]");
         return APCLOUD_E_INVALID;
@@ -336,6 +340,7 @@ void apcloud_default_params(apcloud_params *p) {
     p->poly_degree = 1;
     p->poly_omega = 0.7;
     p->fp32_rcond_min = 1e-3;
+    p->stencil_slots = MAXC_FAST;
 }
 
 apcloud_status apcloud_create(const apcloud_params *params, const apcloud_allocator *alloc, void *stream,
@@ -386,7 +391,7 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->ell_B32, &c->V32, &c->w32a, &c->w32b, &c->r32, &c->e32, &c->gstate2,
                     &c->pz0, &c->pz1, &c->pt, &c->zbasis, &c->ell_rd, &c->ell_A16, &c->ell_B16, &c->beam_off, &c->leaf_beam,
                     &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act,
-                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col, &c->ss_col24,
+                    &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col, &c->ss_col24, &c->stencil_ovf,
                     &c->ss_A, &c->ss_B, &c->ss_A32, &c->ss_B32, &c->tune_b, &c->tune_x, &c->beam_part, &c->ilu_lrows, &c->ilu_urows, &c->ilu_lrp, &c->ilu_urp,
                     &c->ilu_lcol, &c->ilu_ucol, &c->ilu_lval, &c->ilu_uval, &c->ilu_dinv};
     for (DBuf *b : bufs) free_buf(c, *b);

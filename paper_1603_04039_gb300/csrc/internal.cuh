@@ -16,6 +16,7 @@ constexpr int KEY_DEPTH = 21;   // 63-bit Morton keys (Section 4.3)
 constexpr int NCOL = 9;         // unknowns of the 3-D second-order GFD system (Section 3.1)
 constexpr int MMAX = 32;        // widest stencil, one warp lane per neighbour
 constexpr int MAXC = 512;       // ring candidates held per node in shared memory
+constexpr int MAXC_FAST = 256;  // the same in the stencil kernel over all nodes (overflow: redone with MAXC)
 constexpr double RANK_TOL = 1e-6;
 constexpr int MAX_RESTART = 64;
 
@@ -202,6 +203,7 @@ struct apcloud_ctx {
     // inside windows of 256 rows, so 32-row slices pad little (see build_sorted_sweep)
     apc::DBuf ss_perm, ss_w, ss_o, ss_col, ss_A, ss_B;
     apc::DBuf ss_col24;                             // chunk columns of the sorted copy, 24 bits each
+    apc::DBuf stencil_ovf;                          // nodes whose k-ring outgrew MAXC_FAST candidates
     bool ss_col24_ok = false;
     apc::DBuf ss_A32, ss_B32;   // FP32 values in the same layout (Arnoldi products of the mixed form)
     apc::DBuf beam_part;        // per-beam norms: partial sums, BSQ_CH per beam

@@ -159,6 +159,31 @@ def test_dependent_launch_does_not_change_results(graphs):
         assert np.array_equal(phi, r_phi) and iters == r_iters
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_stencil_slots_do_not_change_results(precision):
+    """The first stencil pass gathers at most stencil_slots k-ring candidates
+    per node; nodes whose rings outgrow them are redone by the second pass with
+    512.  With 16 or 32 slots most or many nodes take the second pass: the
+    stencils, and the solve, are bit-identical to the default's."""
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(60000, 28)
+    res = []
+    for slots in (256, 32, 16):
+        ap = APCloud(max_depth=7, c_refine=0.2, precision=precision, poly_degree=8, poly_omega=1.0,
+                     stencil_slots=slots)
+        ap.build_octree(_t(x), _t(y), _t(z))
+        for ww in (4, 8):
+            ap.set_launch_shape(256, ww, 1, 0)
+            ap.stencils()
+        g = ap.get_stencils()
+        ap.deposit(q_uniform=1.0 / len(x), rtol=1e-11)
+        phi, info = ap.solve(rtol=1e-11)
+        res.append([g[k].cpu().numpy() for k in sorted(g)] + [phi.cpu().numpy()])
+    for r in res[1:]:
+        for a, b in zip(res[0], r):
+            assert np.array_equal(a, b)
+
+
 def test_autotune_choices_and_rejects():
     from paper_1603_04039_gb300 import APCloud, APCloudError
     x, y, z, q = inputs.beam_with_halo(80000, 24)
