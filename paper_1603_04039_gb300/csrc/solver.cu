@@ -1776,6 +1776,9 @@ struct BKry {
     const int32_t *nbo;       // beam of every node
     double *H, *cs, *sn, *g, *h1, *h2, *y;   // per beam: (m+1) x m, m, m, m+1, m+1, m+1, m
     double *bnorm, *binv, *r2, *relres;
+    // per beam for DCGS2 (k_bdcgs_*): s = V^T q_j (m+1), nu, 1 / nu, nut, gpre,
+    // and the step's 2 j + 3 sums (64)
+    double *dq, *nu, *inu, *nut, *gpre, *fs;
     int *done;                // cycle finished (converged, breakdown or m steps)
     int *conv;                // converged: frozen for the rest of the solve
     int *jend;
@@ -1961,6 +1964,202 @@ __global__ void k_bsolve_y(BKry bk) {
         double t = g[k];
         for (int l = k + 1; l < je; ++l) t -= H[k * M + l] * y[l];
         y[k] = t / H[k * M + k];
+    }
+}
+
+// ---- DCGS2 for per-beam Krylov spaces (the batch form of k_dcgs_dots,
+// dcgs_tail and k_dcgs_update; FP32 vectors with a flexible basis).
+// Step j's pass over one item: s = V_{<j}^T q_j and t = V_{<j}^T w over its
+// rows (a warp per basis vector), q.q, q.w, w.w; compensated FP32 sums, the
+// products entering exactly.  partial[item * 64 + i], i < 2 j + 3.
+template <class T>
+__global__ void __launch_bounds__(BGT) k_bdcgs_dots(const T *__restrict__ V, int64_t ldv, int j,
+                                                    const T *__restrict__ w, BKry bk,
+                                                    const GmresState *__restrict__ st, double *__restrict__ partial) {
+    static_assert(sizeof(T) == 4, "DCGS2 runs on FP32 vectors");
+    __shared__ T qs[BITEM], ws[BITEM];
+    __shared__ F2 red[3][BGT / 32];
+    if (st->done) return;
+    const int4 it = bk.items[blockIdx.x];
+    const int beam = it.x, lo = it.y, cnt = it.z - it.y;
+    if (bk.done[beam]) return;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const T *q = V + (int64_t)j * ldv + lo;
+    F2 aa{0.f, 0.f}, ab{0.f, 0.f}, ac{0.f, 0.f};
+    for (int r = tid; r < cnt; r += BGT) {
+        const T qi = q[r], wi = w[lo + r];
+        qs[r] = qi;
+        ws[r] = wi;
+        const float p1 = qi * qi, p2 = qi * wi, p3 = wi * wi;
+        aa = f2add(aa, F2{p1, fmaf(qi, qi, -p1)});
+        ab = f2add(ab, F2{p2, fmaf(qi, wi, -p2)});
+        ac = f2add(ac, F2{p3, fmaf(wi, wi, -p3)});
+    }
+    __syncthreads();
+    for (int k = wid; k < j; k += BGT / 32) {
+        const T *vk = V + (int64_t)k * ldv + lo;
+        T a = (T)0, b = (T)0;
+        for (int r = lane; r < cnt; r += 32) {
+            const T x = vk[r];
+            a = fma(x, qs[r], a);
+            b = fma(x, ws[r], b);
+        }
+        const F2 sa = warp_sum_f2(F2{a, 0.f}), sb = warp_sum_f2(F2{b, 0.f});
+        if (lane == 0) {
+            partial[(int64_t)blockIdx.x * 64 + k] = f2_value(sa);
+            partial[(int64_t)blockIdx.x * 64 + j + k] = f2_value(sb);
+        }
+    }
+    aa = warp_sum_f2(aa);
+    ab = warp_sum_f2(ab);
+    ac = warp_sum_f2(ac);
+    if (lane == 0) {
+        red[0][wid] = aa;
+        red[1][wid] = ab;
+        red[2][wid] = ac;
+    }
+    __syncthreads();
+    if (tid < 3) {
+        F2 v{0.f, 0.f};
+        for (int qd = 0; qd < BGT / 32; ++qd) v = f2add(v, red[tid][qd]);
+        partial[(int64_t)blockIdx.x * 64 + 2 * j + tid] = f2_value(v);
+    }
+}
+
+// per beam: its items' sums of step j (fixed order) into bk.fs
+__global__ void k_bdcgs_sum(int j, BKry bk, const GmresState *__restrict__ st, const double *__restrict__ partial) {
+    if (st->done) return;
+    const int beam = blockIdx.x, i = threadIdx.x;
+    if (bk.done[beam] || i >= 2 * j + 3) return;
+    double s = 0.0;
+    for (int qd = bk.item_off[beam]; qd < bk.item_off[beam + 1]; ++qd) s += partial[(int64_t)qd * 64 + i];
+    bk.fs[(int64_t)beam * 64 + i] = s;
+}
+
+// per beam (one thread each): dcgs_tail's algebra on the beam's sums --
+// column j - 1 finished, column j projected with a tentative rotation, the
+// beam's stopping test; then (single-block launch) the number of beams still
+// in their cycle decides st->done
+__global__ void __launch_bounds__(256) k_bdcgs_tail(int j, BKry bk, GmresState *st, cudaGraphConditionalHandle next,
+                                                    int set_next) {
+    __shared__ int act[256];
+    int a = 0;
+    if (!st->done) {
+        const int M = bk.m;
+        for (int beam = threadIdx.x; beam < bk.nb; beam += blockDim.x) {
+            if (bk.done[beam]) continue;
+            const double *fs = bk.fs + (int64_t)beam * 64, *s = fs, *t = fs + j;
+            const double alpha = fs[2 * j], beta = fs[2 * j + 1], gamma = fs[2 * j + 2];
+            double *H = bk.H + (int64_t)beam * (M + 1) * M, *cs = bk.cs + (int64_t)beam * M,
+                   *sn = bk.sn + (int64_t)beam * M, *g = bk.g + (int64_t)beam * (M + 1);
+            double *h1 = bk.h1 + (int64_t)beam * (M + 1), *dq = bk.dq + (int64_t)beam * (M + 1);
+            double nu = 1.0, gj = g[0], ss = 0.0, stt = 0.0, tt = 0.0;
+            for (int k = 0; k < j; ++k) {
+                ss = fma(s[k], s[k], ss);
+                stt = fma(s[k], t[k], stt);
+                tt = fma(t[k], t[k], tt);
+            }
+            if (j > 0) {
+                nu = sqrt(fmax(alpha - ss, 0.0));
+                const double nut = bk.nut[beam];
+                // column j - 1: (h_{j-1} + nut s, nut nu), rotations 0 .. j - 2, then its own
+                double carried = fma(nut, s[0], h1[0]);
+                for (int i = 0; i + 1 < j; ++i) {
+                    const double x0 = carried, x1 = fma(nut, s[i + 1], h1[i + 1]);
+                    H[i * M + j - 1] = cs[i] * x0 + sn[i] * x1;
+                    carried = -sn[i] * x0 + cs[i] * x1;
+                }
+                double c, sv, r;
+                givens(carried, nut * nu, c, sv, r);
+                cs[j - 1] = c;
+                sn[j - 1] = sv;
+                H[(j - 1) * M + j - 1] = r;
+                H[j * M + j - 1] = 0.0;
+                const double gp = bk.gpre[beam];
+                g[j - 1] = c * gp;
+                gj = -sv * gp;
+            }
+            const double tau = nu > 0.0 ? (beta - stt) / nu : 0.0;
+            const double nut1 = sqrt(fmax(gamma - tt - tau * tau, 0.0));
+            // column j: (t, tau, nut1), rotations 0 .. j - 1, then its tentative own
+            double carried = j > 0 ? t[0] : tau;
+            for (int i = 0; i < j; ++i) {
+                const double x0 = carried, x1 = i + 1 < j ? t[i + 1] : tau;
+                H[i * M + j] = cs[i] * x0 + sn[i] * x1;
+                carried = -sn[i] * x0 + cs[i] * x1;
+            }
+            double c, sv, r;
+            givens(carried, nut1, c, sv, r);
+            cs[j] = c;
+            sn[j] = sv;
+            H[j * M + j] = r;
+            H[(j + 1) * M + j] = 0.0;
+            bk.gpre[beam] = gj;
+            g[j] = c * gj;
+            g[j + 1] = -sv * gj;
+            for (int k = 0; k < j; ++k) {
+                h1[k] = t[k];
+                dq[k] = s[k];
+            }
+            h1[j] = tau;
+            bk.nu[beam] = nu;
+            bk.inu[beam] = nu > 0.0 ? 1.0 / nu : 0.0;
+            bk.nut[beam] = nut1;
+            bk.binv[beam] = nut1 > 0.0 ? 1.0 / nut1 : 0.0;
+            bk.jend[beam] = j + 1;
+            const bool fin = fabs(sv * gj) <= st->rtol * bk.bnorm[beam] || nut1 == 0.0 || nu == 0.0 || j + 1 >= M;
+            bk.done[beam] = fin ? 1 : 0;
+            if (!fin) ++a;
+        }
+    }
+    act[threadIdx.x] = a;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) act[threadIdx.x] += act[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && !st->done && act[0] == 0) st->done = 1;
+    if (threadIdx.x == 0 && set_next) cudaGraphSetConditional(next, st->done ? 0u : 1u);
+}
+
+// start of step j >= 1 over one item: v_{j-1} = (q_{j-1} - V s) / nu (slot 0
+// holds v_0 already), q_j = (w - V h_{j-1}) / nut_j, z = omega q_j
+template <class T>
+__global__ void __launch_bounds__(BGT) k_bdcgs_update(T *__restrict__ V, int64_t ldv, int j,
+                                                      const T *__restrict__ w, T *__restrict__ z, BKry bk,
+                                                      const GmresState *__restrict__ st) {
+    __shared__ T sq[MAX_RESTART], th[MAX_RESTART + 1];
+    __shared__ T sc[2];
+    if (st->done) return;
+    const int4 it = bk.items[blockIdx.x];
+    const int beam = it.x, lo = it.y, cnt = it.z - it.y;
+    if (bk.done[beam]) return;
+    const int p = j - 1, tid = threadIdx.x;
+    const int64_t bo = (int64_t)beam * (bk.m + 1);
+    if (tid < p) sq[tid] = (T)bk.dq[bo + tid];
+    if (tid <= p) th[tid] = (T)bk.h1[bo + tid];
+    if (tid == 0) {
+        sc[0] = (T)bk.inu[beam];
+        sc[1] = (T)bk.binv[beam];
+    }
+    __syncthreads();
+    const T inu = sc[0], inut = sc[1], om = (T)st->omega;
+    T *vp = V + (int64_t)p * ldv + lo, *vj = V + (int64_t)j * ldv + lo;
+    for (int r = tid; r < cnt; r += BGT) {
+        T a = vp[r], b = w[lo + r];
+        for (int k = 0; k < p; ++k) {
+            const T x = V[(int64_t)k * ldv + lo + r];
+            a = fma(-x, sq[k], a);
+            b = fma(-x, th[k], b);
+        }
+        if (p > 0) {
+            a *= inu;
+            vp[r] = a;
+        }
+        b = fma(-a, th[p], b);
+        const T qv = b * inut;
+        vj[r] = qv;
+        z[lo + r] = om * qv;
     }
 }
 
@@ -2225,6 +2424,13 @@ apcloud_status bstart_launches(apcloud_ctx *c, const Krylov<T> &K) {
 
 // One restart cycle with an independent Krylov space per beam (same launches
 // for every beam), the update of u and the residual that opens the next cycle.
+// DCGS2 on a batch's per-beam spaces (k_bdcgs_*): FP32 vectors with a
+// flexible basis, while a cycle's 2 j + 3 sums per item fit its 64 slots
+template <class T>
+bool bdcgs_on(const Krylov<T> &K, int jmax) {
+    return sizeof(T) == 4 && K.bk && K.pdeg > 1 && K.Z != nullptr && 2 * jmax + 1 <= 64;
+}
+
 template <class T>
 apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, const Krylov<T> &K, int jmax) {
     const int n = c->n_tot;
@@ -2233,6 +2439,7 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
     GmresState *st = K.st;
     const BKry &bk = *K.bk;
     const RowSkip active{bk.nbo, bk.done, bk.binv};
+    const bool dcgs = bdcgs_on(K, jmax);
     for (int j = 0; j < jmax; ++j) {
         begin_step(c, j);
         if (K.pdeg <= 1) {
@@ -2240,11 +2447,29 @@ apcloud_status bcycle_launches(apcloud_ctx *c, const T *val, const T *b, T *u, c
                         (const T *)nullptr, st, (double *)nullptr, active);
         } else {
             T *vj = K.V + (int64_t)j * K.ldv;
-            APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_bnormalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
-                       bk.nbo, (const int *)bk.done, (const double *)bk.binv, (const GmresState *)st);
+            if (dcgs && j > 0)
+                APC_LAUNCH(c, K_UPDNORM, bk.nitems, BGT, 0, k_bdcgs_update<T>, K.V, K.ldv, j, (const T *)K.w,
+                           K.z0, bk, (const GmresState *)st);
+            else
+                APC_LAUNCH(c, K_VEC, div_up(n, 256), 256, 0, k_bnormalize_first<T>, (const T *)K.wraw, vj, K.z0, n,
+                           bk.nbo, (const int *)bk.done, (const double *)bk.binv, (const GmresState *)st);
             T *z = poly_apply<T>(c, val, vj, K.z0, K, st, RowSkip{bk.nbo, bk.done, nullptr},
                                  K.Z ? K.Z + (int64_t)j * K.ldv : nullptr);
             arnoldi_product<T>(c, val, K, (const T *)z, st, RowSkip{bk.nbo, bk.done, nullptr});
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (dcgs) {   // one pass and one sum per step (k_bdcgs_*)
+                APC_LAUNCH(c, K_DOT, bk.nitems, BGT, 0, k_bdcgs_dots<T>, (const T *)K.V, K.ldv, j, (const T *)K.w,
+                           bk, (const GmresState *)st, K.partial);
+                APC_LAUNCH(c, K_DOT, bk.nb, 64, 0, k_bdcgs_sum, j, bk, (const GmresState *)st,
+                           (const double *)K.partial);
+                APC_LAUNCH(c, K_DOT, 1, 256, 0, k_bdcgs_tail, j, bk, st, next_step_cond(c, j),
+                           (c->capturing && j + 1 < jmax) ? 1 : 0);
+                end_step(c);
+                APC_TRY(stop_when_done(c, st));
+                if (c->stopped) break;
+                continue;
+            }
         }
         APC_LAUNCH(c, K_DOT, bk.nitems, BGT, 0, (k_bgs_dots<0, T>), (const T *)K.V, K.ldv, j, K.w, bk,
                    (const GmresState *)st, K.partial);
@@ -2477,7 +2702,7 @@ apcloud_status gmres_core(apcloud_ctx *c, const T *val, const T *b, T *u, double
             account(c, K_SPMV, ((vb + pcb) * nnz + 2.0 * vb * dn) * prods, 2.0 * nnz * prods);
             account(c, K_SWEEP, ((sb + cb) * nnz + 3.0 * vb * dn) * sweeps, 2.0 * nnz * sweeps);
         }
-        const bool dcgs = gs_dcgs(K, jmax), fused = gs_fused(K, jmax) && !dcgs;
+        const bool dcgs = gs_dcgs(K, jmax) || bdcgs_on(K, jmax), fused = gs_fused(K, jmax) && !dcgs;
         for (int j = 0; j < je; ++j) {
             if (dcgs) {
                 // one pass over j basis vectors, q_j and w; step j >= 1 opened by one
@@ -2611,7 +2836,7 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         const int ni = (int)items.size();
         int4 *ditems = ensure<int4>(c, c->bk_items, ni > 0 ? ni : 1);
         int *dioff = ensure<int>(c, c->bk_ioff, nb + 1);
-        const int64_t per = (int64_t)(m + 1) * m + 2 * m + 3 * (m + 1) + m + 3;
+        const int64_t per = (int64_t)(m + 1) * m + 2 * m + 3 * (m + 1) + m + 3 + (m + 1) + 4 + 64;
         double *dd = ensure<double>(c, c->bk_d, per * nb + 1);
         int *di = ensure<int>(c, c->bk_i, 3 * (int64_t)nb);
         double *part2 = ensure<double>(c, c->partial, std::max<int64_t>(npart, (int64_t)ni * 64), true);
@@ -2634,7 +2859,13 @@ apcloud_status gmres_solve(apcloud_ctx *c, int which, const double *b, double *x
         bkv.bnorm = q; q += nb;
         bkv.binv = q; q += nb;
         bkv.r2 = q; q += nb;
-        bkv.relres = q;
+        bkv.relres = q; q += nb;
+        bkv.dq = q; q += (int64_t)(m + 1) * nb;
+        bkv.nu = q; q += nb;
+        bkv.inu = q; q += nb;
+        bkv.nut = q; q += nb;
+        bkv.gpre = q; q += nb;
+        bkv.fs = q;
         bkv.done = di; bkv.conv = di + nb; bkv.jend = di + 2 * nb;
         bk = &bkv;
     }

@@ -97,6 +97,35 @@ def test_polynomial_preconditioner_matches_oracle(precision, tol):
     assert ip["iters"] * 4 < ip1["iters"]
 
 
+@pytest.mark.parametrize("restart", [8, 30, 40])
+def test_gram_schmidt_forms_match_oracle(restart):
+    """The mixed polynomial form orthogonalises by DCGS2 (one reduction per
+    Arnoldi step, the second projection delayed a step) while a restart cycle
+    fits its 2 j + 3 partial sums in 64 slots (restart <= 31), by CGS2 above
+    that: short and long cycles of both reach the oracle's fields, and the two
+    forms need about the same number of Arnoldi steps."""
+    from paper_1603_04039_gb300 import APCloud
+    x, y, z, q = inputs.beam_with_halo(100000, 6)
+    ap = APCloud(max_depth=6, c_refine=0.5, precision="mixed", poly_degree=16, poly_omega=1.0, restart=restart)
+    ap.build_octree(_t(x), _t(y), _t(z))
+    ap.stencils()
+    rho, ir = ap.deposit(q=_t(q), rtol=1e-10)
+    phi, ip = ap.solve(rtol=1e-10)
+    php, ex, ey, ez = ap.gather_field()
+    assert ir["status"] == 0 and ip["status"] == 0 and ip["relres"] <= 1e-10
+    ref = oracle.Oracle(max_depth=6, c_refine=0.5).run(x, y, z, q=q, rtol=1e-13)
+    for a, k in ((phi, "phi"), (php, "phi_p"), (ex, "ex"), (ey, "ey"), (ez, "ez")):
+        assert rel(a.cpu().numpy(), ref[k]) < 1e-6, k
+    # the same cycles at restart 40 (CGS2) and 30 (DCGS2) need about as many steps
+    if restart == 40:
+        ap30 = APCloud(max_depth=6, c_refine=0.5, precision="mixed", poly_degree=16, poly_omega=1.0, restart=30)
+        ap30.build_octree(_t(x), _t(y), _t(z))
+        ap30.stencils()
+        ap30.deposit(q=_t(q), rtol=1e-10)
+        _, ip30 = ap30.solve(rtol=1e-10)
+        assert 0.7 * ip30["iters"] <= ip["iters"] <= 1.5 * ip30["iters"] + 4
+
+
 @pytest.mark.parametrize("rcond_min", [0.05, 2.0])
 def test_fp64_refactorisation_of_uncertified_blocks(rcond_min):
     """Mixed form: a block whose FP32 condition estimate falls below
