@@ -81,7 +81,7 @@ typedef struct {
                               Cholesky QR squares the condition number).  apcloud_get_sizes
                               counts those blocks. */
     int stencil_slots;     /* k-ring candidates a node may gather in the first stencil pass,
-                              16..256 (default 256); a node whose ring outgrows them is
+                              16..128 (default 128); a node whose ring outgrows them is
                               redone in a second pass with 512 slots, with the same result
                               (launch mechanics, no counterpart in the paper) */
 } apcloud_params;
@@ -105,7 +105,7 @@ typedef struct apcloud_ctx apcloud_ctx;
 /* Fills *p with the defaults: domain [-1,1]^3, max_depth 6, c_refine 1,
  * m_target 20, ring_max 5, weight_c 4, poisson_c 1, restart 30, FP64,
  * Jacobi preconditioning (poly_degree 1, poly_omega 0.7), fp32_rcond_min 1e-3,
- * stencil_slots 256. */
+ * stencil_slots 128. */
 void apcloud_default_params(apcloud_params *p);
 
 /* Creates a context bound to `cuda_stream` (a cudaStream_t; NULL = legacy

@@ -230,7 +230,7 @@ class APCloud:
 
     def __init__(self, lo=-1.0, hi=1.0, max_depth=6, c_refine=1.0, m_target=20, ring_max=5, weight_c=4.0,
                  poisson_c=1.0, restart=30, precision="fp64", poly_degree=1, poly_omega=0.7, device="cuda:0",
-                 stream=None, allocator="torch", fp32_rcond_min=1e-3, stencil_slots=256):
+                 stream=None, allocator="torch", fp32_rcond_min=1e-3, stencil_slots=128):
         """allocator: "torch" (default) gives the context PyTorch's caching
         allocator; None selects the library's own cudaMallocAsync pool; a
         TorchAllocator instance is used as given."""

@@ -16,7 +16,7 @@ constexpr int KEY_DEPTH = 21;   // 63-bit Morton keys (Section 4.3)
 constexpr int NCOL = 9;         // unknowns of the 3-D second-order GFD system (Section 3.1)
 constexpr int MMAX = 32;        // widest stencil, one warp lane per neighbour
 constexpr int MAXC = 512;       // ring candidates held per node in shared memory
-constexpr int MAXC_FAST = 256;  // the same in the stencil kernel over all nodes (overflow: redone with MAXC)
+constexpr int MAXC_FAST = 128;  // the same in the stencil kernel over all nodes (overflow: redone with MAXC)
 constexpr double RANK_TOL = 1e-6;
 constexpr int MAX_RESTART = 64;
 

@@ -329,14 +329,15 @@ __device__ __forceinline__ void write_block_d(const unsigned char *smem_raw, uns
 
 // SW warps (nodes) per block, one WarpSmemT<MC> each (and the block's
 // arrival count after them); the autotuner picks SW.  With MC = MAXC_FAST
-// (LIST false, every node): 8.5 KB of shared memory per warp and 24 warps per
-// SM at a register budget that spills ~0.5 KB per thread, 12% faster than 16
-// warps at MAXC; a node whose ring outgrows MC candidates goes to ovf_list
-// instead of failing.  With MC = MAXC and LIST: the nodes of that list
+// (LIST false, every node): 6.6 KB of shared memory per warp and 32 warps per
+// SM at a register budget that spills part of the FP32 factorisation; a node
+// whose ring outgrows MC candidates goes to ovf_list instead of failing.
+// Against 512 slots at 16 warps: 7.1 -> 5.9 ms on a 1e7-particle beam and
+// 31.6 -> 26.1 ms on a 64-beam batch (both passes).  With MC = MAXC and LIST: the nodes of that list
 // (n_list of them), each warp writing its own D columns.  slots <= MC is the
 // capacity in force (the context's stencil_slots in the first kernel).
 template <int SW, int MC, bool LIST>
-__global__ void __launch_bounds__(SW * 32, (MC < MAXC ? 24 : 16) / SW) k_stencil(
+__global__ void __launch_bounds__(SW * 32, (MC < MAXC ? 32 : 16) / SW) k_stencil(
     const int4 *__restrict__ ic, const int32_t *__restrict__ adj, const int32_t *__restrict__ bowner, int n_int,
     int m_target, int ring_max, double unit, double ec, double inv_1mec, int32_t *__restrict__ nbr_out,
     int32_t *__restrict__ m_out, int32_t *__restrict__ ring_out, double *__restrict__ lap_out,

@@ -47,7 +47,7 @@ def test_param_validation_without_gpu(lib):
     assert p.weight_c == 4.0 and p.poisson_c == 1.0 and p.c_refine == 1.0
     ctx = C.c_void_p()
     for field, bad in (("max_depth", 22), ("m_target", 8), ("m_target", 33), ("ring_max", 1), ("restart", 0),
-                       ("precision", 2), ("stencil_slots", 15), ("stencil_slots", 257)):
+                       ("precision", 2), ("stencil_slots", 15), ("stencil_slots", 129)):
         q = B.Params()
         l.apcloud_default_params(C.byref(q))
         setattr(q, field, bad)

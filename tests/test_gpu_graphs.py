@@ -168,7 +168,7 @@ def test_stencil_slots_do_not_change_results(precision):
     from paper_1603_04039_gb300 import APCloud
     x, y, z, q = inputs.beam_with_halo(60000, 28)
     res = []
-    for slots in (256, 32, 16):
+    for slots in (128, 32, 16):
         ap = APCloud(max_depth=7, c_refine=0.2, precision=precision, poly_degree=8, poly_omega=1.0,
                      stencil_slots=slots)
         ap.build_octree(_t(x), _t(y), _t(z))
