@@ -18,6 +18,7 @@
 // signalled through an mbarrier, results read back with tcgen05.ld.  The
 // graph products (P H, P^T G), features, head, loss and Adam run on the CUDA
 // cores.  Every reduction has a fixed order, so a training run is repeatable.
+#include <atomic>
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -852,13 +853,16 @@ apcloud_status build_graph(apcloud_ctx *c) {
 }
 
 apcloud_status tc_launch(apcloud_ctx *c, int mode, const TcArgs &a, int grid) {
-    static bool attr[3] = {false, false, false};
-    if (!attr[mode]) {
+    // the shared-memory limit is a per-device property of the function: one
+    // bit per (device, mode) once it is set there (devices past 63: every call)
+    static std::atomic<uint64_t> attr_set[3];
+    const uint64_t bit = c->device >= 0 && c->device < 64 ? uint64_t(1) << c->device : 0;
+    if (!bit || !(attr_set[mode].load(std::memory_order_relaxed) & bit)) {
         cudaError_t e = mode == 0   ? cudaFuncSetAttribute(k_dense_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
                         : mode == 1 ? cudaFuncSetAttribute(k_dense_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM)
                                     : cudaFuncSetAttribute(k_dense_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
         APC_CUDA(c, e);
-        attr[mode] = true;
+        attr_set[mode].fetch_or(bit, std::memory_order_relaxed);
     }
     if (mode == 0) APC_LAUNCH(c, K_MPNN_TC, grid, TC_THREADS, TC_SMEM, k_dense_tc<0>, a);
     else if (mode == 1) APC_LAUNCH(c, K_MPNN_TC, grid, TC_THREADS, TC_SMEM, k_dense_tc<1>, a);

@@ -698,14 +698,12 @@ apcloud_status launch_stencil(apcloud_ctx *c, int n, double unit, double ec, dou
     if (!ovf) return APCLOUD_E_NOMEM;
     APC_CUDA(c, cudaMemsetAsync(derr + 2, 0, sizeof(unsigned), c->s));
     const size_t smem = SW * sizeof(WarpSmemT<MAXC_FAST>) + 16;   // the warps' areas, then the block's arrival count
-    static bool attr = false;
-    if (!attr) {
-        APC_CUDA(c, cudaFuncSetAttribute(k_stencil<SW, MAXC_FAST, false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        APC_CUDA(c, cudaFuncSetAttribute(k_stencil<4, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(4 * sizeof(WarpSmemT<MAXC>) + 16)));
-        attr = true;
-    }
+    // the limit is a per-device property of the function: set on every build
+    // (one host call each), so that contexts on other devices get it too
+    APC_CUDA(c, cudaFuncSetAttribute(k_stencil<SW, MAXC_FAST, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    APC_CUDA(c, cudaFuncSetAttribute(k_stencil<4, MAXC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(4 * sizeof(WarpSmemT<MAXC>) + 16)));
     APC_LAUNCH(c, K_STENCIL, div_up(n, SW), SW * 32, smem, (k_stencil<SW, MAXC_FAST, false>), ptr<int4>(c->node_ic),
                ptr<int32_t>(c->adj), ptr<int32_t>(c->bowner), n, c->P.m_target, c->P.ring_max, unit, ec, inv_1mec,
                nbr, msz, ring, lap, lapd, D, dstride, rc, c->P.precision == 1 ? 1 : 0, c->P.fp32_rcond_min,
