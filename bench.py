@@ -838,7 +838,8 @@ def run_ilu(args):
             "value": round(speed, 3), "unit": "x", "n_gpus": 1, "steps": len(args.eval_seeds), "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "ilu0_beam_halo_1e7_depth10", "eval_seeds": args.eval_seeds,
-                       "ilu0": "factorised on the host, level-scheduled triangular sweeps on the GPU"},
+                       "ilu0": "factorised on the host, level-scheduled triangular sweeps on the GPU "
+                                "(one-block runs of narrow levels)"},
             "eval": rows}
 
 

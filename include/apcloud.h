@@ -264,8 +264,9 @@ apcloud_status apcloud_solve_system_noalloc(apcloud_ctx *ctx, int which, const d
  * (Saad, Iterative Methods for Sparse Linear Systems, Algorithm 10.4, IKJ
  * order), taken of the stored column-scaled FP64 values; it is computed on
  * the host at every call, and every application (LU)^-1 v runs on the GPU as
- * a forward and a backward sweep, one launch per dependency level (no CUDA
- * graphs).  d_b, d_x and the result are as in apcloud_solve_system (x is the
+ * a forward and a backward sweep of dependency levels: one launch for each
+ * level wider than 4096 rows, one single-block launch for each run of
+ * narrower levels between them (no CUDA graphs).  d_b, d_x and the result are as in apcloud_solve_system (x is the
  * start and the answer, n = interior + boundary nodes, device memory).  FP64
  * form (precision 0) and single-beam contexts only, else APCLOUD_E_INVALID;
  * APCLOUD_E_NUMERIC on a zero pivot.  h_stats (NULL or 4 doubles) receives the

@@ -393,7 +393,8 @@ void apcloud_destroy(apcloud_ctx *c) {
                     &c->beam_rng, &c->beam_norm, &c->beam_r2, &c->beam_done, &c->node_beam, &c->tile_act,
                     &c->bk_items, &c->bk_ioff, &c->bk_d, &c->bk_i, &c->ss_perm, &c->ss_w, &c->ss_o, &c->ss_col, &c->ss_col24, &c->stencil_ovf,
                     &c->ss_A, &c->ss_B, &c->ss_A32, &c->ss_B32, &c->tune_b, &c->tune_x, &c->beam_part, &c->ilu_lrows, &c->ilu_urows, &c->ilu_lrp, &c->ilu_urp,
-                    &c->ilu_lcol, &c->ilu_ucol, &c->ilu_lval, &c->ilu_uval, &c->ilu_dinv};
+                    &c->ilu_lcol, &c->ilu_ucol, &c->ilu_lval, &c->ilu_uval, &c->ilu_dinv,
+                    &c->ilu_loff, &c->ilu_uoff};
     for (DBuf *b : bufs) free_buf(c, *b);
     for (DBuf &b : c->mp) free_buf(c, b);
     cudaStreamSynchronize(c->s);

@@ -8,7 +8,11 @@
 // matrix (the same column-scaled values the Krylov loop multiplies); every
 // application of the preconditioner, z = (LU)^-1 v, runs on the GPU as two
 // level-scheduled triangular sweeps: the rows of a level depend only on rows of
-// earlier levels, so each level is one launch of independent rows.
+// earlier levels.  A wide level is one launch over its rows; a run of
+// consecutive narrow levels is one launch of a single block that takes them in
+// order, with a block barrier between levels (the octree matrices have
+// thousands of levels of a few hundred rows, where a launch per level costs
+// more than the level's work).  Each row sums in the same order either way.
 #include <algorithm>
 #include <chrono>
 #include <vector>
@@ -19,6 +23,32 @@ namespace apc {
 
 namespace {
 
+constexpr int ILU_RUN_THREADS = 1024;   // threads of a one-block run of narrow levels
+constexpr int ILU_WIDE_ROWS = 4096;     // wider levels get a launch of their own
+static_assert(sizeof(int) == sizeof(int32_t), "level offsets are copied to the device as int32");
+
+// s - sum_{e0 <= e < e1} a[e] z[cj[e]], subtracted in order of e.  The
+// entries' columns and values are loaded 8 at a time ahead of the z loads
+// they feed, so a row costs a few dependent loads rather than two per entry.
+__device__ __forceinline__ double row_minus(double s, int64_t e0, int64_t e1, const int32_t *__restrict__ cj,
+                                            const double *__restrict__ a, const double *z) {
+    for (; e0 < e1; e0 += 8) {
+        int j[8];
+        double av[8], zv[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            j[k] = e0 + k < e1 ? cj[e0 + k] : 0;
+            av[k] = e0 + k < e1 ? a[e0 + k] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) zv[k] = e0 + k < e1 ? z[j[k]] : 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (e0 + k < e1) s -= av[k] * zv[k];
+    }
+    return s;
+}
+
 // forward sweep, one level: z[r] = v[r] - sum_{k < r} L_rk z[k] (L unit lower)
 __global__ void k_ilu_lower(const int32_t *__restrict__ rows, int p0, int p1, const int64_t *__restrict__ rp,
                             const int32_t *__restrict__ cj, const double *__restrict__ lv,
@@ -27,8 +57,7 @@ __global__ void k_ilu_lower(const int32_t *__restrict__ rows, int p0, int p1, co
     const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= p1) return;
     const int r = rows[p];
-    double s = v[r];
-    for (int64_t e = rp[p]; e < rp[p + 1]; ++e) s -= lv[e] * z[cj[e]];
+    const double s = row_minus(v[r], rp[p], rp[p + 1], cj, lv, z);
     z[r] = s;
 }
 
@@ -41,9 +70,63 @@ __global__ void k_ilu_upper(const int32_t *__restrict__ rows, int p0, int p1, co
     const int p = p0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= p1) return;
     const int r = rows[p];
-    double s = z[r];
-    for (int64_t e = rp[p]; e < rp[p + 1]; ++e) s -= uv[e] * z[cj[e]];
+    const double s = row_minus(z[r], rp[p], rp[p + 1], cj, uv, z);
     z[r] = s * dinv[p];
+}
+
+// A run of narrow levels [l0, l1) of the forward sweep in one block.  The
+// barrier after each level also makes that level's z values visible to the
+// block's reads in the next, so z is read through the ordinary (coherent) path.
+__global__ void __launch_bounds__(ILU_RUN_THREADS)
+    k_ilu_lower_run(const int32_t *__restrict__ rows, const int32_t *__restrict__ off, int l0, int l1,
+                    const int64_t *__restrict__ rp, const int32_t *__restrict__ cj, const double *__restrict__ lv,
+                    const double *__restrict__ v, double *z, const GmresState *__restrict__ st) {
+    if (st->done) return;
+    for (int l = l0; l < l1; ++l) {
+        const int p1 = off[l + 1];
+        for (int p = off[l] + threadIdx.x; p < p1; p += ILU_RUN_THREADS) {
+            const int r = rows[p];
+            const double s = row_minus(v[r], rp[p], rp[p + 1], cj, lv, z);
+            z[r] = s;
+        }
+        __syncthreads();
+    }
+}
+
+// the backward sweep's run of narrow levels, as k_ilu_lower_run
+__global__ void __launch_bounds__(ILU_RUN_THREADS)
+    k_ilu_upper_run(const int32_t *__restrict__ rows, const int32_t *__restrict__ off, int l0, int l1,
+                    const int64_t *__restrict__ rp, const int32_t *__restrict__ cj, const double *__restrict__ uv,
+                    const double *__restrict__ dinv, double *z, const GmresState *__restrict__ st) {
+    if (st->done) return;
+    for (int l = l0; l < l1; ++l) {
+        const int p1 = off[l + 1];
+        for (int p = off[l] + threadIdx.x; p < p1; p += ILU_RUN_THREADS) {
+            const int r = rows[p];
+            const double s = row_minus(z[r], rp[p], rp[p + 1], cj, uv, z);
+            z[r] = s * dinv[p];
+        }
+        __syncthreads();
+    }
+}
+
+// The launches of one sweep: each level wider than ILU_WIDE_ROWS alone on a
+// grid, the narrow levels between them in one-block runs.
+std::vector<IluSeg> plan_sweep(const std::vector<int> &off) {
+    std::vector<IluSeg> seg;
+    const int nlev = (int)off.size() - 1;
+    for (int l = 0; l < nlev;) {
+        if (off[l + 1] - off[l] > ILU_WIDE_ROWS) {
+            seg.push_back({l, l + 1, true});
+            ++l;
+            continue;
+        }
+        int e = l + 1;
+        while (e < nlev && off[e + 1] - off[e] <= ILU_WIDE_ROWS) ++e;
+        seg.push_back({l, e, false});
+        l = e;
+    }
+    return seg;
 }
 
 // Host CSR of a stored matrix: columns sorted, duplicates merged (the ELL pads
@@ -148,15 +231,25 @@ bool ilu0_factor(int64_t n, const int64_t *rp, const int32_t *cj, const int64_t 
 
 // z = (LU)^-1 v: the forward levels, then the backward levels
 double *ilu_apply(apcloud_ctx *c, const IluDev &I, const double *v, double *z, const GmresState *st) {
-    for (int l = 0; l + 1 < (int)I.loff.size(); ++l) {
-        const int p0 = I.loff[l], p1 = I.loff[l + 1];
-        APC_LAUNCH(c, K_SWEEP, div_up(p1 - p0, 128), 128, 0, k_ilu_lower, I.lrows, p0, p1, I.lrp, I.lcol, I.lval, v, z,
-                   st);
+    for (const IluSeg &g : I.lseg) {
+        if (g.wide) {
+            const int p0 = I.loff[g.l0], p1 = I.loff[g.l1];
+            APC_LAUNCH(c, K_SWEEP, div_up(p1 - p0, 128), 128, 0, k_ilu_lower, I.lrows, p0, p1, I.lrp, I.lcol, I.lval,
+                       v, z, st);
+        } else {
+            APC_LAUNCH(c, K_SWEEP, 1, ILU_RUN_THREADS, 0, k_ilu_lower_run, I.lrows, I.dloff, g.l0, g.l1, I.lrp, I.lcol,
+                       I.lval, v, z, st);
+        }
     }
-    for (int l = 0; l + 1 < (int)I.uoff.size(); ++l) {
-        const int p0 = I.uoff[l], p1 = I.uoff[l + 1];
-        APC_LAUNCH(c, K_SWEEP, div_up(p1 - p0, 128), 128, 0, k_ilu_upper, I.urows, p0, p1, I.urp, I.ucol, I.uval,
-                   I.udinv, z, st);
+    for (const IluSeg &g : I.useg) {
+        if (g.wide) {
+            const int p0 = I.uoff[g.l0], p1 = I.uoff[g.l1];
+            APC_LAUNCH(c, K_SWEEP, div_up(p1 - p0, 128), 128, 0, k_ilu_upper, I.urows, p0, p1, I.urp, I.ucol, I.uval,
+                       I.udinv, z, st);
+        } else {
+            APC_LAUNCH(c, K_SWEEP, 1, ILU_RUN_THREADS, 0, k_ilu_upper_run, I.urows, I.duoff, g.l0, g.l1, I.urp, I.ucol,
+                       I.uval, I.udinv, z, st);
+        }
     }
     return z;
 }
@@ -217,7 +310,10 @@ apcloud_status apcloud_solve_system_ilu0(apcloud_ctx *c, int which, const double
     int32_t *d_lcol = ensure<int32_t>(c, c->ilu_lcol, nl), *d_ucol = ensure<int32_t>(c, c->ilu_ucol, nu);
     double *d_lval = ensure<double>(c, c->ilu_lval, nl), *d_uval = ensure<double>(c, c->ilu_uval, nu);
     double *d_dinv = ensure<double>(c, c->ilu_dinv, n);
-    if (!d_lrows || !d_urows || !d_lrp || !d_urp || !d_lcol || !d_ucol || !d_lval || !d_uval || !d_dinv)
+    int32_t *d_loff = ensure<int32_t>(c, c->ilu_loff, (int64_t)I.loff.size());
+    int32_t *d_uoff = ensure<int32_t>(c, c->ilu_uoff, (int64_t)I.uoff.size());
+    if (!d_lrows || !d_urows || !d_lrp || !d_urp || !d_lcol || !d_ucol || !d_lval || !d_uval || !d_dinv || !d_loff ||
+        !d_uoff)
         return APCLOUD_E_NOMEM;
     APC_CUDA(c, cudaMemcpyAsync(d_lrows, lrows.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->s));
     APC_CUDA(c, cudaMemcpyAsync(d_urows, urows.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, c->s));
@@ -232,9 +328,14 @@ apcloud_status apcloud_solve_system_ilu0(apcloud_ctx *c, int which, const double
         APC_CUDA(c, cudaMemcpyAsync(d_uval, uval.data(), sizeof(double) * uval.size(), cudaMemcpyHostToDevice, c->s));
     }
     APC_CUDA(c, cudaMemcpyAsync(d_dinv, dinv.data(), sizeof(double) * n, cudaMemcpyHostToDevice, c->s));
+    APC_CUDA(c, cudaMemcpyAsync(d_loff, I.loff.data(), sizeof(int32_t) * I.loff.size(), cudaMemcpyHostToDevice, c->s));
+    APC_CUDA(c, cudaMemcpyAsync(d_uoff, I.uoff.data(), sizeof(int32_t) * I.uoff.size(), cudaMemcpyHostToDevice, c->s));
     APC_CUDA(c, cudaStreamSynchronize(c->s));   // the host vectors go out of scope
     I.lrows = d_lrows; I.urows = d_urows; I.lrp = d_lrp; I.urp = d_urp;
     I.lcol = d_lcol; I.ucol = d_ucol; I.lval = d_lval; I.uval = d_uval; I.udinv = d_dinv;
+    I.dloff = d_loff; I.duoff = d_uoff;
+    I.lseg = plan_sweep(I.loff);
+    I.useg = plan_sweep(I.uoff);
     const double setup_ms =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     c->ilu_which = which;

@@ -123,11 +123,21 @@ struct Timer {
 // ILU(0) factors on the device for the comparison solve: rows listed level by
 // level (forward and backward), the strict lower / upper entries of each listed
 // row, 1 / U_rr per backward position; level offsets on the host
+// One launch of a triangular sweep: levels [l0, l1) either as one block that
+// takes them in order (a run of small levels) or, for a single wide level, as
+// a grid over its rows.
+struct IluSeg {
+    int l0, l1;
+    bool wide;
+};
+
 struct IluDev {
     const int32_t *lrows = nullptr, *urows = nullptr, *lcol = nullptr, *ucol = nullptr;
     const int64_t *lrp = nullptr, *urp = nullptr;
     const double *lval = nullptr, *uval = nullptr, *udinv = nullptr;
+    const int32_t *dloff = nullptr, *duoff = nullptr;   // loff, uoff on the device
     std::vector<int> loff, uoff;
+    std::vector<IluSeg> lseg, useg;
 };
 
 }  // namespace apc
@@ -207,11 +217,12 @@ struct apcloud_ctx {
     bool ss_col24_ok = false;
     apc::DBuf ss_A32, ss_B32;   // FP32 values in the same layout (Arnoldi products of the mixed form)
     apc::DBuf beam_part;        // per-beam norms: partial sums, BSQ_CH per beam
-    apc::DBuf tune_b, tune_x;
+    apc::DBuf tune_b, tune_x;   // autotuner: right-hand side and iterate of its timed restart cycles
     // ILU(0) comparison solve: factors of system ilu_which while it runs (-1: none)
     apc::IluDev ilu;
     int ilu_which = -1;
-    apc::DBuf ilu_lrows, ilu_urows, ilu_lrp, ilu_urp, ilu_lcol, ilu_ucol, ilu_lval, ilu_uval, ilu_dinv;   // autotuner: right-hand side and iterate of its timed restart cycles
+    apc::DBuf ilu_lrows, ilu_urows, ilu_lrp, ilu_urp, ilu_lcol, ilu_ucol, ilu_lval, ilu_uval, ilu_dinv;
+    apc::DBuf ilu_loff, ilu_uoff;   // level offsets of the two sweeps, for the one-block runs of small levels
     bool ss_ok = false;
     int64_t ss_entries = 0;
     // solver
